@@ -1,0 +1,149 @@
+"""CPU oracle for the epsilon-similarity join -- TEST INFRASTRUCTURE, NOT THE PRODUCT.
+
+Only tests/, the smoke check and the benchmark's CPU-baseline leg may import
+this package. The CUDA library never calls it and shares no code with it.
+
+`oracle.c` holds the definition (plain single-threaded FP64 nested loop, see its
+header for the paper passages it follows); this module compiles it with
+`-ffp-contract=off` (so the canonical sum is not contracted into FMAs on either
+x86-64 or aarch64), loads it with ctypes and wraps numpy arrays.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+
+CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11"]
+
+_lib = None
+
+
+def build(src: str = _SRC, out: str = _LIB_PATH, extra=()) -> str:
+    """Compile oracle.c into a shared library (gcc, no FMA contraction)."""
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    cmd = ["gcc", *CFLAGS, *extra, "-o", out, src]
+    subprocess.run(cmd, check=True)
+    return out
+
+
+def _needs_build(src: str, out: str) -> bool:
+    return (not os.path.exists(out)) or os.path.getmtime(out) < os.path.getmtime(src)
+
+
+def load(path: str | None = None):
+    """Load (building if needed) the oracle library and declare its signatures."""
+    global _lib
+    if path is None:
+        if _lib is not None:
+            return _lib
+        if _needs_build(_SRC, _LIB_PATH):
+            build()
+        path = _LIB_PATH
+    lib = ctypes.CDLL(path)
+    f32p = ctypes.POINTER(ctypes.c_float)
+    f64p = ctypes.POINTER(ctypes.c_double)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    lib.oracle_sqdist.restype = ctypes.c_double
+    lib.oracle_sqdist.argtypes = [f32p, f32p, ctypes.c_int32]
+    lib.oracle_join.restype = ctypes.c_int64
+    lib.oracle_join.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int32,
+                                ctypes.c_double, ctypes.c_int32, i64p, i64p, ctypes.c_int64]
+    lib.oracle_dist_block.restype = None
+    lib.oracle_dist_block.argtypes = [f32p, ctypes.c_int64, ctypes.c_int64, f32p, ctypes.c_int64,
+                                      ctypes.c_int32, f64p]
+    lib.oracle_topk.restype = ctypes.c_int32
+    lib.oracle_topk.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int32,
+                                ctypes.c_int32, i64p, f64p]
+    if path == _LIB_PATH:
+        _lib = lib
+    return lib
+
+
+def _f32(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+MODE_RXS, MODE_SELF_UPPER, MODE_SELF_FULL = 0, 1, 2
+
+
+class Oracle:
+    """Thin numpy wrapper over one loaded oracle library (the real one, or a test mutant)."""
+
+    def __init__(self, lib=None):
+        self.lib = lib if lib is not None else load()
+
+    def sqdist(self, q, x) -> float:
+        q, qp = _f32(q)
+        x, xp = _f32(x)
+        return float(self.lib.oracle_sqdist(qp, xp, int(q.shape[-1])))
+
+    def dist_block(self, R, S, r0: int = 0, r1: int | None = None) -> np.ndarray:
+        R, Rp = _f32(R)
+        S, Sp = _f32(S)
+        r1 = R.shape[0] if r1 is None else r1
+        out = np.empty((r1 - r0, S.shape[0]), dtype=np.float64)
+        self.lib.oracle_dist_block(Rp, r0, r1, Sp, S.shape[0], R.shape[1],
+                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return out
+
+    def join(self, R, S=None, eps: float = 0.0, mode: int | None = None,
+             cap: int | None = None) -> np.ndarray:
+        """Row-index pairs (int64 [n, 2]) of the epsilon-join, in nested-loop order."""
+        R, Rp = _f32(R)
+        if mode is None:
+            mode = MODE_RXS if S is not None else MODE_SELF_UPPER
+        if S is None:
+            S, Sp, nS = R, Rp, R.shape[0]
+        else:
+            S, Sp = _f32(S)
+            nS = S.shape[0]
+        d = R.shape[1]
+        i64 = ctypes.POINTER(ctypes.c_int64)
+        if cap is None:
+            cap = 1 << 16
+        while True:
+            out_r = np.empty(cap, dtype=np.int64)
+            out_s = np.empty(cap, dtype=np.int64)
+            n = self.lib.oracle_join(Rp, R.shape[0], Sp, nS, d, float(eps), mode,
+                                     out_r.ctypes.data_as(i64), out_s.ctypes.data_as(i64), cap)
+            if n <= cap:
+                return np.stack([out_r[:n], out_s[:n]], axis=1)
+            cap = int(n)
+
+    def topk(self, Q, S, k: int):
+        """(idx int64 [nQ, k], d2 float64 [nQ, k]); unused slots are -1."""
+        Q, Qp = _f32(Q)
+        S, Sp = _f32(S)
+        idx = np.empty((Q.shape[0], k), dtype=np.int64)
+        d2 = np.empty((Q.shape[0], k), dtype=np.float64)
+        rc = self.lib.oracle_topk(Qp, Q.shape[0], Sp, S.shape[0], Q.shape[1], int(k),
+                                  idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                  d2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        if rc != 0:
+            raise MemoryError("oracle_topk: allocation failed")
+        return idx, d2
+
+
+_default = None
+
+
+def default() -> Oracle:
+    global _default
+    if _default is None:
+        _default = Oracle()
+    return _default
+
+
+if __name__ == "__main__":
+    build()
+    print("built", _LIB_PATH, file=sys.stderr)

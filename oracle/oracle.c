@@ -1,0 +1,125 @@
+/*
+ * oracle.c -- TEST INFRASTRUCTURE, NOT THE PRODUCT.
+ *
+ * A plain, single-threaded, FP64 CPU statement of what the epsilon-similarity
+ * join and its top-k variant compute. Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load it. It shares no code, header or
+ * constant with the CUDA library.
+ *
+ * What the paper fixes:
+ *   - Sec. 5 "Nested Loop Join": the join compares every pair of patches from
+ *     the two collections and returns the pairs that satisfy the predicate.
+ *   - Sec. 3.2 "Derived Data": the predicate for image matching compares the
+ *     features of two images and thresholds their similarity; the index the
+ *     paper uses answers Euclidean threshold queries. So the predicate is an
+ *     L2 distance threshold.
+ *   - Sec. 6.2 q1: nearest image to a query image, i.e. the top-k join with k=1.
+ *
+ * Readings where the paper is silent (each listed in the design notes):
+ *   - compare the squared distance with eps*eps (no square root);
+ *   - the threshold is inclusive (D <= eps^2);
+ *   - a self-join returns unordered pairs i<j by default, or all ordered pairs
+ *     including the diagonal in "full" mode;
+ *   - top-k ties are broken by the smaller row index of the store side;
+ *   - "exact" means the canonical FP64 value below: for k = 0..d-1 ascending,
+ *     t = (double)q_k - (double)x_k, s = s + t*t, each operation rounded to
+ *     nearest, no fused multiply-add (build with -ffp-contract=off).
+ *
+ * Parity pins (tests/test_oracle_pins.py): exact rational brute force, integer
+ * grid and one-hot closed forms, symmetry, zero self-distance, monotonicity in
+ * eps, union and permutation laws, top-k/join consistency, and a mutation test
+ * that plants mistakes in a copy of this file.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* Canonical squared Euclidean distance (the definition of "exact"). */
+double oracle_sqdist(const float *q, const float *x, int32_t d)
+{
+    double s = 0.0;
+    for (int32_t k = 0; k < d; ++k) {
+        double t = (double)q[k] - (double)x[k];
+        s = s + t * t;
+    }
+    return s;
+}
+
+/*
+ * Nested-loop epsilon-join (Sec. 5).
+ *   mode 0: R x S, every (i, j).
+ *   mode 1: self-join of R, unordered pairs i < j.
+ *   mode 2: self-join of R, every ordered (i, j) including i == j.
+ * Writes up to `cap` row-index pairs and returns the number of matching pairs.
+ */
+int64_t oracle_join(const float *R, int64_t nR, const float *S, int64_t nS, int32_t d,
+                    double eps, int32_t mode, int64_t *out_r, int64_t *out_s, int64_t cap)
+{
+    const double e2 = eps * eps;
+    const float *T = (mode == 0) ? S : R;
+    const int64_t nT = (mode == 0) ? nS : nR;
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < nR; ++i) {
+        int64_t j0 = (mode == 1) ? i + 1 : 0;
+        for (int64_t j = j0; j < nT; ++j) {
+            double s = oracle_sqdist(R + i * (int64_t)d, T + j * (int64_t)d, d);
+            if (s <= e2) {
+                if (cnt < cap) {
+                    out_r[cnt] = i;
+                    out_s[cnt] = j;
+                }
+                ++cnt;
+            }
+        }
+    }
+    return cnt;
+}
+
+/* Canonical distances of rows [r0, r1) of R against every row of S, row-major. */
+void oracle_dist_block(const float *R, int64_t r0, int64_t r1, const float *S, int64_t nS,
+                       int32_t d, double *out)
+{
+    for (int64_t i = r0; i < r1; ++i)
+        for (int64_t j = 0; j < nS; ++j)
+            out[(i - r0) * nS + j] = oracle_sqdist(R + i * (int64_t)d, S + j * (int64_t)d, d);
+}
+
+typedef struct {
+    double d2;
+    int64_t j;
+} oracle_cand;
+
+static int cand_cmp(const void *a, const void *b)
+{
+    const oracle_cand *x = (const oracle_cand *)a, *y = (const oracle_cand *)b;
+    if (x->d2 < y->d2) return -1;
+    if (x->d2 > y->d2) return 1;
+    return (x->j < y->j) ? -1 : (x->j > y->j);
+}
+
+/*
+ * Top-k join (Sec. 6.2 q1 generalised to k): for every query row, all store rows
+ * ordered by (canonical distance, store row index), first min(k, nS) kept.
+ * out_idx / out_d2 are [nQ][k]; entries past min(k, nS) are set to -1 / -1.0.
+ * Returns 0, or -1 when the scratch allocation fails.
+ */
+int32_t oracle_topk(const float *Q, int64_t nQ, const float *S, int64_t nS, int32_t d, int32_t k,
+                    int64_t *out_idx, double *out_d2)
+{
+    oracle_cand *c = (oracle_cand *)malloc(sizeof(oracle_cand) * (size_t)(nS > 0 ? nS : 1));
+    if (!c) return -1;
+    int64_t keep = (k < nS) ? k : nS;
+    for (int64_t i = 0; i < nQ; ++i) {
+        for (int64_t j = 0; j < nS; ++j) {
+            c[j].d2 = oracle_sqdist(Q + i * (int64_t)d, S + j * (int64_t)d, d);
+            c[j].j = j;
+        }
+        qsort(c, (size_t)nS, sizeof(oracle_cand), cand_cmp);
+        for (int64_t t = 0; t < k; ++t) {
+            out_idx[i * k + t] = (t < keep) ? c[t].j : -1;
+            out_d2[i * k + t] = (t < keep) ? c[t].d2 : -1.0;
+        }
+    }
+    free(c);
+    return 0;
+}

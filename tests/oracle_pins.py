@@ -1,0 +1,292 @@
+"""Pins that tie the CPU oracle to the paper and to mathematics, not to itself.
+
+Each pin takes an `oracle.Oracle` and raises AssertionError when the oracle
+disagrees with something the paper or the mathematics fixes:
+
+  * exact rational arithmetic (fractions.Fraction) on tiny inputs -- the join
+    set of Sec. 5's nested loop under Sec. 3.2's Euclidean threshold, with no
+    rounding at all;
+  * the hand-derived integer fixture in tests/golden/grid_join_small.txt;
+  * closed forms: one-hot histograms (distinct rows are sqrt(2) apart) and
+    integer grids scaled by 2^-3 (exact in every format);
+  * invariants: self-join symmetry, zero self-distance, monotonicity in eps,
+    eps=0 gives exact duplicates, eps=inf gives every pair, permutation and
+    union laws, top-k ordering and top-k/join consistency.
+
+The same suite runs against deliberately broken copies of the oracle
+(tests/test_oracle_mutants.py) to show that a plausible slip fails a pin.
+"""
+
+from __future__ import annotations
+
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+
+from oracle import MODE_RXS, MODE_SELF_FULL, MODE_SELF_UPPER
+from paper_1812_07607_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "grid_join_small.txt")
+
+
+# ----------------------------------------------------------------------------------------
+# exact helpers (plain definitions, written independently of oracle.c)
+# ----------------------------------------------------------------------------------------
+
+def exact_d2(q, x) -> Fraction:
+    """Exact squared Euclidean distance of two float32 rows, as a rational."""
+    s = Fraction(0)
+    for a, b in zip(q.tolist(), x.tolist()):
+        t = Fraction(a) - Fraction(b)
+        s += t * t
+    return s
+
+
+def exact_matrix(R, S):
+    return [[exact_d2(R[i], S[j]) for j in range(S.shape[0])] for i in range(R.shape[0])]
+
+
+def pair_set(p):
+    return set(map(tuple, np.asarray(p).reshape(-1, 2).tolist()))
+
+
+def eps_between(values, lo_rank: int):
+    """An eps whose square (in FP64) lies strictly inside a wide gap of `values`.
+
+    Sorts the distinct exact distances, picks the first gap at or after rank
+    `lo_rank` that is wider than 1e-6 relative, and returns eps with
+    fl(eps*eps) inside it, so that no distance is near the threshold.
+    """
+    vals = sorted(set(values))
+    for r in range(max(0, lo_rank), len(vals) - 1):
+        a, b = vals[r], vals[r + 1]
+        if b - a > Fraction(1, 10**6) * max(b, Fraction(1, 10**30)):
+            mid = (a + b) / 2
+            eps = math.sqrt(float(mid))
+            e2 = Fraction(eps * eps)
+            if a < e2 < b:
+                return eps, e2
+    raise AssertionError("no usable gap")
+
+
+def _g(seed):
+    return W.rng(seed)
+
+
+# ----------------------------------------------------------------------------------------
+# pins
+# ----------------------------------------------------------------------------------------
+
+def pin_sqdist_within_rounding_of_exact(orc):
+    """|D64 - D| <= (d+3) 2^-53 D for the canonical FP64 sum (standard error bound)."""
+    g = _g(11)
+    for d in (1, 2, 3, 7, 16, 33):
+        for gen in (W.mixed_magnitude_rows, lambda g, n, d: W.dirichlet_histograms(g, n, d)):
+            X = gen(g, 6, d)
+            for i in range(X.shape[0]):
+                for j in range(X.shape[0]):
+                    D = exact_d2(X[i], X[j])
+                    got = orc.sqdist(X[i], X[j])
+                    if D == 0:
+                        assert got == 0.0, (d, i, j, got)
+                    else:
+                        err = abs(Fraction(got) - D)
+                        assert err <= Fraction(d + 3, 2**53) * D, (d, i, j, got, float(D))
+
+
+def pin_join_matches_exact_rational(orc):
+    """All three join modes equal the exact-rational nested loop on tiny inputs."""
+    g = _g(12)
+    for d, nR, nS in ((1, 9, 11), (5, 23, 31), (12, 17, 13)):
+        R = W.mixed_magnitude_rows(g, nR, d) if d != 12 else W.dirichlet_histograms(g, nR, d)
+        S = W.mixed_magnitude_rows(g, nS, d) if d != 12 else W.dirichlet_histograms(g, nS, d)
+        M = exact_matrix(R, S)
+        vals = [v for row in M for v in row]
+        for rank in (0, len(vals) // 7, len(vals) // 2):
+            eps, e2 = eps_between(vals, rank)
+            want = {(i, j) for i in range(nR) for j in range(nS) if M[i][j] <= e2}
+            assert pair_set(orc.join(R, S, eps, MODE_RXS)) == want, (d, rank)
+        MS = exact_matrix(R, R)
+        svals = [MS[i][j] for i in range(nR) for j in range(nR) if i != j]
+        eps, e2 = eps_between(svals, len(svals) // 3)
+        up = {(i, j) for i in range(nR) for j in range(i + 1, nR) if MS[i][j] <= e2}
+        full = {(i, j) for i in range(nR) for j in range(nR) if MS[i][j] <= e2}
+        assert pair_set(orc.join(R, None, eps, MODE_SELF_UPPER)) == up, d
+        assert pair_set(orc.join(R, None, eps, MODE_SELF_FULL)) == full, d
+
+
+def read_golden(path=GOLDEN):
+    R, S, T, Q = [], [], [], []
+    entries = {}
+    with open(path) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            tok = line.split()
+            if tok[0] == "d":
+                continue
+            if tok[0] in ("R", "S"):
+                (R if tok[0] == "R" else S).append([float(v) for v in tok[1:]])
+            elif tok[0] == "topk_ties" and tok[1] in ("Q", "T"):
+                (Q if tok[1] == "Q" else T).append([float(v) for v in tok[2:]])
+            else:
+                key, val = line.split(":")
+                entries[key.strip()] = val.split()
+    f32 = lambda a: np.asarray(a, dtype=np.float32)
+    return f32(R), f32(S), f32(Q), f32(T), entries
+
+
+def _pairs_tok(toks):
+    return {tuple(int(v) for v in t.split(",")) for t in toks}
+
+
+def pin_golden_fixture(orc):
+    """The hand-derived integer fixture (tests/golden/grid_join_small.txt)."""
+    R, S, Q, T, e = read_golden()
+    for key, toks in e.items():
+        parts = key.split()
+        if parts[0] == "join_rxs":
+            assert pair_set(orc.join(R, S, float(parts[1]), MODE_RXS)) == _pairs_tok(toks), key
+        elif parts[0] == "join_self_upper":
+            assert pair_set(orc.join(R, None, float(parts[1]), MODE_SELF_UPPER)) == _pairs_tok(toks), key
+    idx, d2 = orc.topk(R, S, 1)
+    assert idx[:, 0].tolist() == [int(v) for v in e["top1"]]
+    assert d2[:, 0].tolist() == [float(v) for v in e["top1_d2"]]
+    idx, d2 = orc.topk(R, S, 2)
+    assert [tuple(r) for r in idx.tolist()] == [tuple(int(v) for v in t.split(",")) for t in e["top2"]]
+    assert [tuple(r) for r in d2.tolist()] == [tuple(float(v) for v in t.split(",")) for t in e["top2_d2"]]
+    idx, d2 = orc.topk(Q, T, 3)
+    assert idx[0].tolist() == [int(v) for v in e["topk_ties top3"]]
+    assert d2[0].tolist() == [float(v) for v in e["topk_ties top3_d2"]]
+
+
+def pin_boundary_closed_forms(orc):
+    """Inclusive threshold at exact distances: one-hot rows and 2^-3 grids."""
+    g = _g(13)
+    X = W.one_hot_rows(g, 40, 16)
+    same = {(i, j) for i in range(40) for j in range(40) if (X[i] == X[j]).all()}
+    # fl(sqrt(2))^2 rounds to just above 2, so every distinct pair (D = 2) is kept.
+    assert pair_set(orc.join(X, None, math.sqrt(2.0), MODE_SELF_FULL)) == \
+        {(i, j) for i in range(40) for j in range(40)}
+    assert pair_set(orc.join(X, None, 1.414, MODE_SELF_FULL)) == same
+    # 1-D grid 0, 3/8, 6/8: eps = 3/8 exactly -> eps^2 = 9/64 exactly, neighbours kept.
+    P = np.array([[0.0], [0.375], [0.75]], dtype=np.float32)
+    assert pair_set(orc.join(P, None, 0.375, MODE_SELF_UPPER)) == {(0, 1), (1, 2)}
+    assert pair_set(orc.join(P, None, float(np.nextafter(0.375, 0.0)), MODE_SELF_UPPER)) == set()
+    # d-dim grid: eps^2 set exactly equal to one realised distance
+    G = W.grid_points(g, 30, 6)
+    M = exact_matrix(G, G)
+    # pick a realised distance m/64 with m a perfect square, so eps = sqrt(m)/8 is exact
+    hit = next((i, j) for i in range(30) for j in range(i + 1, 30)
+               if M[i][j] > 0 and math.isqrt(int(M[i][j] * 64)) ** 2 == M[i][j] * 64)
+    target = M[hit[0]][hit[1]]
+    eps = math.isqrt(int(target * 64)) / 8.0
+    assert Fraction(eps * eps) == target
+    want = {(i, j) for i in range(30) for j in range(i + 1, 30) if M[i][j] <= target}
+    assert hit in want
+    assert pair_set(orc.join(G, None, eps, MODE_SELF_UPPER)) == want
+    just_below = float(np.nextafter(eps, 0.0))
+    assert hit not in pair_set(orc.join(G, None, just_below, MODE_SELF_UPPER))
+
+
+def pin_self_join_symmetry_and_diagonal(orc):
+    """Full mode is symmetric and holds every (i, i); upper mode is its i<j half."""
+    g = _g(14)
+    X = W.dirichlet_histograms(g, 120, 8)
+    eps = 0.25
+    full = pair_set(orc.join(X, None, eps, MODE_SELF_FULL))
+    assert all((j, i) in full for (i, j) in full)
+    assert all((i, i) in full for i in range(120))
+    up = pair_set(orc.join(X, None, eps, MODE_SELF_UPPER))
+    assert up == {(i, j) for (i, j) in full if i < j}
+    assert pair_set(orc.join(X, X, eps, MODE_RXS)) == full
+
+
+def pin_monotone_in_eps(orc):
+    """eps1 < eps2 implies J(eps1) is a subset of J(eps2); eps=0 and eps=inf limits."""
+    g = _g(15)
+    R = W.grid_points(g, 50, 5, levels=4, dup_frac=0.2)
+    S = np.concatenate([R[:10], W.grid_points(g, 30, 5, levels=4)])
+    prev = None
+    for eps in (0.0, 0.1, 0.2, 0.25, 0.3, 0.45, 0.6, 1.0):
+        cur = pair_set(orc.join(R, S, eps, MODE_RXS))
+        if prev is not None:
+            assert prev <= cur, eps
+        prev = cur
+    dup = {(i, j) for i in range(R.shape[0]) for j in range(S.shape[0]) if (R[i] == S[j]).all()}
+    assert pair_set(orc.join(R, S, 0.0, MODE_RXS)) == dup
+    assert len(dup) >= 10
+    assert pair_set(orc.join(R, S, math.inf, MODE_RXS)) == \
+        {(i, j) for i in range(R.shape[0]) for j in range(S.shape[0])}
+
+
+def pin_permutation_and_union(orc):
+    """Row permutations map the result; J(R, S1 u S2) = J(R, S1) u J(R, S2)."""
+    g = _g(16)
+    R = W.dirichlet_histograms(g, 70, 6)
+    S = W.dirichlet_histograms(g, 90, 6)
+    eps = 0.3
+    base = pair_set(orc.join(R, S, eps))
+    pr = g.permutation(70)
+    ps = g.permutation(90)
+    perm = pair_set(orc.join(R[pr], S[ps], eps))
+    assert {(int(pr[i]), int(ps[j])) for (i, j) in perm} == base
+    a = pair_set(orc.join(R, S[:40], eps))
+    b = {(i, j + 40) for (i, j) in pair_set(orc.join(R, S[40:], eps))}
+    assert a | b == base
+
+
+def pin_topk_matches_exact_order(orc):
+    """Top-k equals the exact-rational order (distance, then index) on tiny inputs."""
+    g = _g(17)
+    Q = W.dirichlet_histograms(g, 9, 7)
+    S = np.concatenate([W.dirichlet_histograms(g, 25, 7), W.dirichlet_histograms(g, 1, 7)])
+    S = np.concatenate([S, S[3:6]])  # exact duplicates: ties broken by the smaller index
+    M = exact_matrix(Q, S)
+    for k in (1, 4, 11):
+        idx, d2 = orc.topk(Q, S, k)
+        for i in range(Q.shape[0]):
+            order = sorted(range(S.shape[0]), key=lambda j: (M[i][j], j))[:k]
+            assert idx[i].tolist() == order, (k, i)
+            for t, j in enumerate(order):
+                assert d2[i, t] == orc.sqdist(Q[i], S[j])
+                assert abs(Fraction(float(d2[i, t])) - M[i][j]) <= Fraction(10, 2**53) * M[i][j]
+
+
+def pin_topk_small_store_and_join_consistency(orc):
+    """k >= |S| returns every row sorted; top-k rows lie inside the join at eps_k."""
+    g = _g(18)
+    Q = W.dirichlet_histograms(g, 6, 5)
+    S = W.dirichlet_histograms(g, 7, 5)
+    idx, d2 = orc.topk(Q, S, 10)
+    D = orc.dist_block(Q, S)
+    for i in range(6):
+        order = sorted(range(7), key=lambda j: (D[i, j], j))
+        assert idx[i, :7].tolist() == order
+        assert (idx[i, 7:] == -1).all() and (d2[i, 7:] == -1.0).all()
+    S2 = W.dirichlet_histograms(g, 60, 5)
+    k = 5
+    idx, d2 = orc.topk(Q, S2, k)
+    for i in range(6):
+        kth = d2[i, k - 1]
+        eps = math.sqrt(kth)
+        while eps * eps < kth:
+            eps = float(np.nextafter(eps, math.inf))
+        row = {j for (r, j) in pair_set(orc.join(Q[i:i + 1], S2, eps)) if r == 0}
+        assert set(idx[i].tolist()) <= row
+
+
+ALL_PINS = [
+    pin_sqdist_within_rounding_of_exact,
+    pin_join_matches_exact_rational,
+    pin_golden_fixture,
+    pin_boundary_closed_forms,
+    pin_self_join_symmetry_and_diagonal,
+    pin_monotone_in_eps,
+    pin_permutation_and_union,
+    pin_topk_matches_exact_order,
+    pin_topk_small_store_and_join_consistency,
+]

@@ -1,0 +1,56 @@
+"""Plant plausible mistakes in a copy of the oracle and check that a pin catches each.
+
+Every mutant is a one-line edit of oracle/oracle.c (a dropped term, a wrong sign
+or index, a transposed operand, a strict instead of inclusive comparison, a
+missing tie-break ...). It is compiled to a temporary library with the same
+flags as the real oracle and the full pin suite runs against it: at least one
+pin must fail. Runs on the CPU only.
+"""
+
+import os
+
+import pytest
+
+import oracle
+from oracle_pins import ALL_PINS
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
+
+MUTANTS = {
+    "square_dropped": ("s = s + t * t;", "s = s + t;"),
+    "sum_dropped": ("s = s + t * t;", "s = t * t;"),
+    "sign_flipped": ("(double)q[k] - (double)x[k]", "(double)q[k] + (double)x[k]"),
+    "index_slip": ("(double)q[k] - (double)x[k]", "(double)q[k] - (double)x[0]"),
+    "first_term_dropped": ("for (int32_t k = 0; k < d; ++k)", "for (int32_t k = 1; k < d; ++k)"),
+    "strict_threshold": ("if (s <= e2)", "if (s < e2)"),
+    "eps_not_squared": ("const double e2 = eps * eps;", "const double e2 = eps;"),
+    "diagonal_in_upper": ("int64_t j0 = (mode == 1) ? i + 1 : 0;", "int64_t j0 = (mode == 1) ? i : 0;"),
+    "second_operand_is_R": ("const float *T = (mode == 0) ? S : R;", "const float *T = R;"),
+    "pair_transposed": ("out_s[cnt] = j;", "out_s[cnt] = i;"),
+    "tie_break_reversed": ("return (x->j < y->j) ? -1 : (x->j > y->j);",
+                           "return (x->j > y->j) ? -1 : (x->j < y->j);"),
+    "topk_descending": ("if (x->d2 < y->d2) return -1;\n    if (x->d2 > y->d2) return 1;",
+                        "if (x->d2 < y->d2) return 1;\n    if (x->d2 > y->d2) return -1;"),
+    "topk_keep_k": ("int64_t keep = (k < nS) ? k : nS;", "int64_t keep = k;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation anchor not found: {old!r}"
+    mutated = src.replace(old, new, 1)
+    path = tmp_path / f"oracle_{name}.c"
+    path.write_text(mutated)
+    lib = oracle.load(oracle.build(str(path), str(tmp_path / f"lib_{name}.so")))
+    orc = oracle.Oracle(lib)
+    failed = []
+    for pin in ALL_PINS:
+        try:
+            pin(orc)
+        except AssertionError:
+            failed.append(pin.__name__)
+        except (IndexError, ValueError, MemoryError, OverflowError, StopIteration):
+            failed.append(pin.__name__)
+    assert failed, f"mutant {name} passed every pin"
