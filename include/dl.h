@@ -1,0 +1,200 @@
+/*
+ * dl.h -- C ABI of the GB300 exact epsilon-similarity join and top-k join.
+ *
+ * The operation (Krishnan, Dziedzic, Elmore, "DeepLens: Towards a Visual Data
+ * Management System", CIDR 2019):
+ *   - Sec. 2.2: a patch is (ImgRef, Data, MetaData) where Data is a dense
+ *     n-dimensional vector; here a patch is an opaque int64 id plus a float32
+ *     feature row of length d (ImgRef and MetaData are not used by the join).
+ *   - Sec. 5 "Nested Loop Join": compare every pair of patches from two
+ *     collections and return the pairs that satisfy the predicate.
+ *   - Sec. 3.2: the image-matching predicate thresholds feature similarity with
+ *     a Euclidean distance threshold. Read here as
+ *         D(q, x) = sum_k (q_k - x_k)^2  <=  eps^2      (inclusive)
+ *     with D evaluated as the canonical FP64 sum: k ascending,
+ *     t = (double)q_k - (double)x_k, s = s + t*t, round-to-nearest, no FMA.
+ *     The returned pair set is exactly the set that evaluation selects.
+ *   - Sec. 6.2 q1 (closest image to a query image): the top-k join, ordered by
+ *     (canonical D, store row index).
+ *
+ * Conventions for every entry point:
+ *   - Return an int status (dl_status); nothing throws across the ABI.
+ *     dl_last_error() gives a thread-local message for the last failure.
+ *   - Inputs are copied; the caller may free them when the call returns.
+ *   - Stores and results are owned by the library until their destroy/free call.
+ *   - A stream argument is a cudaStream_t passed as void*; NULL is the legacy
+ *     default stream. Calls that return a count synchronise that stream.
+ *   - Everything runs on the CUDA device current on the calling thread, which
+ *     must be an sm_103 GPU (GB300); there is no CPU fallback: without a usable
+ *     GPU every compute call fails with DL_ECUDA.
+ */
+#ifndef DL_H
+#define DL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dl_status {
+    DL_OK = 0,
+    DL_EINVAL = 1,        /* bad argument: null pointer, size, d, eps, k, non-finite feature ... */
+    DL_ENOMEM = 2,        /* a device or pinned-host allocation failed */
+    DL_EOVERFLOW = 3,     /* a fixed output capacity was too small; see dl_result_count */
+    DL_EAGAIN = 4,        /* (server) request not finished yet */
+    DL_ETIMEOUT = 5,      /* (server) poll timed out / a bounded device wait expired */
+    DL_ECUDA = 6,         /* a CUDA runtime call or kernel failed */
+    DL_ECANCELED = 7,     /* (server) request was cancelled */
+    DL_ENOMEM_ADMIT = 8,  /* (server) request can never fit the memory budget */
+    DL_EFAILED = 9,       /* (server) request failed; it may be resubmitted */
+    DL_EUNSUPPORTED = 10  /* valid request this build does not serve (e.g. d too large for a precision) */
+} dl_status;
+
+typedef enum dl_metric {
+    DL_METRIC_L2 = 0      /* squared Euclidean distance compared with eps^2 (Sec. 3.2) */
+} dl_metric;
+
+typedef enum dl_precision {
+    DL_PREC_AUTO = 0,       /* BF16 tensor-core path when d <= 512, else FP32 */
+    DL_PREC_BF16 = 1,       /* -2 q.x on tcgen05 tensor cores in BF16, FP32 accumulate; exact result */
+    DL_PREC_FP8E4M3 = 2,    /* as BF16 but FP8 e4m3 with per-row scales; exact result */
+    DL_PREC_FP32 = 3,       /* FP32 SIMT distances + bound + FP64 recheck; exact result */
+    DL_PREC_FP32_PLAIN = 4  /* plain FP32 SIMT join D32 <= (float)(eps*eps): the comparison
+                               baseline, NOT exact near the threshold */
+} dl_precision;
+
+typedef enum dl_memkind {
+    DL_MEM_HOST = 0,      /* pointer is host memory (pageable or pinned) */
+    DL_MEM_DEVICE = 1     /* pointer is device memory of the current device */
+} dl_memkind;
+
+typedef enum dl_self_mode {
+    DL_SELF_UPPER = 0,    /* self-join returns unordered pairs (i, j) with row i < row j */
+    DL_SELF_FULL = 1      /* self-join returns every ordered pair, diagonal included */
+} dl_self_mode;
+
+typedef struct dl_store dl_store;
+typedef struct dl_result dl_result;
+typedef struct dl_server dl_server;
+
+typedef struct dl_join_opts {
+    int32_t precision;      /* dl_precision */
+    int32_t self_mode;      /* dl_self_mode; used when the second store is NULL */
+    int64_t out_capacity;   /* 0: the library sizes the output and re-runs on overflow;
+                               >0: fixed capacity, overflow returns DL_EOVERFLOW with the
+                               required count available through dl_result_count */
+    void *cuda_stream;      /* cudaStream_t the work is ordered on */
+    int32_t tile_n;         /* 0: autotuned; else the tensor-core tile width (128 or 256) */
+    int32_t timing;         /* 1: record CUDA events around each kernel (dl_result_stats) */
+} dl_join_opts;
+
+/* Fill `o` with defaults: AUTO precision, upper self mode, auto capacity, NULL stream. */
+void dl_join_opts_default(dl_join_opts *o);
+
+/* ---------------------------------------------------------------------------------
+ * Stores: the device-resident patch collection (Sec. 3.2 "materialize" / Sec. 4.1).
+ * ------------------------------------------------------------------------------- */
+
+/*
+ * Create a store of n patches with int64 `ids` [n] and float32 `feats` [n][d]
+ * (row-major, contiguous). `where` tells whether both pointers are host or
+ * device memory; the data are copied, then one pass (K1) derives the per-row
+ * norms, the BF16 copy and the error-bound statistics the join kernels use.
+ * Requirements: 1 <= d <= 1024, 0 <= n < 2^31, every feature finite with
+ * |x| <= 2^40 (else DL_EINVAL). Ids are opaque and may repeat. On success *out
+ * owns device memory until dl_store_destroy. Ordered on `cuda_stream`; the
+ * call synchronises it (to report validation errors).
+ */
+int dl_store_create(dl_store **out, const int64_t *ids, const float *feats, int64_t n, int32_t d,
+                    int32_t where, void *cuda_stream);
+
+/* Free a store. Joins that use it must have completed. NULL is accepted. */
+int dl_store_destroy(dl_store *s);
+
+/* Number of rows and dimension of a store. */
+int dl_store_shape(const dl_store *s, int64_t *n, int32_t *d);
+
+/* ---------------------------------------------------------------------------------
+ * Joins.
+ * ------------------------------------------------------------------------------- */
+
+/*
+ * Epsilon-similarity join (Sec. 5 nested-loop semantics, Sec. 3.2 predicate):
+ * every pair (r in R, s in S) with canonical D(r, s) <= eps*eps, as id pairs.
+ * S == NULL is a self-join of R, in opts->self_mode. eps must be >= 0 and not
+ * NaN; eps = +inf returns every pair. metric must be DL_METRIC_L2. opts may be
+ * NULL (defaults). On success *out holds the result (free with
+ * dl_result_free); on DL_EOVERFLOW *out is also set so that the required
+ * count can be read. The pair order is unspecified (the result is a set).
+ */
+int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps,
+                const dl_join_opts *opts, dl_result **out);
+
+/*
+ * Top-k join (Sec. 6.2 q1 generalised to k): for every row of Q, the min(k, |S|)
+ * rows of S with the smallest canonical D, ordered by (D, S row index); ties
+ * beyond the k-th are not returned. 1 <= k <= 1024.
+ */
+int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric, int32_t k,
+                 const dl_join_opts *opts, dl_result **out);
+
+/* ---------------------------------------------------------------------------------
+ * Results.
+ * ------------------------------------------------------------------------------- */
+
+/* Number of pairs of an epsilon-join result (also valid after DL_EOVERFLOW). */
+int dl_result_count(const dl_result *r, int64_t *n);
+
+/*
+ * Pair ids of an epsilon-join result: r_ids[i], s_ids[i] for i < *n. With
+ * where == DL_MEM_DEVICE the pointers are device memory owned by the result;
+ * with DL_MEM_HOST the first call copies them into result-owned host memory.
+ */
+int dl_result_pairs(dl_result *r, int32_t where, const int64_t **r_ids, const int64_t **s_ids,
+                    int64_t *n);
+
+/*
+ * Top-k result: ids[nq][k] (int64) and dist2[nq][k] (double, the canonical D).
+ * Slots past min(k, |S|) hold id -1 and dist2 -1.0. `where` as for dl_result_pairs.
+ */
+int dl_result_topk(dl_result *r, int32_t where, const int64_t **ids, const double **dist2,
+                   int32_t *k, int64_t *nq);
+
+typedef struct dl_join_stats {
+    int64_t pairs_evaluated;    /* pairs the join is defined over (|R||S| or N(N-1)/2) */
+    int64_t pairs_out;          /* pairs returned */
+    int64_t band_pairs;         /* pairs whose low-precision distance was within the bound of eps */
+    int64_t fp64_pairs;         /* band pairs the FP32 recheck could not decide (FP64 evaluated) */
+    int64_t reruns;             /* times the call re-ran after growing an internal buffer */
+    int32_t precision;          /* dl_precision actually used */
+    int32_t tile_n;             /* tensor-core tile width used (0 for SIMT paths) */
+    float ms_main;              /* device time of the main join kernel (opts.timing) */
+    float ms_recheck;           /* device time of the recheck kernel (opts.timing) */
+    float ms_total;             /* device time of all kernels of the call (opts.timing) */
+    int32_t kernels_launched;   /* kernels this call launched */
+} dl_join_stats;
+
+int dl_result_stats(const dl_result *r, dl_join_stats *st);
+
+/* Free a result (NULL accepted). */
+int dl_result_free(dl_result *r);
+
+/* ---------------------------------------------------------------------------------
+ * Library.
+ * ------------------------------------------------------------------------------- */
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char *dl_last_error(void);
+
+/* Library version string. */
+const char *dl_version(void);
+
+/* Total kernels this library has launched in this process (for launch accounting). */
+int64_t dl_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DL_H */

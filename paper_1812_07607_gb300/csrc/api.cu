@@ -1,0 +1,593 @@
+// api.cu -- the C ABI: join orchestration, results and options.
+//
+// dl_sim_join runs, on the caller's stream:
+//   k_rowpar (per-row thresholds for this eps)           [tensor-core path]
+//   tc_join_kernel  or  k8_simt_join                       (classify every pair)
+//   k6_recheck (settle the band pairs exactly)             [exact paths]
+//   k_diag (self-join full mode: the diagonal)
+// then reads the three counters back (one 32-byte copy), re-runs with larger
+// buffers if an internal buffer overflowed, and hands the id pairs over as a
+// result that stays on the device until the caller asks for a host copy.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "kernels.h"
+
+namespace dl {
+
+// ------------------------------------------------------------------ pinned host memory
+static thread_local unsigned long long *t_counters = nullptr;
+
+static int pinned_counters(unsigned long long **p)
+{
+    if (!t_counters) {
+        cudaError_t e = cudaHostAlloc((void **)&t_counters, 64, cudaHostAllocDefault);
+        if (e != cudaSuccess) {
+            t_counters = nullptr;
+            return cuda_fail(e, "cudaHostAlloc(counters)");
+        }
+    }
+    *p = t_counters;
+    return DL_OK;
+}
+
+// A small pool of pinned host blocks, reused across results (pinning is slow).
+static std::mutex g_hpool_mu;
+static std::multimap<size_t, void *> g_hpool;
+
+static void *hpool_get(size_t bytes, size_t *got)
+{
+    {
+        std::lock_guard<std::mutex> lk(g_hpool_mu);
+        auto it = g_hpool.lower_bound(bytes);
+        if (it != g_hpool.end() && it->first <= 2 * bytes + (1 << 20)) {
+            void *p = it->second;
+            *got = it->first;
+            g_hpool.erase(it);
+            return p;
+        }
+    }
+    void *p = nullptr;
+    if (cudaHostAlloc(&p, bytes, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    *got = bytes;
+    return p;
+}
+
+static void hpool_put(void *p, size_t bytes)
+{
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_hpool_mu);
+    g_hpool.emplace(bytes, p);
+}
+
+// ------------------------------------------------------------------ unit lists
+// Work units of the tensor-core kernel: (R tile m, S tiles [nb, ne)). For a
+// self-join only tiles holding some column c > row r are listed.
+static std::mutex g_units_mu;
+static std::map<std::tuple<int, int64_t, int64_t, int, int, int>, std::pair<int4 *, int>> g_units;
+
+static void build_units(int64_t nR, int64_t nS, bool upper, int BN, int L, std::vector<int4> *v)
+{
+    const int mt = (int)((nR + 127) / 128), nt = (int)((nS + BN - 1) / BN);
+    v->clear();
+    for (int m = 0; m < mt; ++m) {
+        int nf = 0;
+        if (upper) {
+            const long long num = (long long)m * 128 + 2 - BN;
+            nf = num <= 0 ? 0 : (int)((num + BN - 1) / BN);
+        }
+        for (int nb = nf; nb < nt; nb += L) v->push_back(make_int4(m, nb, std::min(nb + L, nt), 0));
+    }
+}
+
+static int get_units(int64_t nR, int64_t nS, bool upper, int BN, int sms, const int4 **d_units, int *n_units)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int mt = (int)((nR + 127) / 128), nt = (int)((nS + BN - 1) / BN);
+    int L = 16;
+    while (L > 1) {
+        long long cnt = 0;
+        for (int m = 0; m < mt; ++m) {
+            int nf = 0;
+            if (upper) {
+                const long long num = (long long)m * 128 + 2 - BN;
+                nf = num <= 0 ? 0 : (int)((num + BN - 1) / BN);
+            }
+            cnt += (nt - nf + L - 1) / L;
+        }
+        if (cnt >= 4LL * sms) break;
+        L >>= 1;
+    }
+    auto key = std::make_tuple(dev, nR, nS, (int)upper, BN, L);
+    std::lock_guard<std::mutex> lk(g_units_mu);
+    auto it = g_units.find(key);
+    if (it == g_units.end()) {
+        std::vector<int4> v;
+        build_units(nR, nS, upper, BN, L, &v);
+        int4 *d = nullptr;
+        if (!v.empty()) {
+            cudaError_t e = cudaMalloc(&d, v.size() * sizeof(int4));
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(units)");
+            e = cudaMemcpy(d, v.data(), v.size() * sizeof(int4), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(units)");
+        }
+        it = g_units.emplace(key, std::make_pair(d, (int)v.size())).first;
+    }
+    *d_units = it->second.first;
+    *n_units = it->second.second;
+    return DL_OK;
+}
+
+// ------------------------------------------------------------------ one pass of a join
+struct PassCfg {
+    const dl_store *R, *S;
+    bool self, mirror;
+    int prec;
+    int BN;
+    double e2;
+    float t_acc, t_rej;     // FP32 thresholds (exact: recheck/SIMT; plain: SIMT only)
+    int64_t cap, band_cap;
+    bool timing;
+    cudaStream_t st;
+};
+
+struct PassOut {
+    int64_t *out_r = nullptr, *out_s = nullptr;
+    unsigned long long out_cnt = 0, band_cnt = 0, fp64_cnt = 0;
+    int err = 0;
+    float ms_main = 0, ms_recheck = 0, ms_total = 0;
+    int launches = 0;
+};
+
+static int run_pass(const PassCfg &c, PassOut *po)
+{
+    const dl_store *R = c.R, *S = c.S;
+    cudaStream_t st = c.st;
+    const int64_t nR = R->n, nS = S->n;
+    const int d = R->d;
+    const int sms = device_sm_count();
+
+    // output block (kept by the result) and workspace block (freed here)
+    void *outb = nullptr, *ws = nullptr;
+    const size_t cap = (size_t)std::max<int64_t>(c.cap, 1);
+    int rc = dev_alloc(&outb, 2 * cap * sizeof(int64_t), st);
+    if (rc) return rc;
+    const int64_t mt = (nR + 127) / 128;
+    const size_t b_band = ((size_t)std::max<int64_t>(c.band_cap, 1) * sizeof(uint2) + 255) & ~size_t(255);
+    const size_t b_rowpar = (size_t)mt * 128 * sizeof(float4);
+    rc = dev_alloc(&ws, 256 + b_band + b_rowpar, st);
+    if (rc) {
+        dev_free(outb, st);
+        return rc;
+    }
+    po->out_r = (int64_t *)outb;
+    po->out_s = po->out_r + cap;
+    unsigned long long *cnt = (unsigned long long *)ws;   // [0] out [1] band [2] fp64 [3] err
+    uint2 *band = (uint2 *)((char *)ws + 256);
+    float4 *rowpar = (float4 *)((char *)ws + 256 + b_band);
+
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    auto cleanup_ws = [&]() {
+        dev_free(ws, st);
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    };
+    if (c.timing)
+        for (auto &e : ev) cudaEventCreate(&e);
+    cudaError_t e = cudaMemsetAsync(cnt, 0, 64, st);
+    if (e != cudaSuccess) {
+        cleanup_ws();
+        dev_free(outb, st);
+        return cuda_fail(e, "cudaMemsetAsync(counters)");
+    }
+    if (c.timing) cudaEventRecord(ev[0], st);
+
+    JoinOut jo;
+    jo.r_ids = R->ids;
+    jo.s_ids = S->ids;
+    jo.out_r = po->out_r;
+    jo.out_s = po->out_s;
+    jo.out_cnt = cnt + 0;
+    jo.out_cap = (unsigned long long)c.cap;
+    jo.band = band;
+    jo.band_cnt = cnt + 1;
+    jo.band_cap = (unsigned long long)c.band_cap;
+    jo.mirror = c.mirror ? 1 : 0;
+
+    int launches = 0;
+    if (nR > 0 && nS > 0) {
+        if (c.prec == DL_PREC_BF16) {
+            rc = launch_rowpar(R->nq64, R->rowb, nR, mt * 128, R->dp, c.e2, gamma64(d), rowpar, st);
+            ++launches;
+            const CUtensorMap *tmA = nullptr, *tmB = nullptr;
+            if (!rc) rc = get_tmap(const_cast<dl_store *>(R), 128, &tmA);
+            if (!rc) rc = get_tmap(const_cast<dl_store *>(S), c.BN, &tmB);
+            const int4 *units = nullptr;
+            int n_units = 0;
+            if (!rc) rc = get_units(nR, nS, c.self, c.BN, sms, &units, &n_units);
+            if (!rc && n_units > 0) {
+                TcLaunch L;
+                L.tmA = tmA;
+                L.tmB = tmB;
+                L.BN = c.BN;
+                L.grid = std::min(n_units, sms);
+                L.p.units = units;
+                L.p.n_units = n_units;
+                L.p.nR = (int)nR;
+                L.p.nS = (int)nS;
+                L.p.kc = R->dp / 64;
+                L.p.stages = tc_pick_stages(c.BN, R->dp / 64);
+                L.p.upper = c.self ? 1 : 0;
+                L.p.rowpar = rowpar;
+                L.p.beta = S->beta;
+                L.p.cstat = S->cstat;
+                L.p.out = jo;
+                L.p.err = (int *)(cnt + 3);
+                rc = launch_tc_join(L, st);
+                ++launches;
+            }
+        } else {
+            SimtParams sp;
+            sp.R = R->x32;
+            sp.S = S->x32;
+            sp.nR = (int)nR;
+            sp.nS = (int)nS;
+            sp.d = d;
+            sp.upper = c.self ? 1 : 0;
+            sp.tiles_m = 0;
+            sp.exact = (c.prec == DL_PREC_FP32) ? 1 : 0;
+            sp.t_acc = c.t_acc;
+            sp.t_rej = c.t_rej;
+            sp.out = jo;
+            rc = launch_simt_join(sp, st);
+            ++launches;
+        }
+        if (c.timing) cudaEventRecord(ev[1], st);
+        if (!rc && c.prec != DL_PREC_FP32_PLAIN) {
+            rc = launch_recheck(band, cnt + 1, (unsigned long long)c.band_cap, R->x32, S->x32, d, c.e2, c.t_acc, c.t_rej,
+                                jo, cnt + 2, sms * 8, st);
+            ++launches;
+        }
+        if (c.timing) cudaEventRecord(ev[2], st);
+    } else if (c.timing) {
+        cudaEventRecord(ev[1], st);
+        cudaEventRecord(ev[2], st);
+    }
+    if (!rc && c.mirror) {
+        rc = launch_diag(R->ids, nR, po->out_r, po->out_s, cnt + 0, (unsigned long long)c.cap, st);
+        ++launches;
+    }
+    if (c.timing) cudaEventRecord(ev[3], st);
+    unsigned long long *hc = nullptr;
+    if (!rc) rc = pinned_counters(&hc);
+    if (!rc) {
+        e = cudaMemcpyAsync(hc, cnt, 32, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "join kernels");
+    }
+    if (!rc) {
+        po->out_cnt = hc[0];
+        po->band_cnt = hc[1];
+        po->fp64_cnt = hc[2];
+        po->err = (int)hc[3];
+        if (c.timing) {
+            cudaEventElapsedTime(&po->ms_main, ev[0], ev[1]);
+            cudaEventElapsedTime(&po->ms_recheck, ev[1], ev[2]);
+            cudaEventElapsedTime(&po->ms_total, ev[0], ev[3]);
+        }
+    }
+    po->launches = launches;
+    cleanup_ws();
+    if (rc) {
+        dev_free(outb, st);
+        po->out_r = po->out_s = nullptr;
+    }
+    return rc;
+}
+
+static int check_device(const dl_store *s)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != s->device) {
+        set_error("store lives on device %d but device %d is current", s->device, dev);
+        return DL_EINVAL;
+    }
+    return DL_OK;
+}
+
+}  // namespace dl
+
+using namespace dl;
+
+extern "C" {
+
+void dl_join_opts_default(dl_join_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->precision = DL_PREC_AUTO;
+    o->self_mode = DL_SELF_UPPER;
+}
+
+int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps, const dl_join_opts *opts,
+                dl_result **out)
+{
+    clear_error();
+    if (!out) {
+        set_error("dl_sim_join: out is NULL");
+        return DL_EINVAL;
+    }
+    *out = nullptr;
+    if (!R) {
+        set_error("dl_sim_join: R is NULL");
+        return DL_EINVAL;
+    }
+    if (metric != DL_METRIC_L2) {
+        set_error("dl_sim_join: unsupported metric %d", metric);
+        return DL_EINVAL;
+    }
+    if (std::isnan(eps) || eps < 0.0) {
+        set_error("dl_sim_join: eps must be >= 0 (got %g)", eps);
+        return DL_EINVAL;
+    }
+    dl_join_opts o;
+    if (opts)
+        o = *opts;
+    else
+        dl_join_opts_default(&o);
+    const bool self = (S == nullptr);
+    const dl_store *Sx = self ? R : S;
+    if (Sx->d != R->d) {
+        set_error("dl_sim_join: dimension mismatch %d vs %d", R->d, Sx->d);
+        return DL_EINVAL;
+    }
+    if (o.self_mode != DL_SELF_UPPER && o.self_mode != DL_SELF_FULL) {
+        set_error("dl_sim_join: bad self_mode %d", o.self_mode);
+        return DL_EINVAL;
+    }
+    int rc = check_device(R);
+    if (!rc) rc = check_device(Sx);
+    if (rc) return rc;
+    int prec = o.precision;
+    if (prec == DL_PREC_AUTO) prec = (R->dp <= 512) ? DL_PREC_BF16 : DL_PREC_FP32;
+    if (prec == DL_PREC_FP8E4M3) {
+        set_error("dl_sim_join: FP8 e4m3 path not available in this build");
+        return DL_EUNSUPPORTED;
+    }
+    if (prec != DL_PREC_BF16 && prec != DL_PREC_FP32 && prec != DL_PREC_FP32_PLAIN) {
+        set_error("dl_sim_join: bad precision %d", prec);
+        return DL_EINVAL;
+    }
+    if (prec == DL_PREC_BF16 && R->dp > 512) {
+        set_error("dl_sim_join: BF16 tensor-core path supports d <= 512 (d=%d)", R->d);
+        return DL_EUNSUPPORTED;
+    }
+    int BN = o.tile_n ? o.tile_n : 256;
+    if (BN != 128 && BN != 256) {
+        set_error("dl_sim_join: tile_n must be 0, 128 or 256");
+        return DL_EINVAL;
+    }
+    if (o.out_capacity < 0) {
+        set_error("dl_sim_join: negative out_capacity");
+        return DL_EINVAL;
+    }
+
+    const int d = R->d;
+    const double e2 = eps * eps;
+    PassCfg c;
+    c.R = R;
+    c.S = Sx;
+    c.self = self;
+    c.mirror = self && o.self_mode == DL_SELF_FULL;
+    c.prec = prec;
+    c.BN = BN;
+    c.e2 = e2;
+    if (prec == DL_PREC_FP32_PLAIN) {
+        const float ef = (float)eps;
+        c.t_acc = ef * ef;
+        c.t_rej = c.t_acc;
+    } else {
+        const double g64 = gamma64(d), g32 = gamma32(d);
+        const double abs32 = (double)(d + 8) * 1.401298464324817e-45 * 2.0;
+        c.t_acc = f32_rd(e2 * (1.0 - g64) * (1.0 - g32) * (1.0 - 8.881784197001252e-16) - abs32);
+        c.t_rej = f32_ru(e2 * (1.0 + 2.0 * g64) * (1.0 + g32) * (1.0 + 8.881784197001252e-16) + abs32);
+    }
+    c.timing = o.timing != 0;
+    c.st = (cudaStream_t)o.cuda_stream;
+    const bool fixed = o.out_capacity > 0;
+    {
+        std::lock_guard<std::mutex> lk(const_cast<dl_store *>(R)->mu);
+        c.cap = fixed ? o.out_capacity : std::max<int64_t>(1 << 16, R->hint_pairs + R->hint_pairs / 4);
+        c.band_cap = std::max<int64_t>(1 << 16, R->hint_band + R->hint_band / 4);
+    }
+
+    PassOut po;
+    int reruns = 0;
+    for (int attempt = 0;; ++attempt) {
+        po = PassOut();
+        rc = run_pass(c, &po);
+        if (rc) return rc;
+        if (po.err) {
+            dev_free(po.out_r, c.st);
+            set_error("dl_sim_join: a bounded device wait expired (kernel pipeline stalled)");
+            return DL_ETIMEOUT;
+        }
+        const bool band_over = po.band_cnt > (unsigned long long)c.band_cap;
+        const bool out_over = po.out_cnt > (unsigned long long)c.cap;
+        if (band_over || (out_over && !fixed)) {
+            if (attempt >= 4) {
+                dev_free(po.out_r, c.st);
+                set_error("dl_sim_join: output keeps overflowing");
+                return DL_ENOMEM;
+            }
+            dev_free(po.out_r, c.st);
+            if (band_over) c.band_cap = (int64_t)po.band_cnt + (int64_t)(po.band_cnt / 8) + 1024;
+            if (out_over) c.cap = (int64_t)po.out_cnt + (int64_t)(po.out_cnt / 8) + 1024;
+            ++reruns;
+            continue;
+        }
+        break;
+    }
+    {
+        std::lock_guard<std::mutex> lk(const_cast<dl_store *>(R)->mu);
+        const_cast<dl_store *>(R)->hint_pairs = (int64_t)po.out_cnt;
+        const_cast<dl_store *>(R)->hint_band = (int64_t)po.band_cnt;
+    }
+    dl_result *res = new dl_result();
+    res->kind = 0;
+    res->device = R->device;
+    res->stream = c.st;
+    res->count = (int64_t)po.out_cnt;
+    res->cap = c.cap;
+    res->d_r = po.out_r;
+    res->d_s = po.out_s;
+    dl_join_stats &s = res->stats;
+    s.pairs_evaluated = self ? (c.mirror ? R->n * R->n : R->n * (R->n - 1) / 2) : R->n * Sx->n;
+    s.pairs_out = (int64_t)po.out_cnt;
+    s.band_pairs = (int64_t)po.band_cnt;
+    s.fp64_pairs = (int64_t)po.fp64_cnt;
+    s.reruns = reruns;
+    s.precision = prec;
+    s.tile_n = prec == DL_PREC_BF16 ? BN : 0;
+    s.ms_main = po.ms_main;
+    s.ms_recheck = po.ms_recheck;
+    s.ms_total = po.ms_total;
+    s.kernels_launched = po.launches * (reruns + 1);
+    *out = res;
+    if (fixed && po.out_cnt > (unsigned long long)c.cap) {
+        set_error("dl_sim_join: %llu pairs exceed out_capacity %lld", po.out_cnt, (long long)c.cap);
+        return DL_EOVERFLOW;
+    }
+    return DL_OK;
+}
+
+int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric, int32_t k, const dl_join_opts *opts,
+                 dl_result **out);   // defined in topk.cu
+
+int dl_result_count(const dl_result *r, int64_t *n)
+{
+    if (!r || !n) {
+        set_error("dl_result_count: NULL argument");
+        return DL_EINVAL;
+    }
+    *n = r->kind == 0 ? r->count : r->nq * r->k;
+    return DL_OK;
+}
+
+int dl_result_pairs(dl_result *r, int32_t where, const int64_t **r_ids, const int64_t **s_ids, int64_t *n)
+{
+    if (!r || r->kind != 0) {
+        set_error("dl_result_pairs: not an epsilon-join result");
+        return DL_EINVAL;
+    }
+    const int64_t cnt = std::min(r->count, r->cap);
+    if (n) *n = cnt;
+    if (where == DL_MEM_DEVICE) {
+        if (r_ids) *r_ids = r->d_r;
+        if (s_ids) *s_ids = r->d_s;
+        return DL_OK;
+    }
+    if (where != DL_MEM_HOST) {
+        set_error("dl_result_pairs: bad memory kind");
+        return DL_EINVAL;
+    }
+    if (!r->h_r) {
+        size_t got = 0;
+        const size_t bytes = std::max<size_t>(16, (size_t)cnt * 2 * sizeof(int64_t));
+        void *h = hpool_get(bytes, &got);
+        if (!h) {
+            set_error("dl_result_pairs: pinned host allocation of %zu bytes failed", bytes);
+            return DL_ENOMEM;
+        }
+        r->h_r = (int64_t *)h;
+        r->h_s = r->h_r + cnt;
+        r->h_bytes = got;
+        cudaError_t e = cudaSuccess;
+        if (cnt > 0) e = cudaMemcpyAsync(r->h_r, r->d_r, cnt * sizeof(int64_t), cudaMemcpyDeviceToHost, r->stream);
+        if (e == cudaSuccess && cnt > 0)
+            e = cudaMemcpyAsync(r->h_s, r->d_s, cnt * sizeof(int64_t), cudaMemcpyDeviceToHost, r->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "dl_result_pairs copy");
+    }
+    if (r_ids) *r_ids = r->h_r;
+    if (s_ids) *s_ids = r->h_s;
+    return DL_OK;
+}
+
+int dl_result_topk(dl_result *r, int32_t where, const int64_t **ids, const double **dist2, int32_t *k, int64_t *nq)
+{
+    if (!r || r->kind != 1) {
+        set_error("dl_result_topk: not a top-k result");
+        return DL_EINVAL;
+    }
+    if (k) *k = r->k;
+    if (nq) *nq = r->nq;
+    if (where == DL_MEM_DEVICE) {
+        if (ids) *ids = r->d_ids;
+        if (dist2) *dist2 = r->d_d2;
+        return DL_OK;
+    }
+    if (where != DL_MEM_HOST) {
+        set_error("dl_result_topk: bad memory kind");
+        return DL_EINVAL;
+    }
+    if (!r->h_ids) {
+        const size_t n = (size_t)r->nq * r->k;
+        size_t got = 0;
+        void *h = hpool_get(std::max<size_t>(16, n * 16), &got);
+        if (!h) {
+            set_error("dl_result_topk: pinned host allocation failed");
+            return DL_ENOMEM;
+        }
+        r->h_ids = (int64_t *)h;
+        r->h_d2 = (double *)(r->h_ids + n);
+        r->h_bytes = got;
+        cudaError_t e = cudaSuccess;
+        if (n > 0) e = cudaMemcpyAsync(r->h_ids, r->d_ids, n * 8, cudaMemcpyDeviceToHost, r->stream);
+        if (e == cudaSuccess && n > 0) e = cudaMemcpyAsync(r->h_d2, r->d_d2, n * 8, cudaMemcpyDeviceToHost, r->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "dl_result_topk copy");
+    }
+    if (ids) *ids = r->h_ids;
+    if (dist2) *dist2 = r->h_d2;
+    return DL_OK;
+}
+
+int dl_result_stats(const dl_result *r, dl_join_stats *st)
+{
+    if (!r || !st) {
+        set_error("dl_result_stats: NULL argument");
+        return DL_EINVAL;
+    }
+    *st = r->stats;
+    return DL_OK;
+}
+
+int dl_result_free(dl_result *r)
+{
+    if (!r) return DL_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != r->device) cudaSetDevice(r->device);
+    if (r->kind == 0)
+        dev_free(r->d_r, r->stream);   // d_s lives in the same block
+    else
+        dev_free(r->d_ids, r->stream); // d_d2 lives in the same block
+    if (prev != r->device) cudaSetDevice(prev);
+    if (r->h_r) hpool_put(r->h_r, r->h_bytes);
+    if (r->h_ids) hpool_put(r->h_ids, r->h_bytes);
+    delete r;
+    return DL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,125 @@
+// internal.h -- declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <mutex>
+#include <string>
+
+#include "dl.h"
+
+namespace dl {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char *fmt, ...);
+void clear_error();
+int cuda_fail(cudaError_t e, const char *what);
+
+#define DL_CUDA_TRY(expr)                                      \
+    do {                                                       \
+        cudaError_t _e = (expr);                               \
+        if (_e != cudaSuccess) return ::dl::cuda_fail(_e, #expr); \
+    } while (0)
+
+extern std::atomic<int64_t> g_launches;
+inline void count_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------- numeric constants
+// Unit roundoff of FP32 / FP64 (round to nearest).
+constexpr double kU32 = 5.9604644775390625e-08;   // 2^-24
+constexpr double kU64 = 1.1102230246251565e-16;   // 2^-53
+
+// Relative bound of the canonical FP64 distance sum against the exact real
+// value: |D64 - D| <= (d+3) 2^-53 D (the oracle's first pin checks the same
+// bound); one extra unit of margin.
+inline double gamma64(int d) { return (d + 4) * kU64; }
+
+// Relative bound of any FP32 evaluation of sum_k (q_k - x_k)^2 the library
+// performs (sequential FMA chain, or lane partial sums plus a 5-level shuffle
+// tree): (d + 8) 2^-24.
+inline double gamma32(int d) { return (d + 8) * kU32; }
+
+// Assumed relative bound of the tensor-core FP32 accumulation of d BF16 x BF16
+// products (the products are exact in FP32; summation order and rounding of the
+// hardware adder are not documented): d * 2^-20, sixteen times the textbook
+// d * 2^-24. Checked empirically by the bound-validity test.
+inline double gamma_tc(int dp) { return dp * 9.5367431640625e-07; }
+
+// Absolute slack covering underflow/flush of tiny products.
+inline double abs_slack_tc(int dp) { return dp * 8.271806125530277e-25; }   // dp * 2^-80
+
+// ---------------------------------------------------------------- store
+struct TmapCache {
+    bool valid = false;
+    int box_rows = 0;
+    CUtensorMap map;
+};
+
+struct Store {
+    int64_t n = 0;
+    int32_t d = 0;
+    int32_t dp = 0;          // d rounded up to a multiple of 64 (BF16 copy row length)
+    int64_t n_pad = 0;       // n rounded up to a multiple of 256 (column-side padding)
+    int device = 0;
+    int64_t *ids = nullptr;  // [n]
+    float *x32 = nullptr;    // [n][d] FP32 master copy
+    __nv_bfloat16 *xb = nullptr;  // [n][dp] BF16 copy, zero padded
+    double *nq64 = nullptr;  // [n] sum of squares in FP64
+    float *beta = nullptr;   // [n_pad] RN32(nq64 / 2); +inf in padding
+    float4 *rowb = nullptr;  // [n] {||x - x~|| up, ||x~|| up, ||x|| up, |beta - ||x||^2/2| up}
+    float4 *cstat = nullptr; // [n_pad / 32] per 32-row chunk {P1, P2, P3, 0} of the BF16 bound
+    TmapCache tmaps[3];      // box rows 128, 256, 128-for-B (cached per box height)
+    std::mutex mu;           // guards tmaps and hints
+    int64_t hint_pairs = 0;  // last output size seen with this store as R (capacity hint)
+    int64_t hint_band = 0;
+};
+
+// Build (or fetch from the store's cache) a 2-D BF16 tensor map over the store's
+// BF16 copy with a box of 64 columns x box_rows rows and the 128-byte swizzle.
+int get_tmap(Store *s, int box_rows, const CUtensorMap **out);
+
+// ---------------------------------------------------------------- device pools
+// Stream-ordered allocation from the current device's default memory pool.
+int dev_alloc(void **p, size_t bytes, cudaStream_t st);
+void dev_free(void *p, cudaStream_t st);
+
+int device_sm_count();
+
+// Host-side directed conversions FP64 -> FP32 (the default conversion rounds to nearest).
+inline float f32_ru(double x)
+{
+    float f = (float)x;
+    if ((double)f < x) f = nextafterf(f, __builtin_inff());
+    return f;
+}
+inline float f32_rd(double x)
+{
+    float f = (float)x;
+    if ((double)f > x) f = nextafterf(f, -__builtin_inff());
+    return f;
+}
+
+}  // namespace dl
+
+struct dl_store : public dl::Store {};
+
+struct dl_result {
+    int kind = 0;             // 0 pairs, 1 topk
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int64_t count = 0;        // pairs (kind 0)
+    int64_t cap = 0;
+    int64_t *d_r = nullptr, *d_s = nullptr;   // device pair ids
+    int64_t *h_r = nullptr, *h_s = nullptr;   // host copies (pinned)
+    int32_t k = 0;
+    int64_t nq = 0;
+    int64_t *d_ids = nullptr; double *d_d2 = nullptr;
+    int64_t *h_ids = nullptr; double *h_d2 = nullptr;
+    size_t h_bytes = 0;       // size of the pinned host block (h_r or h_ids)
+    dl_join_stats stats{};
+};

@@ -1,0 +1,58 @@
+// kernels.h -- launch interfaces of the library's kernels (host side).
+#pragma once
+
+#include <cuda.h>
+
+#include "emit.cuh"
+#include "internal.h"
+
+namespace dl {
+
+// ---- K2+K3+K5 tensor-core epsilon-join (join_tc.cu)
+struct TcParams {
+    const int4 *units;       // {m, nb, ne, 0}: R tile m against S tiles [nb, ne)
+    int n_units;
+    int nR, nS;
+    int kc;                  // K chunks of 64 (dp / 64)
+    int stages;              // S ring depth
+    int upper;               // 1: self-join, only columns c > r are pairs
+    const float4 *rowpar;    // [m_tiles*128] {alpha_acc, alpha_rej, rq, nqt}
+    const float *beta;       // S: RN32(||x||^2/2), +inf padding
+    const float4 *cstat;     // S: per 32-column chunk {P1, P2, P3, 0}
+    JoinOut out;
+    int *err;                // set to 1 when a bounded wait expired
+};
+
+struct TcLaunch {
+    const CUtensorMap *tmA, *tmB;
+    TcParams p;
+    int BN;
+    int grid;
+};
+
+int tc_pick_stages(int BN, int kc);
+int launch_tc_join(const TcLaunch &L, cudaStream_t st);
+
+// ---- K8 SIMT FP32 join (join_simt.cu)
+struct SimtParams {
+    const float *R;
+    const float *S;
+    int nR, nS, d;
+    int upper;          // self-join: only c > r
+    int tiles_m;        // filled by the launcher
+    int exact;          // 0 plain, 1 exact (band output)
+    float t_acc, t_rej; // exact thresholds; plain uses t_acc only
+    JoinOut out;
+};
+int launch_simt_join(SimtParams p, cudaStream_t st);
+
+// ---- K6 recheck and small per-join kernels (recheck.cu)
+int launch_recheck(const uint2 *band, const unsigned long long *band_cnt, unsigned long long band_cap, const float *R,
+                   const float *S, int d, double e2, float t_acc, float t_rej, const JoinOut &out,
+                   unsigned long long *n_fp64, int grid, cudaStream_t st);
+int launch_rowpar(const double *nq64, const float4 *rowb, int64_t n, int64_t n_tot, int dp, double e2, double g64,
+                  float4 *rowpar, cudaStream_t st);
+int launch_diag(const int64_t *ids, int64_t n, int64_t *out_r, int64_t *out_s, unsigned long long *out_cnt,
+                unsigned long long cap, cudaStream_t st);
+
+}  // namespace dl

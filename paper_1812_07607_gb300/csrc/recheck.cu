@@ -1,0 +1,136 @@
+// recheck.cu -- K6 (exact recheck of band pairs) and the small per-join kernels.
+//
+// A band pair is one whose low-precision distance could not be placed on one
+// side of eps^2 by the error bound. K6 settles it exactly:
+//   1. FP32, one warp per pair: D32 = sum_k fl(q_k - x_k)^2 (lane partial FMA
+//      chains + a shuffle tree), bound |D32 - D| <= (d+8) 2^-24 D + tiny; if that
+//      decides the pair against the canonical-FP64 slack, done;
+//   2. otherwise the canonical FP64 value itself: k ascending,
+//      t = (double)q_k - (double)x_k, s = s + t*t, every operation rounded to
+//      nearest with no contraction (__dsub_rn / __dmul_rn / __dadd_rn), compared
+//      with fl64(eps*eps) -- the very expression that defines the result, so the
+//      decision is identical to the FP64 nested loop's.
+#include "kernels.h"
+
+namespace dl {
+
+__global__ void __launch_bounds__(256)
+    k6_recheck(const uint2 *__restrict__ band, const unsigned long long *__restrict__ band_cnt,
+               unsigned long long band_cap, const float *__restrict__ R, const float *__restrict__ S, int d, double e2,
+               float t_acc, float t_rej, JoinOut out, unsigned long long *__restrict__ n_fp64)
+{
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned long long nb = min(*band_cnt, band_cap);
+    const unsigned long long w0 = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    for (unsigned long long i = w0; i < nb; i += nw) {
+        const uint2 pr = band[i];
+        const float *q = R + (size_t)pr.x * d;
+        const float *x = S + (size_t)pr.y * d;
+        float s = 0.f;
+        for (int k = lane; k < d; k += 32) {
+            const float t = __ldg(q + k) - __ldg(x + k);
+            s = fmaf(t, t, s);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        bool acc = (s <= t_acc);
+        const bool rej = (s > t_rej);
+        if (!acc && !rej) {
+            double sum = 0.0;
+            for (int k0 = 0; k0 < d; k0 += 32) {
+                double pk = 0.0;
+                const int k = k0 + (int)lane;
+                if (k < d) {
+                    const double t = __dsub_rn((double)__ldg(q + k), (double)__ldg(x + k));
+                    pk = __dmul_rn(t, t);
+                }
+                const int lim = min(32, d - k0);
+                for (int l = 0; l < lim; ++l) sum = __dadd_rn(sum, __shfl_sync(0xffffffffu, pk, l));
+            }
+            acc = (sum <= e2);
+            if (lane == 0) atomicAdd(n_fp64, 1ULL);
+        }
+        warp_emit(out, acc && lane == 0, false, (int)pr.x, (int)pr.y);
+    }
+}
+
+// Per-row thresholds of the tensor-core epilogue for one join:
+//   alpha_acc = RU32((||q||^2_up - e2 (1 - g64)) / 2)   accept iff h >= alpha_acc + E
+//   alpha_rej = RD32((||q||^2_dn - e2 (1 + 2 g64)) / 2) reject iff h <  alpha_rej - E
+// with h = q.x - ||x||^2/2 (so D = ||q||^2 - 2h), plus the row's bound terms.
+// Padding rows get +inf thresholds (never emit).
+__global__ void __launch_bounds__(256)
+    k_rowpar(const double *__restrict__ nq64, const float4 *__restrict__ rowb, int64_t n, int64_t n_tot, int dp,
+             double e2, double g64, float4 *__restrict__ rowpar)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_tot) return;
+    const float inf = __int_as_float(0x7f800000);
+    if (i >= n) {
+        rowpar[i] = make_float4(inf, inf, 0.f, 0.f);
+        return;
+    }
+    const double nq = nq64[i];
+    const double rel = (double)(dp + 2) * 2.220446049250313e-16;
+    const double nq_up = __dmul_ru(nq, 1.0 + rel);
+    const double nq_dn = __dmul_rd(nq, 1.0 - rel);
+    const double a_acc = __dsub_ru(nq_up, __dmul_rd(e2, 1.0 - g64)) * 0.5;
+    const double a_rej = __dsub_rd(nq_dn, __dmul_ru(e2, 1.0 + 2.0 * g64)) * 0.5;
+    const float4 rb = rowb[i];
+    rowpar[i] = make_float4(__double2float_ru(a_acc), __double2float_rd(a_rej), rb.x, rb.y);
+}
+
+// Self-join full mode: every (i, i) is a pair (canonical D = 0 <= eps^2).
+__global__ void __launch_bounds__(256) k_diag(const int64_t *__restrict__ ids, int64_t n, int64_t *out_r,
+                                             int64_t *out_s, unsigned long long *out_cnt, unsigned long long cap)
+{
+    __shared__ unsigned long long base;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t blk0 = (int64_t)blockIdx.x * blockDim.x;
+    const int cnt = (int)min((int64_t)blockDim.x, n - blk0);
+    if (threadIdx.x == 0) base = atomicAdd(out_cnt, (unsigned long long)cnt);
+    __syncthreads();
+    if (i < n) {
+        const unsigned long long pos = base + threadIdx.x;
+        if (pos < cap) {
+            out_r[pos] = ids[i];
+            out_s[pos] = ids[i];
+        }
+    }
+}
+
+int launch_recheck(const uint2 *band, const unsigned long long *band_cnt, unsigned long long band_cap, const float *R,
+                   const float *S, int d, double e2, float t_acc, float t_rej, const JoinOut &out,
+                   unsigned long long *n_fp64, int grid, cudaStream_t st)
+{
+    k6_recheck<<<grid, 256, 0, st>>>(band, band_cnt, band_cap, R, S, d, e2, t_acc, t_rej, out, n_fp64);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k6_recheck launch");
+    return DL_OK;
+}
+
+int launch_rowpar(const double *nq64, const float4 *rowb, int64_t n, int64_t n_tot, int dp, double e2, double g64,
+                  float4 *rowpar, cudaStream_t st)
+{
+    if (n_tot == 0) return DL_OK;
+    k_rowpar<<<(unsigned)((n_tot + 255) / 256), 256, 0, st>>>(nq64, rowb, n, n_tot, dp, e2, g64, rowpar);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_rowpar launch");
+    return DL_OK;
+}
+
+int launch_diag(const int64_t *ids, int64_t n, int64_t *out_r, int64_t *out_s, unsigned long long *out_cnt,
+                unsigned long long cap, cudaStream_t st)
+{
+    if (n == 0) return DL_OK;
+    k_diag<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ids, n, out_r, out_s, out_cnt, cap);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_diag launch");
+    return DL_OK;
+}
+
+}  // namespace dl

@@ -1,0 +1,373 @@
+// store.cu -- the device-resident patch store and its derivation pass (K1).
+//
+// A store keeps a patch collection resident on the GPU (the in-memory form of
+// "materialize", Sec. 3.2 / Sec. 4.1 of the paper): int64 ids, the FP32
+// feature rows (the ground truth), a zero-padded BF16 copy for the tensor
+// cores, and per-row / per-32-row-chunk statistics from which the join
+// kernels derive sound error bounds.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "internal.h"
+
+namespace dl {
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string t_err;
+
+void set_error(const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+}
+
+void clear_error() { t_err.clear(); }
+
+const char *last_error() { return t_err.c_str(); }
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+    return DL_ECUDA;
+}
+
+std::atomic<int64_t> g_launches{0};
+
+// ------------------------------------------------------------------ pools
+static std::mutex g_pool_mu;
+static bool g_pool_ready[64];
+
+int dev_alloc(void **p, size_t bytes, cudaStream_t st)
+{
+    int dev = 0;
+    DL_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64) {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (!g_pool_ready[dev]) {
+            // Keep freed blocks in the pool so repeated calls do not return memory
+            // to the driver (a per-process pool attribute).
+            cudaMemPool_t pool;
+            if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+                uint64_t thr = UINT64_MAX;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+            }
+            g_pool_ready[dev] = true;
+        }
+    }
+    if (bytes == 0) bytes = 256;
+    cudaError_t e = cudaMallocAsync(p, bytes, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        *p = nullptr;
+        return DL_ENOMEM;
+    }
+    return DL_OK;
+}
+
+void dev_free(void *p, cudaStream_t st)
+{
+    if (p) cudaFreeAsync(p, st);
+}
+
+int device_sm_count()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+// ------------------------------------------------------------------ K1
+// One warp per row. Computes, from the FP32 row x:
+//   nq64  = sum x_k^2 in FP64 (products exact, rounding only in the sum),
+//   the BF16 copy x~ = RN_bf16(x) (zero padded to dp),
+//   upper bounds of ||x - x~||, ||x~||, ||x|| (FP64 sums, inflated by the sum
+//   and sqrt rounding, rounded up to FP32),
+//   beta = RN32(nq64 / 2) and an upper bound of |beta - ||x||^2 / 2|,
+// and flags rows with a non-finite value or |x_k| > 2^40.
+__global__ void __launch_bounds__(256) k1_norm_quant(const float *__restrict__ x32, int64_t n, int d, int dp,
+                                                     __nv_bfloat16 *__restrict__ xb, double *__restrict__ nq64,
+                                                     float *__restrict__ beta, float4 *__restrict__ rowb,
+                                                     int *__restrict__ err)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * 8 + warp;
+    if (row >= n) return;
+    const float *xr = x32 + row * d;
+    __nv_bfloat16 *br = xb + row * dp;
+    double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    bool bad = false;
+    for (int k = lane; k < dp; k += 32) {
+        const float v = (k < d) ? __ldg(xr + k) : 0.0f;
+        if (!(fabsf(v) <= 1099511627776.0f)) bad = true;  // also catches NaN
+        const __nv_bfloat16 b = __float2bfloat16_rn(v);
+        br[k] = b;
+        const double dv = (double)v, db = (double)__bfloat162float(b);
+        const double e = dv - db;   // exact: x~ shares x's leading bits
+        s1 = __dadd_rn(s1, __dmul_rn(dv, dv));
+        s2 = __dadd_rn(s2, __dmul_rn(e, e));
+        s3 = __dadd_rn(s3, __dmul_rn(db, db));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 = __dadd_rn(s1, __shfl_xor_sync(0xffffffffu, s1, o));
+        s2 = __dadd_rn(s2, __shfl_xor_sync(0xffffffffu, s2, o));
+        s3 = __dadd_rn(s3, __shfl_xor_sync(0xffffffffu, s3, o));
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+        if (bad) atomicOr(err, 1);
+        // Any-order FP64 sum of dp non-negative exact terms: relative error <= (dp-1) 2^-53.
+        const double fac = 1.0 + (double)(dp + 4) * 2.220446049250313e-16;
+        const double grow = 1.0 + 8.881784197001252e-16;   // 1 + 2^-50 covers the sqrt / product roundings
+        nq64[row] = s1;
+        const float rq = __double2float_ru(sqrt(s2 * fac) * grow);
+        const float nqt = __double2float_ru(sqrt(s3 * fac) * grow);
+        const float nx = __double2float_ru(sqrt(s1 * fac) * grow);
+        const double h = 0.5 * s1;
+        const float bt = __double2float_rn(h);
+        const float berr = __double2float_ru((fabs((double)bt - h) + h * (double)(dp + 2) * 2.220446049250313e-16) * grow);
+        beta[row] = bt;
+        rowb[row] = make_float4(rq, nqt, nx, berr);
+    }
+}
+
+// One warp per 32-row chunk: column-side maxima of the BF16 error-bound terms,
+//   P1 = max ||x||,   P2 = max ||x - x~|| + (gamma_tc + 1.01 u) max ||x~||,
+//   P3 = max |beta err| + u max beta + absolute slack,
+// so that for a query row q and any column x in the chunk the error of the
+// epilogue value h = fl(A~ - beta) is at most  rq * P1 + ||q~|| * P2 + P3.
+// Also fills beta's padding with +inf (padded columns can never match).
+__global__ void __launch_bounds__(256) k1_chunk_stats(const float *__restrict__ beta_in, const float4 *__restrict__ rowb,
+                                                      int64_t n, int64_t n_pad, float g2, float p3_abs,
+                                                      float *__restrict__ beta, float4 *__restrict__ cstat)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t chunk = (int64_t)blockIdx.x * 8 + warp;
+    if (chunk * 32 >= n_pad) return;
+    const int64_t row = chunk * 32 + lane;
+    float rq = 0.f, nqt = 0.f, nx = 0.f, berr = 0.f, bt = 0.f;
+    if (row < n) {
+        const float4 rb = rowb[row];
+        rq = rb.x;
+        nqt = rb.y;
+        nx = rb.z;
+        berr = rb.w;
+        bt = fabsf(beta_in[row]);
+    } else {
+        beta[row] = __int_as_float(0x7f800000);   // +inf
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rq = fmaxf(rq, __shfl_xor_sync(0xffffffffu, rq, o));
+        nqt = fmaxf(nqt, __shfl_xor_sync(0xffffffffu, nqt, o));
+        nx = fmaxf(nx, __shfl_xor_sync(0xffffffffu, nx, o));
+        berr = fmaxf(berr, __shfl_xor_sync(0xffffffffu, berr, o));
+        bt = fmaxf(bt, __shfl_xor_sync(0xffffffffu, bt, o));
+    }
+    if (lane == 0) {
+        const float p2 = __fmaf_ru(g2, nqt, rq);
+        const float p3 = __fadd_ru(__fmaf_ru(5.9604644775390625e-08f, bt, berr), p3_abs);
+        cstat[chunk] = make_float4(nx, p2, p3, 0.f);
+    }
+}
+
+// ------------------------------------------------------------------ tensor maps
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+int get_tmap(Store *s, int box_rows, const CUtensorMap **out)
+{
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto &t : s->tmaps)
+        if (t.valid && t.box_rows == box_rows) {
+            *out = &t.map;
+            return DL_OK;
+        }
+    TmapCache *slot = nullptr;
+    for (auto &t : s->tmaps)
+        if (!t.valid) {
+            slot = &t;
+            break;
+        }
+    if (!slot) slot = &s->tmaps[0];
+    auto fn = encode_fn();
+    if (!fn) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return DL_ECUDA;
+    }
+    cuuint64_t gdim[2] = {(cuuint64_t)s->dp, (cuuint64_t)(s->n > 0 ? s->n : 1)};
+    cuuint64_t gstride[1] = {(cuuint64_t)s->dp * sizeof(__nv_bfloat16)};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    cuuint32_t estride[2] = {1, 1};
+    CUresult r = fn(&slot->map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)s->xb, gdim, gstride, box, estride,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d) for dp=%d rows=%lld box=%d", (int)r, s->dp,
+                  (long long)s->n, box_rows);
+        return DL_ECUDA;
+    }
+    slot->valid = true;
+    slot->box_rows = box_rows;
+    *out = &slot->map;
+    return DL_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace dl
+
+using namespace dl;
+
+extern "C" {
+
+int dl_store_create(dl_store **out, const int64_t *ids, const float *feats, int64_t n, int32_t d, int32_t where,
+                    void *cuda_stream)
+{
+    clear_error();
+    if (!out) {
+        set_error("dl_store_create: out is NULL");
+        return DL_EINVAL;
+    }
+    *out = nullptr;
+    if (n < 0 || n >= (int64_t(1) << 31)) {
+        set_error("dl_store_create: n=%lld out of range [0, 2^31)", (long long)n);
+        return DL_EINVAL;
+    }
+    if (d < 1 || d > 1024) {
+        set_error("dl_store_create: d=%d out of range [1, 1024]", d);
+        return DL_EINVAL;
+    }
+    if (n > 0 && (!ids || !feats)) {
+        set_error("dl_store_create: ids/feats is NULL");
+        return DL_EINVAL;
+    }
+    if (where != DL_MEM_HOST && where != DL_MEM_DEVICE) {
+        set_error("dl_store_create: bad memory kind %d", where);
+        return DL_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    dl_store *s = new dl_store();
+    s->n = n;
+    s->d = d;
+    s->dp = (d + 63) / 64 * 64;
+    s->n_pad = (n + 255) / 256 * 256;
+    if (s->n_pad == 0) s->n_pad = 256;
+    DL_CUDA_TRY(cudaGetDevice(&s->device));
+
+    const size_t b_ids = align256(sizeof(int64_t) * n), b_x32 = align256(sizeof(float) * n * d),
+                 b_xb = align256(sizeof(__nv_bfloat16) * n * s->dp), b_nq = align256(sizeof(double) * n),
+                 b_beta = align256(sizeof(float) * s->n_pad), b_rowb = align256(sizeof(float4) * n),
+                 b_cst = align256(sizeof(float4) * (s->n_pad / 32)), b_err = 256;
+    const size_t total = b_ids + b_x32 + b_xb + b_nq + b_beta + b_rowb + b_cst + b_err;
+    void *base = nullptr;
+    int rc = dev_alloc(&base, total, st);
+    if (rc != DL_OK) {
+        delete s;
+        return rc;
+    }
+    char *p = (char *)base;
+    s->ids = (int64_t *)p;
+    p += b_ids;
+    s->x32 = (float *)p;
+    p += b_x32;
+    s->xb = (__nv_bfloat16 *)p;
+    p += b_xb;
+    s->nq64 = (double *)p;
+    p += b_nq;
+    s->beta = (float *)p;
+    p += b_beta;
+    s->rowb = (float4 *)p;
+    p += b_rowb;
+    s->cstat = (float4 *)p;
+    p += b_cst;
+    int *d_err = (int *)p;
+
+    auto fail = [&](int code) {
+        dev_free(base, st);
+        cudaStreamSynchronize(st);
+        delete s;
+        return code;
+    };
+    const cudaMemcpyKind kind = (where == DL_MEM_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess && n > 0) e = cudaMemcpyAsync(s->ids, ids, sizeof(int64_t) * n, kind, st);
+    if (e == cudaSuccess && n > 0) e = cudaMemcpyAsync(s->x32, feats, sizeof(float) * n * d, kind, st);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "dl_store_create copy"));
+    if (n > 0) {
+        k1_norm_quant<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(s->x32, n, d, s->dp, s->xb, s->nq64, s->beta, s->rowb,
+                                                               d_err);
+        count_launch();
+    }
+    const float g2 = f32_ru(gamma_tc(s->dp) + 1.01 * kU32);
+    const float p3a = f32_ru(abs_slack_tc(s->dp));
+    k1_chunk_stats<<<(unsigned)((s->n_pad / 32 + 7) / 8), 256, 0, st>>>(s->beta, s->rowb, n, s->n_pad, g2, p3a, s->beta,
+                                                                        s->cstat);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(cuda_fail(e, "store kernels launch"));
+    int h_err = 0;
+    e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "dl_store_create sync"));
+    if (h_err) {
+        set_error("dl_store_create: a feature is non-finite or exceeds 2^40 in magnitude");
+        return fail(DL_EINVAL);
+    }
+    *out = s;
+    return DL_OK;
+}
+
+int dl_store_destroy(dl_store *s)
+{
+    if (!s) return DL_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != s->device) cudaSetDevice(s->device);
+    dev_free(s->ids, 0);   // ids is the base of the store's single allocation
+    if (prev != s->device) cudaSetDevice(prev);
+    delete s;
+    return DL_OK;
+}
+
+int dl_store_shape(const dl_store *s, int64_t *n, int32_t *d)
+{
+    if (!s) {
+        set_error("dl_store_shape: NULL store");
+        return DL_EINVAL;
+    }
+    if (n) *n = s->n;
+    if (d) *d = s->d;
+    return DL_OK;
+}
+
+const char *dl_last_error(void) { return dl::last_error(); }
+
+const char *dl_version(void) { return "dl-simjoin 0.1 (sm_103a)"; }
+
+int64_t dl_kernel_launches(void) { return dl::g_launches.load(); }
+
+}  // extern "C"

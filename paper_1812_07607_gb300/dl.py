@@ -1,0 +1,278 @@
+"""Thin ctypes binding of the C ABI declared in include/dl.h.
+
+Argument marshalling only: every step of the join runs in the library's CUDA
+kernels. PyTorch supplies device memory and streams. There is no CPU
+fallback: if the library is missing or no GB300 is usable, calls raise.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdlsimjoin.so")
+
+# dl_status
+DL_OK, DL_EINVAL, DL_ENOMEM, DL_EOVERFLOW, DL_EAGAIN, DL_ETIMEOUT, DL_ECUDA, DL_ECANCELED, \
+    DL_ENOMEM_ADMIT, DL_EFAILED, DL_EUNSUPPORTED = range(11)
+STATUS_NAMES = {0: "DL_OK", 1: "DL_EINVAL", 2: "DL_ENOMEM", 3: "DL_EOVERFLOW", 4: "DL_EAGAIN",
+                5: "DL_ETIMEOUT", 6: "DL_ECUDA", 7: "DL_ECANCELED", 8: "DL_ENOMEM_ADMIT",
+                9: "DL_EFAILED", 10: "DL_EUNSUPPORTED"}
+DL_METRIC_L2 = 0
+DL_PREC_AUTO, DL_PREC_BF16, DL_PREC_FP8E4M3, DL_PREC_FP32, DL_PREC_FP32_PLAIN = range(5)
+PRECISIONS = {"auto": 0, "bf16": 1, "fp8": 2, "fp32": 3, "fp32_plain": 4}
+DL_MEM_HOST, DL_MEM_DEVICE = 0, 1
+DL_SELF_UPPER, DL_SELF_FULL = 0, 1
+
+# Every function include/dl.h declares (checked by the CPU test suite).
+EXPORTS = [
+    "dl_join_opts_default", "dl_store_create", "dl_store_destroy", "dl_store_shape",
+    "dl_sim_join", "dl_topk_join", "dl_result_count", "dl_result_pairs", "dl_result_topk",
+    "dl_result_stats", "dl_result_free", "dl_last_error", "dl_version", "dl_kernel_launches",
+]
+
+
+class DLError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class dl_join_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("self_mode", ctypes.c_int32),
+                ("out_capacity", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
+                ("tile_n", ctypes.c_int32), ("timing", ctypes.c_int32)]
+
+
+class dl_join_stats(ctypes.Structure):
+    _fields_ = [("pairs_evaluated", ctypes.c_int64), ("pairs_out", ctypes.c_int64),
+                ("band_pairs", ctypes.c_int64), ("fp64_pairs", ctypes.c_int64),
+                ("reruns", ctypes.c_int64), ("precision", ctypes.c_int32), ("tile_n", ctypes.c_int32),
+                ("ms_main", ctypes.c_float), ("ms_recheck", ctypes.c_float), ("ms_total", ctypes.c_float),
+                ("kernels_launched", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return LIB_PATH
+
+
+def load(path: str | None = None):
+    """Load the C-ABI library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run paper_1812_07607_gb300.build)")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    L.dl_join_opts_default.argtypes = [ctypes.POINTER(dl_join_opts)]
+    L.dl_join_opts_default.restype = None
+    L.dl_store_create.argtypes = [pp, vp, vp, i64, i32, i32, vp]
+    L.dl_store_destroy.argtypes = [vp]
+    L.dl_store_shape.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)]
+    L.dl_sim_join.argtypes = [vp, vp, i32, f64, ctypes.POINTER(dl_join_opts), pp]
+    L.dl_topk_join.argtypes = [vp, vp, i32, i32, ctypes.POINTER(dl_join_opts), pp]
+    L.dl_result_count.argtypes = [vp, ctypes.POINTER(i64)]
+    L.dl_result_pairs.argtypes = [vp, i32, pp, pp, ctypes.POINTER(i64)]
+    L.dl_result_topk.argtypes = [vp, i32, pp, pp, ctypes.POINTER(i32), ctypes.POINTER(i64)]
+    L.dl_result_stats.argtypes = [vp, ctypes.POINTER(dl_join_stats)]
+    L.dl_result_free.argtypes = [vp]
+    L.dl_last_error.restype = ctypes.c_char_p
+    L.dl_version.restype = ctypes.c_char_p
+    L.dl_kernel_launches.restype = i64
+    for name in ("dl_store_create", "dl_store_destroy", "dl_store_shape", "dl_sim_join", "dl_topk_join",
+                 "dl_result_count", "dl_result_pairs", "dl_result_topk", "dl_result_stats",
+                 "dl_result_free"):
+        getattr(L, name).restype = ctypes.c_int
+    if path == LIB_PATH:
+        _lib = L
+    return L
+
+
+def _check(rc: int, what: str):
+    if rc != DL_OK:
+        msg = load().dl_last_error().decode(errors="replace")
+        raise DLError(rc, f"{what}: {msg}")
+
+
+def last_error() -> str:
+    return load().dl_last_error().decode(errors="replace")
+
+
+def kernel_launches() -> int:
+    return int(load().dl_kernel_launches())
+
+
+def version() -> str:
+    return load().dl_version().decode()
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class _DevView:
+    """Expose a library-owned device buffer to torch through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, n: int, typestr: str, owner):
+        self._owner = owner
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
+                                         "version": 2, "strides": None}
+
+
+class Store:
+    """A device-resident patch store (ids + float32 features), see dl_store_create."""
+
+    def __init__(self, ids, feats, stream=None):
+        L = load()
+        h = ctypes.c_void_p()
+        if hasattr(feats, "data_ptr"):   # torch tensor: device, or (pinned) host memory
+            import torch
+            feats = feats.contiguous().to(torch.float32)
+            ids = ids.contiguous().to(device=feats.device, dtype=torch.int64)
+            n, d = feats.shape
+            where = DL_MEM_DEVICE if feats.is_cuda else DL_MEM_HOST
+            st = _stream_handle(stream)
+            rc = L.dl_store_create(ctypes.byref(h), ids.data_ptr(), feats.data_ptr(), n, d, where, st)
+        else:
+            feats = np.ascontiguousarray(feats, dtype=np.float32)
+            ids = np.ascontiguousarray(ids, dtype=np.int64)
+            n, d = feats.shape
+            st = 0 if stream is None else _stream_handle(stream)
+            rc = L.dl_store_create(ctypes.byref(h), ids.ctypes.data, feats.ctypes.data, n, d, DL_MEM_HOST, st)
+        _check(rc, "dl_store_create")
+        self._h = h
+        self.n, self.d = int(n), int(d)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().dl_store_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _is_torch_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(getattr(x, "is_cuda"))
+
+
+class Result:
+    """A join result owned by the library (dl_result)."""
+
+    def __init__(self, h):
+        self._h = h
+
+    def count(self) -> int:
+        n = ctypes.c_int64()
+        _check(load().dl_result_count(self._h, ctypes.byref(n)), "dl_result_count")
+        return int(n.value)
+
+    def stats(self) -> dict:
+        st = dl_join_stats()
+        _check(load().dl_result_stats(self._h, ctypes.byref(st)), "dl_result_stats")
+        return {f: getattr(st, f) for f, _ in dl_join_stats._fields_}
+
+    def pairs_host(self):
+        """(r_ids, s_ids) as int64 numpy arrays (copied out of the result)."""
+        a, b, n = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int64()
+        _check(load().dl_result_pairs(self._h, DL_MEM_HOST, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)),
+               "dl_result_pairs")
+        n = int(n.value)
+        if n == 0:
+            return np.empty(0, np.int64), np.empty(0, np.int64)
+        ra = np.ctypeslib.as_array(ctypes.cast(a, ctypes.POINTER(ctypes.c_int64)), shape=(n,)).copy()
+        sa = np.ctypeslib.as_array(ctypes.cast(b, ctypes.POINTER(ctypes.c_int64)), shape=(n,)).copy()
+        return ra, sa
+
+    def pairs_device(self):
+        """(r_ids, s_ids) as torch int64 CUDA tensors viewing the result's memory."""
+        import torch
+        a, b, n = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int64()
+        _check(load().dl_result_pairs(self._h, DL_MEM_DEVICE, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)),
+               "dl_result_pairs")
+        n = int(n.value)
+        if n == 0:
+            return (torch.empty(0, dtype=torch.int64, device="cuda"),) * 2
+        return (torch.as_tensor(_DevView(a.value, n, "<i8", self), device="cuda"),
+                torch.as_tensor(_DevView(b.value, n, "<i8", self), device="cuda"))
+
+    def topk_host(self):
+        """(ids [nq, k] int64, dist2 [nq, k] float64) numpy copies."""
+        a, b = ctypes.c_void_p(), ctypes.c_void_p()
+        k, nq = ctypes.c_int32(), ctypes.c_int64()
+        _check(load().dl_result_topk(self._h, DL_MEM_HOST, ctypes.byref(a), ctypes.byref(b), ctypes.byref(k),
+                                     ctypes.byref(nq)), "dl_result_topk")
+        k, nq = int(k.value), int(nq.value)
+        if k * nq == 0:
+            return np.empty((nq, k), np.int64), np.empty((nq, k), np.float64)
+        ids = np.ctypeslib.as_array(ctypes.cast(a, ctypes.POINTER(ctypes.c_int64)), shape=(nq, k)).copy()
+        d2 = np.ctypeslib.as_array(ctypes.cast(b, ctypes.POINTER(ctypes.c_double)), shape=(nq, k)).copy()
+        return ids, d2
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().dl_result_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def make_opts(precision="auto", self_mode="upper", out_capacity=0, stream=None, tile_n=0, timing=False):
+    o = dl_join_opts()
+    load().dl_join_opts_default(ctypes.byref(o))
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.self_mode = DL_SELF_FULL if self_mode == "full" else DL_SELF_UPPER
+    o.out_capacity = int(out_capacity)
+    o.cuda_stream = _stream_handle(stream)
+    o.tile_n = int(tile_n)
+    o.timing = 1 if timing else 0
+    return o
+
+
+def sim_join(R: Store, S: Store | None, eps: float, precision="auto", self_mode="upper", out_capacity=0,
+             stream=None, tile_n=0, timing=False, allow_overflow=False) -> Result:
+    """dl_sim_join: every pair with canonical squared L2 distance <= eps^2."""
+    o = make_opts(precision, self_mode, out_capacity, stream, tile_n, timing)
+    h = ctypes.c_void_p()
+    rc = load().dl_sim_join(R.handle, None if S is None else S.handle, DL_METRIC_L2, float(eps),
+                            ctypes.byref(o), ctypes.byref(h))
+    if rc == DL_EOVERFLOW and allow_overflow:
+        return Result(h)
+    if h.value and rc != DL_OK:
+        Result(h).free()
+    _check(rc, "dl_sim_join")
+    return Result(h)
+
+
+def topk_join(Q: Store, S: Store, k: int, precision="auto", stream=None, timing=False) -> Result:
+    """dl_topk_join: the k nearest store rows of every query row, by (canonical D, row)."""
+    o = make_opts(precision, "upper", 0, stream, 0, timing)
+    h = ctypes.c_void_p()
+    rc = load().dl_topk_join(Q.handle, S.handle, DL_METRIC_L2, int(k), ctypes.byref(o), ctypes.byref(h))
+    _check(rc, "dl_topk_join")
+    return Result(h)

@@ -1,0 +1,244 @@
+"""Parity of the CUDA epsilon-join (through the C ABI) with the FP64 CPU oracle.
+
+The bar is exact set equality: every path except the plain-FP32 baseline must
+return exactly the pairs the canonical FP64 nested loop returns, for every
+shape, ragged tail, self-join mode and adversarial threshold below.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1812_07607_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+EXACT = ("bf16", "fp32")
+
+
+@pytest.fixture(scope="module")
+def dl():
+    import torch
+    from paper_1812_07607_gb300 import build as B, dl as D
+    assert torch.cuda.is_available()
+    B.build()
+    D.load()
+    return D
+
+
+@pytest.fixture(scope="module")
+def orc():
+    return oracle.default()
+
+
+def _store(dl, ids, X):
+    import torch
+    return dl.Store(torch.from_numpy(np.ascontiguousarray(ids)).cuda(),
+                    torch.from_numpy(np.ascontiguousarray(X)).cuda())
+
+
+def _ids(n, off=0):
+    return (np.arange(n, dtype=np.int64) * 3 + 11 + off)
+
+
+def gpu_pairs(dl, R, S, eps, prec, self_mode="upper", rid=None, sid=None, **kw):
+    rid = _ids(R.shape[0]) if rid is None else rid
+    Rs = _store(dl, rid, R)
+    if S is None:
+        Ss, sid = None, rid
+    else:
+        sid = _ids(S.shape[0], 1 << 40) if sid is None else sid
+        Ss = _store(dl, sid, S)
+    res = dl.sim_join(Rs, Ss, eps, precision=prec, self_mode=self_mode, **kw)
+    r, s = res.pairs_host()
+    st = res.stats()
+    res.free()
+    pairs = list(zip(r.tolist(), s.tolist()))
+    assert len(set(pairs)) == len(pairs), "duplicate pair in output"
+    return set(pairs), st, rid, sid
+
+
+def oracle_pairs(orc, R, S, eps, mode, rid, sid):
+    p = orc.join(R, S, eps, mode)
+    return set(zip(rid[p[:, 0]].tolist(), sid[p[:, 1]].tolist()))
+
+
+def check(dl, orc, R, S, eps, self_mode="upper", precs=EXACT, **kw):
+    mode = oracle.MODE_RXS if S is not None else (oracle.MODE_SELF_FULL if self_mode == "full"
+                                                  else oracle.MODE_SELF_UPPER)
+    want = None
+    for prec in precs:
+        got, st, rid, sid = gpu_pairs(dl, R, S, eps, prec, self_mode, **kw)
+        if want is None:
+            want = oracle_pairs(orc, R, S, eps, mode, rid, sid)
+        assert got == want, (f"{prec}: {len(got - want)} extra, {len(want - got)} missing "
+                             f"of {len(want)}; stats={st}")
+    return want
+
+
+def test_rxs_histograms_2k_exact(dl, orc):
+    """2,000 x 2,000 Dirichlet(0.5) d=64 histograms at the calibrated 0.1% selectivity."""
+    wl = W.rxs_histograms_2k()
+    want = check(dl, orc, wl.R, wl.S, wl.eps, rid=wl.r_ids, sid=wl.s_ids)
+    assert 3000 < len(want) < 5000
+
+
+def test_plain_fp32_baseline_is_close(dl, orc):
+    """The plain FP32 join is the throughput baseline; it may differ only at the boundary."""
+    wl = W.rxs_histograms_2k()
+    got, _, rid, sid = gpu_pairs(dl, wl.R, wl.S, wl.eps, "fp32_plain", rid=wl.r_ids, sid=wl.s_ids)
+    want = oracle_pairs(orc, wl.R, wl.S, wl.eps, oracle.MODE_RXS, rid, sid)
+    assert len(got ^ want) <= max(4, len(want) // 1000)
+
+
+@pytest.mark.parametrize("nR,nS,d", [
+    (1, 1, 1), (1, 300, 7), (127, 129, 16), (129, 255, 63), (300, 257, 64), (257, 700, 65),
+    (513, 300, 128), (200, 1000, 200), (130, 390, 512), (64, 64, 1000),
+])
+def test_ragged_shapes(dl, orc, nR, nS, d):
+    g = W.rng(1000 + nR + 7 * nS + 13 * d)
+    R = W.dirichlet_histograms(g, nR, d)
+    S = W.dirichlet_histograms(g, nS, d)
+    D = orc.dist_block(R, S)
+    eps = math.sqrt(float(np.quantile(D, 0.02)))
+    precs = EXACT if d <= 512 else ("fp32", "auto")
+    check(dl, orc, R, S, eps, precs=precs)
+
+
+@pytest.mark.parametrize("n", [1, 2, 129, 257, 1500])
+@pytest.mark.parametrize("self_mode", ["upper", "full"])
+def test_self_join_modes(dl, orc, n, self_mode):
+    g = W.rng(2000 + n)
+    X, _ = W.clustered_histograms(g, n, 96, max(1, n // 8), 0.01)
+    eps = 0.12
+    check(dl, orc, X, None, eps, self_mode=self_mode)
+
+
+def test_eps_zero_duplicates_and_inf(dl, orc):
+    g = W.rng(31)
+    R = W.grid_points(g, 300, 40, levels=3, dup_frac=0.3)
+    S = np.concatenate([R[::3], W.grid_points(g, 100, 40, levels=3)])
+    want = check(dl, orc, R, S, 0.0)
+    assert len(want) >= 100
+    check(dl, orc, R[:150], S[:120], math.inf)
+    check(dl, orc, R, None, 0.0, self_mode="full")
+
+
+def test_boundary_inclusive_exact_grid(dl, orc):
+    """eps^2 lands exactly on realised grid distances: the inclusive predicate keeps them."""
+    g = W.rng(32)
+    R = W.grid_points(g, 400, 24, levels=4)
+    S = W.grid_points(g, 333, 24, levels=4)
+    for m in (9, 16, 25, 36):            # D = m/64 exactly, eps = sqrt(m)/8 exactly
+        eps = math.sqrt(m) / 8.0
+        want = check(dl, orc, R, S, eps)
+        assert want
+
+
+def test_adversarial_band_near_ulp(dl, orc):
+    """Thresholds 1-4 ulps either side of realised canonical distances force the FP64 step."""
+    g = W.rng(33)
+    d = 128
+    R = W.dirichlet_histograms(g, 200, d)
+    S = np.concatenate([R + g.normal(0, 2e-4, size=R.shape).astype(np.float32),
+                        W.dirichlet_histograms(g, 100, d)]).astype(np.float32)
+    D = orc.dist_block(R, S)
+    targets = np.sort(D.ravel())[[50, 300, 1000, 2000]]
+    for t in targets:
+        base = math.sqrt(float(t))
+        for step in (-4, -1, 0, 1, 4):
+            eps = base
+            for _ in range(abs(step)):
+                eps = float(np.nextafter(eps, math.inf if step > 0 else 0.0))
+            check(dl, orc, R, S, eps)
+
+
+def test_mixed_magnitudes(dl, orc):
+    g = W.rng(34)
+    R = W.mixed_magnitude_rows(g, 150, 32)
+    S = np.concatenate([R[:40] * np.float32(1.0000001), W.mixed_magnitude_rows(g, 90, 32)])
+    D = orc.dist_block(R, S)
+    for q in (0.001, 0.05):
+        check(dl, orc, R, S, math.sqrt(float(np.quantile(D, q))))
+
+
+def test_fixed_capacity_overflow_then_retry(dl, orc):
+    wl = W.rxs_histograms_2k(n=600)
+    Rs = _store(dl, wl.r_ids[:600], wl.R)
+    Ss = _store(dl, wl.s_ids[:600], wl.S)
+    eps = 0.25
+    res = dl.sim_join(Rs, Ss, eps, out_capacity=10, allow_overflow=True)
+    need = res.count()
+    res.free()
+    assert need > 10
+    with pytest.raises(dl.DLError) as ei:
+        dl.sim_join(Rs, Ss, eps, out_capacity=10)
+    assert ei.value.status == dl.DL_EOVERFLOW
+    res = dl.sim_join(Rs, Ss, eps, out_capacity=need)
+    assert res.count() == need
+    res.free()
+
+
+def test_invalid_arguments(dl):
+    import torch
+    X = torch.rand(10, 8, device="cuda")
+    ids = torch.arange(10, device="cuda")
+    S = dl.Store(ids, X)
+    with pytest.raises(dl.DLError) as ei:
+        dl.sim_join(S, None, -1.0)
+    assert ei.value.status == dl.DL_EINVAL
+    with pytest.raises(dl.DLError) as ei:
+        dl.sim_join(S, None, float("nan"))
+    assert ei.value.status == dl.DL_EINVAL
+    bad = X.clone()
+    bad[3, 2] = float("inf")
+    with pytest.raises(dl.DLError) as ei:
+        dl.Store(ids, bad)
+    assert ei.value.status == dl.DL_EINVAL
+    T = dl.Store(ids, torch.rand(10, 9, device="cuda"))
+    with pytest.raises(dl.DLError) as ei:
+        dl.sim_join(S, T, 0.1)
+    assert ei.value.status == dl.DL_EINVAL
+
+
+def test_empty_store(dl):
+    import torch
+    E = dl.Store(torch.empty(0, dtype=torch.int64, device="cuda"), torch.empty(0, 16, device="cuda"))
+    X = dl.Store(torch.arange(5, device="cuda"), torch.rand(5, 16, device="cuda"))
+    for a, b in ((E, X), (X, E), (E, None)):
+        res = dl.sim_join(a, b, 1.0)
+        assert res.count() == 0
+        res.free()
+
+
+def test_self_clustered_262k_full_size_sampled(dl, orc):
+    """The bench workload at full size: BF16 and exact-FP32 sets agree; sampled rows match the oracle."""
+    wl = W.self_clustered_262k()
+    rid = wl.r_ids
+    Rs = _store(dl, rid, wl.R)
+    res = dl.sim_join(Rs, None, wl.eps, precision="bf16")
+    r, s = res.pairs_host()
+    st = res.stats()
+    res.free()
+    res2 = dl.sim_join(Rs, None, wl.eps, precision="fp32")
+    r2, s2 = res2.pairs_host()
+    res2.free()
+    a = set(zip(r.tolist(), s.tolist()))
+    b = set(zip(r2.tolist(), s2.tolist()))
+    assert len(a) == len(r) and a == b, (len(a ^ b), st)
+    assert 1_500_000 < len(a) < 4_000_000, st
+    # sampled rows: every pair touching a sampled row, against the oracle
+    g = W.rng(77)
+    rows = np.sort(g.choice(wl.R.shape[0], size=24, replace=False))
+    e2 = wl.eps * wl.eps
+    for i in rows.tolist():
+        D = orc.dist_block(wl.R[i:i + 1], wl.R)[0]
+        want = {int(rid[j]) for j in np.nonzero(D <= e2)[0].tolist() if j != i}
+        got = set(s[r == rid[i]].tolist()) | set(r[s == rid[i]].tolist())
+        assert got == want, (i, len(got ^ want))
+    # unordered pairs come out as (lower row, higher row)
+    pos = np.empty(rid.max() + 1, dtype=np.int64)
+    pos[rid] = np.arange(rid.shape[0])
+    assert (pos[r] < pos[s]).all()
