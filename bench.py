@@ -1,0 +1,351 @@
+"""Benchmark: exact epsilon-join throughput (Gpairs/s) on one or more GB300s.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (default): self-join of 262,144 patches with d=128 colour-histogram
+features (8,192 Dirichlet(0.5) centroids + N(0, 0.01^2) jitter, clipped and
+renormalised; eps calibrated for ~20 matches per patch), synthetic and seeded.
+A step is one dl_sim_join call on the resident store -- the tensor-core pass,
+the exact recheck of the band pairs and the id-pair write-out -- and the metric
+is the N(N-1)/2 pairs it is defined over divided by the step time.
+
+Rank 0 prints one JSON line. With N > 1 (torchrun), every rank joins its own
+replica of the workload (the join has no cross-rank exchange) and the value is
+all ranks' pairs over the slowest rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "exact eps-join pair-distances/sec"
+UNIT = "Gpairs/s"
+L2_FLUSH_BYTES = 512 << 20      # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle sample")
+    ap.add_argument("--no-baselines", action="store_true", help="skip the plain-FP32 and CPU legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return {"bf16_tflops": j.get("bf16_tflops"), "bf16_tflops_sustained": j.get("bf16_tflops_sustained"),
+                "hbm_gbs": j.get("hbm_gbs"), "source": "measured"}
+    return {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [r.split(", ") for r in self.tmp.read().strip().splitlines() if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip() == "Active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_workload(rank: int):
+    from paper_1812_07607_gb300 import workloads as W
+    return W.self_clustered_262k()
+
+
+def traffic_record():
+    """DRAM bytes per launch of the join kernel from the committed ncu summary, if still current."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "tc_join_kernel_self_clustered_262k.json")
+    src = os.path.join(ROOT, "paper_1812_07607_gb300", "csrc", "join_tc.cu")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return rec.get("dram_bytes_per_launch") if rec.get("join_tc_sha256") == h else None
+
+
+def cpu_oracle_rate(wl, budget_s: float):
+    """Pairs/s of the FP64 CPU oracle (single thread) on a bounded sample of the workload."""
+    import oracle
+    orc = oracle.default()
+    R = wl.R
+    n = R.shape[0]
+    eps = wl.eps
+    t0 = time.perf_counter()
+    orc.join(R[:4], R, eps, oracle.MODE_RXS)
+    dt = time.perf_counter() - t0
+    per_row = max(dt / 4, 1e-6)
+    rows = int(max(4, min(n, budget_s / per_row)))
+    t0 = time.perf_counter()
+    orc.join(R[4:4 + rows], R, eps, oracle.MODE_RXS)
+    dt = time.perf_counter() - t0
+    pairs = rows * n
+    return pairs / dt / 1e9, {"rows": rows, "pairs": pairs, "seconds": round(dt, 3)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = load_workload(0)
+    import oracle
+    orc = oracle.default()
+    n = wl.R.shape[0]
+    t0 = time.perf_counter()
+    orc.join(wl.R[:2], wl.R, wl.eps, oracle.MODE_RXS)
+    per_row = (time.perf_counter() - t0) / 2
+    step_budget = max(0.5, min(6.0, 150.0 / max(1, args.steps + args.warmup)))
+    rows = int(max(1, min(n, step_budget / per_row)))
+    times = []
+    for i in range(args.warmup + args.steps):
+        r0 = (i * rows) % max(1, n - rows)
+        t0 = time.perf_counter()
+        orc.join(wl.R[r0:r0 + rows], wl.R, wl.eps, oracle.MODE_RXS)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    pairs = rows * n
+    value = pairs * len(times) / sum(times) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "self_clustered_262k", "n": n, "d": wl.d, "eps": wl.eps,
+                   "step_sample": f"{rows} rows x {n} rows"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{rows} query rows x all {n} rows per step, FP64 nested loop, 1 thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1812_07607_gb300 import build as B
+    B.build()
+    from paper_1812_07607_gb300 import dl
+
+    wl = load_workload(rank)
+    n, d = wl.R.shape
+    P = wl.pairs
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    feats = torch.from_numpy(wl.R).to(dev)
+    ids = torch.from_numpy(wl.r_ids).to(dev)
+    store = dl.Store(ids, feats)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as tdist
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    def one_step(timing=True):
+        res = dl.sim_join(store, None, wl.eps, precision=args.precision, stream=stream, timing=timing)
+        st = res.stats()
+        res.free()
+        return st
+
+    for _ in range(args.warmup):
+        one_step()
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = dl.kernel_launches()
+    step_ms, main_ms, stats = [], [], None
+    barrier()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats = one_step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        main_ms.append(stats["ms_main"])
+    barrier()
+    launches = dl.kernel_launches() - launches0
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    if ws > 1:
+        import torch.distributed as tdist
+        t = torch.tensor([total_ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * P * args.steps / (total_ms / 1e3) / 1e9
+
+    # ---- end to end through the C ABI from pinned host memory (store upload + join + pair download)
+    h_feats = torch.from_numpy(wl.R).pin_memory()
+    h_ids = torch.from_numpy(wl.r_ids).pin_memory()
+    e2e_ms = []
+    d2h = 0
+    for i in range(2 + max(3, args.steps // 4)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = dl.Store(h_ids, h_feats, stream=stream)
+        res = dl.sim_join(s2, None, wl.eps, precision=args.precision, stream=stream)
+        r_ids, s_ids = res.pairs_host()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) * 1e3
+        d2h = r_ids.nbytes + s_ids.nbytes + 32
+        res.free()
+        s2.close()
+        if i >= 2:
+            e2e_ms.append(dt)
+    e2e_value = P / (statistics.median(e2e_ms) / 1e3) / 1e9
+    h2d = h_feats.numel() * 4 + h_ids.numel() * 8
+
+    # ---- plain FP32 SIMT join on the same GPU (the comparison baseline; not exact)
+    plain = None
+    if not args.no_baselines:
+        one = lambda: dl.sim_join(store, None, wl.eps, precision="fp32_plain", stream=stream, timing=True)
+        r = one()
+        r.free()
+        pm = []
+        for _ in range(3):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = one()
+            e1.record(stream)
+            e1.synchronize()
+            pm.append(e0.elapsed_time(e1))
+            r.free()
+        plain = {"value": P / (statistics.median(pm) / 1e3) / 1e9, "unit": UNIT,
+                 "ms_per_step": statistics.median(pm), "kernel": "k8_simt_join (FP32 FMA, inexact at eps)"}
+
+    pk = peaks()
+    flops = 2.0 * d * P
+    kern_ms = statistics.median(main_ms)
+    achieved = flops / (kern_ms / 1e3) / 1e12
+    roof = {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+            "frac": achieved / pk["bf16_tflops"], "traffic": traffic_record(),
+            "kernel": "tc_join_kernel<256>", "kernel_ms": kern_ms,
+            "peak_kind": f"bf16 dense burst ({pk['source']})",
+            "algorithmic": f"2*d flops/pair x {P} pairs = {flops:.4g} flops per launch"}
+
+    cpu = None
+    if rank == 0 and not args.no_baselines:
+        v, info = cpu_oracle_rate(wl, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{info['rows']} query rows x all {n} rows ({info['pairs']} pairs, {info['seconds']} s), "
+                         f"FP64 nested loop, 1 thread"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "self_clustered_262k", "n": n, "d": d, "eps": wl.eps, "pairs_per_step": P,
+                       "mode": "self-join, unordered pairs", "precision": args.precision,
+                       "pairs_out": stats["pairs_out"], "band_pairs": stats["band_pairs"],
+                       "fp64_pairs": stats["fp64_pairs"], "tile_n": stats["tile_n"],
+                       "l2": "512 MiB memset between timed steps (outside the events)",
+                       "parallelism": f"replicas x{ws}"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "ms_per_step": statistics.median(e2e_ms)},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "plain_fp32_gpu": plain,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    store.close()
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

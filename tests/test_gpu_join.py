@@ -130,11 +130,15 @@ def test_boundary_inclusive_exact_grid(dl, orc):
     """eps^2 lands exactly on realised grid distances: the inclusive predicate keeps them."""
     g = W.rng(32)
     R = W.grid_points(g, 400, 24, levels=4)
-    S = W.grid_points(g, 333, 24, levels=4)
-    for m in (9, 16, 25, 36):            # D = m/64 exactly, eps = sqrt(m)/8 exactly
+    # S: grid neighbours of R rows (a few coordinates moved by whole steps of 1/8)
+    base = R[g.integers(0, 400, size=333)]
+    step = g.integers(-3, 4, size=base.shape) * (g.uniform(size=base.shape) < 0.15)
+    S = (base + step.astype(np.float32) / 8.0).astype(np.float32)
+    for m in (1, 4, 9, 16, 25):            # D = m/64 exactly, eps = sqrt(m)/8 exactly
         eps = math.sqrt(m) / 8.0
         want = check(dl, orc, R, S, eps)
-        assert want
+        D = orc.dist_block(R, S)
+        assert (D == m / 64.0).any() and len(want) == int((D <= m / 64.0).sum())
 
 
 def test_adversarial_band_near_ulp(dl, orc):
