@@ -139,6 +139,32 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
 int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric, int32_t k,
                  const dl_join_opts *opts, dl_result **out);
 
+/*
+ * Exact epsilon-join that allocates nothing (no counterpart in the paper; it
+ * exists for callers that cannot allocate device memory when they join, e.g.
+ * code running under a memory planner that owns the whole device or a
+ * real-time loop that must not enter the allocator).
+ * All pointers are DEVICE memory owned by the caller: R [nR][d] float32 and
+ * r_ids [nR]; S [nS][d] and s_ids [nS], or S == NULL for a self-join of R in
+ * `self_mode`; out_r / out_s receive up to out_cap id pairs. *n_out (host)
+ * receives the number of matching pairs. The result is the same set
+ * dl_sim_join returns (exact FP32 path: FP32 distances with an error bound,
+ * FP64 recheck of the undecided pairs).
+ * Working memory is a 512 KiB static device array in the library, held by every
+ * GPU that loads it until exit; it holds at most 65,536 pairs inside the FP32
+ * error band of eps^2. A call that needs more returns DL_EOVERFLOW (outputs
+ * incomplete); more than out_cap matches also returns DL_EOVERFLOW with the
+ * required count in *n_out. The first call on each device looks up the
+ * array's device address, so make that first call before any stream capture.
+ * Every call shares the one array: calls whose work overlaps on the GPU
+ * (other streams, other host threads) race and must not be issued. The call
+ * synchronises `cuda_stream`.
+ */
+int dl_sim_join_noalloc(const float *R, const int64_t *r_ids, int64_t nR, const float *S,
+                        const int64_t *s_ids, int64_t nS, int32_t d, double eps, int32_t self_mode,
+                        int64_t *out_r, int64_t *out_s, int64_t out_cap, int64_t *n_out,
+                        void *cuda_stream);
+
 /* ---------------------------------------------------------------------------------
  * Results.
  * ------------------------------------------------------------------------------- */

@@ -32,6 +32,7 @@ EXPORTS = [
     "dl_join_opts_default", "dl_store_create", "dl_store_destroy", "dl_store_shape",
     "dl_sim_join", "dl_topk_join", "dl_result_count", "dl_result_pairs", "dl_result_topk",
     "dl_result_stats", "dl_result_free", "dl_last_error", "dl_version", "dl_kernel_launches",
+    "dl_sim_join_noalloc",
 ]
 
 
@@ -85,6 +86,9 @@ def load(path: str | None = None):
     L.dl_result_topk.argtypes = [vp, i32, pp, pp, ctypes.POINTER(i32), ctypes.POINTER(i64)]
     L.dl_result_stats.argtypes = [vp, ctypes.POINTER(dl_join_stats)]
     L.dl_result_free.argtypes = [vp]
+    L.dl_sim_join_noalloc.argtypes = [vp, vp, i64, vp, vp, i64, i32, f64, i32, vp, vp, i64,
+                                      ctypes.POINTER(i64), vp]
+    L.dl_sim_join_noalloc.restype = ctypes.c_int
     L.dl_last_error.restype = ctypes.c_char_p
     L.dl_version.restype = ctypes.c_char_p
     L.dl_kernel_launches.restype = i64
