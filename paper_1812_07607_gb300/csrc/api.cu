@@ -224,7 +224,7 @@ static int run_pass(const PassCfg &c, PassOut *po)
                 L.p.nR = (int)nR;
                 L.p.nS = (int)nS;
                 L.p.kc = R->dp / 64;
-                L.p.stages = tc_pick_stages(c.BN, R->dp / 64);
+                tc_plan(c.BN, R->dp / 64, &L.p.stages, &L.p.a_slots);
                 L.p.upper = c.self ? 1 : 0;
                 L.p.rowpar = rowpar;
                 L.p.beta = S->beta;

@@ -10,16 +10,19 @@
 // recheck kernel settles exactly.
 //
 // Per CTA (persistent, one per SM, 192 threads, warp-specialised):
-//   warp 0      TMA producer: the 128-row R tile (all d/64 K-chunks) stays
-//               resident for a unit; S tiles stream through a ring of stages,
-//               one 64-column K-chunk of BN rows per stage (128-byte swizzle).
+//   warp 0      TMA producer: the 128-row R tile (all d/64 K-chunks) is loaded
+//               once per unit into one of one or two A slots; S tiles stream
+//               through a ring of stages, one 64-column K-chunk of BN rows per
+//               stage (128-byte swizzle).
 //   warp 1      MMA issuer: 4 x tcgen05.mma (K=16 each) per stage into one of two
 //               TMEM accumulators (128 lanes x BN FP32 columns each), then
 //               tcgen05.commit to free the stage / publish the accumulator.
-//   warps 2-5   epilogue: tcgen05.ld 32 columns at a time, h = A - beta_x,
-//               a running max against the row's reject threshold (2 FP32 ops
-//               per pair), and only for the rare chunks that pass, the exact
-//               accept/band classification with warp-aggregated output.
+//   warps 2-5   epilogue: tcgen05.ld 64 columns at a time (double-buffered),
+//               h = A - beta_x with packed FP32 adds against -beta staged in
+//               shared memory one tile ahead, a max tree against the row's
+//               reject threshold (about 1.5 issue slots per pair), and only for
+//               the chunks that pass, the exact accept/band classification
+//               into bit masks and warp-aggregated output.
 // A unit is (R tile m, S tiles [nb, ne)); units are handed out round-robin.
 #include <cuda.h>
 
@@ -27,8 +30,6 @@
 #include "ptx.cuh"
 
 namespace dl {
-
-
 
 __device__ __forceinline__ bool mbar_wait_plain(uint64_t *bar, uint32_t parity)
 {
@@ -38,6 +39,75 @@ __device__ __forceinline__ bool mbar_wait_plain(uint64_t *bar, uint32_t parity)
     return true;
 }
 
+// Walks this CTA's (unit, S tile) sequence.
+struct TileIter {
+    int u, n;
+    int4 un;
+    bool valid;
+    __device__ __forceinline__ void start(const TcParams &p)
+    {
+        u = blockIdx.x;
+        valid = u < p.n_units;
+        if (valid) {
+            un = p.units[u];
+            n = un.y;
+        }
+    }
+    __device__ __forceinline__ void next(const TcParams &p)
+    {
+        if (!valid) return;
+        if (++n == un.z) {
+            u += gridDim.x;
+            valid = u < p.n_units;
+            if (valid) {
+                un = p.units[u];
+                n = un.y;
+            }
+        }
+    }
+};
+
+// Classify the 32 pairs (r, col0 + j) of one sub-chunk whose values h[j] are
+// known; emit proven matches and band pairs (warp-collective).
+__device__ __forceinline__ void classify_emit(const TcParams &p, const float (&h)[32], int r, int col0,
+                                              float tau_acc, float tau_rej)
+{
+    uint32_t am = 0, bm = 0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const bool a = h[j] >= tau_acc;
+        const bool b = !a && (h[j] >= tau_rej);
+        am |= (a ? 1u : 0u) << j;
+        bm |= (b ? 1u : 0u) << j;
+    }
+    uint32_t vm = 0xffffffffu;
+    const int rem = p.nS - col0;
+    if (rem < 32) vm = rem <= 0 ? 0u : ((1u << rem) - 1u);
+    if (p.upper) {
+        const int k = r - col0;   // columns j <= k are not pairs (need c > r)
+        if (k >= 31)
+            vm = 0u;
+        else if (k >= 0)
+            vm &= ~((2u << k) - 1u);
+    }
+    if (r >= p.nR) vm = 0u;
+    am &= vm;
+    bm &= vm;
+    while (__any_sync(0xffffffffu, (am | bm) != 0u)) {
+        const bool has_a = am != 0u;
+        const bool has_b = !has_a && bm != 0u;
+        int j = 0;
+        if (has_a) {
+            j = __ffs(am) - 1;
+            am &= am - 1u;
+        } else if (has_b) {
+            j = __ffs(bm) - 1;
+            bm &= bm - 1u;
+        }
+        warp_emit(p.out, has_a, has_b, r, col0 + j);
+    }
+}
+
 template <int BN>
 __global__ void __launch_bounds__(192, 1)
     tc_join_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -45,36 +115,40 @@ __global__ void __launch_bounds__(192, 1)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int kc = p.kc, stages = p.stages;
-    uint8_t *sA = smem;                       // kc x [128 rows x 128 B]
-    uint8_t *sB = smem + kc * 16384;          // stages x [BN rows x 128 B]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + stages * BN * 128);
+    const int kc = p.kc, stages = p.stages, a_slots = p.a_slots;
+    constexpr uint32_t kStageBytes = BN * 128;
+    constexpr uint32_t kTmemCols = 2 * BN;
+    constexpr int kSub = BN / 32;            // 32-column sub-chunks per tile
+    const uint32_t a_bytes = (uint32_t)kc * 16384;
+    uint8_t *sA = smem;                                    // a_slots x kc x [128 rows x 128 B]
+    uint8_t *sB = smem + a_slots * a_bytes;                // stages x [BN rows x 128 B]
+    float *s_nbeta = reinterpret_cast<float *>(sB + stages * kStageBytes);   // 2 x BN: -beta of a tile
+    float4 *s_cst = reinterpret_cast<float4 *>(s_nbeta + 2 * BN);           // 2 x kSub chunk stats
+    uint64_t *bars = reinterpret_cast<uint64_t *>(s_cst + 2 * kSub);
     uint64_t *full = bars;                    // [8]
     uint64_t *empty = bars + 8;               // [8]
-    uint64_t *a_full = bars + 16;
-    uint64_t *a_empty = bars + 17;
-    uint64_t *acc_full = bars + 18;           // [2]
-    uint64_t *acc_empty = bars + 20;          // [2]
-    uint64_t *done = bars + 22;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 24);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 25);
+    uint64_t *a_full = bars + 16;             // [2]
+    uint64_t *a_empty = bars + 18;            // [2]
+    uint64_t *acc_full = bars + 20;           // [2]
+    uint64_t *acc_empty = bars + 22;          // [2]
+    uint64_t *done = bars + 24;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 25);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 26);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    constexpr uint32_t kTmemCols = 2 * BN;
-    constexpr uint32_t kStageBytes = BN * 128;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
             mbar_init(full + s, 1);
             mbar_init(empty + s, 1);
         }
-        mbar_init(a_full, 1);
-        mbar_init(a_empty, 1);
-        mbar_init(acc_full + 0, 1);
-        mbar_init(acc_full + 1, 1);
-        mbar_init(acc_empty + 0, 4);
-        mbar_init(acc_empty + 1, 4);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(a_full + s, 1);
+            mbar_init(a_empty + s, 1);
+            mbar_init(acc_full + s, 1);
+            mbar_init(acc_empty + s, 4);
+        }
         mbar_init(done, 1);
         *abort_flag = 0;
         fence_mbar_init();
@@ -95,24 +169,25 @@ __global__ void __launch_bounds__(192, 1)
     if (warp == 0) {
         // ------------------------------------------------------------ TMA producer
         if (lane == 0) {
-            uint32_t stage = 0, phase = 0, a_phase = 0;
-            uint32_t pend_par[8];
-            bool pend[8];
+            uint32_t stage = 0, phase = 0;
+            uint32_t pend_par[8], a_pend_par[2];
+            bool pend[8], a_pend[2] = {false, false};
             for (int s = 0; s < 8; ++s) pend[s] = false;
-            bool a_pend = false;
-            uint32_t a_pend_par = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < p.n_units && ok; u += gridDim.x) {
+            int i = 0;   // unit count of this CTA
+            for (int u = blockIdx.x; u < p.n_units && ok; u += gridDim.x, ++i) {
                 const int4 un = p.units[u];
-                if (!mbar_wait(a_empty, a_phase ^ 1, abort_flag)) {
+                const int slot = i % a_slots;
+                const uint32_t use = (uint32_t)(i / a_slots);
+                if (!mbar_wait(a_empty + slot, (use & 1) ^ 1, abort_flag)) {
                     ok = false;
                     break;
                 }
-                mbar_arrive_expect_tx(a_full, kc * 16384);
-                for (int c = 0; c < kc; ++c) tma_load_2d(sA + c * 16384, &tmA, a_full, c * 64, un.x * 128);
-                a_pend = true;
-                a_pend_par = a_phase;
-                a_phase ^= 1;
+                mbar_arrive_expect_tx(a_full + slot, a_bytes);
+                for (int c = 0; c < kc; ++c)
+                    tma_load_2d(sA + slot * a_bytes + c * 16384, &tmA, a_full + slot, c * 64, un.x * 128);
+                a_pend[slot] = true;
+                a_pend_par[slot] = use & 1;
                 for (int n = un.y; n < un.z && ok; ++n) {
                     for (int c = 0; c < kc; ++c) {
                         if (!mbar_wait(empty + stage, phase ^ 1, abort_flag)) {
@@ -136,23 +211,27 @@ __global__ void __launch_bounds__(192, 1)
                 // Let every copy this thread started land before the CTA exits.
                 for (int s = 0; s < stages; ++s)
                     if (pend[s]) mbar_wait_plain(full + s, pend_par[s]);
-                if (a_pend) mbar_wait_plain(a_full, a_pend_par);
+                for (int s = 0; s < 2; ++s)
+                    if (a_pend[s]) mbar_wait_plain(a_full + s, a_pend_par[s]);
             }
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_bf16_f32(128, BN);
-            uint32_t stage = 0, phase = 0, a_phase = 0, t = 0;
+            uint32_t stage = 0, phase = 0, t = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < p.n_units && ok; u += gridDim.x) {
+            int i = 0;
+            for (int u = blockIdx.x; u < p.n_units && ok; u += gridDim.x, ++i) {
                 const int4 un = p.units[u];
-                if (!mbar_wait(a_full, a_phase, abort_flag)) {
+                const int slot = i % a_slots;
+                const uint32_t use = (uint32_t)(i / a_slots);
+                if (!mbar_wait(a_full + slot, use & 1, abort_flag)) {
                     ok = false;
                     break;
                 }
-                a_phase ^= 1;
                 tc_fence_after();
+                const uint32_t a_base = smem_u32(sA + slot * a_bytes);
                 for (int n = un.y; n < un.z && ok; ++n) {
                     const uint32_t b = t & 1;
                     if (!mbar_wait(acc_empty + b, ((t >> 1) & 1) ^ 1, abort_flag)) {
@@ -167,7 +246,7 @@ __global__ void __launch_bounds__(192, 1)
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t a_addr = smem_u32(sA + c * 16384);
+                        const uint32_t a_addr = a_base + c * 16384;
                         const uint32_t b_addr = smem_u32(sB + stage * kStageBytes);
 #pragma unroll
                         for (int k = 0; k < 4; ++k)
@@ -183,7 +262,7 @@ __global__ void __launch_bounds__(192, 1)
                     mma_commit(acc_full + b);
                     ++t;
                 }
-                if (ok) mma_commit(a_empty);
+                if (ok) mma_commit(a_empty + slot);
             }
             if (!ok) {
                 *abort_flag = 1;
@@ -197,57 +276,126 @@ __global__ void __launch_bounds__(192, 1)
         // ------------------------------------------------------------ epilogue
         const int quad = warp & 3;   // TMEM lanes this warp may access: 32*quad .. +31
         const uint32_t lane_base = static_cast<uint32_t>(quad * 32) << 16;
+        const int te = threadIdx.x - 64;   // 0..127 among the epilogue threads
+        constexpr int kPer = BN / 128;     // -beta values each epilogue thread stages per tile
+        TileIter cur, nxt;
+        cur.start(p);
+        nxt = cur;
+        nxt.next(p);
+
+        // stage tile `it` of -beta / chunk stats into slot `s`
+        auto stage_regs = [&](const TileIter &it, float (&nb)[kPer], float4 &cs) {
+            if (it.valid) {
+#pragma unroll
+                for (int q = 0; q < kPer; ++q) nb[q] = -__ldg(p.beta + it.n * BN + te + 128 * q);
+                if (te < kSub) cs = __ldg(p.cstat + it.n * kSub + te);
+            }
+        };
+        auto stage_store = [&](int s, const float (&nb)[kPer], const float4 &cs) {
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) s_nbeta[s * BN + te + 128 * q] = nb[q];
+            if (te < kSub) s_cst[s * kSub + te] = cs;
+        };
+        {
+            float nb[kPer];
+            float4 cs = make_float4(0.f, 0.f, 0.f, 0.f);
+            stage_regs(cur, nb, cs);
+            stage_store(0, nb, cs);
+            named_bar_sync(1, 128);
+        }
+
         uint32_t t = 0;
         bool ok = true;
-        for (int u = blockIdx.x; u < p.n_units && ok; u += gridDim.x) {
-            const int4 un = p.units[u];
-            const int r = un.x * 128 + quad * 32 + lane;
-            const float4 rp = p.rowpar[r];
-            for (int n = un.y; n < un.z; ++n) {
-                const uint32_t b = t & 1;
-                if (!mbar_wait(acc_full + b, (t >> 1) & 1, abort_flag)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-#pragma unroll 1
-                for (int cc = 0; cc < BN / 32; ++cc) {
-                    uint32_t v[32];
-                    tmem_ld_32x32b_x32(tmem_base + lane_base + b * BN + cc * 32, v);
-                    tmem_ld_wait();
-                    const int col0 = n * BN + cc * 32;
-                    const float4 cs = __ldg(p.cstat + (col0 >> 5));
-                    const float eh = __fmaf_ru(rp.z, cs.x, __fmaf_ru(rp.w, cs.y, cs.z));
-                    const float tau_rej = __fsub_rd(rp.y, eh);
-                    const float4 *b4 = reinterpret_cast<const float4 *>(p.beta + col0);
-                    float h[32];
-                    float mx = __int_as_float(0xff800000);   // -inf
+        float4 rp = make_float4(0.f, 0.f, 0.f, 0.f);
+        while (cur.valid) {
+            const int r = cur.un.x * 128 + quad * 32 + lane;
+            if (cur.n == cur.un.y) rp = p.rowpar[r];
+            float nbn[kPer];
+            float4 csn = make_float4(0.f, 0.f, 0.f, 0.f);
+            stage_regs(nxt, nbn, csn);   // prefetch the next tile's -beta (latency hidden by this tile)
+
+            const uint32_t b = t & 1;
+            const int slot = t & 1;
+            if (!mbar_wait(acc_full + b, (t >> 1) & 1, abort_flag)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t tbase = tmem_base + lane_base + b * BN;
+            const float *nbeta = s_nbeta + slot * BN;
+            const float4 *cst = s_cst + slot * kSub;
+
+            // process 32 columns [c32*32, c32*32+32) of this tile held in v[off..off+31]
+            auto process32 = [&](const uint32_t *v, int c32) {
+                const float4 cs = cst[c32];
+                const float eh = __fmaf_ru(rp.z, cs.x, __fmaf_ru(rp.w, cs.y, cs.z));
+                const float tau_rej = __fsub_rd(rp.y, eh);
+                const float4 *nb4 = reinterpret_cast<const float4 *>(nbeta + c32 * 32);
+                float h[32];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const float4 bb = __ldg(b4 + i);
-                        h[4 * i + 0] = __uint_as_float(v[4 * i + 0]) - bb.x;
-                        h[4 * i + 1] = __uint_as_float(v[4 * i + 1]) - bb.y;
-                        h[4 * i + 2] = __uint_as_float(v[4 * i + 2]) - bb.z;
-                        h[4 * i + 3] = __uint_as_float(v[4 * i + 3]) - bb.w;
-                        mx = fmaxf(mx, fmaxf(fmaxf(h[4 * i + 0], h[4 * i + 1]), fmaxf(h[4 * i + 2], h[4 * i + 3])));
-                    }
-                    if (__any_sync(0xffffffffu, mx >= tau_rej)) {
-                        const float tau_acc = __fadd_ru(rp.x, eh);
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int c = col0 + j;
-                            const bool valid = (r < p.nR) && (c < p.nS) && (!p.upper || c > r);
-                            const bool acc = valid && (h[j] >= tau_acc);
-                            const bool band = valid && !acc && (h[j] >= tau_rej);
-                            warp_emit(p.out, acc, band, r, c);
-                        }
-                    }
+                for (int i = 0; i < 8; ++i) {
+                    const float4 bb = nb4[i];
+                    const float2 h01 = __fadd2_rn(make_float2(__uint_as_float(v[4 * i + 0]), __uint_as_float(v[4 * i + 1])),
+                                                  make_float2(bb.x, bb.y));
+                    const float2 h23 = __fadd2_rn(make_float2(__uint_as_float(v[4 * i + 2]), __uint_as_float(v[4 * i + 3])),
+                                                  make_float2(bb.z, bb.w));
+                    h[4 * i + 0] = h01.x;
+                    h[4 * i + 1] = h01.y;
+                    h[4 * i + 2] = h23.x;
+                    h[4 * i + 3] = h23.y;
                 }
+                float m[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) m[i] = fmaxf(h[2 * i], h[2 * i + 1]);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) m[i] = fmaxf(m[2 * i], m[2 * i + 1]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) m[i] = fmaxf(m[2 * i], m[2 * i + 1]);
+                const float mx = fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3]));
+                if (__any_sync(0xffffffffu, mx >= tau_rej)) {
+                    const float tau_acc = __fadd_ru(rp.x, eh);
+                    classify_emit(p, h, r, cur.n * BN + c32 * 32, tau_acc, tau_rej);
+                }
+            };
+
+            uint32_t va[64], vb[64];
+            tmem_ld_32x32b_x64(tbase, va);
+            tmem_ld_wait_regs(va);
+            if constexpr (BN == 256) {
+                tmem_ld_32x32b_x64(tbase + 64, vb);
+                process32(va, 0);
+                process32(va + 32, 1);
+                tmem_ld_wait_regs(vb);
+                tmem_ld_32x32b_x64(tbase + 128, va);
+                process32(vb, 2);
+                process32(vb + 32, 3);
+                tmem_ld_wait_regs(va);
+                tmem_ld_32x32b_x64(tbase + 192, vb);
+                process32(va, 4);
+                process32(va + 32, 5);
+                tmem_ld_wait_regs(vb);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acc_empty + b);   // TMEM buffer free; the rest is in registers
+                process32(vb, 6);
+                process32(vb + 32, 7);
+            } else {
+                tmem_ld_32x32b_x64(tbase + 64, vb);
+                process32(va, 0);
+                process32(va + 32, 1);
+                tmem_ld_wait_regs(vb);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(acc_empty + b);
-                ++t;
+                process32(vb, 2);
+                process32(vb + 32, 3);
             }
+            // publish the next tile's -beta into the other slot
+            stage_store(slot ^ 1, nbn, csn);
+            named_bar_sync(1, 128);
+            cur = nxt;
+            nxt.next(p);
+            ++t;
         }
         if (!ok) {
             *abort_flag = 1;
@@ -262,24 +410,39 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
-static size_t tc_smem_bytes(int BN, int kc, int stages)
+static size_t tc_extra_bytes(int BN)
 {
-    return 1024 + (size_t)kc * 16384 + (size_t)stages * BN * 128 + 256;
+    return (size_t)2 * BN * 4 + (size_t)2 * (BN / 32) * 16 + 27 * 8;
 }
 
-int tc_pick_stages(int BN, int kc)
+static size_t tc_smem_bytes(int BN, int kc, int stages, int a_slots)
 {
-    const long avail = 232448 - 1024 - 256 - (long)kc * 16384;
-    long s = avail / ((long)BN * 128);
-    if (s > 8) s = 8;
-    return (int)s;
+    return 1024 + (size_t)a_slots * kc * 16384 + (size_t)stages * BN * 128 + tc_extra_bytes(BN);
 }
 
-
+// Shared-memory plan: two A slots when that still leaves at least three S stages.
+void tc_plan(int BN, int kc, int *stages, int *a_slots)
+{
+    const long cap = 232448;
+    for (int slots = 2; slots >= 1; --slots) {
+        const long avail = cap - 1024 - (long)tc_extra_bytes(BN) - (long)slots * kc * 16384;
+        long s = avail / ((long)BN * 128);
+        if (s > 8) s = 8;
+        if (s >= 3 || slots == 1) {
+            *stages = (int)s;
+            *a_slots = slots;
+            return;
+        }
+    }
+}
 
 int launch_tc_join(const TcLaunch &L, cudaStream_t st)
 {
-    const size_t smem = tc_smem_bytes(L.BN, L.p.kc, L.p.stages);
+    const size_t smem = tc_smem_bytes(L.BN, L.p.kc, L.p.stages, L.p.a_slots);
+    if (L.p.stages < 2 || smem > 232448) {
+        set_error("tensor-core join: no shared-memory plan for d=%d, tile %d", L.p.kc * 64, L.BN);
+        return DL_EUNSUPPORTED;
+    }
     cudaError_t e;
     if (L.BN == 256) {
         e = cudaFuncSetAttribute(tc_join_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

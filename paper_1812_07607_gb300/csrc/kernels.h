@@ -15,6 +15,7 @@ struct TcParams {
     int nR, nS;
     int kc;                  // K chunks of 64 (dp / 64)
     int stages;              // S ring depth
+    int a_slots;             // R-tile slots (2: the next unit's R tile loads during this one)
     int upper;               // 1: self-join, only columns c > r are pairs
     const float4 *rowpar;    // [m_tiles*128] {alpha_acc, alpha_rej, rq, nqt}
     const float *beta;       // S: RN32(||x||^2/2), +inf padding
@@ -30,7 +31,7 @@ struct TcLaunch {
     int grid;
 };
 
-int tc_pick_stages(int BN, int kc);
+void tc_plan(int BN, int kc, int *stages, int *a_slots);
 int launch_tc_join(const TcLaunch &L, cudaStream_t st);
 
 // ---- K8 SIMT FP32 join (join_simt.cu)
