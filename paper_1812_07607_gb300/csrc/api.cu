@@ -141,7 +141,7 @@ struct PassCfg {
 
 struct PassOut {
     int64_t *out_r = nullptr, *out_s = nullptr;
-    unsigned long long out_cnt = 0, band_cnt = 0, fp64_cnt = 0;
+    unsigned long long out_cnt = 0, band_cnt = 0, band_only = 0, fp64_cnt = 0;
     int err = 0;
     float ms_main = 0, ms_recheck = 0, ms_total = 0;
     int launches = 0;
@@ -170,7 +170,7 @@ static int run_pass(const PassCfg &c, PassOut *po)
     }
     po->out_r = (int64_t *)outb;
     po->out_s = po->out_r + cap;
-    unsigned long long *cnt = (unsigned long long *)ws;   // [0] out [1] band [2] fp64 [3] err
+    unsigned long long *cnt = (unsigned long long *)ws;   // [0] out [1] band/candidates [2] band pairs [3] fp64 [4] err
     uint2 *band = (uint2 *)((char *)ws + 256);
     float4 *rowpar = (float4 *)((char *)ws + 256 + b_band);
 
@@ -229,8 +229,10 @@ static int run_pass(const PassCfg &c, PassOut *po)
                 L.p.rowpar = rowpar;
                 L.p.beta = S->beta;
                 L.p.cstat = S->cstat;
-                L.p.out = jo;
-                L.p.err = (int *)(cnt + 3);
+                L.p.cand = band;                 // candidates share the band buffer and counter
+                L.p.cand_cnt = cnt + 1;
+                L.p.cand_cap = (unsigned long long)c.band_cap;
+                L.p.err = (int *)(cnt + 4);
                 rc = launch_tc_join(L, st);
                 ++launches;
             }
@@ -251,9 +253,13 @@ static int run_pass(const PassCfg &c, PassOut *po)
             ++launches;
         }
         if (c.timing) cudaEventRecord(ev[1], st);
-        if (!rc && c.prec != DL_PREC_FP32_PLAIN) {
+        if (!rc && c.prec == DL_PREC_BF16) {
+            rc = launch_finalize(band, cnt + 1, (unsigned long long)c.band_cap, R->x32, S->x32, d, c.e2, c.t_acc,
+                                 c.t_rej, jo, cnt + 3, cnt + 2, sms * 8, st);
+            ++launches;
+        } else if (!rc && c.prec == DL_PREC_FP32) {
             rc = launch_recheck(band, cnt + 1, (unsigned long long)c.band_cap, R->x32, S->x32, d, c.e2, c.t_acc, c.t_rej,
-                                jo, cnt + 2, sms * 8, st);
+                                jo, cnt + 3, sms * 8, st);
             ++launches;
         }
         if (c.timing) cudaEventRecord(ev[2], st);
@@ -269,15 +275,16 @@ static int run_pass(const PassCfg &c, PassOut *po)
     unsigned long long *hc = nullptr;
     if (!rc) rc = pinned_counters(&hc);
     if (!rc) {
-        e = cudaMemcpyAsync(hc, cnt, 32, cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(hc, cnt, 40, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = cuda_fail(e, "join kernels");
     }
     if (!rc) {
         po->out_cnt = hc[0];
-        po->band_cnt = hc[1];
-        po->fp64_cnt = hc[2];
-        po->err = (int)hc[3];
+        po->band_cnt = hc[1];                                  // list fill (band or candidate list)
+        po->band_only = c.prec == DL_PREC_BF16 ? hc[2] : hc[1];
+        po->fp64_cnt = hc[3];
+        po->err = (int)hc[4];
         if (c.timing) {
             cudaEventElapsedTime(&po->ms_main, ev[0], ev[1]);
             cudaEventElapsedTime(&po->ms_recheck, ev[1], ev[2]);
@@ -408,7 +415,9 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
     {
         std::lock_guard<std::mutex> lk(const_cast<dl_store *>(R)->mu);
         c.cap = fixed ? o.out_capacity : std::max<int64_t>(1 << 16, R->hint_pairs + R->hint_pairs / 4);
-        c.band_cap = std::max<int64_t>(1 << 16, R->hint_band + R->hint_band / 4);
+        // the BF16 path's candidate list holds proven matches and band pairs
+        const int64_t want = (prec == DL_PREC_BF16 ? R->hint_pairs : 0) + R->hint_band;
+        c.band_cap = std::max<int64_t>(1 << 16, want + want / 4);
     }
 
     PassOut po;
@@ -441,7 +450,7 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
     {
         std::lock_guard<std::mutex> lk(const_cast<dl_store *>(R)->mu);
         const_cast<dl_store *>(R)->hint_pairs = (int64_t)po.out_cnt;
-        const_cast<dl_store *>(R)->hint_band = (int64_t)po.band_cnt;
+        const_cast<dl_store *>(R)->hint_band = (int64_t)po.band_only;
     }
     dl_result *res = new dl_result();
     res->kind = 0;
@@ -454,7 +463,7 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
     dl_join_stats &s = res->stats;
     s.pairs_evaluated = self ? (c.mirror ? R->n * R->n : R->n * (R->n - 1) / 2) : R->n * Sx->n;
     s.pairs_out = (int64_t)po.out_cnt;
-    s.band_pairs = (int64_t)po.band_cnt;
+    s.band_pairs = (int64_t)po.band_only;
     s.fp64_pairs = (int64_t)po.fp64_cnt;
     s.reruns = reruns;
     s.precision = prec;

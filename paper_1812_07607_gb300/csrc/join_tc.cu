@@ -9,7 +9,7 @@
 // proven match, a proven non-match, or an undecided "band" pair that the
 // recheck kernel settles exactly.
 //
-// Per CTA (persistent, one per SM, 192 threads, warp-specialised):
+// Per CTA (persistent, one per SM, 320 threads, warp-specialised):
 //   warp 0      TMA producer: the 128-row R tile (all d/64 K-chunks) is loaded
 //               once per unit into one of one or two A slots; S tiles stream
 //               through a ring of stages, one 64-column K-chunk of BN rows per
@@ -17,12 +17,16 @@
 //   warp 1      MMA issuer: 4 x tcgen05.mma (K=16 each) per stage into one of two
 //               TMEM accumulators (128 lanes x BN FP32 columns each), then
 //               tcgen05.commit to free the stage / publish the accumulator.
-//   warps 2-5   epilogue: tcgen05.ld 64 columns at a time (double-buffered),
-//               h = A - beta_x with packed FP32 adds against -beta staged in
-//               shared memory one tile ahead, a max tree against the row's
-//               reject threshold (about 1.5 issue slots per pair), and only for
-//               the chunks that pass, the exact accept/band classification
-//               into bit masks and warp-aggregated output.
+//   warps 2-9   epilogue, two warps per TMEM lane quadrant, each owning half of
+//               the tile's columns: tcgen05.ld 64 columns at a time
+//               (double-buffered), h = A - beta_x with packed FP32 adds against
+//               -beta that each warp stages in shared memory one tile ahead, a
+//               max tree against the row's reject threshold (about 1.5 issue
+//               slots per pair), and only for the 64-column pieces that pass,
+//               the exact accept/band classification into bit masks. Matches
+//               and band pairs go to a per-warp shared-memory buffer as (r, c)
+//               candidates, flushed to the global candidate list with one
+//               atomic per flush; k_finalize turns them into id pairs.
 // A unit is (R tile m, S tiles [nb, ne)); units are handed out round-robin.
 #include <cuda.h>
 
@@ -67,49 +71,85 @@ struct TileIter {
     }
 };
 
-// Classify the 32 pairs (r, col0 + j) of one sub-chunk whose values h[j] are
-// known; emit proven matches and band pairs (warp-collective).
-__device__ __forceinline__ void classify_emit(const TcParams &p, const float (&h)[32], int r, int col0,
-                                              float tau_acc, float tau_rej)
+constexpr int kStageCap = 128;   // candidate entries a warp buffers before flushing
+
+// Copy a warp's buffered candidates to the global list (one atomic per flush).
+__device__ __forceinline__ void flush_stage(const TcParams &p, uint2 *stg, uint32_t &scnt)
 {
-    uint32_t am = 0, bm = 0;
+    const unsigned lane = threadIdx.x & 31;
+    __syncwarp();
+    unsigned long long base = 0;
+    if (lane == 0 && scnt) base = atomicAdd(p.cand_cnt, (unsigned long long)scnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (uint32_t i = lane; i < scnt; i += 32) {
+        const unsigned long long idx = base + i;
+        if (idx < p.cand_cap) p.cand[idx] = stg[i];
+    }
+    __syncwarp();
+    scnt = 0;
+}
+
+// Slow path for one 64-column piece whose running max reached a reject
+// threshold: recompute h = A - beta for the 64 pairs (r, col0 + j), classify
+// them against the piece's two (accept, reject) threshold pairs, and buffer
+// every proven match and band pair. Warp-collective; rarely taken.
+__device__ __forceinline__ uint32_t slow_piece(const TcParams &p, const uint32_t (&v)[64], const float *nb, float rx, float ry,
+                                            float eh0, float eh1, int r, int col0, uint2 *stg, uint32_t scnt)
+{
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const bool a = h[j] >= tau_acc;
-        const bool b = !a && (h[j] >= tau_rej);
-        am |= (a ? 1u : 0u) << j;
-        bm |= (b ? 1u : 0u) << j;
-    }
-    uint32_t vm = 0xffffffffu;
-    const int rem = p.nS - col0;
-    if (rem < 32) vm = rem <= 0 ? 0u : ((1u << rem) - 1u);
-    if (p.upper) {
-        const int k = r - col0;   // columns j <= k are not pairs (need c > r)
-        if (k >= 31)
-            vm = 0u;
-        else if (k >= 0)
-            vm &= ~((2u << k) - 1u);
-    }
-    if (r >= p.nR) vm = 0u;
-    am &= vm;
-    bm &= vm;
-    while (__any_sync(0xffffffffu, (am | bm) != 0u)) {
-        const bool has_a = am != 0u;
-        const bool has_b = !has_a && bm != 0u;
-        int j = 0;
-        if (has_a) {
-            j = __ffs(am) - 1;
-            am &= am - 1u;
-        } else if (has_b) {
-            j = __ffs(bm) - 1;
-            bm &= bm - 1u;
+    for (int hh = 0; hh < 2; ++hh) {
+        const float eh = hh ? eh1 : eh0;
+        const float tau_acc = __fadd_ru(rx, eh);
+        const float tau_rej = __fsub_rd(ry, eh);
+        const int c0 = col0 + hh * 32;
+        uint32_t am = 0, bm = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const float h = __uint_as_float(v[hh * 32 + j]) + nb[hh * 32 + j];
+            const bool a = h >= tau_acc;
+            const bool b = !a && (h >= tau_rej);
+            am |= (a ? 1u : 0u) << j;
+            bm |= (b ? 1u : 0u) << j;
         }
-        warp_emit(p.out, has_a, has_b, r, col0 + j);
+        uint32_t vm = 0xffffffffu;
+        const int rem = p.nS - c0;
+        if (rem < 32) vm = rem <= 0 ? 0u : ((1u << rem) - 1u);
+        if (p.upper) {
+            const int k = r - c0;   // columns j <= k are not pairs (need c > r)
+            if (k >= 31)
+                vm = 0u;
+            else if (k >= 0)
+                vm &= ~((2u << k) - 1u);
+        }
+        if (r >= p.nR) vm = 0u;
+        am &= vm;
+        bm &= vm;
+        while (__any_sync(0xffffffffu, (am | bm) != 0u)) {
+            const bool has_a = am != 0u;
+            const bool has = has_a || bm != 0u;
+            int j = 0;
+            if (has_a) {
+                j = __ffs(am) - 1;
+                am &= am - 1u;
+            } else if (has) {
+                j = __ffs(bm) - 1;
+                bm &= bm - 1u;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, has);
+            if (scnt + __popc(m) > kStageCap) flush_stage(p, stg, scnt);
+            if (has)
+                stg[scnt + __popc(m & lt)] = make_uint2((uint32_t)r, (uint32_t)(c0 + j) | (has_a ? 0u : kBandFlag));
+            scnt += __popc(m);
+        }
     }
+    (void)lane;
+    return scnt;
 }
 
 template <int BN>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(320, 1)
     tc_join_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcParams p)
 {
@@ -118,13 +158,15 @@ __global__ void __launch_bounds__(192, 1)
     const int kc = p.kc, stages = p.stages, a_slots = p.a_slots;
     constexpr uint32_t kStageBytes = BN * 128;
     constexpr uint32_t kTmemCols = 2 * BN;
-    constexpr int kSub = BN / 32;            // 32-column sub-chunks per tile
+    constexpr int HC = BN / 2;               // columns of a tile each epilogue warp owns
+    constexpr int kSubW = HC / 32;           // 32-column chunks per warp per tile
     const uint32_t a_bytes = (uint32_t)kc * 16384;
     uint8_t *sA = smem;                                    // a_slots x kc x [128 rows x 128 B]
     uint8_t *sB = smem + a_slots * a_bytes;                // stages x [BN rows x 128 B]
-    float *s_nbeta = reinterpret_cast<float *>(sB + stages * kStageBytes);   // 2 x BN: -beta of a tile
-    float4 *s_cst = reinterpret_cast<float4 *>(s_nbeta + 2 * BN);           // 2 x kSub chunk stats
-    uint64_t *bars = reinterpret_cast<uint64_t *>(s_cst + 2 * kSub);
+    float *s_nbeta = reinterpret_cast<float *>(sB + stages * kStageBytes);   // 8 warps x 2 x HC: -beta
+    float4 *s_cst = reinterpret_cast<float4 *>(s_nbeta + 8 * 2 * HC);       // 8 warps x 2 x kSubW chunk stats
+    uint2 *s_stage = reinterpret_cast<uint2 *>(s_cst + 8 * 2 * kSubW);       // 8 warps x kStageCap candidates
+    uint64_t *bars = reinterpret_cast<uint64_t *>(s_stage + 8 * kStageCap);
     uint64_t *full = bars;                    // [8]
     uint64_t *empty = bars + 8;               // [8]
     uint64_t *a_full = bars + 16;             // [2]
@@ -147,7 +189,7 @@ __global__ void __launch_bounds__(192, 1)
             mbar_init(a_full + s, 1);
             mbar_init(a_empty + s, 1);
             mbar_init(acc_full + s, 1);
-            mbar_init(acc_empty + s, 4);
+            mbar_init(acc_empty + s, 8);
         }
         mbar_init(done, 1);
         *abort_flag = 0;
@@ -274,34 +316,39 @@ __global__ void __launch_bounds__(192, 1)
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        const int quad = warp & 3;   // TMEM lanes this warp may access: 32*quad .. +31
+        const int e = warp - 2;            // 0..7
+        const int quad = warp & 3;         // TMEM lanes this warp may access: 32*quad .. +31
+        const int half = e >> 2;           // which half of the tile's columns
         const uint32_t lane_base = static_cast<uint32_t>(quad * 32) << 16;
-        const int te = threadIdx.x - 64;   // 0..127 among the epilogue threads
-        constexpr int kPer = BN / 128;     // -beta values each epilogue thread stages per tile
+        float *my_nb = s_nbeta + e * (2 * HC);
+        float4 *my_cs = s_cst + e * (2 * kSubW);
+        uint2 *my_stg = s_stage + e * kStageCap;
+        uint32_t scnt = 0;
+        constexpr int kPer = HC / 32;      // -beta values a lane stages per tile (4 or 2)
         TileIter cur, nxt;
         cur.start(p);
         nxt = cur;
         nxt.next(p);
 
-        // stage tile `it` of -beta / chunk stats into slot `s`
         auto stage_regs = [&](const TileIter &it, float (&nb)[kPer], float4 &cs) {
             if (it.valid) {
+                const int c0 = it.n * BN + half * HC;
 #pragma unroll
-                for (int q = 0; q < kPer; ++q) nb[q] = -__ldg(p.beta + it.n * BN + te + 128 * q);
-                if (te < kSub) cs = __ldg(p.cstat + it.n * kSub + te);
+                for (int q = 0; q < kPer; ++q) nb[q] = -__ldg(p.beta + c0 + lane * kPer + q);
+                if (lane < kSubW) cs = __ldg(p.cstat + (c0 >> 5) + lane);
             }
         };
         auto stage_store = [&](int s, const float (&nb)[kPer], const float4 &cs) {
 #pragma unroll
-            for (int q = 0; q < kPer; ++q) s_nbeta[s * BN + te + 128 * q] = nb[q];
-            if (te < kSub) s_cst[s * kSub + te] = cs;
+            for (int q = 0; q < kPer; ++q) my_nb[s * HC + lane * kPer + q] = nb[q];
+            if (lane < kSubW) my_cs[s * kSubW + lane] = cs;
+            __syncwarp();
         };
         {
             float nb[kPer];
             float4 cs = make_float4(0.f, 0.f, 0.f, 0.f);
             stage_regs(cur, nb, cs);
             stage_store(0, nb, cs);
-            named_bar_sync(1, 128);
         }
 
         uint32_t t = 0;
@@ -321,82 +368,71 @@ __global__ void __launch_bounds__(192, 1)
                 break;
             }
             tc_fence_after();
-            const uint32_t tbase = tmem_base + lane_base + b * BN;
-            const float *nbeta = s_nbeta + slot * BN;
-            const float4 *cst = s_cst + slot * kSub;
+            const uint32_t tbase = tmem_base + lane_base + b * BN + half * HC;
+            const float *nbeta = my_nb + slot * HC;
+            const float4 *cst = my_cs + slot * kSubW;
+            const int colw = cur.n * BN + half * HC;   // first column this warp owns in the tile
 
-            // process 32 columns [c32*32, c32*32+32) of this tile held in v[off..off+31]
-            auto process32 = [&](const uint32_t *v, int c32) {
-                const float4 cs = cst[c32];
-                const float eh = __fmaf_ru(rp.z, cs.x, __fmaf_ru(rp.w, cs.y, cs.z));
-                const float tau_rej = __fsub_rd(rp.y, eh);
-                const float4 *nb4 = reinterpret_cast<const float4 *>(nbeta + c32 * 32);
-                float h[32];
+            // 64 columns [piece*64, piece*64+64) of this warp's half, values in v
+            auto process64 = [&](const uint32_t (&v)[64], int piece) {
+                const float4 cs0 = cst[2 * piece], cs1 = cst[2 * piece + 1];
+                const float eh0 = __fmaf_ru(rp.z, cs0.x, __fmaf_ru(rp.w, cs0.y, cs0.z));
+                const float eh1 = __fmaf_ru(rp.z, cs1.x, __fmaf_ru(rp.w, cs1.y, cs1.z));
+                const float tr0 = __fsub_rd(rp.y, eh0);
+                const float tr1 = __fsub_rd(rp.y, eh1);
+                const float4 *nb4 = reinterpret_cast<const float4 *>(nbeta + piece * 64);
+                float m0[8], m1[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const float4 bb = nb4[i];
-                    const float2 h01 = __fadd2_rn(make_float2(__uint_as_float(v[4 * i + 0]), __uint_as_float(v[4 * i + 1])),
+                    const float4 bc = nb4[8 + i];
+                    const float2 x01 = __fadd2_rn(make_float2(__uint_as_float(v[4 * i + 0]), __uint_as_float(v[4 * i + 1])),
                                                   make_float2(bb.x, bb.y));
-                    const float2 h23 = __fadd2_rn(make_float2(__uint_as_float(v[4 * i + 2]), __uint_as_float(v[4 * i + 3])),
+                    const float2 x23 = __fadd2_rn(make_float2(__uint_as_float(v[4 * i + 2]), __uint_as_float(v[4 * i + 3])),
                                                   make_float2(bb.z, bb.w));
-                    h[4 * i + 0] = h01.x;
-                    h[4 * i + 1] = h01.y;
-                    h[4 * i + 2] = h23.x;
-                    h[4 * i + 3] = h23.y;
+                    const float2 y01 = __fadd2_rn(make_float2(__uint_as_float(v[32 + 4 * i + 0]), __uint_as_float(v[32 + 4 * i + 1])),
+                                                  make_float2(bc.x, bc.y));
+                    const float2 y23 = __fadd2_rn(make_float2(__uint_as_float(v[32 + 4 * i + 2]), __uint_as_float(v[32 + 4 * i + 3])),
+                                                  make_float2(bc.z, bc.w));
+                    m0[i] = fmaxf(fmaxf(x01.x, x01.y), fmaxf(x23.x, x23.y));
+                    m1[i] = fmaxf(fmaxf(y01.x, y01.y), fmaxf(y23.x, y23.y));
                 }
-                float m[16];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) m[i] = fmaxf(h[2 * i], h[2 * i + 1]);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) m[i] = fmaxf(m[2 * i], m[2 * i + 1]);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) m[i] = fmaxf(m[2 * i], m[2 * i + 1]);
-                const float mx = fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3]));
-                if (__any_sync(0xffffffffu, mx >= tau_rej)) {
-                    const float tau_acc = __fadd_ru(rp.x, eh);
-                    classify_emit(p, h, r, cur.n * BN + c32 * 32, tau_acc, tau_rej);
+                for (int i = 0; i < 4; ++i) {
+                    m0[i] = fmaxf(m0[2 * i], m0[2 * i + 1]);
+                    m1[i] = fmaxf(m1[2 * i], m1[2 * i + 1]);
                 }
+                const float mx0 = fmaxf(fmaxf(m0[0], m0[1]), fmaxf(m0[2], m0[3]));
+                const float mx1 = fmaxf(fmaxf(m1[0], m1[1]), fmaxf(m1[2], m1[3]));
+                if (__any_sync(0xffffffffu, (mx0 >= tr0) || (mx1 >= tr1)))
+                    scnt = slow_piece(p, v, nbeta + piece * 64, rp.x, rp.y, eh0, eh1, r, colw + piece * 64, my_stg,
+                                      scnt);
             };
 
-            uint32_t va[64], vb[64];
-            tmem_ld_32x32b_x64(tbase, va);
-            tmem_ld_wait_regs(va);
-            if constexpr (BN == 256) {
-                tmem_ld_32x32b_x64(tbase + 64, vb);
-                process32(va, 0);
-                process32(va + 32, 1);
-                tmem_ld_wait_regs(vb);
-                tmem_ld_32x32b_x64(tbase + 128, va);
-                process32(vb, 2);
-                process32(vb + 32, 3);
+            // One 64-column load at a time: the other epilogue warp on this SM
+            // sub-partition hides the TMEM load latency.
+            uint32_t va[64];
+            if constexpr (HC == 128) {
+                tmem_ld_32x32b_x64(tbase, va);
                 tmem_ld_wait_regs(va);
-                tmem_ld_32x32b_x64(tbase + 192, vb);
-                process32(va, 4);
-                process32(va + 32, 5);
-                tmem_ld_wait_regs(vb);
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(acc_empty + b);   // TMEM buffer free; the rest is in registers
-                process32(vb, 6);
-                process32(vb + 32, 7);
+                process64(va, 0);
+                tmem_ld_32x32b_x64(tbase + 64, va);
+                tmem_ld_wait_regs(va);
             } else {
-                tmem_ld_32x32b_x64(tbase + 64, vb);
-                process32(va, 0);
-                process32(va + 32, 1);
-                tmem_ld_wait_regs(vb);
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(acc_empty + b);
-                process32(vb, 2);
-                process32(vb + 32, 3);
+                tmem_ld_32x32b_x64(tbase, va);
+                tmem_ld_wait_regs(va);
             }
-            // publish the next tile's -beta into the other slot
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty + b);   // TMEM buffer free; the rest is in registers
+            process64(va, HC == 128 ? 1 : 0);
+            // publish the next tile's -beta into the other slot (this warp's own copy)
             stage_store(slot ^ 1, nbn, csn);
-            named_bar_sync(1, 128);
             cur = nxt;
             nxt.next(p);
             ++t;
         }
+        flush_stage(p, my_stg, scnt);
         if (!ok) {
             *abort_flag = 1;
             atomicExch(p.err, 1);
@@ -412,7 +448,9 @@ __global__ void __launch_bounds__(192, 1)
 
 static size_t tc_extra_bytes(int BN)
 {
-    return (size_t)2 * BN * 4 + (size_t)2 * (BN / 32) * 16 + 27 * 8;
+    // per epilogue warp: 2 x BN/2 floats of -beta, 2 x BN/64 chunk stats, the
+    // candidate buffer; then 27 barrier / flag words
+    return (size_t)8 * (2 * (BN / 2) * 4 + 2 * (BN / 64) * 16 + kStageCap * 8) + 27 * 8;
 }
 
 static size_t tc_smem_bytes(int BN, int kc, int stages, int a_slots)
@@ -447,11 +485,11 @@ int launch_tc_join(const TcLaunch &L, cudaStream_t st)
     if (L.BN == 256) {
         e = cudaFuncSetAttribute(tc_join_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_join_kernel<256>)");
-        tc_join_kernel<256><<<L.grid, 192, smem, st>>>(*L.tmA, *L.tmB, L.p);
+        tc_join_kernel<256><<<L.grid, 320, smem, st>>>(*L.tmA, *L.tmB, L.p);
     } else if (L.BN == 128) {
         e = cudaFuncSetAttribute(tc_join_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_join_kernel<128>)");
-        tc_join_kernel<128><<<L.grid, 192, smem, st>>>(*L.tmA, *L.tmB, L.p);
+        tc_join_kernel<128><<<L.grid, 320, smem, st>>>(*L.tmA, *L.tmB, L.p);
     } else {
         set_error("tensor-core tile width %d not supported (128 or 256)", L.BN);
         return DL_EINVAL;

@@ -20,9 +20,14 @@ struct TcParams {
     const float4 *rowpar;    // [m_tiles*128] {alpha_acc, alpha_rej, rq, nqt}
     const float *beta;       // S: RN32(||x||^2/2), +inf padding
     const float4 *cstat;     // S: per 32-column chunk {P1, P2, P3, 0}
-    JoinOut out;
+    uint2 *cand;             // candidates: {r, c | 0x80000000 if a band pair, else a proven match}
+    unsigned long long *cand_cnt;
+    unsigned long long cand_cap;
     int *err;                // set to 1 when a bounded wait expired
 };
+
+// Candidate entry flag: set for a band pair (needs the exact recheck).
+constexpr uint32_t kBandFlag = 0x80000000u;
 
 struct TcLaunch {
     const CUtensorMap *tmA, *tmB;
@@ -53,6 +58,11 @@ int launch_recheck(const uint2 *band, const unsigned long long *band_cnt, unsign
                    unsigned long long *n_fp64, int grid, cudaStream_t st);
 int launch_rowpar(const double *nq64, const float4 *rowb, int64_t n, int64_t n_tot, int dp, double e2, double g64,
                   float4 *rowpar, cudaStream_t st);
+// Turn the tensor-core kernel's candidate list into id pairs: proven matches are
+// translated directly, band pairs are rechecked exactly first (recheck.cu).
+int launch_finalize(const uint2 *cand, const unsigned long long *cand_cnt, unsigned long long cand_cap, const float *R,
+                    const float *S, int d, double e2, float t_acc, float t_rej, const JoinOut &out,
+                    unsigned long long *n_fp64, unsigned long long *n_band, int grid, cudaStream_t st);
 int launch_diag(const int64_t *ids, int64_t n, int64_t *out_r, int64_t *out_s, unsigned long long *out_cnt,
                 unsigned long long cap, cudaStream_t st);
 

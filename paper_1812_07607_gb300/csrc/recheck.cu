@@ -14,6 +14,37 @@
 
 namespace dl {
 
+// Exact decision for the pair (q, x), taken by the whole warp (same answer in
+// every lane): FP32 first, the canonical FP64 sum only when FP32 cannot decide.
+__device__ __forceinline__ bool warp_exact_decide(const float *__restrict__ q, const float *__restrict__ x, int d,
+                                                  double e2, float t_acc, float t_rej,
+                                                  unsigned long long *__restrict__ n_fp64)
+{
+    const unsigned lane = threadIdx.x & 31;
+    float s = 0.f;
+    for (int k = lane; k < d; k += 32) {
+        const float t = __ldg(q + k) - __ldg(x + k);
+        s = fmaf(t, t, s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (s <= t_acc) return true;
+    if (s > t_rej) return false;
+    double sum = 0.0;
+    for (int k0 = 0; k0 < d; k0 += 32) {
+        double pk = 0.0;
+        const int k = k0 + (int)lane;
+        if (k < d) {
+            const double t = __dsub_rn((double)__ldg(q + k), (double)__ldg(x + k));
+            pk = __dmul_rn(t, t);
+        }
+        const int lim = min(32, d - k0);
+        for (int l = 0; l < lim; ++l) sum = __dadd_rn(sum, __shfl_sync(0xffffffffu, pk, l));
+    }
+    if (lane == 0) atomicAdd(n_fp64, 1ULL);
+    return sum <= e2;
+}
+
 __global__ void __launch_bounds__(256)
     k6_recheck(const uint2 *__restrict__ band, const unsigned long long *__restrict__ band_cnt,
                unsigned long long band_cap, const float *__restrict__ R, const float *__restrict__ S, int d, double e2,
@@ -25,33 +56,44 @@ __global__ void __launch_bounds__(256)
     const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
     for (unsigned long long i = w0; i < nb; i += nw) {
         const uint2 pr = band[i];
-        const float *q = R + (size_t)pr.x * d;
-        const float *x = S + (size_t)pr.y * d;
-        float s = 0.f;
-        for (int k = lane; k < d; k += 32) {
-            const float t = __ldg(q + k) - __ldg(x + k);
-            s = fmaf(t, t, s);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        bool acc = (s <= t_acc);
-        const bool rej = (s > t_rej);
-        if (!acc && !rej) {
-            double sum = 0.0;
-            for (int k0 = 0; k0 < d; k0 += 32) {
-                double pk = 0.0;
-                const int k = k0 + (int)lane;
-                if (k < d) {
-                    const double t = __dsub_rn((double)__ldg(q + k), (double)__ldg(x + k));
-                    pk = __dmul_rn(t, t);
-                }
-                const int lim = min(32, d - k0);
-                for (int l = 0; l < lim; ++l) sum = __dadd_rn(sum, __shfl_sync(0xffffffffu, pk, l));
-            }
-            acc = (sum <= e2);
-            if (lane == 0) atomicAdd(n_fp64, 1ULL);
-        }
+        const bool acc =
+            warp_exact_decide(R + (size_t)pr.x * d, S + (size_t)pr.y * d, d, e2, t_acc, t_rej, n_fp64);
         warp_emit(out, acc && lane == 0, false, (int)pr.x, (int)pr.y);
+    }
+}
+
+// Candidates of the tensor-core kernel -> id pairs. Each warp takes 32 entries:
+// proven matches are emitted as they are; the warp rechecks the band entries
+// one at a time (all lanes cooperate on each), then emits the survivors.
+__global__ void __launch_bounds__(256)
+    k_finalize(const uint2 *__restrict__ cand, const unsigned long long *__restrict__ cand_cnt,
+               unsigned long long cand_cap, const float *__restrict__ R, const float *__restrict__ S, int d, double e2,
+               float t_acc, float t_rej, JoinOut out, unsigned long long *__restrict__ n_fp64,
+               unsigned long long *__restrict__ n_band)
+{
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned long long n = min(*cand_cnt, cand_cap);
+    const unsigned long long w0 = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    for (unsigned long long base = w0 * 32; base < n; base += nw * 32) {
+        const unsigned long long i = base + lane;
+        const bool valid = i < n;
+        const uint2 e = valid ? cand[i] : make_uint2(0u, 0u);
+        const int r = (int)e.x;
+        const int c = (int)(e.y & ~kBandFlag);
+        const bool band = valid && (e.y & kBandFlag);
+        bool acc = valid && !band;
+        unsigned bm = __ballot_sync(0xffffffffu, band);
+        if (lane == 0 && bm) atomicAdd(n_band, (unsigned long long)__popc(bm));
+        while (bm) {
+            const int l = __ffs(bm) - 1;
+            bm &= bm - 1;
+            const int rr = __shfl_sync(0xffffffffu, r, l);
+            const int cc = __shfl_sync(0xffffffffu, c, l);
+            const bool dec = warp_exact_decide(R + (size_t)rr * d, S + (size_t)cc * d, d, e2, t_acc, t_rej, n_fp64);
+            if ((int)lane == l) acc = dec;
+        }
+        warp_emit(out, acc, false, r, c);
     }
 }
 
@@ -108,6 +150,17 @@ int launch_recheck(const uint2 *band, const unsigned long long *band_cnt, unsign
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k6_recheck launch");
+    return DL_OK;
+}
+
+int launch_finalize(const uint2 *cand, const unsigned long long *cand_cnt, unsigned long long cand_cap, const float *R,
+                    const float *S, int d, double e2, float t_acc, float t_rej, const JoinOut &out,
+                    unsigned long long *n_fp64, unsigned long long *n_band, int grid, cudaStream_t st)
+{
+    k_finalize<<<grid, 256, 0, st>>>(cand, cand_cnt, cand_cap, R, S, d, e2, t_acc, t_rej, out, n_fp64, n_band);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_finalize launch");
     return DL_OK;
 }
 
