@@ -201,6 +201,7 @@ static int run_pass(const PassCfg &c, PassOut *po)
     jo.band_cnt = cnt + 1;
     jo.band_cap = (unsigned long long)c.band_cap;
     jo.mirror = c.mirror ? 1 : 0;
+    jo.orig = (c.self && !c.mirror) ? R->orig : nullptr;
 
     int launches = 0;
     if (nR > 0 && nS > 0) {

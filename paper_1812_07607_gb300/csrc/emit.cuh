@@ -22,6 +22,8 @@ struct JoinOut {
     unsigned long long *band_cnt;
     unsigned long long band_cap;
     int mirror;                    // 1: self-join full mode, also write (s, r)
+    const int32_t *orig;           // self-join upper mode: caller's row index per store row, so that
+                                   // each unordered pair is written (lower caller row, higher); else NULL
 };
 
 __device__ __forceinline__ unsigned lanemask_lt()
@@ -46,7 +48,12 @@ __device__ __forceinline__ void warp_emit(const JoinOut &o, bool acc, bool band,
         base = __shfl_sync(0xffffffffu, base, 0);
         if (acc) {
             const unsigned long long pos = base + (unsigned long long)(__popc(am & lt) * mult);
-            const int64_t ri = o.r_ids[r], si = o.s_ids[c];
+            int64_t ri = o.r_ids[r], si = o.s_ids[c];
+            if (o.orig && o.orig[r] > o.orig[c]) {
+                const int64_t tmp = ri;
+                ri = si;
+                si = tmp;
+            }
             if (pos < o.out_cap) {
                 o.out_r[pos] = ri;
                 o.out_s[pos] = si;

@@ -66,13 +66,14 @@ struct Store {
     int32_t dp = 0;          // d rounded up to a multiple of 64 (BF16 copy row length)
     int64_t n_pad = 0;       // n rounded up to a multiple of 256 (column-side padding)
     int device = 0;
-    int64_t *ids = nullptr;  // [n]
-    float *x32 = nullptr;    // [n][d] FP32 master copy
+    int64_t *ids = nullptr;  // [n] ids, in store order
+    int32_t *orig = nullptr; // [n] caller's row index of each store row (rows are kept in norm order)
+    float *x32 = nullptr;    // [n][d] FP32 master copy, in store order
     __nv_bfloat16 *xb = nullptr;  // [n][dp] BF16 copy, zero padded
     double *nq64 = nullptr;  // [n] sum of squares in FP64
     float *beta = nullptr;   // [n_pad] RN32(nq64 / 2); +inf in padding
     float4 *rowb = nullptr;  // [n] {||x - x~|| up, ||x~|| up, ||x|| up, |beta - ||x||^2/2| up}
-    float4 *cstat = nullptr; // [n_pad / 32] per 32-row chunk {P1, P2, P3, 0} of the BF16 bound
+    float4 *cstat = nullptr; // [n_pad / 32] per 32-row chunk {P1, P2, P3, min beta} of the BF16 bound
     TmapCache tmaps[3];      // box rows 128, 256, 128-for-B (cached per box height)
     std::mutex mu;           // guards tmaps and hints
     int64_t hint_pairs = 0;  // last output size seen with this store as R (capacity hint)

@@ -18,15 +18,17 @@
 //               TMEM accumulators (128 lanes x BN FP32 columns each), then
 //               tcgen05.commit to free the stage / publish the accumulator.
 //   warps 2-9   epilogue, two warps per TMEM lane quadrant, each owning half of
-//               the tile's columns: tcgen05.ld 64 columns at a time
-//               (double-buffered), h = A - beta_x with packed FP32 adds against
-//               -beta that each warp stages in shared memory one tile ahead, a
-//               max tree against the row's reject threshold (about 1.5 issue
-//               slots per pair), and only for the 64-column pieces that pass,
-//               the exact accept/band classification into bit masks. Matches
-//               and band pairs go to a per-warp shared-memory buffer as (r, c)
-//               candidates, flushed to the global candidate list with one
-//               atomic per flush; k_finalize turns them into id pairs.
+//               the tile's columns: tcgen05.ld 64 columns at a time, then a max
+//               tree over the raw accumulators of each 32-column chunk and one
+//               compare of fl_ru(max A - min beta of the chunk) against the
+//               row's reject threshold (about one issue slot per pair; store
+//               rows are in norm order so a chunk's betas are nearly equal).
+//               Only chunks that this bound cannot reject compute
+//               h = fl(A - beta) per pair (against -beta each warp stages in
+//               shared memory a tile ahead) and classify them exactly; proven
+//               matches and band pairs go to a per-warp shared-memory buffer as
+//               (r, c) candidates, flushed to the global candidate list with one
+//               atomic per flush. k_finalize turns them into id pairs.
 // A unit is (R tile m, S tiles [nb, ne)); units are handed out round-robin.
 #include <cuda.h>
 
@@ -89,17 +91,20 @@ __device__ __forceinline__ void flush_stage(const TcParams &p, uint2 *stg, uint3
     scnt = 0;
 }
 
-// Slow path for one 64-column piece whose running max reached a reject
-// threshold: recompute h = A - beta for the 64 pairs (r, col0 + j), classify
-// them against the piece's two (accept, reject) threshold pairs, and buffer
-// every proven match and band pair. Warp-collective; rarely taken.
-__device__ __forceinline__ uint32_t slow_piece(const TcParams &p, const uint32_t (&v)[64], const float *nb, float rx, float ry,
-                                            float eh0, float eh1, int r, int col0, uint2 *stg, uint32_t scnt)
+// Slow path for a 64-column piece that a chunk bound could not reject: for each
+// 32-column half that some lane could not reject, compute h = fl(A - beta) for
+// the pairs (r, col0 + j), classify them against the half's (accept, reject)
+// thresholds, and buffer every proven match and band pair. Warp-collective;
+// rarely taken.
+__device__ __forceinline__ uint32_t slow_piece(const TcParams &p, const uint32_t (&v)[64], const float *nb, float rx,
+                                              float ry, float eh0, float eh1, bool hit0, bool hit1, int r, int col0,
+                                              uint2 *stg, uint32_t scnt)
 {
     const unsigned lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh) {
+        if (!__any_sync(0xffffffffu, hh ? hit1 : hit0)) continue;
         const float eh = hh ? eh1 : eh0;
         const float tau_acc = __fadd_ru(rx, eh);
         const float tau_rej = __fsub_rd(ry, eh);
@@ -380,22 +385,18 @@ __global__ void __launch_bounds__(320, 1)
                 const float eh1 = __fmaf_ru(rp.z, cs1.x, __fmaf_ru(rp.w, cs1.y, cs1.z));
                 const float tr0 = __fsub_rd(rp.y, eh0);
                 const float tr1 = __fsub_rd(rp.y, eh1);
-                const float4 *nb4 = reinterpret_cast<const float4 *>(nbeta + piece * 64);
-                float m0[8], m1[8];
+                // Whole-chunk reject: with beta_j >= beta_min(chunk), every h_j = fl(A_j - beta_j)
+                // is <= fl_ru(max_j A_j - beta_min); rows are in norm order, so beta_min is tight.
+                float m0[16], m1[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    m0[i] = fmaxf(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+                    m1[i] = fmaxf(__uint_as_float(v[32 + 2 * i]), __uint_as_float(v[32 + 2 * i + 1]));
+                }
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    const float4 bb = nb4[i];
-                    const float4 bc = nb4[8 + i];
-                    const float2 x01 = __fadd2_rn(make_float2(__uint_as_float(v[4 * i + 0]), __uint_as_float(v[4 * i + 1])),
-                                                  make_float2(bb.x, bb.y));
-                    const float2 x23 = __fadd2_rn(make_float2(__uint_as_float(v[4 * i + 2]), __uint_as_float(v[4 * i + 3])),
-                                                  make_float2(bb.z, bb.w));
-                    const float2 y01 = __fadd2_rn(make_float2(__uint_as_float(v[32 + 4 * i + 0]), __uint_as_float(v[32 + 4 * i + 1])),
-                                                  make_float2(bc.x, bc.y));
-                    const float2 y23 = __fadd2_rn(make_float2(__uint_as_float(v[32 + 4 * i + 2]), __uint_as_float(v[32 + 4 * i + 3])),
-                                                  make_float2(bc.z, bc.w));
-                    m0[i] = fmaxf(fmaxf(x01.x, x01.y), fmaxf(x23.x, x23.y));
-                    m1[i] = fmaxf(fmaxf(y01.x, y01.y), fmaxf(y23.x, y23.y));
+                    m0[i] = fmaxf(m0[2 * i], m0[2 * i + 1]);
+                    m1[i] = fmaxf(m1[2 * i], m1[2 * i + 1]);
                 }
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
@@ -404,9 +405,11 @@ __global__ void __launch_bounds__(320, 1)
                 }
                 const float mx0 = fmaxf(fmaxf(m0[0], m0[1]), fmaxf(m0[2], m0[3]));
                 const float mx1 = fmaxf(fmaxf(m1[0], m1[1]), fmaxf(m1[2], m1[3]));
-                if (__any_sync(0xffffffffu, (mx0 >= tr0) || (mx1 >= tr1)))
-                    scnt = slow_piece(p, v, nbeta + piece * 64, rp.x, rp.y, eh0, eh1, r, colw + piece * 64, my_stg,
-                                      scnt);
+                const bool hit0 = __fsub_ru(mx0, cs0.w) >= tr0;
+                const bool hit1 = __fsub_ru(mx1, cs1.w) >= tr1;
+                if (__any_sync(0xffffffffu, hit0 || hit1))
+                    scnt = slow_piece(p, v, nbeta + piece * 64, rp.x, rp.y, eh0, eh1, hit0, hit1, r,
+                                      colw + piece * 64, my_stg, scnt);
             };
 
             // One 64-column load at a time: the other epilogue warp on this SM

@@ -124,6 +124,7 @@ extern "C" int dl_sim_join_noalloc(const float *R, const int64_t *r_ids, int64_t
     jo.band_cnt = cnt + 1;
     jo.band_cap = kNoAllocBandMax;
     jo.mirror = mirror ? 1 : 0;
+    jo.orig = nullptr;   // caller's row order is the store order here
 
     if (nR > 0 && nS > 0) {
         SimtParams sp;

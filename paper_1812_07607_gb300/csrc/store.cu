@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(256) k1_norm_quant(const float *__restrict__ x
 // One warp per 32-row chunk: column-side maxima of the BF16 error-bound terms,
 //   P1 = max ||x||,   P2 = max ||x - x~|| + (gamma_tc + 1.01 u) max ||x~||,
 //   P3 = max |beta err| + u max beta + absolute slack,
+//   and the chunk's smallest beta (for the epilogue's whole-chunk reject test),
 // so that for a query row q and any column x in the chunk the error of the
 // epilogue value h = fl(A~ - beta) is at most  rq * P1 + ||q~|| * P2 + P3.
 // Also fills beta's padding with +inf (padded columns can never match).
@@ -157,6 +158,7 @@ __global__ void __launch_bounds__(256) k1_chunk_stats(const float *__restrict__ 
     if (chunk * 32 >= n_pad) return;
     const int64_t row = chunk * 32 + lane;
     float rq = 0.f, nqt = 0.f, nx = 0.f, berr = 0.f, bt = 0.f;
+    float bmin = __int_as_float(0x7f800000);   // +inf: padding rows do not lower the chunk minimum
     if (row < n) {
         const float4 rb = rowb[row];
         rq = rb.x;
@@ -164,6 +166,7 @@ __global__ void __launch_bounds__(256) k1_chunk_stats(const float *__restrict__ 
         nx = rb.z;
         berr = rb.w;
         bt = fabsf(beta_in[row]);
+        bmin = beta_in[row];
     } else {
         beta[row] = __int_as_float(0x7f800000);   // +inf
     }
@@ -174,11 +177,109 @@ __global__ void __launch_bounds__(256) k1_chunk_stats(const float *__restrict__ 
         nx = fmaxf(nx, __shfl_xor_sync(0xffffffffu, nx, o));
         berr = fmaxf(berr, __shfl_xor_sync(0xffffffffu, berr, o));
         bt = fmaxf(bt, __shfl_xor_sync(0xffffffffu, bt, o));
+        bmin = fminf(bmin, __shfl_xor_sync(0xffffffffu, bmin, o));
     }
     if (lane == 0) {
         const float p2 = __fmaf_ru(g2, nqt, rq);
         const float p3 = __fadd_ru(__fmaf_ru(5.9604644775390625e-08f, bt, berr), p3_abs);
-        cstat[chunk] = make_float4(nx, p2, p3, 0.f);
+        cstat[chunk] = make_float4(nx, p2, p3, bmin);
+    }
+}
+
+// ------------------------------------------------------------------ norm ordering
+// A store keeps its rows ordered by squared norm (a bucket sort into 65,536
+// equal-width buckets between the smallest and largest norm; order inside a
+// bucket is arbitrary). Neighbouring rows then have nearly equal ||x||^2/2, so
+// the join epilogue can bound a whole 32-column chunk with the chunk's
+// smallest beta. The caller's row index of every store row is kept (orig).
+constexpr int kSortBuckets = 65536;
+
+__global__ void __launch_bounds__(256) k_sort_keys(const float *__restrict__ x, int64_t n, int d,
+                                                   float *__restrict__ keys, unsigned *__restrict__ minmax)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * 8 + warp;
+    if (row >= n) return;
+    const float *xr = x + row * d;
+    float s = 0.f;
+    for (int k = lane; k < d; k += 32) {
+        const float v = __ldg(xr + k);
+        s = fmaf(v, v, s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        if (!(s <= 3.0e38f)) s = 3.0e38f;   // non-finite rows are rejected later; keep the key ordered
+        keys[row] = s;
+        atomicMin(minmax + 0, __float_as_uint(s));   // non-negative floats order like their bits
+        atomicMax(minmax + 1, __float_as_uint(s));
+    }
+}
+
+__device__ __forceinline__ int sort_bucket(float k, const unsigned *minmax)
+{
+    const float lo = __uint_as_float(minmax[0]), hi = __uint_as_float(minmax[1]);
+    if (!(hi > lo)) return 0;
+    const float f = (k - lo) / (hi - lo) * (float)kSortBuckets;
+    int b = (int)f;
+    return b < 0 ? 0 : (b >= kSortBuckets ? kSortBuckets - 1 : b);
+}
+
+__global__ void __launch_bounds__(256) k_sort_hist(const float *__restrict__ keys, int64_t n,
+                                                   const unsigned *__restrict__ minmax, unsigned *__restrict__ hist)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(hist + sort_bucket(keys[i], minmax), 1u);
+}
+
+// Exclusive prefix sum of the 65,536 bucket counts, one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_sort_scan(unsigned *__restrict__ hist)
+{
+    __shared__ unsigned part[1024];
+    constexpr int kPer = kSortBuckets / 1024;
+    const int t = threadIdx.x;
+    unsigned loc = 0;
+    for (int i = 0; i < kPer; ++i) loc += hist[t * kPer + i];
+    part[t] = loc;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const unsigned v = (t >= off) ? part[t - off] : 0u;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    unsigned run = part[t] - loc;
+    for (int i = 0; i < kPer; ++i) {
+        const unsigned c = hist[t * kPer + i];
+        hist[t * kPer + i] = run;
+        run += c;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_sort_scatter(const float *__restrict__ keys, int64_t n,
+                                                      const unsigned *__restrict__ minmax, unsigned *__restrict__ offs,
+                                                      int32_t *__restrict__ perm)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) perm[atomicAdd(offs + sort_bucket(keys[i], minmax), 1u)] = (int32_t)i;
+}
+
+// Store row i <- caller row perm[i] (features and id), one warp per row.
+__global__ void __launch_bounds__(256) k_gather_rows(const float *__restrict__ src, const int64_t *__restrict__ src_ids,
+                                                     const int32_t *__restrict__ perm, int64_t n, int d,
+                                                     float *__restrict__ dst, int64_t *__restrict__ dst_ids,
+                                                     int32_t *__restrict__ orig)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * 8 + warp;
+    if (row >= n) return;
+    const int32_t j = perm[row];
+    const float *sr = src + (int64_t)j * d;
+    float *dr = dst + row * d;
+    for (int k = lane; k < d; k += 32) dr[k] = __ldg(sr + k);
+    if (lane == 0) {
+        dst_ids[row] = src_ids[j];
+        orig[row] = j;
     }
 }
 
@@ -278,11 +379,12 @@ int dl_store_create(dl_store **out, const int64_t *ids, const float *feats, int6
     if (s->n_pad == 0) s->n_pad = 256;
     DL_CUDA_TRY(cudaGetDevice(&s->device));
 
-    const size_t b_ids = align256(sizeof(int64_t) * n), b_x32 = align256(sizeof(float) * n * d),
-                 b_xb = align256(sizeof(__nv_bfloat16) * n * s->dp), b_nq = align256(sizeof(double) * n),
-                 b_beta = align256(sizeof(float) * s->n_pad), b_rowb = align256(sizeof(float4) * n),
-                 b_cst = align256(sizeof(float4) * (s->n_pad / 32)), b_err = 256;
-    const size_t total = b_ids + b_x32 + b_xb + b_nq + b_beta + b_rowb + b_cst + b_err;
+    const size_t b_ids = align256(sizeof(int64_t) * n), b_orig = align256(sizeof(int32_t) * n),
+                 b_x32 = align256(sizeof(float) * n * d), b_xb = align256(sizeof(__nv_bfloat16) * n * s->dp),
+                 b_nq = align256(sizeof(double) * n), b_beta = align256(sizeof(float) * s->n_pad),
+                 b_rowb = align256(sizeof(float4) * n), b_cst = align256(sizeof(float4) * (s->n_pad / 32)),
+                 b_err = 256;
+    const size_t total = b_ids + b_orig + b_x32 + b_xb + b_nq + b_beta + b_rowb + b_cst + b_err;
     void *base = nullptr;
     int rc = dev_alloc(&base, total, st);
     if (rc != DL_OK) {
@@ -292,6 +394,8 @@ int dl_store_create(dl_store **out, const int64_t *ids, const float *feats, int6
     char *p = (char *)base;
     s->ids = (int64_t *)p;
     p += b_ids;
+    s->orig = (int32_t *)p;
+    p += b_orig;
     s->x32 = (float *)p;
     p += b_x32;
     s->xb = (__nv_bfloat16 *)p;
@@ -306,21 +410,59 @@ int dl_store_create(dl_store **out, const int64_t *ids, const float *feats, int6
     p += b_cst;
     int *d_err = (int *)p;
 
+    // scratch for the norm ordering (and for host inputs, the uploaded rows)
+    const bool host = (where == DL_MEM_HOST);
+    const size_t t_x = host ? align256(sizeof(float) * n * d) : 0, t_ids = host ? align256(sizeof(int64_t) * n) : 0,
+                 t_keys = align256(sizeof(float) * n), t_perm = align256(sizeof(int32_t) * n),
+                 t_hist = sizeof(unsigned) * kSortBuckets, t_mm = 256;
+    void *tmp = nullptr;
+    if (n > 0) {
+        rc = dev_alloc(&tmp, t_x + t_ids + t_keys + t_perm + t_hist + t_mm, st);
+        if (rc != DL_OK) {
+            dev_free(base, st);
+            delete s;
+            return rc;
+        }
+    }
     auto fail = [&](int code) {
         dev_free(base, st);
+        dev_free(tmp, st);
         cudaStreamSynchronize(st);
         delete s;
         return code;
     };
-    const cudaMemcpyKind kind = (where == DL_MEM_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
-    if (e == cudaSuccess && n > 0) e = cudaMemcpyAsync(s->ids, ids, sizeof(int64_t) * n, kind, st);
-    if (e == cudaSuccess && n > 0) e = cudaMemcpyAsync(s->x32, feats, sizeof(float) * n * d, kind, st);
-    if (e != cudaSuccess) return fail(cuda_fail(e, "dl_store_create copy"));
+    if (e != cudaSuccess) return fail(cuda_fail(e, "dl_store_create memset"));
     if (n > 0) {
-        k1_norm_quant<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(s->x32, n, d, s->dp, s->xb, s->nq64, s->beta, s->rowb,
-                                                               d_err);
-        count_launch();
+        char *q = (char *)tmp;
+        const float *src_x = feats;
+        const int64_t *src_ids = ids;
+        if (host) {
+            float *hx = (float *)q;
+            int64_t *hid = (int64_t *)(q + t_x);
+            e = cudaMemcpyAsync(hx, feats, sizeof(float) * n * d, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hid, ids, sizeof(int64_t) * n, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return fail(cuda_fail(e, "dl_store_create upload"));
+            src_x = hx;
+            src_ids = hid;
+        }
+        q += t_x + t_ids;
+        float *keys = (float *)q;
+        int32_t *perm = (int32_t *)(q + t_keys);
+        unsigned *hist = (unsigned *)(q + t_keys + t_perm);
+        unsigned *mm = (unsigned *)(q + t_keys + t_perm + t_hist);
+        e = cudaMemsetAsync(hist, 0, t_hist, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(mm, 0xff, 4, st);      // min <- 0xffffffff
+        if (e == cudaSuccess) e = cudaMemsetAsync(mm + 1, 0, 4, st);     // max <- 0
+        if (e != cudaSuccess) return fail(cuda_fail(e, "dl_store_create memset"));
+        const unsigned gw = (unsigned)((n + 7) / 8), gt = (unsigned)((n + 255) / 256);
+        k_sort_keys<<<gw, 256, 0, st>>>(src_x, n, d, keys, mm);
+        k_sort_hist<<<gt, 256, 0, st>>>(keys, n, mm, hist);
+        k_sort_scan<<<1, 1024, 0, st>>>(hist);
+        k_sort_scatter<<<gt, 256, 0, st>>>(keys, n, mm, hist, perm);
+        k_gather_rows<<<gw, 256, 0, st>>>(src_x, src_ids, perm, n, d, s->x32, s->ids, s->orig);
+        k1_norm_quant<<<gw, 256, 0, st>>>(s->x32, n, d, s->dp, s->xb, s->nq64, s->beta, s->rowb, d_err);
+        count_launch(6);
     }
     const float g2 = f32_ru(gamma_tc(s->dp) + 1.01 * kU32);
     const float p3a = f32_ru(abs_slack_tc(s->dp));
@@ -337,6 +479,7 @@ int dl_store_create(dl_store **out, const int64_t *ids, const float *feats, int6
         set_error("dl_store_create: a feature is non-finite or exceeds 2^40 in magnitude");
         return fail(DL_EINVAL);
     }
+    dev_free(tmp, st);
     *out = s;
     return DL_OK;
 }
