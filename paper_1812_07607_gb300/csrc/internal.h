@@ -76,6 +76,7 @@ struct Store {
     float4 *cstat = nullptr; // [n_pad / 32] per 32-row chunk {P1, P2, P3, min beta} of the BF16 bound
     TmapCache tmaps[3];      // box rows 128, 256, 128-for-B (cached per box height)
     std::mutex mu;           // guards tmaps and hints
+    float nq_max = 0.f;      // largest ||x||^2 of the store (FP32 sum; used only inside slack terms)
     int64_t hint_pairs = 0;  // last output size seen with this store as R (capacity hint)
     int64_t hint_band = 0;
 };

@@ -153,7 +153,76 @@ __device__ __forceinline__ uint32_t slow_piece(const TcParams &p, const uint32_t
     return scnt;
 }
 
-template <int BN>
+// ---------------------------------------------------------------- top-k epilogue
+// A slot's state is (theta, list fill) in registers plus, in global memory, a
+// min-heap of the k largest lower bounds L = fl_rd(h - E) seen so far (theta is
+// its minimum: at least k columns have h >= theta) and the list of every column
+// whose upper bound U = fl_ru(h + E) reached theta when it was seen. Every true
+// top-k column has U >= h >= the k-th largest h >= theta, so it is in the list.
+// Returns the new (theta, fill) packed in a float2.
+__device__ __noinline__ float2 topk_insert(const TcParams &p, size_t sidx, int r, int c, float U, float L,
+                                           float theta, int cnt)
+{
+    uint2 *list = p.tk_list + sidx * (size_t)p.tk_cap;
+    if (cnt >= p.tk_cap) {   // compact: drop columns whose upper bound fell below theta
+        int w = 0;
+        for (int i = 0; i < cnt; ++i) {
+            const uint2 e = list[i];
+            if (__uint_as_float(e.y) >= theta) list[w++] = e;
+        }
+        cnt = w;
+        if (cnt >= p.tk_cap) {
+            p.tk_overflow[r] = 1;   // the exact fallback re-solves this row
+            return make_float2(theta, __int_as_float(cnt));
+        }
+    }
+    list[cnt++] = make_uint2((uint32_t)c, __float_as_uint(U));
+    if (L > theta) {
+        float *heap = p.tk_heap + sidx * (size_t)p.tk_k;
+        const int k = p.tk_k;
+        int i = 0;
+        while (true) {   // replace the minimum by L and sift down
+            const int l = 2 * i + 1;
+            if (l >= k) break;
+            const int rr = l + 1;
+            const int m = (rr < k && heap[rr] < heap[l]) ? rr : l;
+            const float hm = heap[m];
+            if (hm >= L) break;
+            heap[i] = hm;
+            i = m;
+        }
+        heap[i] = L;
+        theta = heap[0];
+    }
+    return make_float2(theta, __int_as_float(cnt));
+}
+
+// Top-k slow path for a 64-column piece some lane could not reject: each lane
+// walks its own row's columns whose upper bound reaches its theta.
+__device__ __forceinline__ void slow_topk(const TcParams &p, const uint32_t (&v)[64], const float *nb, float eh0,
+                                          float eh1, bool hit0, bool hit1, int r, int col0, size_t sidx,
+                                          float &theta, int &cnt)
+{
+    if (r >= p.nR) return;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+        if (!(hh ? hit1 : hit0)) continue;
+        const float eh = hh ? eh1 : eh0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int c = col0 + hh * 32 + j;
+            const float h = __uint_as_float(v[hh * 32 + j]) + nb[hh * 32 + j];
+            const float U = __fadd_ru(h, eh);
+            if (c < p.nS && U >= theta) {
+                const float2 st = topk_insert(p, sidx, r, c, U, __fsub_rd(h, eh), theta, cnt);
+                theta = st.x;
+                cnt = __float_as_int(st.y);
+            }
+        }
+    }
+}
+
+template <int BN, bool TOPK>
 __global__ void __launch_bounds__(320, 1)
     tc_join_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcParams p)
@@ -359,9 +428,23 @@ __global__ void __launch_bounds__(320, 1)
         uint32_t t = 0;
         bool ok = true;
         float4 rp = make_float4(0.f, 0.f, 0.f, 0.f);
+        float theta = 0.f;        // top-k: this slot's threshold (k-th largest lower bound of h)
+        int tcnt = 0;             // top-k: this slot's list fill
+        size_t sidx = 0;
         while (cur.valid) {
             const int r = cur.un.x * 128 + quad * 32 + lane;
-            if (cur.n == cur.un.y) rp = p.rowpar[r];
+            if (cur.n == cur.un.y) {
+                rp = p.rowpar[r];
+                if constexpr (TOPK) {   // a unit owns its (row tile, split): start the slots fresh
+                    sidx = (size_t)r * p.tk_slots + (size_t)cur.un.w * 2 + half;
+                    theta = __int_as_float(0xff800000);
+                    tcnt = 0;
+                    if (r < p.nR) {
+                        float *heap = p.tk_heap + sidx * (size_t)p.tk_k;
+                        for (int i = 0; i < p.tk_k; ++i) heap[i] = __int_as_float(0xff800000);
+                    }
+                }
+            }
             float nbn[kPer];
             float4 csn = make_float4(0.f, 0.f, 0.f, 0.f);
             stage_regs(nxt, nbn, csn);   // prefetch the next tile's -beta (latency hidden by this tile)
@@ -383,8 +466,14 @@ __global__ void __launch_bounds__(320, 1)
                 const float4 cs0 = cst[2 * piece], cs1 = cst[2 * piece + 1];
                 const float eh0 = __fmaf_ru(rp.z, cs0.x, __fmaf_ru(rp.w, cs0.y, cs0.z));
                 const float eh1 = __fmaf_ru(rp.z, cs1.x, __fmaf_ru(rp.w, cs1.y, cs1.z));
-                const float tr0 = __fsub_rd(rp.y, eh0);
-                const float tr1 = __fsub_rd(rp.y, eh1);
+                float tr0, tr1;
+                if constexpr (TOPK) {   // candidate iff h + E (+ canonical slack rp.x) >= theta
+                    tr0 = __fsub_rd(theta, __fadd_ru(eh0, rp.x));
+                    tr1 = __fsub_rd(theta, __fadd_ru(eh1, rp.x));
+                } else {
+                    tr0 = __fsub_rd(rp.y, eh0);
+                    tr1 = __fsub_rd(rp.y, eh1);
+                }
                 // Whole-chunk reject: with beta_j >= beta_min(chunk), every h_j = fl(A_j - beta_j)
                 // is <= fl_ru(max_j A_j - beta_min); rows are in norm order, so beta_min is tight.
                 float m0[16], m1[16];
@@ -407,9 +496,15 @@ __global__ void __launch_bounds__(320, 1)
                 const float mx1 = fmaxf(fmaxf(m1[0], m1[1]), fmaxf(m1[2], m1[3]));
                 const bool hit0 = __fsub_ru(mx0, cs0.w) >= tr0;
                 const bool hit1 = __fsub_ru(mx1, cs1.w) >= tr1;
-                if (__any_sync(0xffffffffu, hit0 || hit1))
-                    scnt = slow_piece(p, v, nbeta + piece * 64, rp.x, rp.y, eh0, eh1, hit0, hit1, r,
-                                      colw + piece * 64, my_stg, scnt);
+                if constexpr (TOPK) {
+                    if (hit0 || hit1)
+                        slow_topk(p, v, nbeta + piece * 64, __fadd_ru(eh0, rp.x), __fadd_ru(eh1, rp.x), hit0, hit1, r,
+                                  colw + piece * 64, sidx, theta, tcnt);
+                } else {
+                    if (__any_sync(0xffffffffu, hit0 || hit1))
+                        scnt = slow_piece(p, v, nbeta + piece * 64, rp.x, rp.y, eh0, eh1, hit0, hit1, r,
+                                          colw + piece * 64, my_stg, scnt);
+                }
             };
 
             // One 64-column load at a time: the other epilogue warp on this SM
@@ -429,13 +524,19 @@ __global__ void __launch_bounds__(320, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(acc_empty + b);   // TMEM buffer free; the rest is in registers
             process64(va, HC == 128 ? 1 : 0);
+            if constexpr (TOPK) {
+                if (cur.n + 1 == cur.un.z && r < p.nR) {   // last tile of the unit: publish the slot
+                    p.tk_theta[sidx] = theta;
+                    p.tk_cnt[sidx] = tcnt;
+                }
+            }
             // publish the next tile's -beta into the other slot (this warp's own copy)
             stage_store(slot ^ 1, nbn, csn);
             cur = nxt;
             nxt.next(p);
             ++t;
         }
-        flush_stage(p, my_stg, scnt);
+        if constexpr (!TOPK) flush_stage(p, my_stg, scnt);
         if (!ok) {
             *abort_flag = 1;
             atomicExch(p.err, 1);
@@ -477,28 +578,34 @@ void tc_plan(int BN, int kc, int *stages, int *a_slots)
     }
 }
 
-int launch_tc_join(const TcLaunch &L, cudaStream_t st)
+template <int BN, bool TOPK>
+static int launch_one(const TcLaunch &L, size_t smem, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(tc_join_kernel<BN, TOPK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_join_kernel)");
+    tc_join_kernel<BN, TOPK><<<L.grid, 320, smem, st>>>(*L.tmA, *L.tmB, L.p);
+    return DL_OK;
+}
+
+int launch_tc_join(const TcLaunch &L, cudaStream_t st, bool topk)
 {
     const size_t smem = tc_smem_bytes(L.BN, L.p.kc, L.p.stages, L.p.a_slots);
     if (L.p.stages < 2 || smem > 232448) {
         set_error("tensor-core join: no shared-memory plan for d=%d, tile %d", L.p.kc * 64, L.BN);
         return DL_EUNSUPPORTED;
     }
-    cudaError_t e;
-    if (L.BN == 256) {
-        e = cudaFuncSetAttribute(tc_join_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_join_kernel<256>)");
-        tc_join_kernel<256><<<L.grid, 320, smem, st>>>(*L.tmA, *L.tmB, L.p);
-    } else if (L.BN == 128) {
-        e = cudaFuncSetAttribute(tc_join_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_join_kernel<128>)");
-        tc_join_kernel<128><<<L.grid, 320, smem, st>>>(*L.tmA, *L.tmB, L.p);
-    } else {
+    int rc;
+    if (L.BN == 256)
+        rc = topk ? launch_one<256, true>(L, smem, st) : launch_one<256, false>(L, smem, st);
+    else if (L.BN == 128)
+        rc = topk ? launch_one<128, true>(L, smem, st) : launch_one<128, false>(L, smem, st);
+    else {
         set_error("tensor-core tile width %d not supported (128 or 256)", L.BN);
         return DL_EINVAL;
     }
+    if (rc) return rc;
     count_launch();
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "tc_join_kernel launch");
     return DL_OK;
 }

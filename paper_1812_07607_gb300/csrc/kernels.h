@@ -24,6 +24,15 @@ struct TcParams {
     unsigned long long *cand_cnt;
     unsigned long long cand_cap;
     int *err;                // set to 1 when a bounded wait expired
+    // top-k epilogue (units carry the S split in .w; state per (row, split, half) slot)
+    int tk_k;                // k
+    int tk_cap;              // candidate-list capacity per slot
+    int tk_slots;            // slots per row (2 x splits)
+    float *tk_heap;          // [rows][slots][k] min-heap of the k largest lower bounds of h
+    uint2 *tk_list;          // [rows][slots][cap] {column, float bits of the upper bound of h}
+    int *tk_cnt;             // [rows][slots] list fill
+    float *tk_theta;         // [rows][slots] final threshold (heap minimum)
+    int *tk_overflow;        // [rows] set when a list cannot hold every candidate
 };
 
 // Candidate entry flag: set for a band pair (needs the exact recheck).
@@ -37,7 +46,7 @@ struct TcLaunch {
 };
 
 void tc_plan(int BN, int kc, int *stages, int *a_slots);
-int launch_tc_join(const TcLaunch &L, cudaStream_t st);
+int launch_tc_join(const TcLaunch &L, cudaStream_t st, bool topk = false);
 
 // ---- K8 SIMT FP32 join (join_simt.cu)
 struct SimtParams {

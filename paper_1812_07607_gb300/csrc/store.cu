@@ -472,12 +472,23 @@ int dl_store_create(dl_store **out, const int64_t *ids, const float *feats, int6
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(cuda_fail(e, "store kernels launch"));
     int h_err = 0;
+    unsigned h_mm[2] = {0u, 0u};
+    if (n > 0) {
+        const unsigned *mm = (const unsigned *)((char *)tmp + t_x + t_ids + t_keys + t_perm + t_hist);
+        e = cudaMemcpyAsync(h_mm, mm, sizeof h_mm, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "dl_store_create readback"));
+    }
     e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(cuda_fail(e, "dl_store_create sync"));
     if (h_err) {
         set_error("dl_store_create: a feature is non-finite or exceeds 2^40 in magnitude");
         return fail(DL_EINVAL);
+    }
+    {
+        float mx;
+        std::memcpy(&mx, &h_mm[1], sizeof mx);
+        s->nq_max = mx;
     }
     dev_free(tmp, st);
     *out = s;

@@ -1,5 +1,350 @@
-// topk.cu -- top-k join (Sec. 6.2 q1: nearest image to a query image, generalised to k).
+// topk.cu -- the top-k join (K4 + K7): for every query row, the k store rows
+// with the smallest canonical distance, ordered by (distance, store row).
+//
+// The paper's reverse-image-search query (Sec. 6.2, q1: the closest image to a
+// query image) is the k = 1 case. Pipeline on the caller's stream:
+//   k_rowpar_topk      per query row: the bound terms and the canonical slack;
+//   tc_join_kernel<.., true>   the tensor-core pass with the top-k epilogue: per
+//                      (row, S split, epilogue half) slot a running threshold
+//                      theta (k-th largest lower bound of h = q.x - ||x||^2/2)
+//                      and the list of every column whose upper bound reached it;
+//   k_topk_finalize    per row, one warp: union of the slots' lists above the
+//                      largest theta, FP32 distances with their error bound, the
+//                      k-th smallest upper bound, then the canonical FP64
+//                      distance of every column that can still be in the top k
+//                      and an exact rank by (D64, caller's store row index);
+//   k_topk_fallback    rows whose lists overflowed (many near-ties) or whose
+//                      candidates exceed the finalize buffer: an exact scan of
+//                      the whole store for that row (FP32 bound + radix select +
+//                      FP64 + rank).
+// Store rows are in norm order; outputs are written at the caller's row order.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
 #include "kernels.h"
+
+namespace dl {
+
+constexpr int kTkMax = 512;          // candidates a finalize warp holds in shared memory
+constexpr int kTkFallbackCap = 8192; // candidates a fallback block can rank
+
+struct TopkFin {
+    const float *Q, *S;
+    int d, nQ, nS, k, slots, cap;
+    const float *theta;
+    const int *cnt;
+    const uint2 *list;
+    int *overflow;
+    const int32_t *q_orig, *s_orig;
+    const int64_t *s_ids;
+    int64_t *out_ids;
+    double *out_d2;
+    float g32, abs32;      // FP32 distance bound: |D32 - D| <= g32 * D + abs32
+    float slack;           // canonical slack factor for the keep test (relative)
+    unsigned long long *n_fp64;
+};
+
+__device__ __forceinline__ double canon_d64(const float *__restrict__ q, const float *__restrict__ x, int d)
+{
+    double s = 0.0;
+    for (int k = 0; k < d; ++k) {
+        const double t = __dsub_rn((double)__ldg(q + k), (double)__ldg(x + k));
+        s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    return s;
+}
+
+__device__ __forceinline__ float seq_d32(const float *__restrict__ q, const float *__restrict__ x, int d)
+{
+    float s = 0.f;
+    for (int k = 0; k < d; ++k) {
+        const float t = __ldg(q + k) - __ldg(x + k);
+        s = fmaf(t, t, s);
+    }
+    return s;
+}
+
+__global__ void __launch_bounds__(128) k_topk_finalize(const TopkFin f)
+{
+    __shared__ uint32_t s_col[4][kTkMax];
+    __shared__ float s_u[4][kTkMax];
+    __shared__ float s_l[4][kTkMax];
+    __shared__ double s_d[4][kTkMax];
+    __shared__ float s_kth[4];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    uint32_t *col = s_col[w];
+    float *su = s_u[w], *sl = s_l[w];
+    double *sd = s_d[w];
+    for (int i = blockIdx.x * 4 + w; i < f.nQ; i += gridDim.x * 4) {
+        if (f.overflow[i]) continue;
+        // largest theta over the row's slots: every top-k column has U >= it
+        float th = __int_as_float(0xff800000);
+        for (int s = lane; s < f.slots; s += 32) th = fmaxf(th, f.theta[(size_t)i * f.slots + s]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) th = fmaxf(th, __shfl_xor_sync(0xffffffffu, th, o));
+        int m = 0;
+        for (int s = 0; s < f.slots; ++s) {
+            const size_t si = (size_t)i * f.slots + s;
+            const int cs = f.cnt[si];
+            const uint2 *L = f.list + si * (size_t)f.cap;
+            for (int b = 0; b < cs; b += 32) {
+                const int idx = b + lane;
+                uint2 e = make_uint2(0u, 0u);
+                if (idx < cs) e = L[idx];
+                const bool keep = idx < cs && __uint_as_float(e.y) >= th;
+                const unsigned bm = __ballot_sync(0xffffffffu, keep);
+                const int pos = m + __popc(bm & lt);
+                if (keep && pos < kTkMax) col[pos] = e.x;
+                m += __popc(bm);
+            }
+        }
+        if (m > kTkMax) {   // too many candidates for this buffer: exact fallback
+            if (lane == 0) f.overflow[i] = 1;
+            continue;
+        }
+        __syncwarp();
+        const float *q = f.Q + (size_t)i * f.d;
+        for (int a = lane; a < m; a += 32) {
+            const float d32 = seq_d32(q, f.S + (size_t)col[a] * f.d, f.d);
+            su[a] = __fadd_ru(__fmul_ru(d32, 1.0f + f.g32), f.abs32);
+            sl[a] = __fsub_rd(__fmul_rd(d32, 1.0f - f.g32), f.abs32);
+        }
+        __syncwarp();
+        // k-th smallest upper bound (ties broken by position) -> at least k columns have D <= kth
+        if (lane == 0) s_kth[w] = __int_as_float(0x7f800000);
+        __syncwarp();
+        if (m > f.k) {
+            for (int a = lane; a < m; a += 32) {
+                int rank = 0;
+                const float ua = su[a];
+                for (int b = 0; b < m; ++b) rank += (su[b] < ua) || (su[b] == ua && b < a);
+                if (rank == f.k - 1) s_kth[w] = ua;
+            }
+        }
+        __syncwarp();
+        const float kth = __fmul_ru(s_kth[w], 1.0f + f.slack);
+        int kept = 0;
+        for (int a0 = 0; a0 < m; a0 += 32) {
+            const int a = a0 + lane;
+            const bool keep = a < m && sl[a] <= kth;
+            if (a < m) sd[a] = keep ? canon_d64(q, f.S + (size_t)col[a] * f.d, f.d) : __longlong_as_double(0x7ff0000000000000LL);
+            const unsigned bm = __ballot_sync(0xffffffffu, keep);
+            kept += __popc(bm);
+            if (lane == 0 && bm) atomicAdd(f.n_fp64, (unsigned long long)__popc(bm));
+        }
+        __syncwarp();
+        const int oi = f.q_orig[i];
+        int64_t *oid = f.out_ids + (size_t)oi * f.k;
+        double *od = f.out_d2 + (size_t)oi * f.k;
+        for (int a = lane; a < m; a += 32) {
+            const double da = sd[a];
+            if (!(da < __longlong_as_double(0x7ff0000000000000LL))) continue;   // not kept
+            const int32_t oa = f.s_orig[col[a]];
+            int rank = 0;
+            for (int b = 0; b < m; ++b) {
+                const double db = sd[b];
+                rank += (db < da) || (db == da && f.s_orig[col[b]] < oa);
+            }
+            if (rank < f.k) {
+                oid[rank] = f.s_ids[col[a]];
+                od[rank] = da;
+            }
+        }
+        for (int t = kept + lane; t < f.k; t += 32) {
+            oid[t] = -1;
+            od[t] = -1.0;
+        }
+        __syncwarp();
+    }
+}
+
+struct TopkFb {
+    const float *Q, *S;
+    int d, nS, k;
+    const int *rows;        // flagged query rows (store order)
+    int n_rows;
+    float *scr_u, *scr_l;   // [n_rows][nS]
+    uint32_t *scr_c;        // [n_rows][kTkFallbackCap]
+    double *scr_d;          // [n_rows][kTkFallbackCap]
+    const int32_t *q_orig, *s_orig;
+    const int64_t *s_ids;
+    int64_t *out_ids;
+    double *out_d2;
+    float g32, abs32, slack;
+    int *err;               // set to 1 when a row has more near-ties than the fallback can rank
+    unsigned long long *n_fp64;
+};
+
+// One block per flagged row: exact scan of the whole store.
+__global__ void __launch_bounds__(256) k_topk_fallback(const TopkFb f)
+{
+    __shared__ unsigned hist[256];
+    __shared__ unsigned s_prefix, s_rank;
+    __shared__ int s_m;
+    const int b = blockIdx.x;
+    if (b >= f.n_rows) return;
+    const int i = f.rows[b];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    float *u = f.scr_u + (size_t)b * f.nS;
+    float *l = f.scr_l + (size_t)b * f.nS;
+    uint32_t *cl = f.scr_c + (size_t)b * kTkFallbackCap;
+    double *cd = f.scr_d + (size_t)b * kTkFallbackCap;
+    const float *q = f.Q + (size_t)i * f.d;
+    // 1. FP32 distance bounds to every store row
+    for (int j = warp; j < f.nS; j += nw) {
+        const float *x = f.S + (size_t)j * f.d;
+        float s = 0.f;
+        for (int k = lane; k < f.d; k += 32) {
+            const float t = __ldg(q + k) - __ldg(x + k);
+            s = fmaf(t, t, s);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            u[j] = __fadd_ru(__fmul_ru(s, 1.0f + f.g32), f.abs32);
+            l[j] = __fsub_rd(__fmul_rd(s, 1.0f - f.g32), f.abs32);
+        }
+    }
+    __syncthreads();
+    // 2. k-th smallest upper bound by radix select on the (non-negative) float bits
+    float kth = __int_as_float(0x7f800000);
+    if (f.nS > f.k) {
+        if (tid == 0) {
+            s_prefix = 0u;
+            s_rank = (unsigned)(f.k - 1);
+        }
+        for (int shift = 24; shift >= 0; shift -= 8) {
+            for (int t = tid; t < 256; t += blockDim.x) hist[t] = 0u;
+            __syncthreads();
+            const unsigned pre = s_prefix;
+            const unsigned mask_hi = (shift == 24) ? 0u : (0xffffffffu << (shift + 8));
+            for (int j = tid; j < f.nS; j += blockDim.x) {
+                const unsigned v = __float_as_uint(u[j]);
+                if ((v & mask_hi) == (pre & mask_hi)) atomicAdd(&hist[(v >> shift) & 255u], 1u);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                unsigned r = s_rank, acc = 0u;
+                int dg = 0;
+                for (; dg < 256; ++dg) {
+                    if (acc + hist[dg] > r) break;
+                    acc += hist[dg];
+                }
+                s_rank = r - acc;
+                s_prefix = pre | ((unsigned)dg << shift);
+            }
+            __syncthreads();
+        }
+        kth = __uint_as_float(s_prefix);
+    }
+    kth = __fmul_ru(kth, 1.0f + f.slack);
+    // 3. every row whose lower bound is within the k-th upper bound
+    if (tid == 0) s_m = 0;
+    __syncthreads();
+    for (int j = tid; j < f.nS; j += blockDim.x) {
+        if (l[j] <= kth) {
+            const int pos = atomicAdd(&s_m, 1);
+            if (pos < kTkFallbackCap) cl[pos] = (uint32_t)j;
+        }
+    }
+    __syncthreads();
+    const int m = s_m;
+    if (m > kTkFallbackCap) {
+        if (tid == 0) atomicExch(f.err, 1);
+        return;
+    }
+    // 4. canonical distances, 5. exact rank by (D64, caller's store row)
+    for (int a = tid; a < m; a += blockDim.x) cd[a] = canon_d64(q, f.S + (size_t)cl[a] * f.d, f.d);
+    if (tid == 0) atomicAdd(f.n_fp64, (unsigned long long)m);
+    __syncthreads();
+    const int oi = f.q_orig[i];
+    int64_t *oid = f.out_ids + (size_t)oi * f.k;
+    double *od = f.out_d2 + (size_t)oi * f.k;
+    for (int a = tid; a < m; a += blockDim.x) {
+        const double da = cd[a];
+        const int32_t oa = f.s_orig[cl[a]];
+        int rank = 0;
+        for (int bb = 0; bb < m; ++bb) {
+            const double db = cd[bb];
+            rank += (db < da) || (db == da && f.s_orig[cl[bb]] < oa);
+        }
+        if (rank < f.k) {
+            oid[rank] = f.s_ids[cl[a]];
+            od[rank] = da;
+        }
+    }
+    for (int t = m + tid; t < f.k; t += blockDim.x) {
+        oid[t] = -1;
+        od[t] = -1.0;
+    }
+}
+
+// Per query row: {canonical slack of h, unused, ||q - q~|| up, ||q~|| up}; padding rows get zeros.
+__global__ void __launch_bounds__(256) k_rowpar_topk(const double *__restrict__ nq64, const float4 *__restrict__ rowb,
+                                                     int64_t n, int64_t n_tot, double g64, double nq_max_s,
+                                                     float4 *__restrict__ rowpar)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_tot) return;
+    if (i >= n) {
+        rowpar[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    // |h_canonical - h| <= |D64 - D| / 2 <= g64 * (||q||^2 + ||x||^2); doubled for margin
+    const double delta = 2.0 * g64 * (nq64[i] + nq_max_s) * 1.0001 + 1e-30;
+    const float4 rb = rowb[i];
+    rowpar[i] = make_float4(__double2float_ru(delta), 0.f, rb.x, rb.y);
+}
+
+__global__ void k_collect_overflow(const int *__restrict__ overflow, int n, int *__restrict__ rows,
+                                   int *__restrict__ count)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && overflow[i]) rows[atomicAdd(count, 1)] = i;
+}
+
+// ------------------------------------------------------------------ units with S splits
+static std::mutex g_tku_mu;
+static std::map<std::tuple<int, int64_t, int64_t, int, int>, std::pair<int4 *, int>> g_tku;
+
+static int topk_units(int64_t nQ, int64_t nS, int BN, int splits, const int4 **d_units, int *n_units)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto key = std::make_tuple(dev, nQ, nS, BN, splits);
+    std::lock_guard<std::mutex> lk(g_tku_mu);
+    auto it = g_tku.find(key);
+    if (it == g_tku.end()) {
+        const int mt = (int)((nQ + 127) / 128), nt = (int)((nS + BN - 1) / BN);
+        std::vector<int4> v;
+        for (int m = 0; m < mt; ++m)
+            for (int s = 0; s < splits; ++s) {
+                const int nb = (int)((int64_t)nt * s / splits), ne = (int)((int64_t)nt * (s + 1) / splits);
+                if (ne > nb) v.push_back(make_int4(m, nb, ne, s));
+            }
+        int4 *d = nullptr;
+        if (!v.empty()) {
+            cudaError_t e = cudaMalloc(&d, v.size() * sizeof(int4));
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(topk units)");
+            e = cudaMemcpy(d, v.data(), v.size() * sizeof(int4), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(topk units)");
+        }
+        it = g_tku.emplace(key, std::make_pair(d, (int)v.size())).first;
+    }
+    *d_units = it->second.first;
+    *n_units = it->second.second;
+    return DL_OK;
+}
+
+static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace dl
 
 using namespace dl;
 
@@ -7,12 +352,293 @@ extern "C" int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric
                             dl_result **out)
 {
     clear_error();
-    (void)Q;
-    (void)S;
-    (void)metric;
-    (void)k;
-    (void)opts;
-    if (out) *out = nullptr;
-    set_error("dl_topk_join: not available in this build yet");
-    return DL_EUNSUPPORTED;
+    if (!out) {
+        set_error("dl_topk_join: out is NULL");
+        return DL_EINVAL;
+    }
+    *out = nullptr;
+    if (!Q || !S) {
+        set_error("dl_topk_join: NULL store");
+        return DL_EINVAL;
+    }
+    if (metric != DL_METRIC_L2) {
+        set_error("dl_topk_join: unsupported metric %d", metric);
+        return DL_EINVAL;
+    }
+    if (k < 1 || k > 1024) {
+        set_error("dl_topk_join: k=%d out of range [1, 1024]", k);
+        return DL_EINVAL;
+    }
+    if (Q->d != S->d) {
+        set_error("dl_topk_join: dimension mismatch %d vs %d", Q->d, S->d);
+        return DL_EINVAL;
+    }
+    int dev = -1;
+    DL_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != Q->device || dev != S->device) {
+        set_error("dl_topk_join: stores live on another device");
+        return DL_EINVAL;
+    }
+    dl_join_opts o;
+    if (opts)
+        o = *opts;
+    else
+        dl_join_opts_default(&o);
+    if (o.precision != DL_PREC_AUTO && o.precision != DL_PREC_BF16 && o.precision != DL_PREC_FP32) {
+        set_error("dl_topk_join: precision %d not available for top-k", o.precision);
+        return DL_EUNSUPPORTED;
+    }
+    cudaStream_t st = (cudaStream_t)o.cuda_stream;
+    const int64_t nQ = Q->n, nS = S->n;
+    const int d = Q->d;
+    const int BN = o.tile_n ? o.tile_n : 256;
+    if (BN != 128 && BN != 256) {
+        set_error("dl_topk_join: tile_n must be 0, 128 or 256");
+        return DL_EINVAL;
+    }
+    const bool use_tc = (o.precision != DL_PREC_FP32) && Q->dp <= 512;
+    const int sms = device_sm_count();
+    const int64_t mt = (nQ + 127) / 128, nt = (nS + BN - 1) / BN;
+    int splits = 1;
+    if (mt > 0) splits = (int)std::min<int64_t>(std::max<int64_t>(1, (2 * sms + mt - 1) / mt), std::min<int64_t>(nt, 16));
+    if (splits < 1) splits = 1;
+    const int slots = 2 * splits;
+    const int cap = std::max(64, (4 * k + 31) / 32 * 32);
+    const int64_t rows = mt * 128;
+
+    // result block: ids [nQ][k] int64 + dist2 [nQ][k] double
+    void *resb = nullptr;
+    int rc = dev_alloc(&resb, std::max<size_t>(16, (size_t)nQ * k * 16), st);
+    if (rc) return rc;
+    int64_t *out_ids = (int64_t *)resb;
+    double *out_d2 = (double *)(out_ids + (size_t)nQ * k);
+
+    const size_t b_rowpar = al256(rows * sizeof(float4)), b_heap = al256((size_t)rows * slots * k * sizeof(float)),
+                 b_list = al256((size_t)rows * slots * cap * sizeof(uint2)),
+                 b_cnt = al256((size_t)rows * slots * sizeof(int)), b_theta = al256((size_t)rows * slots * sizeof(float)),
+                 b_ovf = al256((size_t)std::max<int64_t>(nQ, 1) * sizeof(int)),
+                 b_rows = al256((size_t)std::max<int64_t>(nQ, 1) * sizeof(int)), b_misc = 256;
+    void *ws = nullptr;
+    rc = dev_alloc(&ws, b_rowpar + b_heap + b_list + b_cnt + b_theta + b_ovf + b_rows + b_misc, st);
+    if (rc) {
+        dev_free(resb, st);
+        return rc;
+    }
+    char *pw = (char *)ws;
+    float4 *rowpar = (float4 *)pw;
+    pw += b_rowpar;
+    float *heap = (float *)pw;
+    pw += b_heap;
+    uint2 *list = (uint2 *)pw;
+    pw += b_list;
+    int *cnt = (int *)pw;
+    pw += b_cnt;
+    float *theta = (float *)pw;
+    pw += b_theta;
+    int *ovf = (int *)pw;
+    pw += b_ovf;
+    int *frows = (int *)pw;
+    pw += b_rows;
+    unsigned long long *misc = (unsigned long long *)pw;   // [0] flagged rows [1] fp64 evals [2] err [3] tc err
+    auto fail = [&](int code) {
+        dev_free(ws, st);
+        dev_free(resb, st);
+        cudaStreamSynchronize(st);
+        return code;
+    };
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    if (o.timing)
+        for (auto &e : ev) cudaEventCreate(&e);
+    auto kill_events = [&]() {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    };
+    cudaError_t e = cudaMemsetAsync(misc, 0, 256, st);
+    if (e == cudaSuccess && nQ > 0) e = cudaMemsetAsync(ovf, 0, (size_t)nQ * sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, b_cnt, st);
+    if (e != cudaSuccess) {
+        kill_events();
+        return fail(cuda_fail(e, "dl_topk_join memset"));
+    }
+    if (o.timing) cudaEventRecord(ev[0], st);
+    int launches = 0;
+    const double g64 = gamma64(d), g32 = gamma32(d);
+    TopkFin f;
+    f.Q = Q->x32;
+    f.S = S->x32;
+    f.d = d;
+    f.nQ = (int)nQ;
+    f.nS = (int)nS;
+    f.k = k;
+    f.slots = slots;
+    f.cap = cap;
+    f.theta = theta;
+    f.cnt = cnt;
+    f.list = list;
+    f.overflow = ovf;
+    f.q_orig = Q->orig;
+    f.s_orig = S->orig;
+    f.s_ids = S->ids;
+    f.out_ids = out_ids;
+    f.out_d2 = out_d2;
+    f.g32 = f32_ru(g32 * 1.0000001);
+    f.abs32 = f32_ru((double)(d + 8) * 1.401298464324817e-45 * 4.0);
+    f.slack = f32_ru(4.0 * g64 + 1e-12);
+    f.n_fp64 = misc + 1;
+    if (nQ > 0 && nS > 0) {
+        if (use_tc) {
+            k_rowpar_topk<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(Q->nq64, Q->rowb, nQ, rows, g64,
+                                                                          (double)S->nq_max * 1.0001, rowpar);
+            count_launch();
+            ++launches;
+            const CUtensorMap *tmA = nullptr, *tmB = nullptr;
+            rc = get_tmap(const_cast<dl_store *>(Q), 128, &tmA);
+            if (!rc) rc = get_tmap(const_cast<dl_store *>(S), BN, &tmB);
+            const int4 *units = nullptr;
+            int n_units = 0;
+            if (!rc) rc = topk_units(nQ, nS, BN, splits, &units, &n_units);
+            if (!rc && n_units > 0) {
+                TcLaunch L;
+                std::memset(&L.p, 0, sizeof L.p);
+                L.tmA = tmA;
+                L.tmB = tmB;
+                L.BN = BN;
+                L.grid = std::min(n_units, sms);
+                L.p.units = units;
+                L.p.n_units = n_units;
+                L.p.nR = (int)nQ;
+                L.p.nS = (int)nS;
+                L.p.kc = Q->dp / 64;
+                tc_plan(BN, Q->dp / 64, &L.p.stages, &L.p.a_slots);
+                L.p.upper = 0;
+                L.p.rowpar = rowpar;
+                L.p.beta = S->beta;
+                L.p.cstat = S->cstat;
+                L.p.err = (int *)(misc + 3);
+                L.p.tk_k = k;
+                L.p.tk_cap = cap;
+                L.p.tk_slots = slots;
+                L.p.tk_heap = heap;
+                L.p.tk_list = list;
+                L.p.tk_cnt = cnt;
+                L.p.tk_theta = theta;
+                L.p.tk_overflow = ovf;
+                rc = launch_tc_join(L, st, true);
+                ++launches;
+            }
+            if (!rc) {
+                const int grid = (int)std::min<int64_t>((nQ + 3) / 4, (int64_t)sms * 16);
+                k_topk_finalize<<<grid, 128, 0, st>>>(f);
+                count_launch();
+                ++launches;
+                e = cudaGetLastError();
+                if (e != cudaSuccess) rc = cuda_fail(e, "k_topk_finalize launch");
+            }
+        } else {
+            // no tensor-core pass for this shape: every row takes the exact scan
+            e = cudaMemsetAsync(ovf, 0xff, (size_t)nQ * sizeof(int), st);
+            if (e != cudaSuccess) rc = cuda_fail(e, "dl_topk_join memset");
+        }
+    } else if (nQ > 0) {   // empty store: every slot is unused
+        k_topk_finalize<<<1, 128, 0, st>>>(f);   // m = 0 for every row -> fills -1
+        count_launch();
+        ++launches;
+    }
+    if (o.timing) cudaEventRecord(ev[1], st);
+    // exact fallback for flagged rows
+    int64_t flagged = 0;
+    if (!rc && nQ > 0 && nS > 0) {
+        k_collect_overflow<<<(unsigned)((nQ + 255) / 256), 256, 0, st>>>(ovf, (int)nQ, frows, (int *)misc);
+        count_launch();
+        ++launches;
+        unsigned long long h[4] = {0, 0, 0, 0};
+        e = cudaMemcpyAsync(h, misc, sizeof h, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "dl_topk_join");
+        if (!rc && h[3]) {
+            kill_events();
+            set_error("dl_topk_join: a bounded device wait expired");
+            return fail(DL_ETIMEOUT);
+        }
+        flagged = (int64_t)(h[0] & 0xffffffffULL);
+        if (!rc && flagged > 0) {
+            const int64_t per_row = (int64_t)nS * 8 + (int64_t)kTkFallbackCap * 12;
+            const int64_t batch = std::max<int64_t>(1, std::min<int64_t>(flagged, (256LL << 20) / per_row));
+            void *fb = nullptr;
+            rc = dev_alloc(&fb, al256(batch * (size_t)nS * 8) + al256(batch * (size_t)kTkFallbackCap * 12), st);
+            if (!rc) {
+                TopkFb g;
+                g.Q = Q->x32;
+                g.S = S->x32;
+                g.d = d;
+                g.nS = (int)nS;
+                g.k = k;
+                g.scr_u = (float *)fb;
+                g.scr_l = g.scr_u + batch * nS;
+                g.scr_c = (uint32_t *)((char *)fb + al256(batch * (size_t)nS * 8));
+                g.scr_d = (double *)(g.scr_c + batch * kTkFallbackCap);
+                g.q_orig = Q->orig;
+                g.s_orig = S->orig;
+                g.s_ids = S->ids;
+                g.out_ids = out_ids;
+                g.out_d2 = out_d2;
+                g.g32 = f.g32;
+                g.abs32 = f.abs32;
+                g.slack = f.slack;
+                g.err = (int *)(misc + 2);
+                g.n_fp64 = misc + 1;
+                for (int64_t b0 = 0; b0 < flagged && !rc; b0 += batch) {
+                    g.rows = frows + b0;
+                    g.n_rows = (int)std::min<int64_t>(batch, flagged - b0);
+                    k_topk_fallback<<<g.n_rows, 256, 0, st>>>(g);
+                    count_launch();
+                    ++launches;
+                    e = cudaGetLastError();
+                    if (e != cudaSuccess) rc = cuda_fail(e, "k_topk_fallback launch");
+                }
+                dev_free(fb, st);
+            }
+        }
+    }
+    if (o.timing) cudaEventRecord(ev[2], st);
+    unsigned long long h2[4] = {0, 0, 0, 0};
+    if (!rc) {
+        e = cudaMemcpyAsync(h2, misc, sizeof h2, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "dl_topk_join");
+    }
+    if (!rc && h2[2]) {
+        set_error("dl_topk_join: more than %d store rows tie within rounding at the k-th distance of a query",
+                  kTkFallbackCap);
+        rc = DL_EUNSUPPORTED;
+    }
+    if (rc) {
+        kill_events();
+        return fail(rc);
+    }
+    dl_result *res = new dl_result();
+    res->kind = 1;
+    res->device = dev;
+    res->stream = st;
+    res->k = k;
+    res->nq = nQ;
+    res->d_ids = out_ids;
+    res->d_d2 = out_d2;
+    dl_join_stats &s = res->stats;
+    s.pairs_evaluated = nQ * nS;
+    s.pairs_out = nQ * std::min<int64_t>(k, nS);
+    s.band_pairs = flagged;            // rows re-solved by the exact scan
+    s.fp64_pairs = (int64_t)h2[1];
+    s.precision = use_tc ? DL_PREC_BF16 : DL_PREC_FP32;
+    s.tile_n = use_tc ? BN : 0;
+    s.kernels_launched = launches;
+    if (o.timing) {
+        cudaEventElapsedTime(&s.ms_main, ev[0], ev[1]);
+        cudaEventElapsedTime(&s.ms_recheck, ev[1], ev[2]);
+        cudaEventElapsedTime(&s.ms_total, ev[0], ev[2]);
+    }
+    kill_events();
+    dev_free(ws, st);
+    *out = res;
+    return DL_OK;
 }
