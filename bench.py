@@ -116,6 +116,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate(total_ms: float, pairs_per_step: int, steps: int, world: int, device=None):
+    """Whole-job throughput: all ranks' pairs over the slowest rank's timed total (Gpairs/s).
+
+    With world > 1 the per-rank totals are reduced with MAX over the process group.
+    Returns (value, max_total_ms).
+    """
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * pairs_per_step * steps / (total_ms / 1e3) / 1e9, total_ms
+
+
 def load_workload(rank: int):
     from paper_1812_07607_gb300 import workloads as W
     return W.self_clustered_262k()
@@ -246,14 +261,8 @@ def run_ours(args):
     barrier()
     launches = dl.kernel_launches() - launches0
     clocks = sampler.stop()
-    total_ms = sum(step_ms)
-    if ws > 1:
-        import torch.distributed as tdist
-        t = torch.tensor([total_ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    value, total_ms = aggregate(sum(step_ms), P, args.steps, ws, dev)
     ms_per_step = total_ms / args.steps
-    value = ws * P * args.steps / (total_ms / 1e3) / 1e9
 
     # ---- end to end through the C ABI from pinned host memory (store upload + join + pair download)
     h_feats = torch.from_numpy(wl.R).pin_memory()
