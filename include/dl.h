@@ -166,6 +166,47 @@ int dl_sim_join_noalloc(const float *R, const int64_t *r_ids, int64_t nR, const 
                         void *cuda_stream);
 
 /* ---------------------------------------------------------------------------------
+ * Batches: many epsilon-join and top-k requests against one resident store.
+ * ------------------------------------------------------------------------------- */
+
+typedef enum dl_request_kind {
+    DL_REQ_EPS = 0,       /* epsilon-join of the request's query rows against the store */
+    DL_REQ_TOPK = 1       /* top-k join of the request's query rows against the store */
+} dl_request_kind;
+
+typedef struct dl_request {
+    int32_t kind;         /* dl_request_kind */
+    int32_t k;            /* DL_REQ_TOPK: 1..1024 */
+    double eps;           /* DL_REQ_EPS: >= 0, not NaN */
+    int64_t q_begin;      /* first row of this request in the batch's query arrays */
+    int64_t nq;           /* number of query rows (>= 0) */
+} dl_request;
+
+/*
+ * Run n_req requests of uneven sizes as one batch against the store S (the
+ * paper's image-matching queries, Sec. 6.2 q1/q4, issued many at a time).
+ * q_ids [nq_total] and q_feats [nq_total][d] hold every request's query rows;
+ * request i uses rows [q_begin, q_begin + nq) (ranges may overlap). `where`
+ * tells whether both are host or device memory; they are copied. All
+ * epsilon-join rows run in one persistent tensor-core launch (each row with its
+ * request's eps), all top-k rows in another (each row with its request's k),
+ * then the outputs are routed per request. Each request's result is the set (or
+ * ordered list) the single-request call would return. On success *out holds a
+ * batch result; read it with dl_result_request_pairs / dl_result_request_topk.
+ */
+int dl_batch_join(const dl_store *S, const int64_t *q_ids, const float *q_feats, int64_t nq_total, int32_t d,
+                  int32_t where, const dl_request *reqs, int32_t n_req, const dl_join_opts *opts,
+                  dl_result **out);
+
+/* Pairs of epsilon-join request `req` of a batch result (same conventions as dl_result_pairs). */
+int dl_result_request_pairs(dl_result *r, int32_t req, int32_t where, const int64_t **r_ids,
+                            const int64_t **s_ids, int64_t *n);
+
+/* Top-k rows of top-k request `req` of a batch result (same conventions as dl_result_topk). */
+int dl_result_request_topk(dl_result *r, int32_t req, int32_t where, const int64_t **ids,
+                           const double **dist2, int32_t *k, int64_t *nq);
+
+/* ---------------------------------------------------------------------------------
  * Results.
  * ------------------------------------------------------------------------------- */
 

@@ -206,7 +206,7 @@ static int run_pass(const PassCfg &c, PassOut *po)
     int launches = 0;
     if (nR > 0 && nS > 0) {
         if (c.prec == DL_PREC_BF16) {
-            rc = launch_rowpar(R->nq64, R->rowb, nR, mt * 128, R->dp, c.e2, gamma64(d), rowpar, st);
+            rc = launch_rowpar(R->nq64, R->rowb, nR, mt * 128, R->dp, c.e2, nullptr, gamma64(d), rowpar, st);
             ++launches;
             const CUtensorMap *tmA = nullptr, *tmB = nullptr;
             if (!rc) rc = get_tmap(const_cast<dl_store *>(R), 128, &tmA);
@@ -490,7 +490,7 @@ int dl_result_count(const dl_result *r, int64_t *n)
         set_error("dl_result_count: NULL argument");
         return DL_EINVAL;
     }
-    *n = r->kind == 0 ? r->count : r->nq * r->k;
+    *n = (r->kind == 0 || r->kind == 2) ? r->count : r->nq * r->k;
     return DL_OK;
 }
 
@@ -589,14 +589,109 @@ int dl_result_free(dl_result *r)
     int prev = 0;
     cudaGetDevice(&prev);
     if (prev != r->device) cudaSetDevice(r->device);
-    if (r->kind == 0)
-        dev_free(r->d_r, r->stream);   // d_s lives in the same block
-    else
-        dev_free(r->d_ids, r->stream); // d_d2 lives in the same block
+    if (r->kind == 0 || r->kind == 2) dev_free(r->d_r, r->stream);    // d_s lives in the same block
+    if (r->kind == 1 || r->kind == 2) dev_free(r->d_ids, r->stream);  // d_d2 lives in the same block
     if (prev != r->device) cudaSetDevice(prev);
     if (r->h_r) hpool_put(r->h_r, r->h_bytes);
-    if (r->h_ids) hpool_put(r->h_ids, r->h_bytes);
+    if (r->kind == 1 && r->h_ids) hpool_put(r->h_ids, r->h_bytes);
+    if (r->kind == 2 && r->h_batch) hpool_put(r->h_batch, r->h_batch_bytes);
     delete r;
+    return DL_OK;
+}
+
+// Host copy of a batch result's pair arrays (all requests) on first use.
+static int batch_pairs_host(dl_result *r)
+{
+    if (r->h_r) return DL_OK;
+    const int64_t cnt = r->count;
+    size_t got = 0;
+    void *h = hpool_get(std::max<size_t>(16, (size_t)cnt * 16), &got);
+    if (!h) {
+        set_error("batch result: pinned host allocation failed");
+        return DL_ENOMEM;
+    }
+    r->h_r = (int64_t *)h;
+    r->h_s = r->h_r + cnt;
+    r->h_bytes = got;
+    cudaError_t e = cudaSuccess;
+    if (cnt > 0) e = cudaMemcpyAsync(r->h_r, r->d_r, cnt * 8, cudaMemcpyDeviceToHost, r->stream);
+    if (e == cudaSuccess && cnt > 0) e = cudaMemcpyAsync(r->h_s, r->d_s, cnt * 8, cudaMemcpyDeviceToHost, r->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch result copy");
+    return DL_OK;
+}
+
+static int batch_topk_host(dl_result *r)
+{
+    if (r->h_batch) return DL_OK;
+    const int64_t n = r->n_topk_slots;
+    size_t got = 0;
+    void *h = hpool_get(std::max<size_t>(16, (size_t)n * 16), &got);
+    if (!h) {
+        set_error("batch result: pinned host allocation failed");
+        return DL_ENOMEM;
+    }
+    r->h_batch = h;
+    r->h_batch_bytes = got;
+    cudaError_t e = cudaSuccess;
+    if (n > 0) e = cudaMemcpyAsync(h, r->d_ids, n * 8, cudaMemcpyDeviceToHost, r->stream);
+    if (e == cudaSuccess && n > 0)
+        e = cudaMemcpyAsync((char *)h + n * 8, r->d_d2, n * 8, cudaMemcpyDeviceToHost, r->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch result copy");
+    return DL_OK;
+}
+
+int dl_result_request_pairs(dl_result *r, int32_t req, int32_t where, const int64_t **r_ids, const int64_t **s_ids,
+                            int64_t *n)
+{
+    if (!r || r->kind != 2 || req < 0 || req >= (int32_t)r->req_kind.size() || r->req_kind[req] != DL_REQ_EPS) {
+        set_error("dl_result_request_pairs: not an epsilon-join request of a batch result");
+        return DL_EINVAL;
+    }
+    const int64_t o = r->pair_off[req], c = r->pair_off[req + 1] - o;
+    if (n) *n = c;
+    if (where == DL_MEM_DEVICE) {
+        if (r_ids) *r_ids = r->d_r ? r->d_r + o : nullptr;
+        if (s_ids) *s_ids = r->d_s ? r->d_s + o : nullptr;
+        return DL_OK;
+    }
+    if (where != DL_MEM_HOST) {
+        set_error("dl_result_request_pairs: bad memory kind");
+        return DL_EINVAL;
+    }
+    const int rc = batch_pairs_host(r);
+    if (rc) return rc;
+    if (r_ids) *r_ids = r->h_r + o;
+    if (s_ids) *s_ids = r->h_s + o;
+    return DL_OK;
+}
+
+int dl_result_request_topk(dl_result *r, int32_t req, int32_t where, const int64_t **ids, const double **dist2,
+                           int32_t *k, int64_t *nq)
+{
+    if (!r || r->kind != 2 || req < 0 || req >= (int32_t)r->req_kind.size() || r->req_kind[req] != DL_REQ_TOPK) {
+        set_error("dl_result_request_topk: not a top-k request of a batch result");
+        return DL_EINVAL;
+    }
+    const int64_t o = r->topk_off[req];
+    if (k) *k = r->req_k[req];
+    if (nq) *nq = r->req_nq[req];
+    if (where == DL_MEM_DEVICE) {
+        if (ids) *ids = r->d_ids ? r->d_ids + o : nullptr;
+        if (dist2) *dist2 = r->d_d2 ? r->d_d2 + o : nullptr;
+        return DL_OK;
+    }
+    if (where != DL_MEM_HOST) {
+        set_error("dl_result_request_topk: bad memory kind");
+        return DL_EINVAL;
+    }
+    const int rc = batch_topk_host(r);
+    if (rc) return rc;
+    const int64_t *hi = (const int64_t *)r->h_batch;
+    const double *hd = (const double *)((const char *)r->h_batch + r->n_topk_slots * 8);
+    if (ids) *ids = hi + o;
+    if (dist2) *dist2 = hd + o;
     return DL_OK;
 }
 

@@ -1,0 +1,53 @@
+// exact.cuh -- the exact decision for one pair (FP32 bound first, canonical FP64 if needed).
+#pragma once
+
+#include <cstdint>
+
+namespace dl {
+
+// FP32 thresholds for a squared threshold e2 at dimension d: accept if the FP32
+// distance sum D32 <= t_acc, reject if D32 > t_rej, else evaluate the canonical
+// FP64 sum. Sound for |D32 - D| <= (d+8) 2^-24 D + (d+8) 2^-148 and for the
+// canonical sum's (d+4) 2^-53 relative error; the (1 -/+ 2^-50) factors absorb the
+// roundings of this very computation.
+__device__ __forceinline__ void fp32_thresholds(double e2, int d, float *t_acc, float *t_rej)
+{
+    const double g64 = (double)(d + 4) * 1.1102230246251565e-16;
+    const double g32 = (double)(d + 8) * 5.9604644775390625e-08;
+    const double abs32 = (double)(d + 8) * 1.401298464324817e-45 * 2.0;
+    *t_acc = __double2float_rd(e2 * (1.0 - g64) * (1.0 - g32) * (1.0 - 8.881784197001252e-16) - abs32);
+    *t_rej = __double2float_ru(e2 * (1.0 + 2.0 * g64) * (1.0 + g32) * (1.0 + 8.881784197001252e-16) + abs32);
+}
+
+// Exact decision for the pair (q, x), taken by the whole warp (same answer in
+// every lane): FP32 first, the canonical FP64 sum only when FP32 cannot decide.
+__device__ __forceinline__ bool warp_exact_decide(const float *__restrict__ q, const float *__restrict__ x, int d,
+                                                  double e2, float t_acc, float t_rej,
+                                                  unsigned long long *__restrict__ n_fp64)
+{
+    const unsigned lane = threadIdx.x & 31;
+    float s = 0.f;
+    for (int k = lane; k < d; k += 32) {
+        const float t = __ldg(q + k) - __ldg(x + k);
+        s = fmaf(t, t, s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (s <= t_acc) return true;
+    if (s > t_rej) return false;
+    double sum = 0.0;
+    for (int k0 = 0; k0 < d; k0 += 32) {
+        double pk = 0.0;
+        const int k = k0 + (int)lane;
+        if (k < d) {
+            const double t = __dsub_rn((double)__ldg(q + k), (double)__ldg(x + k));
+            pk = __dmul_rn(t, t);
+        }
+        const int lim = min(32, d - k0);
+        for (int l = 0; l < lim; ++l) sum = __dadd_rn(sum, __shfl_sync(0xffffffffu, pk, l));
+    }
+    if (lane == 0) atomicAdd(n_fp64, 1ULL);
+    return sum <= e2;
+}
+
+}  // namespace dl

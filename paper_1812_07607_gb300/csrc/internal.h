@@ -10,8 +10,11 @@
 #include <cstdint>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "dl.h"
+
+struct dl_store;
 
 namespace dl {
 
@@ -81,6 +84,10 @@ struct Store {
     int64_t hint_band = 0;
 };
 
+// Create a store; gather == NULL orders rows by norm, else store row i is caller row gather[i].
+int store_create_impl(dl_store **out, const int64_t *ids, const float *feats, int64_t n, int32_t d, int32_t where,
+                      void *cuda_stream, const int32_t *gather);
+
 // Build (or fetch from the store's cache) a 2-D BF16 tensor map over the store's
 // BF16 copy with a box of 64 columns x box_rows rows and the 128-byte swizzle.
 int get_tmap(Store *s, int box_rows, const CUtensorMap **out);
@@ -111,7 +118,7 @@ inline float f32_rd(double x)
 struct dl_store : public dl::Store {};
 
 struct dl_result {
-    int kind = 0;             // 0 pairs, 1 topk
+    int kind = 0;             // 0 pairs, 1 topk, 2 batch (both, per request)
     int device = 0;
     cudaStream_t stream = nullptr;
     int64_t count = 0;        // pairs (kind 0)
@@ -124,4 +131,12 @@ struct dl_result {
     int64_t *h_ids = nullptr; double *h_d2 = nullptr;
     size_t h_bytes = 0;       // size of the pinned host block (h_r or h_ids)
     dl_join_stats stats{};
+    // batch results: request i's pairs are [pair_off[i], pair_off[i+1]) of d_r/d_s, its top-k
+    // rows are [topk_off[i], topk_off[i] + req_nq[i] * req_k[i]) of d_ids/d_d2
+    std::vector<int32_t> req_kind, req_k;
+    std::vector<int64_t> req_nq, pair_off, topk_off;
+    int64_t n_topk_slots = 0;
+    void *batch_block = nullptr;          // device block holding every batch output
+    void *h_batch = nullptr;              // pinned host copy of batch_block (lazy)
+    size_t batch_bytes = 0, h_batch_bytes = 0;
 };

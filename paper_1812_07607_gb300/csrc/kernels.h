@@ -65,8 +65,8 @@ int launch_simt_join(SimtParams p, cudaStream_t st);
 int launch_recheck(const uint2 *band, const unsigned long long *band_cnt, unsigned long long band_cap, const float *R,
                    const float *S, int d, double e2, float t_acc, float t_rej, const JoinOut &out,
                    unsigned long long *n_fp64, int grid, cudaStream_t st);
-int launch_rowpar(const double *nq64, const float4 *rowb, int64_t n, int64_t n_tot, int dp, double e2, double g64,
-                  float4 *rowpar, cudaStream_t st);
+int launch_rowpar(const double *nq64, const float4 *rowb, int64_t n, int64_t n_tot, int dp, double e2,
+                  const double *row_e2, double g64, float4 *rowpar, cudaStream_t st);
 // Turn the tensor-core kernel's candidate list into id pairs: proven matches are
 // translated directly, band pairs are rechecked exactly first (recheck.cu).
 int launch_finalize(const uint2 *cand, const unsigned long long *cand_cnt, unsigned long long cand_cap, const float *R,
@@ -74,5 +74,9 @@ int launch_finalize(const uint2 *cand, const unsigned long long *cand_cnt, unsig
                     unsigned long long *n_fp64, unsigned long long *n_band, int grid, cudaStream_t st);
 int launch_diag(const int64_t *ids, int64_t n, int64_t *out_r, int64_t *out_s, unsigned long long *out_cnt,
                 unsigned long long cap, cudaStream_t st);
+
+// ---- top-k core (topk.cu): every row of Q against S, outputs at row_off or caller row * k
+int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, const int64_t *row_off,
+              int64_t *out_ids, double *out_d2, const dl_join_opts &o, cudaStream_t st, dl_join_stats *stats);
 
 }  // namespace dl

@@ -10,40 +10,10 @@
 //      nearest with no contraction (__dsub_rn / __dmul_rn / __dadd_rn), compared
 //      with fl64(eps*eps) -- the very expression that defines the result, so the
 //      decision is identical to the FP64 nested loop's.
+#include "exact.cuh"
 #include "kernels.h"
 
 namespace dl {
-
-// Exact decision for the pair (q, x), taken by the whole warp (same answer in
-// every lane): FP32 first, the canonical FP64 sum only when FP32 cannot decide.
-__device__ __forceinline__ bool warp_exact_decide(const float *__restrict__ q, const float *__restrict__ x, int d,
-                                                  double e2, float t_acc, float t_rej,
-                                                  unsigned long long *__restrict__ n_fp64)
-{
-    const unsigned lane = threadIdx.x & 31;
-    float s = 0.f;
-    for (int k = lane; k < d; k += 32) {
-        const float t = __ldg(q + k) - __ldg(x + k);
-        s = fmaf(t, t, s);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (s <= t_acc) return true;
-    if (s > t_rej) return false;
-    double sum = 0.0;
-    for (int k0 = 0; k0 < d; k0 += 32) {
-        double pk = 0.0;
-        const int k = k0 + (int)lane;
-        if (k < d) {
-            const double t = __dsub_rn((double)__ldg(q + k), (double)__ldg(x + k));
-            pk = __dmul_rn(t, t);
-        }
-        const int lim = min(32, d - k0);
-        for (int l = 0; l < lim; ++l) sum = __dadd_rn(sum, __shfl_sync(0xffffffffu, pk, l));
-    }
-    if (lane == 0) atomicAdd(n_fp64, 1ULL);
-    return sum <= e2;
-}
 
 __global__ void __launch_bounds__(256)
     k6_recheck(const uint2 *__restrict__ band, const unsigned long long *__restrict__ band_cnt,
@@ -104,7 +74,7 @@ __global__ void __launch_bounds__(256)
 // Padding rows get +inf thresholds (never emit).
 __global__ void __launch_bounds__(256)
     k_rowpar(const double *__restrict__ nq64, const float4 *__restrict__ rowb, int64_t n, int64_t n_tot, int dp,
-             double e2, double g64, float4 *__restrict__ rowpar)
+             double e2_all, const double *__restrict__ row_e2, double g64, float4 *__restrict__ rowpar)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_tot) return;
@@ -114,6 +84,7 @@ __global__ void __launch_bounds__(256)
         return;
     }
     const double nq = nq64[i];
+    const double e2 = row_e2 ? row_e2[i] : e2_all;
     const double rel = (double)(dp + 2) * 2.220446049250313e-16;
     const double nq_up = __dmul_ru(nq, 1.0 + rel);
     const double nq_dn = __dmul_rd(nq, 1.0 - rel);
@@ -164,11 +135,11 @@ int launch_finalize(const uint2 *cand, const unsigned long long *cand_cnt, unsig
     return DL_OK;
 }
 
-int launch_rowpar(const double *nq64, const float4 *rowb, int64_t n, int64_t n_tot, int dp, double e2, double g64,
-                  float4 *rowpar, cudaStream_t st)
+int launch_rowpar(const double *nq64, const float4 *rowb, int64_t n, int64_t n_tot, int dp, double e2,
+                  const double *row_e2, double g64, float4 *rowpar, cudaStream_t st)
 {
     if (n_tot == 0) return DL_OK;
-    k_rowpar<<<(unsigned)((n_tot + 255) / 256), 256, 0, st>>>(nq64, rowb, n, n_tot, dp, e2, g64, rowpar);
+    k_rowpar<<<(unsigned)((n_tot + 255) / 256), 256, 0, st>>>(nq64, rowb, n, n_tot, dp, e2, row_e2, g64, rowpar);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_rowpar launch");

@@ -341,12 +341,12 @@ static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace dl
 
-using namespace dl;
+namespace dl {
 
-extern "C" {
-
-int dl_store_create(dl_store **out, const int64_t *ids, const float *feats, int64_t n, int32_t d, int32_t where,
-                    void *cuda_stream)
+// Create a store. With gather == NULL the rows are put in squared-norm order;
+// otherwise store row i is caller row gather[i] (device array of n indices).
+int store_create_impl(dl_store **out, const int64_t *ids, const float *feats, int64_t n, int32_t d, int32_t where,
+                      void *cuda_stream, const int32_t *gather)
 {
     clear_error();
     if (!out) {
@@ -457,12 +457,15 @@ int dl_store_create(dl_store **out, const int64_t *ids, const float *feats, int6
         if (e != cudaSuccess) return fail(cuda_fail(e, "dl_store_create memset"));
         const unsigned gw = (unsigned)((n + 7) / 8), gt = (unsigned)((n + 255) / 256);
         k_sort_keys<<<gw, 256, 0, st>>>(src_x, n, d, keys, mm);
-        k_sort_hist<<<gt, 256, 0, st>>>(keys, n, mm, hist);
-        k_sort_scan<<<1, 1024, 0, st>>>(hist);
-        k_sort_scatter<<<gt, 256, 0, st>>>(keys, n, mm, hist, perm);
-        k_gather_rows<<<gw, 256, 0, st>>>(src_x, src_ids, perm, n, d, s->x32, s->ids, s->orig);
+        if (!gather) {
+            k_sort_hist<<<gt, 256, 0, st>>>(keys, n, mm, hist);
+            k_sort_scan<<<1, 1024, 0, st>>>(hist);
+            k_sort_scatter<<<gt, 256, 0, st>>>(keys, n, mm, hist, perm);
+            count_launch(3);
+        }
+        k_gather_rows<<<gw, 256, 0, st>>>(src_x, src_ids, gather ? gather : perm, n, d, s->x32, s->ids, s->orig);
         k1_norm_quant<<<gw, 256, 0, st>>>(s->x32, n, d, s->dp, s->xb, s->nq64, s->beta, s->rowb, d_err);
-        count_launch(6);
+        count_launch(3);
     }
     const float g2 = f32_ru(gamma_tc(s->dp) + 1.01 * kU32);
     const float p3a = f32_ru(abs_slack_tc(s->dp));
@@ -493,6 +496,18 @@ int dl_store_create(dl_store **out, const int64_t *ids, const float *feats, int6
     dev_free(tmp, st);
     *out = s;
     return DL_OK;
+}
+
+}  // namespace dl
+
+using namespace dl;
+
+extern "C" {
+
+int dl_store_create(dl_store **out, const int64_t *ids, const float *feats, int64_t n, int32_t d, int32_t where,
+                    void *cuda_stream)
+{
+    return store_create_impl(out, ids, feats, n, d, where, cuda_stream, nullptr);
 }
 
 int dl_store_destroy(dl_store *s)

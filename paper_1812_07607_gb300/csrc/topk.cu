@@ -44,6 +44,8 @@ struct TopkFin {
     const int64_t *s_ids;
     int64_t *out_ids;
     double *out_d2;
+    const int *row_k;      // per query row k (NULL: k for every row)
+    const int64_t *row_off;// per query row first output slot (NULL: caller row * k)
     float g32, abs32;      // FP32 distance bound: |D32 - D| <= g32 * D + abs32
     float slack;           // canonical slack factor for the keep test (relative)
     unsigned long long *n_fp64;
@@ -119,12 +121,13 @@ __global__ void __launch_bounds__(128) k_topk_finalize(const TopkFin f)
         // k-th smallest upper bound (ties broken by position) -> at least k columns have D <= kth
         if (lane == 0) s_kth[w] = __int_as_float(0x7f800000);
         __syncwarp();
-        if (m > f.k) {
+        const int kk = f.row_k ? f.row_k[i] : f.k;
+        if (m > kk) {
             for (int a = lane; a < m; a += 32) {
                 int rank = 0;
                 const float ua = su[a];
                 for (int b = 0; b < m; ++b) rank += (su[b] < ua) || (su[b] == ua && b < a);
-                if (rank == f.k - 1) s_kth[w] = ua;
+                if (rank == kk - 1) s_kth[w] = ua;
             }
         }
         __syncwarp();
@@ -139,9 +142,9 @@ __global__ void __launch_bounds__(128) k_topk_finalize(const TopkFin f)
             if (lane == 0 && bm) atomicAdd(f.n_fp64, (unsigned long long)__popc(bm));
         }
         __syncwarp();
-        const int oi = f.q_orig[i];
-        int64_t *oid = f.out_ids + (size_t)oi * f.k;
-        double *od = f.out_d2 + (size_t)oi * f.k;
+        const int64_t base = f.row_off ? f.row_off[i] : (int64_t)f.q_orig[i] * f.k;
+        int64_t *oid = f.out_ids + base;
+        double *od = f.out_d2 + base;
         for (int a = lane; a < m; a += 32) {
             const double da = sd[a];
             if (!(da < __longlong_as_double(0x7ff0000000000000LL))) continue;   // not kept
@@ -151,12 +154,12 @@ __global__ void __launch_bounds__(128) k_topk_finalize(const TopkFin f)
                 const double db = sd[b];
                 rank += (db < da) || (db == da && f.s_orig[col[b]] < oa);
             }
-            if (rank < f.k) {
+            if (rank < kk) {
                 oid[rank] = f.s_ids[col[a]];
                 od[rank] = da;
             }
         }
-        for (int t = kept + lane; t < f.k; t += 32) {
+        for (int t = kept + lane; t < kk; t += 32) {
             oid[t] = -1;
             od[t] = -1.0;
         }
@@ -176,6 +179,8 @@ struct TopkFb {
     const int64_t *s_ids;
     int64_t *out_ids;
     double *out_d2;
+    const int *row_k;
+    const int64_t *row_off;
     float g32, abs32, slack;
     int *err;               // set to 1 when a row has more near-ties than the fallback can rank
     unsigned long long *n_fp64;
@@ -213,11 +218,12 @@ __global__ void __launch_bounds__(256) k_topk_fallback(const TopkFb f)
     }
     __syncthreads();
     // 2. k-th smallest upper bound by radix select on the (non-negative) float bits
+    const int kk = f.row_k ? f.row_k[i] : f.k;
     float kth = __int_as_float(0x7f800000);
-    if (f.nS > f.k) {
+    if (f.nS > kk) {
         if (tid == 0) {
             s_prefix = 0u;
-            s_rank = (unsigned)(f.k - 1);
+            s_rank = (unsigned)(kk - 1);
         }
         for (int shift = 24; shift >= 0; shift -= 8) {
             for (int t = tid; t < 256; t += blockDim.x) hist[t] = 0u;
@@ -263,9 +269,9 @@ __global__ void __launch_bounds__(256) k_topk_fallback(const TopkFb f)
     for (int a = tid; a < m; a += blockDim.x) cd[a] = canon_d64(q, f.S + (size_t)cl[a] * f.d, f.d);
     if (tid == 0) atomicAdd(f.n_fp64, (unsigned long long)m);
     __syncthreads();
-    const int oi = f.q_orig[i];
-    int64_t *oid = f.out_ids + (size_t)oi * f.k;
-    double *od = f.out_d2 + (size_t)oi * f.k;
+    const int64_t base = f.row_off ? f.row_off[i] : (int64_t)f.q_orig[i] * f.k;
+    int64_t *oid = f.out_ids + base;
+    double *od = f.out_d2 + base;
     for (int a = tid; a < m; a += blockDim.x) {
         const double da = cd[a];
         const int32_t oa = f.s_orig[cl[a]];
@@ -274,12 +280,12 @@ __global__ void __launch_bounds__(256) k_topk_fallback(const TopkFb f)
             const double db = cd[bb];
             rank += (db < da) || (db == da && f.s_orig[cl[bb]] < oa);
         }
-        if (rank < f.k) {
+        if (rank < kk) {
             oid[rank] = f.s_ids[cl[a]];
             od[rank] = da;
         }
     }
-    for (int t = m + tid; t < f.k; t += blockDim.x) {
+    for (int t = m + tid; t < kk; t += blockDim.x) {
         oid[t] = -1;
         od[t] = -1.0;
     }
@@ -344,56 +350,17 @@ static int topk_units(int64_t nQ, int64_t nS, int BN, int splits, const int4 **d
 
 static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
-}  // namespace dl
-
-using namespace dl;
-
-extern "C" int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric, int32_t k, const dl_join_opts *opts,
-                            dl_result **out)
+// Top-k of every row of Q against S into out_ids / out_d2. k is the largest k of
+// any row (the heap size); row_k (device, optional) gives each row's own k and
+// row_off (device, optional) each row's first output slot (default: caller row * k).
+int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, const int64_t *row_off,
+              int64_t *out_ids, double *out_d2, const dl_join_opts &o, cudaStream_t st, dl_join_stats *stats)
 {
-    clear_error();
-    if (!out) {
-        set_error("dl_topk_join: out is NULL");
-        return DL_EINVAL;
-    }
-    *out = nullptr;
-    if (!Q || !S) {
-        set_error("dl_topk_join: NULL store");
-        return DL_EINVAL;
-    }
-    if (metric != DL_METRIC_L2) {
-        set_error("dl_topk_join: unsupported metric %d", metric);
-        return DL_EINVAL;
-    }
-    if (k < 1 || k > 1024) {
-        set_error("dl_topk_join: k=%d out of range [1, 1024]", k);
-        return DL_EINVAL;
-    }
-    if (Q->d != S->d) {
-        set_error("dl_topk_join: dimension mismatch %d vs %d", Q->d, S->d);
-        return DL_EINVAL;
-    }
-    int dev = -1;
-    DL_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev != Q->device || dev != S->device) {
-        set_error("dl_topk_join: stores live on another device");
-        return DL_EINVAL;
-    }
-    dl_join_opts o;
-    if (opts)
-        o = *opts;
-    else
-        dl_join_opts_default(&o);
-    if (o.precision != DL_PREC_AUTO && o.precision != DL_PREC_BF16 && o.precision != DL_PREC_FP32) {
-        set_error("dl_topk_join: precision %d not available for top-k", o.precision);
-        return DL_EUNSUPPORTED;
-    }
-    cudaStream_t st = (cudaStream_t)o.cuda_stream;
     const int64_t nQ = Q->n, nS = S->n;
     const int d = Q->d;
     const int BN = o.tile_n ? o.tile_n : 256;
     if (BN != 128 && BN != 256) {
-        set_error("dl_topk_join: tile_n must be 0, 128 or 256");
+        set_error("top-k: tile_n must be 0, 128 or 256");
         return DL_EINVAL;
     }
     const bool use_tc = (o.precision != DL_PREC_FP32) && Q->dp <= 512;
@@ -406,24 +373,14 @@ extern "C" int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric
     const int cap = std::max(64, (4 * k + 31) / 32 * 32);
     const int64_t rows = mt * 128;
 
-    // result block: ids [nQ][k] int64 + dist2 [nQ][k] double
-    void *resb = nullptr;
-    int rc = dev_alloc(&resb, std::max<size_t>(16, (size_t)nQ * k * 16), st);
-    if (rc) return rc;
-    int64_t *out_ids = (int64_t *)resb;
-    double *out_d2 = (double *)(out_ids + (size_t)nQ * k);
-
     const size_t b_rowpar = al256(rows * sizeof(float4)), b_heap = al256((size_t)rows * slots * k * sizeof(float)),
                  b_list = al256((size_t)rows * slots * cap * sizeof(uint2)),
                  b_cnt = al256((size_t)rows * slots * sizeof(int)), b_theta = al256((size_t)rows * slots * sizeof(float)),
                  b_ovf = al256((size_t)std::max<int64_t>(nQ, 1) * sizeof(int)),
                  b_rows = al256((size_t)std::max<int64_t>(nQ, 1) * sizeof(int)), b_misc = 256;
     void *ws = nullptr;
-    rc = dev_alloc(&ws, b_rowpar + b_heap + b_list + b_cnt + b_theta + b_ovf + b_rows + b_misc, st);
-    if (rc) {
-        dev_free(resb, st);
-        return rc;
-    }
+    int rc = dev_alloc(&ws, b_rowpar + b_heap + b_list + b_cnt + b_theta + b_ovf + b_rows + b_misc, st);
+    if (rc) return rc;
     char *pw = (char *)ws;
     float4 *rowpar = (float4 *)pw;
     pw += b_rowpar;
@@ -440,26 +397,20 @@ extern "C" int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric
     int *frows = (int *)pw;
     pw += b_rows;
     unsigned long long *misc = (unsigned long long *)pw;   // [0] flagged rows [1] fp64 evals [2] err [3] tc err
-    auto fail = [&](int code) {
-        dev_free(ws, st);
-        dev_free(resb, st);
-        cudaStreamSynchronize(st);
-        return code;
-    };
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     if (o.timing)
         for (auto &e : ev) cudaEventCreate(&e);
-    auto kill_events = [&]() {
+    auto done = [&](int code) {
         for (auto &e : ev)
             if (e) cudaEventDestroy(e);
+        dev_free(ws, st);
+        if (code) cudaStreamSynchronize(st);
+        return code;
     };
     cudaError_t e = cudaMemsetAsync(misc, 0, 256, st);
     if (e == cudaSuccess && nQ > 0) e = cudaMemsetAsync(ovf, 0, (size_t)nQ * sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, b_cnt, st);
-    if (e != cudaSuccess) {
-        kill_events();
-        return fail(cuda_fail(e, "dl_topk_join memset"));
-    }
+    if (e != cudaSuccess) return done(cuda_fail(e, "top-k memset"));
     if (o.timing) cudaEventRecord(ev[0], st);
     int launches = 0;
     const double g64 = gamma64(d), g32 = gamma32(d);
@@ -481,6 +432,8 @@ extern "C" int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric
     f.s_ids = S->ids;
     f.out_ids = out_ids;
     f.out_d2 = out_d2;
+    f.row_k = row_k;
+    f.row_off = row_off;
     f.g32 = f32_ru(g32 * 1.0000001);
     f.abs32 = f32_ru((double)(d + 8) * 1.401298464324817e-45 * 4.0);
     f.slack = f32_ru(4.0 * g64 + 1e-12);
@@ -537,10 +490,10 @@ extern "C" int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric
         } else {
             // no tensor-core pass for this shape: every row takes the exact scan
             e = cudaMemsetAsync(ovf, 0xff, (size_t)nQ * sizeof(int), st);
-            if (e != cudaSuccess) rc = cuda_fail(e, "dl_topk_join memset");
+            if (e != cudaSuccess) rc = cuda_fail(e, "top-k memset");
         }
     } else if (nQ > 0) {   // empty store: every slot is unused
-        k_topk_finalize<<<1, 128, 0, st>>>(f);   // m = 0 for every row -> fills -1
+        k_topk_finalize<<<1, 128, 0, st>>>(f);   // no candidates for any row -> fills -1
         count_launch();
         ++launches;
     }
@@ -554,11 +507,10 @@ extern "C" int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric
         unsigned long long h[4] = {0, 0, 0, 0};
         e = cudaMemcpyAsync(h, misc, sizeof h, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) rc = cuda_fail(e, "dl_topk_join");
+        if (e != cudaSuccess) rc = cuda_fail(e, "top-k");
         if (!rc && h[3]) {
-            kill_events();
-            set_error("dl_topk_join: a bounded device wait expired");
-            return fail(DL_ETIMEOUT);
+            set_error("top-k: a bounded device wait expired");
+            return done(DL_ETIMEOUT);
         }
         flagged = (int64_t)(h[0] & 0xffffffffULL);
         if (!rc && flagged > 0) {
@@ -582,6 +534,8 @@ extern "C" int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric
                 g.s_ids = S->ids;
                 g.out_ids = out_ids;
                 g.out_d2 = out_d2;
+                g.row_k = row_k;
+                g.row_off = row_off;
                 g.g32 = f.g32;
                 g.abs32 = f.abs32;
                 g.slack = f.slack;
@@ -605,17 +559,90 @@ extern "C" int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric
     if (!rc) {
         e = cudaMemcpyAsync(h2, misc, sizeof h2, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) rc = cuda_fail(e, "dl_topk_join");
+        if (e != cudaSuccess) rc = cuda_fail(e, "top-k");
     }
     if (!rc && h2[2]) {
-        set_error("dl_topk_join: more than %d store rows tie within rounding at the k-th distance of a query",
+        set_error("top-k: more than %d store rows tie within rounding at the k-th distance of a query",
                   kTkFallbackCap);
         rc = DL_EUNSUPPORTED;
     }
-    if (rc) {
-        kill_events();
-        return fail(rc);
+    if (rc) return done(rc);
+    if (stats) {
+        dl_join_stats &s = *stats;
+        s.pairs_evaluated = nQ * nS;
+        s.pairs_out = 0;
+        s.band_pairs = flagged;   // rows re-solved by the exact scan
+        s.fp64_pairs = (int64_t)h2[1];
+        s.precision = use_tc ? DL_PREC_BF16 : DL_PREC_FP32;
+        s.tile_n = use_tc ? BN : 0;
+        s.kernels_launched = launches;
+        if (o.timing) {
+            cudaEventElapsedTime(&s.ms_main, ev[0], ev[1]);
+            cudaEventElapsedTime(&s.ms_recheck, ev[1], ev[2]);
+            cudaEventElapsedTime(&s.ms_total, ev[0], ev[2]);
+        }
     }
+    return done(DL_OK);
+}
+
+}  // namespace dl
+
+using namespace dl;
+
+extern "C" int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric, int32_t k, const dl_join_opts *opts,
+                            dl_result **out)
+{
+    clear_error();
+    if (!out) {
+        set_error("dl_topk_join: out is NULL");
+        return DL_EINVAL;
+    }
+    *out = nullptr;
+    if (!Q || !S) {
+        set_error("dl_topk_join: NULL store");
+        return DL_EINVAL;
+    }
+    if (metric != DL_METRIC_L2) {
+        set_error("dl_topk_join: unsupported metric %d", metric);
+        return DL_EINVAL;
+    }
+    if (k < 1 || k > 1024) {
+        set_error("dl_topk_join: k=%d out of range [1, 1024]", k);
+        return DL_EINVAL;
+    }
+    if (Q->d != S->d) {
+        set_error("dl_topk_join: dimension mismatch %d vs %d", Q->d, S->d);
+        return DL_EINVAL;
+    }
+    int dev = -1;
+    DL_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != Q->device || dev != S->device) {
+        set_error("dl_topk_join: stores live on another device");
+        return DL_EINVAL;
+    }
+    dl_join_opts o;
+    if (opts)
+        o = *opts;
+    else
+        dl_join_opts_default(&o);
+    if (o.precision != DL_PREC_AUTO && o.precision != DL_PREC_BF16 && o.precision != DL_PREC_FP32) {
+        set_error("dl_topk_join: precision %d not available for top-k", o.precision);
+        return DL_EUNSUPPORTED;
+    }
+    cudaStream_t st = (cudaStream_t)o.cuda_stream;
+    const int64_t nQ = Q->n;
+    void *resb = nullptr;
+    int rc = dev_alloc(&resb, std::max<size_t>(16, (size_t)nQ * k * 16), st);
+    if (rc) return rc;
+    int64_t *out_ids = (int64_t *)resb;
+    double *out_d2 = (double *)(out_ids + (size_t)nQ * k);
+    dl_join_stats stats{};
+    rc = topk_core(Q, S, k, nullptr, nullptr, out_ids, out_d2, o, st, &stats);
+    if (rc) {
+        dev_free(resb, st);
+        return rc;
+    }
+    stats.pairs_out = nQ * std::min<int64_t>(k, S->n);
     dl_result *res = new dl_result();
     res->kind = 1;
     res->device = dev;
@@ -624,21 +651,7 @@ extern "C" int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric
     res->nq = nQ;
     res->d_ids = out_ids;
     res->d_d2 = out_d2;
-    dl_join_stats &s = res->stats;
-    s.pairs_evaluated = nQ * nS;
-    s.pairs_out = nQ * std::min<int64_t>(k, nS);
-    s.band_pairs = flagged;            // rows re-solved by the exact scan
-    s.fp64_pairs = (int64_t)h2[1];
-    s.precision = use_tc ? DL_PREC_BF16 : DL_PREC_FP32;
-    s.tile_n = use_tc ? BN : 0;
-    s.kernels_launched = launches;
-    if (o.timing) {
-        cudaEventElapsedTime(&s.ms_main, ev[0], ev[1]);
-        cudaEventElapsedTime(&s.ms_recheck, ev[1], ev[2]);
-        cudaEventElapsedTime(&s.ms_total, ev[0], ev[2]);
-    }
-    kill_events();
-    dev_free(ws, st);
+    res->stats = stats;
     *out = res;
     return DL_OK;
 }

@@ -32,7 +32,7 @@ EXPORTS = [
     "dl_join_opts_default", "dl_store_create", "dl_store_destroy", "dl_store_shape",
     "dl_sim_join", "dl_topk_join", "dl_result_count", "dl_result_pairs", "dl_result_topk",
     "dl_result_stats", "dl_result_free", "dl_last_error", "dl_version", "dl_kernel_launches",
-    "dl_sim_join_noalloc",
+    "dl_sim_join_noalloc", "dl_batch_join", "dl_result_request_pairs", "dl_result_request_topk",
 ]
 
 
@@ -55,6 +55,13 @@ class dl_join_stats(ctypes.Structure):
                 ("ms_main", ctypes.c_float), ("ms_recheck", ctypes.c_float), ("ms_total", ctypes.c_float),
                 ("kernels_launched", ctypes.c_int32)]
 
+
+class dl_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("k", ctypes.c_int32), ("eps", ctypes.c_double),
+                ("q_begin", ctypes.c_int64), ("nq", ctypes.c_int64)]
+
+
+DL_REQ_EPS, DL_REQ_TOPK = 0, 1
 
 _lib = None
 
@@ -89,6 +96,13 @@ def load(path: str | None = None):
     L.dl_sim_join_noalloc.argtypes = [vp, vp, i64, vp, vp, i64, i32, f64, i32, vp, vp, i64,
                                       ctypes.POINTER(i64), vp]
     L.dl_sim_join_noalloc.restype = ctypes.c_int
+    L.dl_batch_join.argtypes = [vp, vp, vp, i64, i32, i32, ctypes.POINTER(dl_request), i32,
+                                ctypes.POINTER(dl_join_opts), pp]
+    L.dl_batch_join.restype = ctypes.c_int
+    L.dl_result_request_pairs.argtypes = [vp, i32, i32, pp, pp, ctypes.POINTER(i64)]
+    L.dl_result_request_pairs.restype = ctypes.c_int
+    L.dl_result_request_topk.argtypes = [vp, i32, i32, pp, pp, ctypes.POINTER(i32), ctypes.POINTER(i64)]
+    L.dl_result_request_topk.restype = ctypes.c_int
     L.dl_last_error.restype = ctypes.c_char_p
     L.dl_version.restype = ctypes.c_char_p
     L.dl_kernel_launches.restype = i64
@@ -280,3 +294,60 @@ def topk_join(Q: Store, S: Store, k: int, precision="auto", stream=None, timing=
     rc = load().dl_topk_join(Q.handle, S.handle, DL_METRIC_L2, int(k), ctypes.byref(o), ctypes.byref(h))
     _check(rc, "dl_topk_join")
     return Result(h)
+
+
+class BatchResult(Result):
+    """A batch result: per-request pairs (eps requests) or top-k rows (top-k requests)."""
+
+    def request_pairs(self, i: int):
+        a, b, n = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int64()
+        _check(load().dl_result_request_pairs(self._h, i, DL_MEM_HOST, ctypes.byref(a), ctypes.byref(b),
+                                              ctypes.byref(n)), "dl_result_request_pairs")
+        n = int(n.value)
+        if n == 0:
+            return np.empty(0, np.int64), np.empty(0, np.int64)
+        ra = np.ctypeslib.as_array(ctypes.cast(a, ctypes.POINTER(ctypes.c_int64)), shape=(n,)).copy()
+        sa = np.ctypeslib.as_array(ctypes.cast(b, ctypes.POINTER(ctypes.c_int64)), shape=(n,)).copy()
+        return ra, sa
+
+    def request_topk(self, i: int):
+        a, b = ctypes.c_void_p(), ctypes.c_void_p()
+        k, nq = ctypes.c_int32(), ctypes.c_int64()
+        _check(load().dl_result_request_topk(self._h, i, DL_MEM_HOST, ctypes.byref(a), ctypes.byref(b),
+                                             ctypes.byref(k), ctypes.byref(nq)), "dl_result_request_topk")
+        k, nq = int(k.value), int(nq.value)
+        if k * nq == 0:
+            return np.empty((nq, k), np.int64), np.empty((nq, k), np.float64)
+        ids = np.ctypeslib.as_array(ctypes.cast(a, ctypes.POINTER(ctypes.c_int64)), shape=(nq, k)).copy()
+        d2 = np.ctypeslib.as_array(ctypes.cast(b, ctypes.POINTER(ctypes.c_double)), shape=(nq, k)).copy()
+        return ids, d2
+
+
+def batch_join(S: Store, q_ids, q_feats, requests, stream=None, timing=False) -> BatchResult:
+    """dl_batch_join. `requests` is a list of dicts {kind: 'eps'|'topk', q_begin, nq, eps | k}."""
+    n = len(requests)
+    arr = (dl_request * n)()
+    for i, r in enumerate(requests):
+        arr[i].kind = DL_REQ_TOPK if r["kind"] == "topk" else DL_REQ_EPS
+        arr[i].k = int(r.get("k", 0) or 0)
+        arr[i].eps = float(r.get("eps", 0.0) or 0.0)
+        arr[i].q_begin = int(r["q_begin"])
+        arr[i].nq = int(r["nq"])
+    o = make_opts("auto", "upper", 0, stream, 0, timing)
+    h = ctypes.c_void_p()
+    if hasattr(q_feats, "data_ptr"):
+        import torch
+        q_feats = q_feats.contiguous().to(torch.float32)
+        q_ids = q_ids.contiguous().to(device=q_feats.device, dtype=torch.int64)
+        where = DL_MEM_DEVICE if q_feats.is_cuda else DL_MEM_HOST
+        fp, ip = q_feats.data_ptr(), q_ids.data_ptr()
+        nq_total, d = q_feats.shape
+    else:
+        q_feats = np.ascontiguousarray(q_feats, dtype=np.float32)
+        q_ids = np.ascontiguousarray(q_ids, dtype=np.int64)
+        where = DL_MEM_HOST
+        fp, ip = q_feats.ctypes.data, q_ids.ctypes.data
+        nq_total, d = q_feats.shape
+    rc = load().dl_batch_join(S.handle, ip, fp, nq_total, d, where, arr, n, ctypes.byref(o), ctypes.byref(h))
+    _check(rc, "dl_batch_join")
+    return BatchResult(h)
