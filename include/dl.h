@@ -207,6 +207,59 @@ int dl_result_request_topk(dl_result *r, int32_t req, int32_t where, const int64
                            const double **dist2, int32_t *k, int64_t *nq);
 
 /* ---------------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching over a resident store.
+ * ------------------------------------------------------------------------------- */
+
+typedef struct dl_server_stats {
+    int64_t completed;            /* requests finished */
+    int64_t failed;               /* requests whose batch failed (resubmittable) */
+    int64_t batches;              /* batches launched */
+    int64_t queued;               /* requests waiting for a slot */
+    int32_t in_flight_batches;    /* batches on the GPU now */
+    int64_t admission_waits;      /* times the head request waited for memory */
+    double p50_ms, p99_ms, max_ms, mean_ms;   /* submit-to-ready latency of completed requests */
+    double mean_batch_requests;   /* requests per batch */
+} dl_server_stats;
+
+/*
+ * Start a request loop over store S (kept resident; it must outlive the server).
+ * Up to `slots` batches (1..8) run at once, each on its own CUDA stream, so work
+ * of consecutive batches overlaps on the device. A batch takes queued requests
+ * in arrival order up to `max_batch_rows` query rows and as long as their memory
+ * estimate fits both `mem_budget_bytes` minus what is in flight and the
+ * device's free memory. The paper has no serving layer; this serves its
+ * image-matching queries (Sec. 6.2) arriving one by one.
+ */
+int dl_server_create(dl_server **out, const dl_store *S, int64_t mem_budget_bytes, int32_t slots,
+                     int64_t max_batch_rows, const dl_join_opts *opts);
+
+/*
+ * Queue one request: nq query rows (host memory, copied) and either an
+ * epsilon-join (kind DL_REQ_EPS, eps) or a top-k join (DL_REQ_TOPK, k). Returns
+ * a ticket. DL_ENOMEM_ADMIT if the request could never fit the budget or the
+ * batch row limit.
+ */
+int dl_submit(dl_server *sv, const int64_t *q_ids, const float *q_feats, int64_t nq, int32_t kind, double eps,
+              int32_t k, uint64_t *ticket);
+
+/*
+ * Result of a ticket: DL_OK with *out set (a single-request result, free with
+ * dl_result_free); DL_EAGAIN if not ready and timeout_us == 0; DL_ETIMEOUT if
+ * not ready after waiting timeout_us; DL_ECANCELED; DL_EFAILED (resubmit). A
+ * ticket is consumed by the call that returns its final status.
+ */
+int dl_poll(dl_server *sv, uint64_t ticket, int64_t timeout_us, dl_result **out);
+
+/* Cancel a request that is still queued (DL_EAGAIN if it is already running). */
+int dl_cancel(dl_server *sv, uint64_t ticket);
+
+/* Latency and batching statistics. */
+int dl_server_get_stats(dl_server *sv, dl_server_stats *st);
+
+/* Stop the loop: queued requests are dropped, running batches finish first. */
+int dl_server_destroy(dl_server *sv);
+
+/* ---------------------------------------------------------------------------------
  * Results.
  * ------------------------------------------------------------------------------- */
 

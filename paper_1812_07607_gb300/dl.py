@@ -33,6 +33,7 @@ EXPORTS = [
     "dl_sim_join", "dl_topk_join", "dl_result_count", "dl_result_pairs", "dl_result_topk",
     "dl_result_stats", "dl_result_free", "dl_last_error", "dl_version", "dl_kernel_launches",
     "dl_sim_join_noalloc", "dl_batch_join", "dl_result_request_pairs", "dl_result_request_topk",
+    "dl_server_create", "dl_submit", "dl_poll", "dl_cancel", "dl_server_get_stats", "dl_server_destroy",
 ]
 
 
@@ -62,6 +63,13 @@ class dl_request(ctypes.Structure):
 
 
 DL_REQ_EPS, DL_REQ_TOPK = 0, 1
+
+
+class dl_server_stats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("in_flight_batches", ctypes.c_int32),
+                ("admission_waits", ctypes.c_int64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("mean_batch_requests", ctypes.c_double)]
 
 _lib = None
 
@@ -103,6 +111,14 @@ def load(path: str | None = None):
     L.dl_result_request_pairs.restype = ctypes.c_int
     L.dl_result_request_topk.argtypes = [vp, i32, i32, pp, pp, ctypes.POINTER(i32), ctypes.POINTER(i64)]
     L.dl_result_request_topk.restype = ctypes.c_int
+    L.dl_server_create.argtypes = [pp, vp, i64, i32, i64, ctypes.POINTER(dl_join_opts)]
+    L.dl_submit.argtypes = [vp, vp, vp, i64, i32, f64, i32, ctypes.POINTER(ctypes.c_uint64)]
+    L.dl_poll.argtypes = [vp, ctypes.c_uint64, i64, pp]
+    L.dl_cancel.argtypes = [vp, ctypes.c_uint64]
+    L.dl_server_get_stats.argtypes = [vp, ctypes.POINTER(dl_server_stats)]
+    L.dl_server_destroy.argtypes = [vp]
+    for name in ("dl_server_create", "dl_submit", "dl_poll", "dl_cancel", "dl_server_get_stats", "dl_server_destroy"):
+        getattr(L, name).restype = ctypes.c_int
     L.dl_last_error.restype = ctypes.c_char_p
     L.dl_version.restype = ctypes.c_char_p
     L.dl_kernel_launches.restype = i64
@@ -351,3 +367,58 @@ def batch_join(S: Store, q_ids, q_feats, requests, stream=None, timing=False) ->
     rc = load().dl_batch_join(S.handle, ip, fp, nq_total, d, where, arr, n, ctypes.byref(o), ctypes.byref(h))
     _check(rc, "dl_batch_join")
     return BatchResult(h)
+
+
+class Server:
+    """dl_server: a request loop with continuous batching over a resident store."""
+
+    def __init__(self, S: Store, mem_budget_bytes: int = 8 << 30, slots: int = 2, max_batch_rows: int = 65536,
+                 precision="auto"):
+        self._store = S
+        o = make_opts(precision, "upper", 0, 0, 0, False)
+        h = ctypes.c_void_p()
+        _check(load().dl_server_create(ctypes.byref(h), S.handle, int(mem_budget_bytes), int(slots),
+                                       int(max_batch_rows), ctypes.byref(o)), "dl_server_create")
+        self._h = h
+
+    def submit(self, ids, feats, kind="eps", eps=0.0, k=0) -> int:
+        feats = np.ascontiguousarray(feats, dtype=np.float32)
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        t = ctypes.c_uint64()
+        rc = load().dl_submit(self._h, ids.ctypes.data, feats.ctypes.data, feats.shape[0],
+                              DL_REQ_TOPK if kind == "topk" else DL_REQ_EPS, float(eps), int(k), ctypes.byref(t))
+        _check(rc, "dl_submit")
+        return int(t.value)
+
+    def poll(self, ticket: int, timeout_us: int = 0):
+        """Result when ready; None while pending (DL_EAGAIN / DL_ETIMEOUT); raises on other errors."""
+        h = ctypes.c_void_p()
+        rc = load().dl_poll(self._h, ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(h))
+        if rc in (DL_EAGAIN, DL_ETIMEOUT):
+            return None
+        _check(rc, "dl_poll")
+        return Result(h)
+
+    def poll_status(self, ticket: int, timeout_us: int = 0):
+        h = ctypes.c_void_p()
+        rc = load().dl_poll(self._h, ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(h))
+        return rc, (Result(h) if rc == DL_OK else None)
+
+    def cancel(self, ticket: int) -> int:
+        return int(load().dl_cancel(self._h, ctypes.c_uint64(ticket)))
+
+    def stats(self) -> dict:
+        st = dl_server_stats()
+        _check(load().dl_server_get_stats(self._h, ctypes.byref(st)), "dl_server_get_stats")
+        return {f: getattr(st, f) for f, _ in dl_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().dl_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
