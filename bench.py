@@ -33,6 +33,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "exact eps-join pair-distances/sec"
 UNIT = "Gpairs/s"
+SEED_BATCH = 1812076074
+SEED_SERVE = 1812076075
 L2_FLUSH_BYTES = 512 << 20      # > 129 MB L2
 
 
@@ -45,6 +47,10 @@ def parse():
     ap.add_argument("--precision", default="bf16")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle sample")
     ap.add_argument("--no-baselines", action="store_true", help="skip the plain-FP32 and CPU legs")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-requests leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serving-seconds", type=float, default=4.0)
+    ap.add_argument("--serving-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
     return ap.parse_args()
 
 
@@ -166,6 +172,114 @@ def cpu_oracle_rate(wl, budget_s: float):
     dt = time.perf_counter() - t0
     pairs = rows * n
     return pairs / dt / 1e9, {"rows": rows, "pairs": pairs, "seconds": round(dt, 3)}
+
+
+def batch_leg(dl, store, n_store, n_req=256, seed=SEED_BATCH):
+    """Many eps / top-k requests of uneven sizes in one dl_batch_join (the batching config's mix).
+
+    Request sizes lognormal(5, 1.5) clipped to [1, 8192]; 70% eps-joins at a selectivity
+    uniform in [0.05%, 0.5%] of the store, 30% top-k with k = 10; queries are fresh jitters of
+    the store's centroids. Returns throughput in pairs evaluated per second.
+    """
+    import torch
+    from paper_1812_07607_gb300 import workloads as W
+    g = W.rng(seed)
+    reqs = W.request_mix(g, n_req, 5.0, 1.5, 8192, topk_frac=0.3, ks=(10,), sel_lo=5e-4, sel_hi=5e-3)
+    table = W.eps_table()["self_clustered_262k:selectivity_eps"]
+    off = 0
+    for r in reqs:
+        r["q_begin"] = off
+        off += r["nq"]
+        if r["kind"] == "eps":
+            r["eps"] = W.eps_for_selectivity(table, r["selectivity"])
+    Q = W.self_clustered_queries(off, seed + 1)
+    qid = np.arange(off, dtype=np.int64)
+    Qd = torch.from_numpy(Q).cuda()
+    qd = torch.from_numpy(qid).cuda()
+    times, st, out_pairs = [], None, 0
+    for i in range(4):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = dl.batch_join(store, qd, Qd, reqs)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        st = res.stats()
+        out_pairs = res.count()
+        res.free()
+        if i > 0:
+            times.append(dt)
+    t = statistics.median(times)
+    pairs = off * n_store
+    return {"value": pairs / t / 1e9, "unit": UNIT, "ms_per_batch": 1e3 * t, "requests": n_req,
+            "requests_per_s": n_req / t, "query_rows": off, "pairs_out": out_pairs,
+            "band_pairs": st["band_pairs"], "fp64_pairs": st["fp64_pairs"],
+            "config": "262,144 x 128 store; 256 requests, sizes lognormal(5,1.5) in [1,8192]; "
+                      "70% eps at selectivity U[0.05%,0.5%], 30% top-k k=10"}
+
+
+def serving_leg(dl, store, n_store, seconds=4.0, rate=2000.0, seed=SEED_SERVE):
+    """Poisson arrivals into the request loop; p50/p99 submit-to-ready latency and throughput.
+
+    Mix of the serving config: 70% eps-joins (selectivity U[0.05%, 0.5%]) and 30% top-k with
+    k uniform over {1, 10, 100}; query sizes lognormal(4, 1.5) clipped to [1, 4096].
+    """
+    import threading
+    from paper_1812_07607_gb300 import workloads as W
+    g = W.rng(seed)
+    n = int(seconds * rate)
+    reqs = W.request_mix(g, n, 4.0, 1.5, 4096, topk_frac=0.3, ks=(1, 10, 100), sel_lo=5e-4, sel_hi=5e-3)
+    table = W.eps_table()["self_clustered_262k:selectivity_eps"]
+    arrivals = np.cumsum(g.exponential(1.0 / rate, size=n))
+    total = sum(r["nq"] for r in reqs)
+    Q = W.self_clustered_queries(total, seed + 1)
+    sv = dl.Server(store, mem_budget_bytes=32 << 30, slots=3, max_batch_rows=65536)
+    tickets = []
+    lock = threading.Lock()
+    done_pairs = [0]
+
+    def submitter():
+        off = 0
+        t0 = time.perf_counter()
+        for i, r in enumerate(reqs):
+            while time.perf_counter() - t0 < arrivals[i]:
+                time.sleep(5e-5)
+            q = Q[off:off + r["nq"]]
+            ids = np.arange(off, off + r["nq"], dtype=np.int64)
+            off += r["nq"]
+            if r["kind"] == "eps":
+                t = sv.submit(ids, q, "eps", eps=W.eps_for_selectivity(table, r["selectivity"]))
+            else:
+                t = sv.submit(ids, q, "topk", k=r["k"])
+            with lock:
+                tickets.append(t)
+
+    th = threading.Thread(target=submitter)
+    t_start = time.perf_counter()
+    th.start()
+    got = 0
+    while got < n:
+        with lock:
+            pend = tickets[got:]
+        if not pend:
+            time.sleep(1e-4)
+            continue
+        res = sv.poll(pend[0], timeout_us=200_000)
+        if res is None:
+            continue
+        res.free()
+        got += 1
+    wall = time.perf_counter() - t_start
+    th.join()
+    st = sv.stats()
+    sv.close()
+    pairs = total * n_store
+    return {"offered_req_per_s": rate, "requests": n, "seconds": wall, "completed": st["completed"],
+            "req_per_s": st["completed"] / wall, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "max_ms": st["max_ms"], "pairs_per_s_G": pairs / wall / 1e9, "batches": st["batches"],
+            "mean_batch_requests": st["mean_batch_requests"],
+            "config": "262,144 x 128 store resident; Poisson arrivals; 70% eps at selectivity "
+                      "U[0.05%,0.5%] / 30% top-k k in {1,10,100}; sizes lognormal(4,1.5) in [1,4096]; "
+                      "3 stream slots"}
 
 
 def run_reference(args):
@@ -315,6 +429,13 @@ def run_ours(args):
             "peak_kind": f"bf16 dense burst ({pk['source']})",
             "algorithmic": f"2*d flops/pair x {P} pairs = {flops:.4g} flops per launch"}
 
+    batch = None
+    if rank == 0 and not args.no_batch:
+        batch = batch_leg(dl, store, n)
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = serving_leg(dl, store, n, seconds=args.serving_seconds, rate=args.serving_rate)
+
     cpu = None
     if rank == 0 and not args.no_baselines:
         v, info = cpu_oracle_rate(wl, args.cpu_seconds)
@@ -339,6 +460,8 @@ def run_ours(args):
             "roofline": roof,
             "cpu_baseline": cpu,
             "plain_fp32_gpu": plain,
+            "batch": batch,
+            "serving": serving,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

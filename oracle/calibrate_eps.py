@@ -80,14 +80,21 @@ def calibrate(name: str) -> tuple[str, float, dict]:
         wl = W.self_clustered_262k(eps=0.0)
         g = W.rng(W.SEED_BASE + 101)
         rows = np.sort(g.choice(wl.R.shape[0], size=512, replace=False))
-        sm = smallest_per_row(wl.R[rows], wl.R, keep=400, excl=rows)
+        sm = smallest_per_row(wl.R[rows], wl.R, keep=1600, excl=rows)
         vals = np.sort(sm.ravel())
         target = 20 * len(rows)
         eps = eps_in_gap(vals, target)
         key = f"self_clustered_262k:{W.SEED_BASE + 1}:262144:128:8192"
         per_row = (sm <= eps * eps).sum(axis=1)
+        # selectivity -> eps table (batch / serving request mixes): pooled quantiles of the
+        # sampled rows' canonical distances, s = matches per row / (N - 1)
+        table = []
+        for sel in np.geomspace(1e-5, 5.5e-3, 40):
+            rank = int(round(sel * (wl.R.shape[0] - 1) * len(rows)))
+            table.append([float(sel), eps_in_gap(vals, max(1, rank))])
+        extra = {"self_clustered_262k:selectivity_eps": table}
         return key, eps, {"sample_rows": 512, "mean_matches": float(per_row.mean()),
-                          "max_row_kept_fill": float((sm[:, -1] <= eps * eps).mean())}
+                          "max_row_kept_fill": float((sm[:, -1] <= eps * eps).mean()), "extra": extra}
     if name == "rxs_unit_mixture_1m":
         wl = W.rxs_unit_mixture_1m(eps=0.0)
         g = W.rng(W.SEED_BASE + 102)
@@ -109,6 +116,7 @@ def main(names):
     for n in names:
         key, eps, info = calibrate(n)
         table[key] = eps
+        table.update(info.pop("extra", {}))
         print(n, key, repr(eps), info, file=sys.stderr)
         with open(OUT, "w") as f:
             json.dump(table, f, indent=1, sort_keys=True)

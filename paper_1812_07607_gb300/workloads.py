@@ -96,6 +96,12 @@ def patch_ids(g: np.random.Generator, n: int) -> np.ndarray:
     return base * 7919 + 1_000_003
 
 
+def eps_for_selectivity(table, sel: float) -> float:
+    """eps for a target selectivity from a stored (selectivity, eps) table (log-linear interpolation)."""
+    t = np.asarray(table, dtype=np.float64)
+    return float(np.interp(np.log(sel), np.log(t[:, 0]), t[:, 1]))
+
+
 def eps_table() -> dict:
     """Calibrated epsilon per named workload (written by the oracle's calibration)."""
     with open(_EPS_FILE) as f:
@@ -151,6 +157,20 @@ def self_clustered_262k(seed: int = SEED_BASE + 1, n: int = 262144, d: int = 128
     if eps is None:
         eps = eps_table().get(f"self_clustered_262k:{seed}:{n}:{d}:{n_centroids}")
     return JoinWorkload("self_clustered_262k", X, None, ids, None, eps)
+
+
+def self_clustered_queries(n: int, seed_q: int, seed: int = SEED_BASE + 1, d: int = 128,
+                           n_centroids: int = 8192, sigma: float = 0.01) -> np.ndarray:
+    """Fresh query patches for the 262,144-patch store: new jitters of the store's own centroids."""
+    cents = rng(seed).dirichlet(np.full(d, 0.5, dtype=np.float64), size=n_centroids)
+    g = rng(seed_q)
+    c = cents[g.integers(0, n_centroids, size=n)]
+    x = np.clip(c + g.normal(0.0, sigma, size=(n, d)), 0.0, None)
+    s = x.sum(axis=1, keepdims=True)
+    bad = s[:, 0] <= 0.0
+    x[bad] = c[bad]
+    s[bad] = 1.0
+    return (x / s).astype(np.float32)
 
 
 def rxs_unit_mixture_1m(seed: int = SEED_BASE + 2, n: int = 1048576, d: int = 512,
