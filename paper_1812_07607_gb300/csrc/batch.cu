@@ -54,7 +54,10 @@ __global__ void k_batch_expand(const ReqDev *__restrict__ reqs, int n, int64_t t
     row_req[i] = r.req;
 }
 
-// Candidates -> decisions in place (rejected entries get column 0xffffffff) and per-request counts.
+// Candidates -> decisions in place (rejected entries get column 0xffffffff) and
+// per-request counts. One thread per entry: band entries are rechecked by
+// their own thread (sequential FP32 with its bound, canonical FP64 if needed);
+// counts are aggregated per warp over lanes of the same request.
 __global__ void __launch_bounds__(256)
     k_batch_decide(uint2 *__restrict__ cand, const unsigned long long *__restrict__ cand_cnt, unsigned long long cap,
                    const float *__restrict__ Q, const float *__restrict__ S, int d, const double *__restrict__ row_e2,
@@ -63,37 +66,29 @@ __global__ void __launch_bounds__(256)
 {
     const unsigned lane = threadIdx.x & 31;
     const unsigned long long n = min(*cand_cnt, cap);
-    const unsigned long long w0 = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-    for (unsigned long long base = w0 * 32; base < n; base += nw * 32) {
-        const unsigned long long i = base + lane;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const unsigned long long i = base + threadIdx.x;   // warp-uniform loop bound: base < n
         const bool valid = i < n;
         const uint2 e = valid ? cand[i] : make_uint2(0u, 0u);
         const int r = (int)e.x;
         const int c = (int)(e.y & ~kBandFlag);
         const bool band = valid && (e.y & kBandFlag);
         bool acc = valid && !band;
-        unsigned bm = __ballot_sync(0xffffffffu, band);
-        if (lane == 0 && bm) atomicAdd(n_band, (unsigned long long)__popc(bm));
-        while (bm) {
-            const int l = __ffs(bm) - 1;
-            bm &= bm - 1;
-            const int rr = __shfl_sync(0xffffffffu, r, l);
-            const int cc = __shfl_sync(0xffffffffu, c, l);
-            const double e2 = row_e2[rr];
+        bool f64 = false;
+        if (band) {
+            const double e2 = row_e2[r];
             float ta, tr;
             fp32_thresholds(e2, d, &ta, &tr);
-            const bool dec = warp_exact_decide(Q + (size_t)rr * d, S + (size_t)cc * d, d, e2, ta, tr, n_fp64);
-            if ((int)lane == l) acc = dec;
+            acc = lane_exact_decide(Q + (size_t)r * d, S + (size_t)c * d, d, e2, ta, tr, &f64);
         }
-        if (valid) {
-            if (acc) {
-                cand[i] = make_uint2((uint32_t)r, (uint32_t)c);
-                atomicAdd(req_cnt + row_req[r], 1ULL);
-            } else {
-                cand[i] = make_uint2((uint32_t)r, 0xffffffffu);
-            }
+        const unsigned bm = __ballot_sync(0xffffffffu, band), fm = __ballot_sync(0xffffffffu, f64);
+        if (lane == 0) {
+            if (bm) atomicAdd(n_band, (unsigned long long)__popc(bm));
+            if (fm) atomicAdd(n_fp64, (unsigned long long)__popc(fm));
         }
+        grouped_add(req_cnt, acc ? row_req[r] : 0, acc, 1u);
+        if (valid) cand[i] = acc ? make_uint2((uint32_t)r, (uint32_t)c) : make_uint2((uint32_t)r, 0xffffffffu);
     }
 }
 
@@ -104,14 +99,19 @@ __global__ void __launch_bounds__(256)
                     const int64_t *__restrict__ s_ids, int64_t *__restrict__ out_r, int64_t *__restrict__ out_s)
 {
     const unsigned long long n = min(*cand_cnt, cap);
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint2 e = cand[i];
-        if (e.y == 0xffffffffu) continue;
-        const int32_t q = row_req[e.x];
-        const int64_t o = req_off[q] + (int64_t)atomicAdd(cursor + q, 1ULL);
-        out_r[o] = q_ids[e.x];
-        out_s[o] = s_ids[e.y];
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const unsigned long long i = base + threadIdx.x;
+        const bool valid = i < n;
+        const uint2 e = valid ? cand[i] : make_uint2(0u, 0xffffffffu);
+        const bool acc = valid && e.y != 0xffffffffu;
+        const int32_t q = acc ? row_req[e.x] : 0;
+        const unsigned long long pos = grouped_add(cursor, q, acc, 1u);
+        if (acc) {
+            const int64_t o = req_off[q] + (int64_t)pos;
+            out_r[o] = q_ids[e.x];
+            out_s[o] = s_ids[e.y];
+        }
     }
 }
 
@@ -170,7 +170,6 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
     // ---- request tables (host bookkeeping of n_req entries)
     std::vector<ReqDev> er, kr;
     int64_t ne = 0, nk = 0, slots = 0;
-    int kmax = 0;
     std::vector<int64_t> topk_off(n_req + 1, 0);
     for (int i = 0; i < n_req; ++i) {
         const dl_request &q = reqs[i];
@@ -202,11 +201,23 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
             topk_off[i] = slots;
             slots += q.nq * q.k;
             nk += q.nq;
-            kmax = std::max(kmax, (int)q.k);
             kr.push_back(r);
         } else {
             set_error("dl_batch_join: request %d has kind %d", i, q.kind);
             return DL_EINVAL;
+        }
+    }
+    // top-k rows are grouped by k (each group runs with its own heap size)
+    std::stable_sort(kr.begin(), kr.end(), [](const ReqDev &a, const ReqDev &b) { return a.k < b.k; });
+    std::vector<std::pair<int, std::pair<int64_t, int64_t>>> kgroups;   // k -> [first row, end row)
+    {
+        int64_t off = 0;
+        for (auto &r : kr) {
+            const int64_t nq = reqs[r.req].nq;
+            r.seg_off = off;
+            if (kgroups.empty() || kgroups.back().first != r.k) kgroups.push_back({r.k, {off, off}});
+            off += nq;
+            kgroups.back().second.second = off;
         }
     }
     if (ne >= (int64_t(1) << 31) || nk >= (int64_t(1) << 31)) {
@@ -447,13 +458,16 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
         }
     }
     // ---- top-k part
-    if (nk > 0) {
+    for (const auto &grp : kgroups) {
+        const int kg = grp.first;
+        const int64_t g0 = grp.second.first, g1 = grp.second.second;
+        if (g1 <= g0) continue;
         dl_store *Qk = nullptr;
-        rc = store_create_impl(&Qk, dq_ids, dq, nk, d, DL_MEM_DEVICE, st, g_k);
+        rc = store_create_impl(&Qk, dq_ids, dq, g1 - g0, d, DL_MEM_DEVICE, st, g_k + g0);
         if (!rc) {
             stores.push_back(Qk);
             dl_join_stats ts{};
-            rc = topk_core(Qk, S, kmax, row_k, row_off, (int64_t *)tk_block,
+            rc = topk_core(Qk, S, kg, row_k + g0, row_off + g0, (int64_t *)tk_block,
                            (double *)((char *)tk_block + al(slots * 8)), o, st, &ts);
             stats.fp64_pairs += ts.fp64_pairs;
         }

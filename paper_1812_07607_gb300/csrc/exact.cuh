@@ -50,4 +50,50 @@ __device__ __forceinline__ bool warp_exact_decide(const float *__restrict__ q, c
     return sum <= e2;
 }
 
+// Exact decision for one pair by ONE thread: sequential FP32 FMA chain (bound
+// (d+8) 2^-24 D, the same as the warp version's), then the canonical FP64 sum
+// only when FP32 cannot decide. For lists where most entries are band pairs.
+__device__ __forceinline__ bool lane_exact_decide(const float *__restrict__ q, const float *__restrict__ x, int d,
+                                                  double e2, float t_acc, float t_rej, bool *used_fp64)
+{
+    float s = 0.f;
+    for (int k = 0; k < d; ++k) {
+        const float t = __ldg(q + k) - __ldg(x + k);
+        s = fmaf(t, t, s);
+    }
+    *used_fp64 = false;
+    if (s <= t_acc) return true;
+    if (s > t_rej) return false;
+    *used_fp64 = true;
+    double sum = 0.0;
+    for (int k = 0; k < d; ++k) {
+        const double t = __dsub_rn((double)__ldg(q + k), (double)__ldg(x + k));
+        sum = __dadd_rn(sum, __dmul_rn(t, t));
+    }
+    return sum <= e2;
+}
+
+// Warp-aggregated atomicAdd of `v` to counter[key]: lanes with equal keys are
+// grouped (__match_any_sync), the group's lowest lane adds the group's total and
+// every lane gets its own offset. Every lane of the warp must call it; lanes
+// with active == false add nothing.
+__device__ __forceinline__ unsigned long long grouped_add(unsigned long long *counter, int key, bool active,
+                                                          unsigned v)
+{
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned act = __ballot_sync(0xffffffffu, active);
+    unsigned long long off = 0;
+    if (active) {
+        const unsigned peers = __match_any_sync(act, key);
+        const int leader = __ffs(peers) - 1;
+        const unsigned below = peers & ((1u << lane) - 1u);
+        // prefix of v over the lower peers (v is 1 for every caller here, so popc)
+        unsigned long long base = 0;
+        if ((int)lane == leader) base = atomicAdd(counter + key, (unsigned long long)(__popc(peers) * v));
+        base = __shfl_sync(peers, base, leader);
+        off = base + (unsigned long long)__popc(below) * v;
+    }
+    return off;
+}
+
 }  // namespace dl

@@ -161,14 +161,16 @@ __device__ __forceinline__ uint32_t slow_piece(const TcParams &p, const uint32_t
 // top-k column has U >= h >= the k-th largest h >= theta, so it is in the list.
 // Returns the new (theta, fill) packed in a float2.
 __device__ __noinline__ float2 topk_insert(const TcParams &p, size_t sidx, int r, int c, float U, float L,
-                                           float theta, int cnt)
+                                           float theta, int cnt, float theta_row)
 {
     uint2 *list = p.tk_list + sidx * (size_t)p.tk_cap;
-    if (cnt >= p.tk_cap) {   // compact: drop columns whose upper bound fell below theta
+    if (cnt >= p.tk_cap) {   // compact: drop columns whose upper bound fell below the best threshold
+        const float th = fmaxf(theta, float_from_order_code(__ldcg(p.tk_row_theta + r)));
+        (void)theta_row;
         int w = 0;
         for (int i = 0; i < cnt; ++i) {
             const uint2 e = list[i];
-            if (__uint_as_float(e.y) >= theta) list[w++] = e;
+            if (__uint_as_float(e.y) >= th) list[w++] = e;
         }
         cnt = w;
         if (cnt >= p.tk_cap) {
@@ -193,6 +195,7 @@ __device__ __noinline__ float2 topk_insert(const TcParams &p, size_t sidx, int r
         }
         heap[i] = L;
         theta = heap[0];
+        atomicMax(p.tk_row_theta + r, float_order_code(theta));   // share with the row's other slots
     }
     return make_float2(theta, __int_as_float(cnt));
 }
@@ -201,7 +204,7 @@ __device__ __noinline__ float2 topk_insert(const TcParams &p, size_t sidx, int r
 // walks its own row's columns whose upper bound reaches its theta.
 __device__ __forceinline__ void slow_topk(const TcParams &p, const uint32_t (&v)[64], const float *nb, float eh0,
                                           float eh1, bool hit0, bool hit1, int r, int col0, size_t sidx,
-                                          float &theta, int &cnt)
+                                          float &theta, int &cnt, float theta_row)
 {
     if (r >= p.nR) return;
 #pragma unroll
@@ -213,8 +216,8 @@ __device__ __forceinline__ void slow_topk(const TcParams &p, const uint32_t (&v)
             const int c = col0 + hh * 32 + j;
             const float h = __uint_as_float(v[hh * 32 + j]) + nb[hh * 32 + j];
             const float U = __fadd_ru(h, eh);
-            if (c < p.nS && U >= theta) {
-                const float2 st = topk_insert(p, sidx, r, c, U, __fsub_rd(h, eh), theta, cnt);
+            if (c < p.nS && U >= fmaxf(theta, theta_row)) {
+                const float2 st = topk_insert(p, sidx, r, c, U, __fsub_rd(h, eh), theta, cnt, theta_row);
                 theta = st.x;
                 cnt = __float_as_int(st.y);
             }
@@ -429,6 +432,7 @@ __global__ void __launch_bounds__(320, 1)
         bool ok = true;
         float4 rp = make_float4(0.f, 0.f, 0.f, 0.f);
         float theta = 0.f;        // top-k: this slot's threshold (k-th largest lower bound of h)
+        float theta_row = 0.f;    // top-k: best threshold published by any slot of this row
         int tcnt = 0;             // top-k: this slot's list fill
         size_t sidx = 0;
         while (cur.valid) {
@@ -449,6 +453,10 @@ __global__ void __launch_bounds__(320, 1)
             float4 csn = make_float4(0.f, 0.f, 0.f, 0.f);
             stage_regs(nxt, nbn, csn);   // prefetch the next tile's -beta (latency hidden by this tile)
 
+            if constexpr (TOPK) {
+                theta_row = __int_as_float(0xff800000);
+                if (r < p.nR) theta_row = float_from_order_code(__ldcg(p.tk_row_theta + r));
+            }
             const uint32_t b = t & 1;
             const int slot = t & 1;
             if (!mbar_wait(acc_full + b, (t >> 1) & 1, abort_flag)) {
@@ -467,9 +475,10 @@ __global__ void __launch_bounds__(320, 1)
                 const float eh0 = __fmaf_ru(rp.z, cs0.x, __fmaf_ru(rp.w, cs0.y, cs0.z));
                 const float eh1 = __fmaf_ru(rp.z, cs1.x, __fmaf_ru(rp.w, cs1.y, cs1.z));
                 float tr0, tr1;
-                if constexpr (TOPK) {   // candidate iff h + E (+ canonical slack rp.x) >= theta
-                    tr0 = __fsub_rd(theta, __fadd_ru(eh0, rp.x));
-                    tr1 = __fsub_rd(theta, __fadd_ru(eh1, rp.x));
+                if constexpr (TOPK) {   // candidate iff h + E (+ canonical slack rp.x) >= the best threshold
+                    const float th = fmaxf(theta, theta_row);
+                    tr0 = __fsub_rd(th, __fadd_ru(eh0, rp.x));
+                    tr1 = __fsub_rd(th, __fadd_ru(eh1, rp.x));
                 } else {
                     tr0 = __fsub_rd(rp.y, eh0);
                     tr1 = __fsub_rd(rp.y, eh1);
@@ -499,7 +508,7 @@ __global__ void __launch_bounds__(320, 1)
                 if constexpr (TOPK) {
                     if (hit0 || hit1)
                         slow_topk(p, v, nbeta + piece * 64, __fadd_ru(eh0, rp.x), __fadd_ru(eh1, rp.x), hit0, hit1, r,
-                                  colw + piece * 64, sidx, theta, tcnt);
+                                  colw + piece * 64, sidx, theta, tcnt, theta_row);
                 } else {
                     if (__any_sync(0xffffffffu, hit0 || hit1))
                         scnt = slow_piece(p, v, nbeta + piece * 64, rp.x, rp.y, eh0, eh1, hit0, hit1, r,

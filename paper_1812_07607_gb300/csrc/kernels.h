@@ -32,6 +32,7 @@ struct TcParams {
     uint2 *tk_list;          // [rows][slots][cap] {column, float bits of the upper bound of h}
     int *tk_cnt;             // [rows][slots] list fill
     float *tk_theta;         // [rows][slots] final threshold (heap minimum)
+    unsigned *tk_row_theta;  // [rows] best threshold of any slot of the row (order-preserving encoding)
     int *tk_overflow;        // [rows] set when a list cannot hold every candidate
 };
 
@@ -78,5 +79,17 @@ int launch_diag(const int64_t *ids, int64_t n, int64_t *out_r, int64_t *out_s, u
 // ---- top-k core (topk.cu): every row of Q against S, outputs at row_off or caller row * k
 int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, const int64_t *row_off,
               int64_t *out_ids, double *out_d2, const dl_join_opts &o, cudaStream_t st, dl_join_stats *stats);
+
+// Order-preserving encoding of a float as unsigned (larger float -> larger code),
+// so that a running maximum can be kept with atomicMax.
+__device__ __forceinline__ unsigned float_order_code(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float float_from_order_code(unsigned c)
+{
+    return __uint_as_float((c & 0x80000000u) ? (c & 0x7fffffffu) : ~c);
+}
 
 }  // namespace dl

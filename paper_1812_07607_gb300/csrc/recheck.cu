@@ -33,8 +33,9 @@ __global__ void __launch_bounds__(256)
 }
 
 // Candidates of the tensor-core kernel -> id pairs. Each warp takes 32 entries:
-// proven matches are emitted as they are; the warp rechecks the band entries
-// one at a time (all lanes cooperate on each), then emits the survivors.
+// proven matches are emitted as they are, each band entry is rechecked by its
+// own lane (sequential FP32 with its bound, canonical FP64 if needed), then the
+// warp emits the survivors.
 __global__ void __launch_bounds__(256)
     k_finalize(const uint2 *__restrict__ cand, const unsigned long long *__restrict__ cand_cnt,
                unsigned long long cand_cap, const float *__restrict__ R, const float *__restrict__ S, int d, double e2,
@@ -53,15 +54,12 @@ __global__ void __launch_bounds__(256)
         const int c = (int)(e.y & ~kBandFlag);
         const bool band = valid && (e.y & kBandFlag);
         bool acc = valid && !band;
-        unsigned bm = __ballot_sync(0xffffffffu, band);
-        if (lane == 0 && bm) atomicAdd(n_band, (unsigned long long)__popc(bm));
-        while (bm) {
-            const int l = __ffs(bm) - 1;
-            bm &= bm - 1;
-            const int rr = __shfl_sync(0xffffffffu, r, l);
-            const int cc = __shfl_sync(0xffffffffu, c, l);
-            const bool dec = warp_exact_decide(R + (size_t)rr * d, S + (size_t)cc * d, d, e2, t_acc, t_rej, n_fp64);
-            if ((int)lane == l) acc = dec;
+        bool f64 = false;
+        if (band) acc = lane_exact_decide(R + (size_t)r * d, S + (size_t)c * d, d, e2, t_acc, t_rej, &f64);
+        const unsigned bm = __ballot_sync(0xffffffffu, band), fm = __ballot_sync(0xffffffffu, f64);
+        if (lane == 0) {
+            if (bm) atomicAdd(n_band, (unsigned long long)__popc(bm));
+            if (fm) atomicAdd(n_fp64, (unsigned long long)__popc(fm));
         }
         warp_emit(out, acc, false, r, c);
     }

@@ -37,6 +37,8 @@ struct TopkFin {
     const float *Q, *S;
     int d, nQ, nS, k, slots, cap;
     const float *theta;
+    const float *heap;     // [rows][slots][k] each slot's k largest lower bounds
+    const unsigned *row_theta;
     const int *cnt;
     const uint2 *list;
     int *overflow;
@@ -71,8 +73,46 @@ __device__ __forceinline__ float seq_d32(const float *__restrict__ q, const floa
     return s;
 }
 
+// k-th largest of n floats (by order code), found by one warp with a 4-pass
+// radix select over 8-bit digits; -inf when n < k. hist: 256 words of shared memory.
+__device__ float warp_kth_largest(const float *__restrict__ vals, int n, int k, unsigned *hist)
+{
+    const unsigned lane = threadIdx.x & 31;
+    if (n < k) return __int_as_float(0xff800000);
+    unsigned prefix = 0u, mask = 0u;
+    unsigned rank = (unsigned)(k - 1);   // 0-based, counted from the largest
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int t = lane; t < 256; t += 32) hist[t] = 0u;
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+            const unsigned c = float_order_code(vals[i]);
+            if ((c & mask) == prefix) atomicAdd(&hist[(c >> shift) & 255u], 1u);
+        }
+        __syncwarp();
+        unsigned digit = 0u, r2 = 0u;
+        if (lane == 0) {
+            unsigned acc = 0u;
+            for (int dg = 255; dg >= 0; --dg) {
+                if (acc + hist[dg] > rank) {
+                    digit = (unsigned)dg;
+                    r2 = rank - acc;
+                    break;
+                }
+                acc += hist[dg];
+            }
+        }
+        digit = __shfl_sync(0xffffffffu, digit, 0);
+        rank = __shfl_sync(0xffffffffu, r2, 0);
+        prefix |= digit << shift;
+        mask |= 255u << shift;
+        __syncwarp();
+    }
+    return float_from_order_code(prefix);
+}
+
 __global__ void __launch_bounds__(128) k_topk_finalize(const TopkFin f)
 {
+    __shared__ unsigned s_hist[4][256];
     __shared__ uint32_t s_col[4][kTkMax];
     __shared__ float s_u[4][kTkMax];
     __shared__ float s_l[4][kTkMax];
@@ -85,9 +125,13 @@ __global__ void __launch_bounds__(128) k_topk_finalize(const TopkFin f)
     double *sd = s_d[w];
     for (int i = blockIdx.x * 4 + w; i < f.nQ; i += gridDim.x * 4) {
         if (f.overflow[i]) continue;
-        // largest theta over the row's slots: every top-k column has U >= it
-        float th = __int_as_float(0xff800000);
+        // the row's k-th largest lower bound over all slots' heaps (the heaps hold each
+        // slot's k largest): every top-k column has U >= it
+        const int kk0 = f.row_k ? f.row_k[i] : f.k;
+        float th = warp_kth_largest(f.heap + (size_t)i * f.slots * f.k, f.slots * f.k, kk0, s_hist[w]);
         for (int s = lane; s < f.slots; s += 32) th = fmaxf(th, f.theta[(size_t)i * f.slots + s]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) th = fmaxf(th, __shfl_xor_sync(0xffffffffu, th, o));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) th = fmaxf(th, __shfl_xor_sync(0xffffffffu, th, o));
         int m = 0;
@@ -294,10 +338,11 @@ __global__ void __launch_bounds__(256) k_topk_fallback(const TopkFb f)
 // Per query row: {canonical slack of h, unused, ||q - q~|| up, ||q~|| up}; padding rows get zeros.
 __global__ void __launch_bounds__(256) k_rowpar_topk(const double *__restrict__ nq64, const float4 *__restrict__ rowb,
                                                      int64_t n, int64_t n_tot, double g64, double nq_max_s,
-                                                     float4 *__restrict__ rowpar)
+                                                     float4 *__restrict__ rowpar, unsigned *__restrict__ row_theta)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_tot) return;
+    row_theta[i] = float_order_code(__int_as_float(0xff800000));   // -inf
     if (i >= n) {
         rowpar[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
@@ -376,10 +421,11 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
     const size_t b_rowpar = al256(rows * sizeof(float4)), b_heap = al256((size_t)rows * slots * k * sizeof(float)),
                  b_list = al256((size_t)rows * slots * cap * sizeof(uint2)),
                  b_cnt = al256((size_t)rows * slots * sizeof(int)), b_theta = al256((size_t)rows * slots * sizeof(float)),
+                 b_rth = al256((size_t)std::max<int64_t>(rows, 1) * sizeof(unsigned)),
                  b_ovf = al256((size_t)std::max<int64_t>(nQ, 1) * sizeof(int)),
                  b_rows = al256((size_t)std::max<int64_t>(nQ, 1) * sizeof(int)), b_misc = 256;
     void *ws = nullptr;
-    int rc = dev_alloc(&ws, b_rowpar + b_heap + b_list + b_cnt + b_theta + b_ovf + b_rows + b_misc, st);
+    int rc = dev_alloc(&ws, b_rowpar + b_heap + b_list + b_cnt + b_theta + b_rth + b_ovf + b_rows + b_misc, st);
     if (rc) return rc;
     char *pw = (char *)ws;
     float4 *rowpar = (float4 *)pw;
@@ -392,6 +438,8 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
     pw += b_cnt;
     float *theta = (float *)pw;
     pw += b_theta;
+    unsigned *row_theta = (unsigned *)pw;
+    pw += b_rth;
     int *ovf = (int *)pw;
     pw += b_ovf;
     int *frows = (int *)pw;
@@ -424,6 +472,8 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
     f.slots = slots;
     f.cap = cap;
     f.theta = theta;
+    f.heap = heap;
+    f.row_theta = row_theta;
     f.cnt = cnt;
     f.list = list;
     f.overflow = ovf;
@@ -441,7 +491,7 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
     if (nQ > 0 && nS > 0) {
         if (use_tc) {
             k_rowpar_topk<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(Q->nq64, Q->rowb, nQ, rows, g64,
-                                                                          (double)S->nq_max * 1.0001, rowpar);
+                                                                          (double)S->nq_max * 1.0001, rowpar, row_theta);
             count_launch();
             ++launches;
             const CUtensorMap *tmA = nullptr, *tmB = nullptr;
@@ -475,6 +525,7 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
                 L.p.tk_list = list;
                 L.p.tk_cnt = cnt;
                 L.p.tk_theta = theta;
+                L.p.tk_row_theta = row_theta;
                 L.p.tk_overflow = ovf;
                 rc = launch_tc_join(L, st, true);
                 ++launches;
@@ -493,7 +544,10 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
             if (e != cudaSuccess) rc = cuda_fail(e, "top-k memset");
         }
     } else if (nQ > 0) {   // empty store: every slot is unused
+        k_rowpar_topk<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(Q->nq64, Q->rowb, nQ, rows, g64, 0.0, rowpar,
+                                                                      row_theta);
         k_topk_finalize<<<1, 128, 0, st>>>(f);   // no candidates for any row -> fills -1
+        count_launch();
         count_launch();
         ++launches;
     }
