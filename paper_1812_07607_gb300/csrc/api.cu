@@ -380,11 +380,13 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
         set_error("dl_sim_join: BF16 tensor-core path supports d <= 512 (d=%d)", R->d);
         return DL_EUNSUPPORTED;
     }
-    int BN = o.tile_n ? o.tile_n : 256;
-    if (BN != 128 && BN != 256) {
+    if (o.tile_n != 0 && o.tile_n != 128 && o.tile_n != 256) {
         set_error("dl_sim_join: tile_n must be 0, 128 or 256");
         return DL_EINVAL;
     }
+    bool tune_trial = false;
+    int BN = o.tile_n;
+    if (BN == 0) BN = (prec == DL_PREC_BF16) ? tune_pick(R->dp, self ? 1 : 0, R->n, Sx->n, &tune_trial) : 256;
     if (o.out_capacity < 0) {
         set_error("dl_sim_join: negative out_capacity");
         return DL_EINVAL;
@@ -410,7 +412,7 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
         c.t_acc = f32_rd(e2 * (1.0 - g64) * (1.0 - g32) * (1.0 - 8.881784197001252e-16) - abs32);
         c.t_rej = f32_ru(e2 * (1.0 + 2.0 * g64) * (1.0 + g32) * (1.0 + 8.881784197001252e-16) + abs32);
     }
-    c.timing = o.timing != 0;
+    c.timing = o.timing != 0 || tune_trial;
     c.st = (cudaStream_t)o.cuda_stream;
     const bool fixed = o.out_capacity > 0;
     {
@@ -453,6 +455,9 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
         const_cast<dl_store *>(R)->hint_pairs = (int64_t)po.out_cnt;
         const_cast<dl_store *>(R)->hint_band = (int64_t)po.band_only;
     }
+    if (tune_trial && reruns == 0)
+        tune_record(R->dp, self ? 1 : 0, R->n, Sx->n, BN, po.ms_main,
+                    self ? 0.5 * (double)R->n * (double)R->n : (double)R->n * (double)Sx->n);
     dl_result *res = new dl_result();
     res->kind = 0;
     res->device = R->device;

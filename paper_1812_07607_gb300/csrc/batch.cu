@@ -329,8 +329,12 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
             set_error("dl_batch_join: epsilon requests need d <= 512 (d=%d)", d);
             return DL_EUNSUPPORTED;
         }
-        const int BN = o.tile_n ? o.tile_n : 256;
+        bool tune_trial = false;
+        const int BN = o.tile_n ? o.tile_n : tune_pick(Qe->dp, 0, ne, S->n, &tune_trial);
         const int64_t mt = (ne + 127) / 128;
+        cudaEvent_t tev[2] = {nullptr, nullptr};
+        if (tune_trial)
+            for (auto &ev : tev) cudaEventCreate(&ev);
         std::vector<int4> units;
         batch_units(ne, S->n, BN, sms, &units);
         int64_t cap;
@@ -391,7 +395,9 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
                 L.p.cand_cnt = cnt + 0;
                 L.p.cand_cap = (unsigned long long)cap;
                 L.p.err = (int *)(cnt + 3);
+                if (tune_trial) cudaEventRecord(tev[0], st);
                 rc = launch_tc_join(L, st);
+                if (tune_trial) cudaEventRecord(tev[1], st);
             }
             if (!rc) {
                 k_batch_decide<<<sms * 8, 256, 0, st>>>(cand, cnt + 0, (unsigned long long)cap, Qe->x32, S->x32, d,
@@ -447,9 +453,16 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
                 std::lock_guard<std::mutex> lk(const_cast<dl_store *>(S)->mu);
                 const_cast<dl_store *>(S)->hint_band = (int64_t)hc[0];
             }
+            if (!rc && tune_trial && attempt == 0) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, tev[0], tev[1]);
+                tune_record(Qe->dp, 0, ne, S->n, BN, ms, (double)ne * (double)S->n);
+            }
             dev_free(ws, st);
             break;
         }
+        for (auto &ev : tev)
+            if (ev) cudaEventDestroy(ev);
         if (rc) {
             dev_free(tk_block, st);
             dev_free(pair_block, st);

@@ -99,6 +99,10 @@ void dev_free(void *p, cudaStream_t st);
 
 int device_sm_count();
 
+// Tile-width autotuner (tune.cu). kind: 0 R x S eps-join, 1 self eps-join, 2 top-k.
+int tune_pick(int dp, int kind, int64_t nR, int64_t nS, bool *trial);
+void tune_record(int dp, int kind, int64_t nR, int64_t nS, int bn, double kernel_ms, double pairs);
+
 // Host-side directed conversions FP64 -> FP32 (the default conversion rounds to nearest).
 inline float f32_ru(double x)
 {

@@ -403,12 +403,13 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
 {
     const int64_t nQ = Q->n, nS = S->n;
     const int d = Q->d;
-    const int BN = o.tile_n ? o.tile_n : 256;
-    if (BN != 128 && BN != 256) {
+    if (o.tile_n != 0 && o.tile_n != 128 && o.tile_n != 256) {
         set_error("top-k: tile_n must be 0, 128 or 256");
         return DL_EINVAL;
     }
     const bool use_tc = (o.precision != DL_PREC_FP32) && Q->dp <= 512;
+    bool tune_trial = false;
+    const int BN = o.tile_n ? o.tile_n : (use_tc ? tune_pick(Q->dp, 2, nQ, nS, &tune_trial) : 256);
     const int sms = device_sm_count();
     const int64_t mt = (nQ + 127) / 128, nt = (nS + BN - 1) / BN;
     int splits = 1;
@@ -446,7 +447,8 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
     pw += b_rows;
     unsigned long long *misc = (unsigned long long *)pw;   // [0] flagged rows [1] fp64 evals [2] err [3] tc err
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    if (o.timing)
+    const bool timing = o.timing || tune_trial;
+    if (timing)
         for (auto &e : ev) cudaEventCreate(&e);
     auto done = [&](int code) {
         for (auto &e : ev)
@@ -459,7 +461,7 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
     if (e == cudaSuccess && nQ > 0) e = cudaMemsetAsync(ovf, 0, (size_t)nQ * sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, b_cnt, st);
     if (e != cudaSuccess) return done(cuda_fail(e, "top-k memset"));
-    if (o.timing) cudaEventRecord(ev[0], st);
+    if (timing) cudaEventRecord(ev[0], st);
     int launches = 0;
     const double g64 = gamma64(d), g32 = gamma32(d);
     TopkFin f;
@@ -551,7 +553,7 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
         count_launch();
         ++launches;
     }
-    if (o.timing) cudaEventRecord(ev[1], st);
+    if (timing) cudaEventRecord(ev[1], st);
     // exact fallback for flagged rows
     int64_t flagged = 0;
     if (!rc && nQ > 0 && nS > 0) {
@@ -608,7 +610,7 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
             }
         }
     }
-    if (o.timing) cudaEventRecord(ev[2], st);
+    if (timing) cudaEventRecord(ev[2], st);
     unsigned long long h2[4] = {0, 0, 0, 0};
     if (!rc) {
         e = cudaMemcpyAsync(h2, misc, sizeof h2, cudaMemcpyDeviceToHost, st);
@@ -630,11 +632,16 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
         s.precision = use_tc ? DL_PREC_BF16 : DL_PREC_FP32;
         s.tile_n = use_tc ? BN : 0;
         s.kernels_launched = launches;
-        if (o.timing) {
+        if (timing) {
             cudaEventElapsedTime(&s.ms_main, ev[0], ev[1]);
             cudaEventElapsedTime(&s.ms_recheck, ev[1], ev[2]);
             cudaEventElapsedTime(&s.ms_total, ev[0], ev[2]);
         }
+    }
+    if (tune_trial && flagged == 0) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        tune_record(Q->dp, 2, nQ, nS, BN, ms, (double)nQ * (double)nS);
     }
     return done(DL_OK);
 }

@@ -246,3 +246,36 @@ def test_self_clustered_262k_full_size_sampled(dl, orc):
     pos = np.empty(rid.max() + 1, dtype=np.int64)
     pos[rid] = np.arange(rid.shape[0])
     assert (pos[r] < pos[s]).all()
+
+
+def test_autotuner_tries_both_tiles_and_persists(tmp_path):
+    """Tile width autotuner: first calls of a shape class try 256 then 128, then the faster sticks."""
+    import os
+    import subprocess
+    import sys
+    cache = tmp_path / "tune.txt"
+    code = r'''
+import sys, torch
+sys.path.insert(0, ".")
+from paper_1812_07607_gb300 import dl, workloads as W
+wl = W.rxs_histograms_2k()
+R = dl.Store(torch.from_numpy(wl.r_ids).cuda(), torch.from_numpy(wl.R).cuda())
+S = dl.Store(torch.from_numpy(wl.s_ids).cuda(), torch.from_numpy(wl.S).cuda())
+tiles = []
+for _ in range(4):
+    r = dl.sim_join(R, S, wl.eps)
+    tiles.append(r.stats()["tile_n"])
+    r.free()
+print(tiles)
+'''
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, DL_TUNE_CACHE=str(cache))
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    tiles = eval(out.stdout.strip().splitlines()[-1])
+    assert tiles[:2] == [256, 128] and tiles[2] == tiles[3] and tiles[2] in (128, 256)
+    lines = cache.read_text().split()
+    assert len(lines) == 2 and int(lines[1]) == tiles[2]
+    # a new process starts from the cache
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=300)
+    assert eval(out.stdout.strip().splitlines()[-1]) == [tiles[2]] * 4
