@@ -205,17 +205,26 @@ static int run_pass(const PassCfg &c, PassOut *po)
 
     int launches = 0;
     if (nR > 0 && nS > 0) {
-        if (c.prec == DL_PREC_BF16) {
-            rc = launch_rowpar(R->nq64, R->rowb, nR, mt * 128, R->dp, c.e2, nullptr, gamma64(d), rowpar, st);
+        if (c.prec == DL_PREC_BF16 || c.prec == DL_PREC_FP8E4M3) {
+            const bool fp8 = c.prec == DL_PREC_FP8E4M3;
+            if (fp8) {
+                rc = ensure_fp8(const_cast<dl_store *>(R), st);
+                if (!rc) rc = ensure_fp8(const_cast<dl_store *>(S), st);
+            }
+            if (!rc)
+                rc = launch_rowpar(R->nq64, R->rowb, nR, mt * 128, R->dp, c.e2, nullptr, gamma64(d), rowpar, st,
+                                   fp8 ? R->rowb8 : nullptr);
             ++launches;
             const CUtensorMap *tmA = nullptr, *tmB = nullptr;
-            if (!rc) rc = get_tmap(const_cast<dl_store *>(R), 128, &tmA);
-            if (!rc) rc = get_tmap(const_cast<dl_store *>(S), c.BN, &tmB);
+            if (!rc) rc = fp8 ? get_tmap8(const_cast<dl_store *>(R), 128, &tmA) : get_tmap(const_cast<dl_store *>(R), 128, &tmA);
+            if (!rc)
+                rc = fp8 ? get_tmap8(const_cast<dl_store *>(S), c.BN, &tmB) : get_tmap(const_cast<dl_store *>(S), c.BN, &tmB);
             const int4 *units = nullptr;
             int n_units = 0;
             if (!rc) rc = get_units(nR, nS, c.self, c.BN, sms, &units, &n_units);
             if (!rc && n_units > 0) {
                 TcLaunch L;
+                std::memset(&L.p, 0, sizeof L.p);
                 L.tmA = tmA;
                 L.tmB = tmB;
                 L.BN = c.BN;
@@ -224,17 +233,19 @@ static int run_pass(const PassCfg &c, PassOut *po)
                 L.p.n_units = n_units;
                 L.p.nR = (int)nR;
                 L.p.nS = (int)nS;
-                L.p.kc = R->dp / 64;
-                tc_plan(c.BN, R->dp / 64, &L.p.stages, &L.p.a_slots);
+                L.p.kc = fp8 ? R->dp8 / 128 : R->dp / 64;
+                tc_plan(c.BN, L.p.kc, &L.p.stages, &L.p.a_slots, fp8);
                 L.p.upper = c.self ? 1 : 0;
                 L.p.rowpar = rowpar;
                 L.p.beta = S->beta;
-                L.p.cstat = S->cstat;
+                L.p.cstat = fp8 ? S->cstat8 : S->cstat;
+                L.p.sc_r = fp8 ? R->sc8 : nullptr;
+                L.p.sc_s = fp8 ? S->sc8 : nullptr;
                 L.p.cand = band;                 // candidates share the band buffer and counter
                 L.p.cand_cnt = cnt + 1;
                 L.p.cand_cap = (unsigned long long)c.band_cap;
                 L.p.err = (int *)(cnt + 4);
-                rc = launch_tc_join(L, st);
+                rc = launch_tc_join(L, st, false, fp8);
                 ++launches;
             }
         } else {
@@ -254,7 +265,7 @@ static int run_pass(const PassCfg &c, PassOut *po)
             ++launches;
         }
         if (c.timing) cudaEventRecord(ev[1], st);
-        if (!rc && c.prec == DL_PREC_BF16) {
+        if (!rc && (c.prec == DL_PREC_BF16 || c.prec == DL_PREC_FP8E4M3)) {
             rc = launch_finalize(band, cnt + 1, (unsigned long long)c.band_cap, R->x32, S->x32, d, c.e2, c.t_acc,
                                  c.t_rej, jo, cnt + 3, cnt + 2, sms * 8, st);
             ++launches;
@@ -283,7 +294,7 @@ static int run_pass(const PassCfg &c, PassOut *po)
     if (!rc) {
         po->out_cnt = hc[0];
         po->band_cnt = hc[1];                                  // list fill (band or candidate list)
-        po->band_only = c.prec == DL_PREC_BF16 ? hc[2] : hc[1];
+        po->band_only = (c.prec == DL_PREC_BF16 || c.prec == DL_PREC_FP8E4M3) ? hc[2] : hc[1];
         po->fp64_cnt = hc[3];
         po->err = (int)hc[4];
         if (c.timing) {
@@ -368,11 +379,7 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
     if (rc) return rc;
     int prec = o.precision;
     if (prec == DL_PREC_AUTO) prec = (R->dp <= 512) ? DL_PREC_BF16 : DL_PREC_FP32;
-    if (prec == DL_PREC_FP8E4M3) {
-        set_error("dl_sim_join: FP8 e4m3 path not available in this build");
-        return DL_EUNSUPPORTED;
-    }
-    if (prec != DL_PREC_BF16 && prec != DL_PREC_FP32 && prec != DL_PREC_FP32_PLAIN) {
+    if (prec != DL_PREC_BF16 && prec != DL_PREC_FP8E4M3 && prec != DL_PREC_FP32 && prec != DL_PREC_FP32_PLAIN) {
         set_error("dl_sim_join: bad precision %d", prec);
         return DL_EINVAL;
     }
@@ -387,6 +394,10 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
     bool tune_trial = false;
     int BN = o.tile_n;
     if (BN == 0) BN = (prec == DL_PREC_BF16) ? tune_pick(R->dp, self ? 1 : 0, R->n, Sx->n, &tune_trial) : 256;
+    if (prec == DL_PREC_FP8E4M3 && R->d > 1024) {
+        set_error("dl_sim_join: FP8 path supports d <= 1024");
+        return DL_EUNSUPPORTED;
+    }
     if (o.out_capacity < 0) {
         set_error("dl_sim_join: negative out_capacity");
         return DL_EINVAL;
@@ -419,7 +430,7 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
         std::lock_guard<std::mutex> lk(const_cast<dl_store *>(R)->mu);
         c.cap = fixed ? o.out_capacity : std::max<int64_t>(1 << 16, R->hint_pairs + R->hint_pairs / 4);
         // the BF16 path's candidate list holds proven matches and band pairs
-        const int64_t want = (prec == DL_PREC_BF16 ? R->hint_pairs : 0) + R->hint_band;
+        const int64_t want = ((prec == DL_PREC_BF16 || prec == DL_PREC_FP8E4M3) ? R->hint_pairs : 0) + R->hint_band;
         c.band_cap = std::max<int64_t>(1 << 16, want + want / 4);
     }
 
@@ -434,7 +445,7 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
             set_error("dl_sim_join: a bounded device wait expired (kernel pipeline stalled)");
             return DL_ETIMEOUT;
         }
-        const bool band_over = po.band_cnt > (unsigned long long)c.band_cap;
+        const bool band_over = po.band_cnt > (unsigned long long)c.band_cap;   // candidate / band list
         const bool out_over = po.out_cnt > (unsigned long long)c.cap;
         if (band_over || (out_over && !fixed)) {
             if (attempt >= 4) {
@@ -473,7 +484,7 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
     s.fp64_pairs = (int64_t)po.fp64_cnt;
     s.reruns = reruns;
     s.precision = prec;
-    s.tile_n = prec == DL_PREC_BF16 ? BN : 0;
+    s.tile_n = (prec == DL_PREC_BF16 || prec == DL_PREC_FP8E4M3) ? BN : 0;
     s.ms_main = po.ms_main;
     s.ms_recheck = po.ms_recheck;
     s.ms_total = po.ms_total;

@@ -77,7 +77,15 @@ struct Store {
     float *beta = nullptr;   // [n_pad] RN32(nq64 / 2); +inf in padding
     float4 *rowb = nullptr;  // [n] {||x - x~|| up, ||x~|| up, ||x|| up, |beta - ||x||^2/2| up}
     float4 *cstat = nullptr; // [n_pad / 32] per 32-row chunk {P1, P2, P3, min beta} of the BF16 bound
-    TmapCache tmaps[3];      // box rows 128, 256, 128-for-B (cached per box height)
+    TmapCache tmaps[3];      // BF16 boxes, cached per box height
+    // FP8 e4m3 copy (built on the first FP8 join): row i is s_i * e4m3 codes, s_i a power of two
+    int32_t dp8 = 0;         // d rounded up to a multiple of 128 (one 128-byte swizzle row per K chunk)
+    void *fp8_block = nullptr;
+    uint8_t *x8 = nullptr;   // [n][dp8] e4m3 codes of x / s
+    float *sc8 = nullptr;    // [n_pad] s (1 in padding)
+    float2 *rowb8 = nullptr; // [n] {||x - s x8|| up, ||s x8|| up}
+    float4 *cstat8 = nullptr;// [n_pad/32] {P1, P2 (FP8), P3, 0}
+    TmapCache tmaps8[3];     // FP8 boxes
     std::mutex mu;           // guards tmaps and hints
     float nq_max = 0.f;      // largest ||x||^2 of the store (FP32 sum; used only inside slack terms)
     int64_t hint_pairs = 0;  // last output size seen with this store as R (capacity hint)
@@ -91,6 +99,14 @@ int store_create_impl(dl_store **out, const int64_t *ids, const float *feats, in
 // Build (or fetch from the store's cache) a 2-D BF16 tensor map over the store's
 // BF16 copy with a box of 64 columns x box_rows rows and the 128-byte swizzle.
 int get_tmap(Store *s, int box_rows, const CUtensorMap **out);
+
+// FP8 copy of a store (built once, on first use) and its tensor maps (128-byte rows).
+int ensure_fp8(Store *s, cudaStream_t st);
+int get_tmap8(Store *s, int box_rows, const CUtensorMap **out);
+
+// Assumed bound of the tensor-core accumulation of dp8 e4m3 x e4m3 products: dp8 * 2^-12
+// (the FP8 accumulator's internal precision is not documented; far looser than BF16's).
+inline double gamma_tc8(int dp8) { return dp8 * 2.44140625e-04; }
 
 // ---------------------------------------------------------------- device pools
 // Stream-ordered allocation from the current device's default memory pool.

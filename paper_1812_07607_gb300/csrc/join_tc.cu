@@ -96,6 +96,7 @@ __device__ __forceinline__ void flush_stage(const TcParams &p, uint2 *stg, uint3
 // the pairs (r, col0 + j), classify them against the half's (accept, reject)
 // thresholds, and buffer every proven match and band pair. Warp-collective;
 // rarely taken.
+template <bool FP8>
 __device__ __forceinline__ uint32_t slow_piece(const TcParams &p, const uint32_t (&v)[64], const float *nb, float rx,
                                               float ry, float eh0, float eh1, bool hit0, bool hit1, int r, int col0,
                                               uint2 *stg, uint32_t scnt)
@@ -112,7 +113,7 @@ __device__ __forceinline__ uint32_t slow_piece(const TcParams &p, const uint32_t
         uint32_t am = 0, bm = 0;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-            const float h = __uint_as_float(v[hh * 32 + j]) + nb[hh * 32 + j];
+            const float h = FP8 ? __uint_as_float(v[hh * 32 + j]) : __uint_as_float(v[hh * 32 + j]) + nb[hh * 32 + j];
             const bool a = h >= tau_acc;
             const bool b = !a && (h >= tau_rej);
             am |= (a ? 1u : 0u) << j;
@@ -225,7 +226,7 @@ __device__ __forceinline__ void slow_topk(const TcParams &p, const uint32_t (&v)
     }
 }
 
-template <int BN, bool TOPK>
+template <int BN, bool TOPK, bool FP8>
 __global__ void __launch_bounds__(320, 1)
     tc_join_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcParams p)
@@ -243,7 +244,8 @@ __global__ void __launch_bounds__(320, 1)
     float *s_nbeta = reinterpret_cast<float *>(sB + stages * kStageBytes);   // 8 warps x 2 x HC: -beta
     float4 *s_cst = reinterpret_cast<float4 *>(s_nbeta + 8 * 2 * HC);       // 8 warps x 2 x kSubW chunk stats
     uint2 *s_stage = reinterpret_cast<uint2 *>(s_cst + 8 * 2 * kSubW);       // 8 warps x kStageCap candidates
-    uint64_t *bars = reinterpret_cast<uint64_t *>(s_stage + 8 * kStageCap);
+    float *s_sx = reinterpret_cast<float *>(s_stage + 8 * kStageCap);        // FP8: 8 warps x 2 x HC column scales
+    uint64_t *bars = reinterpret_cast<uint64_t *>(s_sx + (FP8 ? 8 * 2 * HC : 0));
     uint64_t *full = bars;                    // [8]
     uint64_t *empty = bars + 8;               // [8]
     uint64_t *a_full = bars + 16;             // [2]
@@ -337,7 +339,7 @@ __global__ void __launch_bounds__(320, 1)
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16_f32(128, BN);
+            constexpr uint32_t idesc = FP8 ? idesc_e4m3_f32(128, BN) : idesc_bf16_f32(128, BN);
             uint32_t stage = 0, phase = 0, t = 0;
             bool ok = true;
             int i = 0;
@@ -368,9 +370,14 @@ __global__ void __launch_bounds__(320, 1)
                         const uint32_t a_addr = a_base + c * 16384;
                         const uint32_t b_addr = smem_u32(sB + stage * kStageBytes);
 #pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            mma_f16(d_tmem, smem_desc_sw128(a_addr + k * 32), smem_desc_sw128(b_addr + k * 32), idesc,
-                                    (c | k) != 0);
+                        for (int k = 0; k < 4; ++k) {   // 4 x 32 bytes of K per 128-byte chunk
+                            if constexpr (FP8)
+                                mma_f8(d_tmem, smem_desc_sw128(a_addr + k * 32), smem_desc_sw128(b_addr + k * 32),
+                                       idesc, (c | k) != 0);
+                            else
+                                mma_f16(d_tmem, smem_desc_sw128(a_addr + k * 32), smem_desc_sw128(b_addr + k * 32),
+                                        idesc, (c | k) != 0);
+                        }
                         mma_commit(empty + stage);
                         if (++stage == (uint32_t)stages) {
                             stage = 0;
@@ -398,6 +405,7 @@ __global__ void __launch_bounds__(320, 1)
         const int half = e >> 2;           // which half of the tile's columns
         const uint32_t lane_base = static_cast<uint32_t>(quad * 32) << 16;
         float *my_nb = s_nbeta + e * (2 * HC);
+        float *my_sx = s_sx + e * (2 * HC);   // FP8 only
         float4 *my_cs = s_cst + e * (2 * kSubW);
         uint2 *my_stg = s_stage + e * kStageCap;
         uint32_t scnt = 0;
@@ -407,30 +415,39 @@ __global__ void __launch_bounds__(320, 1)
         nxt = cur;
         nxt.next(p);
 
-        auto stage_regs = [&](const TileIter &it, float (&nb)[kPer], float4 &cs) {
+        auto stage_regs = [&](const TileIter &it, float (&nb)[kPer], float (&sx)[kPer], float4 &cs) {
             if (it.valid) {
                 const int c0 = it.n * BN + half * HC;
 #pragma unroll
                 for (int q = 0; q < kPer; ++q) nb[q] = -__ldg(p.beta + c0 + lane * kPer + q);
+                if constexpr (FP8) {
+#pragma unroll
+                    for (int q = 0; q < kPer; ++q) sx[q] = __ldg(p.sc_s + c0 + lane * kPer + q);
+                }
                 if (lane < kSubW) cs = __ldg(p.cstat + (c0 >> 5) + lane);
             }
         };
-        auto stage_store = [&](int s, const float (&nb)[kPer], const float4 &cs) {
+        auto stage_store = [&](int s, const float (&nb)[kPer], const float (&sx)[kPer], const float4 &cs) {
 #pragma unroll
             for (int q = 0; q < kPer; ++q) my_nb[s * HC + lane * kPer + q] = nb[q];
+            if constexpr (FP8) {
+#pragma unroll
+                for (int q = 0; q < kPer; ++q) my_sx[s * HC + lane * kPer + q] = sx[q];
+            }
             if (lane < kSubW) my_cs[s * kSubW + lane] = cs;
             __syncwarp();
         };
         {
-            float nb[kPer];
+            float nb[kPer], sx[kPer];
             float4 cs = make_float4(0.f, 0.f, 0.f, 0.f);
-            stage_regs(cur, nb, cs);
-            stage_store(0, nb, cs);
+            stage_regs(cur, nb, sx, cs);
+            stage_store(0, nb, sx, cs);
         }
 
         uint32_t t = 0;
         bool ok = true;
         float4 rp = make_float4(0.f, 0.f, 0.f, 0.f);
+        float sq = 1.0f;          // FP8: this row's scale
         float theta = 0.f;        // top-k: this slot's threshold (k-th largest lower bound of h)
         float theta_row = 0.f;    // top-k: best threshold published by any slot of this row
         int tcnt = 0;             // top-k: this slot's list fill
@@ -439,6 +456,7 @@ __global__ void __launch_bounds__(320, 1)
             const int r = cur.un.x * 128 + quad * 32 + lane;
             if (cur.n == cur.un.y) {
                 rp = p.rowpar[r];
+                if constexpr (FP8) sq = (r < p.nR) ? p.sc_r[r] : 1.0f;
                 if constexpr (TOPK) {   // a unit owns its (row tile, split): start the slots fresh
                     sidx = (size_t)r * p.tk_slots + (size_t)cur.un.w * 2 + half;
                     theta = __int_as_float(0xff800000);
@@ -449,9 +467,9 @@ __global__ void __launch_bounds__(320, 1)
                     }
                 }
             }
-            float nbn[kPer];
+            float nbn[kPer], sxn[kPer];
             float4 csn = make_float4(0.f, 0.f, 0.f, 0.f);
-            stage_regs(nxt, nbn, csn);   // prefetch the next tile's -beta (latency hidden by this tile)
+            stage_regs(nxt, nbn, sxn, csn);   // prefetch the next tile's -beta (latency hidden by this tile)
 
             if constexpr (TOPK) {
                 theta_row = __int_as_float(0xff800000);
@@ -466,11 +484,30 @@ __global__ void __launch_bounds__(320, 1)
             tc_fence_after();
             const uint32_t tbase = tmem_base + lane_base + b * BN + half * HC;
             const float *nbeta = my_nb + slot * HC;
+            const float *sxs = my_sx + slot * HC;
             const float4 *cst = my_cs + slot * kSubW;
             const int colw = cur.n * BN + half * HC;   // first column this warp owns in the tile
 
             // 64 columns [piece*64, piece*64+64) of this warp's half, values in v
-            auto process64 = [&](const uint32_t (&v)[64], int piece) {
+            auto process64 = [&](uint32_t (&v)[64], int piece) {
+                if constexpr (FP8) {
+                    // h = fma(acc, s_q s_x, -beta): one rounding (s_q s_x is an exact power of two);
+                    // the values in v become h, and the chunk bound below uses beta_min = 0.
+                    const float4 *sx4 = reinterpret_cast<const float4 *>(sxs + piece * 64);
+                    const float4 *nb4 = reinterpret_cast<const float4 *>(nbeta + piece * 64);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const float4 sx = sx4[i], nb = nb4[i];
+                        const float2 a = __ffma2_rn(make_float2(__uint_as_float(v[4 * i]), __uint_as_float(v[4 * i + 1])),
+                                                    make_float2(sq * sx.x, sq * sx.y), make_float2(nb.x, nb.y));
+                        const float2 b = __ffma2_rn(make_float2(__uint_as_float(v[4 * i + 2]), __uint_as_float(v[4 * i + 3])),
+                                                    make_float2(sq * sx.z, sq * sx.w), make_float2(nb.z, nb.w));
+                        v[4 * i] = __float_as_uint(a.x);
+                        v[4 * i + 1] = __float_as_uint(a.y);
+                        v[4 * i + 2] = __float_as_uint(b.x);
+                        v[4 * i + 3] = __float_as_uint(b.y);
+                    }
+                }
                 const float4 cs0 = cst[2 * piece], cs1 = cst[2 * piece + 1];
                 const float eh0 = __fmaf_ru(rp.z, cs0.x, __fmaf_ru(rp.w, cs0.y, cs0.z));
                 const float eh1 = __fmaf_ru(rp.z, cs1.x, __fmaf_ru(rp.w, cs1.y, cs1.z));
@@ -503,16 +540,16 @@ __global__ void __launch_bounds__(320, 1)
                 }
                 const float mx0 = fmaxf(fmaxf(m0[0], m0[1]), fmaxf(m0[2], m0[3]));
                 const float mx1 = fmaxf(fmaxf(m1[0], m1[1]), fmaxf(m1[2], m1[3]));
-                const bool hit0 = __fsub_ru(mx0, cs0.w) >= tr0;
-                const bool hit1 = __fsub_ru(mx1, cs1.w) >= tr1;
+                const bool hit0 = (FP8 ? mx0 : __fsub_ru(mx0, cs0.w)) >= tr0;
+                const bool hit1 = (FP8 ? mx1 : __fsub_ru(mx1, cs1.w)) >= tr1;
                 if constexpr (TOPK) {
                     if (hit0 || hit1)
                         slow_topk(p, v, nbeta + piece * 64, __fadd_ru(eh0, rp.x), __fadd_ru(eh1, rp.x), hit0, hit1, r,
                                   colw + piece * 64, sidx, theta, tcnt, theta_row);
                 } else {
                     if (__any_sync(0xffffffffu, hit0 || hit1))
-                        scnt = slow_piece(p, v, nbeta + piece * 64, rp.x, rp.y, eh0, eh1, hit0, hit1, r,
-                                          colw + piece * 64, my_stg, scnt);
+                        scnt = slow_piece<FP8>(p, v, nbeta + piece * 64, rp.x, rp.y, eh0, eh1, hit0, hit1, r,
+                                               colw + piece * 64, my_stg, scnt);
                 }
             };
 
@@ -540,7 +577,7 @@ __global__ void __launch_bounds__(320, 1)
                 }
             }
             // publish the next tile's -beta into the other slot (this warp's own copy)
-            stage_store(slot ^ 1, nbn, csn);
+            stage_store(slot ^ 1, nbn, sxn, csn);
             cur = nxt;
             nxt.next(p);
             ++t;
@@ -559,24 +596,24 @@ __global__ void __launch_bounds__(320, 1)
     }
 }
 
-static size_t tc_extra_bytes(int BN)
+static size_t tc_extra_bytes(int BN, bool fp8)
 {
-    // per epilogue warp: 2 x BN/2 floats of -beta, 2 x BN/64 chunk stats, the
-    // candidate buffer; then 27 barrier / flag words
-    return (size_t)8 * (2 * (BN / 2) * 4 + 2 * (BN / 64) * 16 + kStageCap * 8) + 27 * 8;
+    // per epilogue warp: 2 x BN/2 floats of -beta (and of the FP8 column scales), 2 x BN/64
+    // chunk stats, the candidate buffer; then 27 barrier / flag words
+    return (size_t)8 * (2 * (BN / 2) * 4 * (fp8 ? 2 : 1) + 2 * (BN / 64) * 16 + kStageCap * 8) + 27 * 8;
 }
 
-static size_t tc_smem_bytes(int BN, int kc, int stages, int a_slots)
+static size_t tc_smem_bytes(int BN, int kc, int stages, int a_slots, bool fp8)
 {
-    return 1024 + (size_t)a_slots * kc * 16384 + (size_t)stages * BN * 128 + tc_extra_bytes(BN);
+    return 1024 + (size_t)a_slots * kc * 16384 + (size_t)stages * BN * 128 + tc_extra_bytes(BN, fp8);
 }
 
 // Shared-memory plan: two A slots when that still leaves at least three S stages.
-void tc_plan(int BN, int kc, int *stages, int *a_slots)
+void tc_plan(int BN, int kc, int *stages, int *a_slots, bool fp8)
 {
     const long cap = 232448;
     for (int slots = 2; slots >= 1; --slots) {
-        const long avail = cap - 1024 - (long)tc_extra_bytes(BN) - (long)slots * kc * 16384;
+        const long avail = cap - 1024 - (long)tc_extra_bytes(BN, fp8) - (long)slots * kc * 16384;
         long s = avail / ((long)BN * 128);
         if (s > 8) s = 8;
         if (s >= 3 || slots == 1) {
@@ -587,27 +624,34 @@ void tc_plan(int BN, int kc, int *stages, int *a_slots)
     }
 }
 
-template <int BN, bool TOPK>
+template <int BN, bool TOPK, bool FP8>
 static int launch_one(const TcLaunch &L, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(tc_join_kernel<BN, TOPK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(tc_join_kernel<BN, TOPK, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_join_kernel)");
-    tc_join_kernel<BN, TOPK><<<L.grid, 320, smem, st>>>(*L.tmA, *L.tmB, L.p);
+    tc_join_kernel<BN, TOPK, FP8><<<L.grid, 320, smem, st>>>(*L.tmA, *L.tmB, L.p);
     return DL_OK;
 }
 
-int launch_tc_join(const TcLaunch &L, cudaStream_t st, bool topk)
+int launch_tc_join(const TcLaunch &L, cudaStream_t st, bool topk, bool fp8)
 {
-    const size_t smem = tc_smem_bytes(L.BN, L.p.kc, L.p.stages, L.p.a_slots);
+    if (topk && fp8) {
+        set_error("top-k runs on the BF16 path only");
+        return DL_EUNSUPPORTED;
+    }
+    const size_t smem = tc_smem_bytes(L.BN, L.p.kc, L.p.stages, L.p.a_slots, fp8);
     if (L.p.stages < 2 || smem > 232448) {
         set_error("tensor-core join: no shared-memory plan for d=%d, tile %d", L.p.kc * 64, L.BN);
         return DL_EUNSUPPORTED;
     }
     int rc;
     if (L.BN == 256)
-        rc = topk ? launch_one<256, true>(L, smem, st) : launch_one<256, false>(L, smem, st);
+        rc = topk ? launch_one<256, true, false>(L, smem, st)
+                  : (fp8 ? launch_one<256, false, true>(L, smem, st) : launch_one<256, false, false>(L, smem, st));
     else if (L.BN == 128)
-        rc = topk ? launch_one<128, true>(L, smem, st) : launch_one<128, false>(L, smem, st);
+        rc = topk ? launch_one<128, true, false>(L, smem, st)
+                  : (fp8 ? launch_one<128, false, true>(L, smem, st) : launch_one<128, false, false>(L, smem, st));
     else {
         set_error("tensor-core tile width %d not supported (128 or 256)", L.BN);
         return DL_EINVAL;

@@ -19,7 +19,9 @@ struct TcParams {
     int upper;               // 1: self-join, only columns c > r are pairs
     const float4 *rowpar;    // [m_tiles*128] {alpha_acc, alpha_rej, rq, nqt}
     const float *beta;       // S: RN32(||x||^2/2), +inf padding
-    const float4 *cstat;     // S: per 32-column chunk {P1, P2, P3, 0}
+    const float4 *cstat;     // S: per 32-column chunk {P1, P2, P3, min beta}
+    const float *sc_r;       // FP8: per-row power-of-two scales of R (NULL for BF16)
+    const float *sc_s;       // FP8: per-row scales of S
     uint2 *cand;             // candidates: {r, c | 0x80000000 if a band pair, else a proven match}
     unsigned long long *cand_cnt;
     unsigned long long cand_cap;
@@ -46,8 +48,8 @@ struct TcLaunch {
     int grid;
 };
 
-void tc_plan(int BN, int kc, int *stages, int *a_slots);
-int launch_tc_join(const TcLaunch &L, cudaStream_t st, bool topk = false);
+void tc_plan(int BN, int kc, int *stages, int *a_slots, bool fp8 = false);
+int launch_tc_join(const TcLaunch &L, cudaStream_t st, bool topk = false, bool fp8 = false);
 
 // ---- K8 SIMT FP32 join (join_simt.cu)
 struct SimtParams {
@@ -67,7 +69,7 @@ int launch_recheck(const uint2 *band, const unsigned long long *band_cnt, unsign
                    const float *S, int d, double e2, float t_acc, float t_rej, const JoinOut &out,
                    unsigned long long *n_fp64, int grid, cudaStream_t st);
 int launch_rowpar(const double *nq64, const float4 *rowb, int64_t n, int64_t n_tot, int dp, double e2,
-                  const double *row_e2, double g64, float4 *rowpar, cudaStream_t st);
+                  const double *row_e2, double g64, float4 *rowpar, cudaStream_t st, const float2 *rowb8 = nullptr);
 // Turn the tensor-core kernel's candidate list into id pairs: proven matches are
 // translated directly, band pairs are rechecked exactly first (recheck.cu).
 int launch_finalize(const uint2 *cand, const unsigned long long *cand_cnt, unsigned long long cand_cap, const float *R,

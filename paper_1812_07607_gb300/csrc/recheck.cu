@@ -71,8 +71,9 @@ __global__ void __launch_bounds__(256)
 // with h = q.x - ||x||^2/2 (so D = ||q||^2 - 2h), plus the row's bound terms.
 // Padding rows get +inf thresholds (never emit).
 __global__ void __launch_bounds__(256)
-    k_rowpar(const double *__restrict__ nq64, const float4 *__restrict__ rowb, int64_t n, int64_t n_tot, int dp,
-             double e2_all, const double *__restrict__ row_e2, double g64, float4 *__restrict__ rowpar)
+    k_rowpar(const double *__restrict__ nq64, const float4 *__restrict__ rowb, const float2 *__restrict__ rowb8,
+             int64_t n, int64_t n_tot, int dp, double e2_all, const double *__restrict__ row_e2, double g64,
+             float4 *__restrict__ rowpar)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_tot) return;
@@ -89,7 +90,8 @@ __global__ void __launch_bounds__(256)
     const double a_acc = __dsub_ru(nq_up, __dmul_rd(e2, 1.0 - g64)) * 0.5;
     const double a_rej = __dsub_rd(nq_dn, __dmul_ru(e2, 1.0 + 2.0 * g64)) * 0.5;
     const float4 rb = rowb[i];
-    rowpar[i] = make_float4(__double2float_ru(a_acc), __double2float_rd(a_rej), rb.x, rb.y);
+    const float2 r8 = rowb8 ? rowb8[i] : make_float2(rb.x, rb.y);
+    rowpar[i] = make_float4(__double2float_ru(a_acc), __double2float_rd(a_rej), r8.x, r8.y);
 }
 
 // Self-join full mode: every (i, i) is a pair (canonical D = 0 <= eps^2).
@@ -134,10 +136,11 @@ int launch_finalize(const uint2 *cand, const unsigned long long *cand_cnt, unsig
 }
 
 int launch_rowpar(const double *nq64, const float4 *rowb, int64_t n, int64_t n_tot, int dp, double e2,
-                  const double *row_e2, double g64, float4 *rowpar, cudaStream_t st)
+                  const double *row_e2, double g64, float4 *rowpar, cudaStream_t st, const float2 *rowb8)
 {
     if (n_tot == 0) return DL_OK;
-    k_rowpar<<<(unsigned)((n_tot + 255) / 256), 256, 0, st>>>(nq64, rowb, n, n_tot, dp, e2, row_e2, g64, rowpar);
+    k_rowpar<<<(unsigned)((n_tot + 255) / 256), 256, 0, st>>>(nq64, rowb, rowb8, n, n_tot, dp, e2, row_e2, g64,
+                                                              rowpar);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_rowpar launch");

@@ -13,6 +13,8 @@
 #include <cstdio>
 #include <cstring>
 
+#include <cuda_fp8.h>
+
 #include "internal.h"
 
 namespace dl {
@@ -193,6 +195,7 @@ __global__ void __launch_bounds__(256) k1_chunk_stats(const float *__restrict__ 
 // the join epilogue can bound a whole 32-column chunk with the chunk's
 // smallest beta. The caller's row index of every store row is kept (orig).
 constexpr int kSortBuckets = 65536;
+static size_t align256(size_t x);
 
 __global__ void __launch_bounds__(256) k_sort_keys(const float *__restrict__ x, int64_t n, int d,
                                                    float *__restrict__ keys, unsigned *__restrict__ minmax)
@@ -283,6 +286,121 @@ __global__ void __launch_bounds__(256) k_gather_rows(const float *__restrict__ s
     }
 }
 
+// ------------------------------------------------------------------ FP8 copy
+// One warp per row: s = the power of two with max|x| / s <= 448 (the largest
+// finite e4m3), codes = RN_e4m3(x / s) (x / s is exact), and FP64 upper bounds
+// of ||x - s*dec(codes)|| and ||s*dec(codes)||.
+__global__ void __launch_bounds__(256) k1_fp8(const float *__restrict__ x32, int64_t n, int d, int dp8,
+                                              uint8_t *__restrict__ x8, float *__restrict__ sc8,
+                                              float2 *__restrict__ rowb8)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * 8 + warp;
+    if (row >= n) return;
+    const float *xr = x32 + row * d;
+    float mx = 0.f;
+    for (int k = lane; k < d; k += 32) mx = fmaxf(mx, fabsf(__ldg(xr + k)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    float sc = 1.0f;
+    if (mx > 0.f) {
+        int e;
+        const float m = frexpf(mx / 448.0f, &e);   // mx/448 = m 2^e, m in [0.5, 1)
+        int c = (m == 0.5f) ? e - 1 : e;           // ceil(log2(mx / 448))
+        if (c < -126) c = -126;
+        sc = ldexpf(1.0f, c);
+        while (mx / sc > 448.0f) sc *= 2.0f;
+    }
+    uint8_t *br = x8 + row * dp8;
+    double s2 = 0.0, s3 = 0.0;
+    for (int k = lane; k < dp8; k += 32) {
+        const float v = (k < d) ? __ldg(xr + k) : 0.0f;
+        const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(v / sc, __NV_SATFINITE, __NV_E4M3);
+        br[k] = (uint8_t)q;
+        const float dec = __half2float(__half(__nv_cvt_fp8_to_halfraw(q, __NV_E4M3))) * sc;
+        const double e = (double)v - (double)dec;
+        s2 = __dadd_rn(s2, __dmul_rn(e, e));
+        s3 = __dadd_rn(s3, __dmul_rn((double)dec, (double)dec));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s2 = __dadd_rn(s2, __shfl_xor_sync(0xffffffffu, s2, o));
+        s3 = __dadd_rn(s3, __shfl_xor_sync(0xffffffffu, s3, o));
+    }
+    if (lane == 0) {
+        const double fac = 1.0 + (double)(dp8 + 4) * 2.220446049250313e-16;
+        const double grow = 1.0 + 8.881784197001252e-16;
+        sc8[row] = sc;
+        rowb8[row] = make_float2(__double2float_ru(sqrt(s2 * fac) * grow), __double2float_ru(sqrt(s3 * fac) * grow));
+    }
+}
+
+// Per 32-row chunk: {max ||x||, max r8 + (gamma_tc8 + 1.01u) max ||x~8||, P3 (as BF16), 0}.
+__global__ void __launch_bounds__(256) k1_fp8_stats(const float2 *__restrict__ rowb8, const float4 *__restrict__ cstat,
+                                                    int64_t n, int64_t n_pad, float g2, float *__restrict__ sc8,
+                                                    float4 *__restrict__ cstat8)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t chunk = (int64_t)blockIdx.x * 8 + warp;
+    if (chunk * 32 >= n_pad) return;
+    const int64_t row = chunk * 32 + lane;
+    float rq = 0.f, nqt = 0.f;
+    if (row < n) {
+        const float2 rb = rowb8[row];
+        rq = rb.x;
+        nqt = rb.y;
+    } else {
+        sc8[row] = 1.0f;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rq = fmaxf(rq, __shfl_xor_sync(0xffffffffu, rq, o));
+        nqt = fmaxf(nqt, __shfl_xor_sync(0xffffffffu, nqt, o));
+    }
+    if (lane == 0) {
+        const float4 c = cstat[chunk];
+        cstat8[chunk] = make_float4(c.x, __fmaf_ru(g2, nqt, rq), c.z, 0.f);
+    }
+}
+
+int ensure_fp8(Store *s, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->fp8_block) return DL_OK;
+    const int dp8 = (s->d + 127) / 128 * 128;
+    const size_t b_x = align256((size_t)s->n * dp8), b_sc = align256(sizeof(float) * s->n_pad),
+                 b_rb = align256(sizeof(float2) * std::max<int64_t>(s->n, 1)),
+                 b_cs = align256(sizeof(float4) * (s->n_pad / 32));
+    void *blk = nullptr;
+    int rc = dev_alloc(&blk, b_x + b_sc + b_rb + b_cs, st);
+    if (rc) return rc;
+    char *p = (char *)blk;
+    uint8_t *x8 = (uint8_t *)p;
+    float *sc8 = (float *)(p + b_x);
+    float2 *rowb8 = (float2 *)(p + b_x + b_sc);
+    float4 *cstat8 = (float4 *)(p + b_x + b_sc + b_rb);
+    if (s->n > 0) {
+        k1_fp8<<<(unsigned)((s->n + 7) / 8), 256, 0, st>>>(s->x32, s->n, s->d, dp8, x8, sc8, rowb8);
+        count_launch();
+    }
+    const float g2 = f32_ru(gamma_tc8(dp8) + 1.01 * kU32);
+    k1_fp8_stats<<<(unsigned)((s->n_pad / 32 + 7) / 8), 256, 0, st>>>(rowb8, s->cstat, s->n, s->n_pad, g2, sc8, cstat8);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        dev_free(blk, st);
+        return cuda_fail(e, "FP8 store copy");
+    }
+    s->dp8 = dp8;
+    s->x8 = x8;
+    s->sc8 = sc8;
+    s->rowb8 = rowb8;
+    s->cstat8 = cstat8;
+    s->fp8_block = blk;
+    return DL_OK;
+}
+
 // ------------------------------------------------------------------ tensor maps
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
@@ -329,6 +447,43 @@ int get_tmap(Store *s, int box_rows, const CUtensorMap **out)
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed (%d) for dp=%d rows=%lld box=%d", (int)r, s->dp,
                   (long long)s->n, box_rows);
+        return DL_ECUDA;
+    }
+    slot->valid = true;
+    slot->box_rows = box_rows;
+    *out = &slot->map;
+    return DL_OK;
+}
+
+int get_tmap8(Store *s, int box_rows, const CUtensorMap **out)
+{
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto &t : s->tmaps8)
+        if (t.valid && t.box_rows == box_rows) {
+            *out = &t.map;
+            return DL_OK;
+        }
+    TmapCache *slot = nullptr;
+    for (auto &t : s->tmaps8)
+        if (!t.valid) {
+            slot = &t;
+            break;
+        }
+    if (!slot) slot = &s->tmaps8[0];
+    auto fn = encode_fn();
+    if (!fn || !s->x8) {
+        set_error("FP8 tensor map: driver entry point or FP8 copy missing");
+        return DL_ECUDA;
+    }
+    cuuint64_t gdim[2] = {(cuuint64_t)s->dp8, (cuuint64_t)(s->n > 0 ? s->n : 1)};
+    cuuint64_t gstride[1] = {(cuuint64_t)s->dp8};
+    cuuint32_t box[2] = {128, (cuuint32_t)box_rows};
+    cuuint32_t estride[2] = {1, 1};
+    CUresult r = fn(&slot->map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void *)s->x8, gdim, gstride, box, estride,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled (FP8) failed (%d)", (int)r);
         return DL_ECUDA;
     }
     slot->valid = true;
@@ -517,6 +672,7 @@ int dl_store_destroy(dl_store *s)
     cudaGetDevice(&prev);
     if (prev != s->device) cudaSetDevice(s->device);
     dev_free(s->ids, 0);   // ids is the base of the store's single allocation
+    if (s->fp8_block) dev_free(s->fp8_block, 0);
     if (prev != s->device) cudaSetDevice(prev);
     delete s;
     return DL_OK;
