@@ -165,6 +165,18 @@ int dl_sim_join_noalloc(const float *R, const int64_t *r_ids, int64_t nR, const 
                         int64_t *out_r, int64_t *out_s, int64_t out_cap, int64_t *n_out,
                         void *cuda_stream);
 
+/*
+ * Diagnostics for the error bound of the low-precision stage (no counterpart in
+ * the paper). Runs the tensor-core pass of an R x S join in `precision`
+ * (DL_PREC_BF16 or DL_PREC_FP8E4M3) and writes, for every pair at the callers'
+ * row order, the kernel's approximation h~ of h = q.x - ||x||^2/2 (so that
+ * D = ||q||^2 - 2h) into h_out[|R|][|S|] and the bound E it uses into
+ * e_out[|R|][|S|] (device memory, caller-owned). |R| |S| <= 2^28. A sound kernel
+ * has |h~ - h| <= E for every pair.
+ */
+int dl_debug_scores(const dl_store *R, const dl_store *S, int32_t precision, float *h_out, float *e_out,
+                    void *cuda_stream);
+
 /* ---------------------------------------------------------------------------------
  * Batches: many epsilon-join and top-k requests against one resident store.
  * ------------------------------------------------------------------------------- */

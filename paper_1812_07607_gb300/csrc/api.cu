@@ -500,6 +500,86 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
 int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric, int32_t k, const dl_join_opts *opts,
                  dl_result **out);   // defined in topk.cu
 
+int dl_debug_scores(const dl_store *R, const dl_store *S, int32_t precision, float *h_out, float *e_out,
+                    void *cuda_stream)
+{
+    clear_error();
+    if (!R || !S || !h_out || !e_out || R->d != S->d) {
+        set_error("dl_debug_scores: bad arguments");
+        return DL_EINVAL;
+    }
+    if (precision != DL_PREC_BF16 && precision != DL_PREC_FP8E4M3) {
+        set_error("dl_debug_scores: precision must be BF16 or FP8");
+        return DL_EINVAL;
+    }
+    if (R->n * S->n > (int64_t(1) << 28) || R->n == 0 || S->n == 0) {
+        set_error("dl_debug_scores: |R| |S| must be in [1, 2^28]");
+        return DL_EINVAL;
+    }
+    const bool fp8 = precision == DL_PREC_FP8E4M3;
+    if ((!fp8 && R->dp > 512) || (fp8 && R->d > 1024)) {
+        set_error("dl_debug_scores: d too large for this precision");
+        return DL_EUNSUPPORTED;
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int rc = DL_OK;
+    if (fp8) {
+        rc = ensure_fp8(const_cast<dl_store *>(R), st);
+        if (!rc) rc = ensure_fp8(const_cast<dl_store *>(S), st);
+        if (rc) return rc;
+    }
+    const int64_t mt = (R->n + 127) / 128;
+    void *ws = nullptr;
+    rc = dev_alloc(&ws, 256 + mt * 128 * sizeof(float4) + 65536 * sizeof(uint2), st);
+    if (rc) return rc;
+    unsigned long long *cnt = (unsigned long long *)ws;
+    float4 *rowpar = (float4 *)((char *)ws + 256);
+    uint2 *cand = (uint2 *)((char *)rowpar + mt * 128 * sizeof(float4));
+    cudaMemsetAsync(cnt, 0, 256, st);
+    // thresholds for eps = 0 (the dump does not depend on them; candidates are discarded)
+    rc = launch_rowpar(R->nq64, R->rowb, R->n, mt * 128, R->dp, 0.0, nullptr, gamma64(R->d), rowpar, st,
+                       fp8 ? R->rowb8 : nullptr);
+    const CUtensorMap *tmA = nullptr, *tmB = nullptr;
+    const int BN = 256;
+    if (!rc) rc = fp8 ? get_tmap8(const_cast<dl_store *>(R), 128, &tmA) : get_tmap(const_cast<dl_store *>(R), 128, &tmA);
+    if (!rc) rc = fp8 ? get_tmap8(const_cast<dl_store *>(S), BN, &tmB) : get_tmap(const_cast<dl_store *>(S), BN, &tmB);
+    const int4 *units = nullptr;
+    int n_units = 0;
+    if (!rc) rc = get_units(R->n, S->n, false, BN, device_sm_count(), &units, &n_units);
+    if (!rc) {
+        TcLaunch L;
+        std::memset(&L.p, 0, sizeof L.p);
+        L.tmA = tmA;
+        L.tmB = tmB;
+        L.BN = BN;
+        L.grid = std::min(n_units, device_sm_count());
+        L.p.units = units;
+        L.p.n_units = n_units;
+        L.p.nR = (int)R->n;
+        L.p.nS = (int)S->n;
+        L.p.kc = fp8 ? R->dp8 / 128 : R->dp / 64;
+        tc_plan(BN, L.p.kc, &L.p.stages, &L.p.a_slots, fp8);
+        L.p.rowpar = rowpar;
+        L.p.beta = S->beta;
+        L.p.cstat = fp8 ? S->cstat8 : S->cstat;
+        L.p.sc_r = fp8 ? R->sc8 : nullptr;
+        L.p.sc_s = fp8 ? S->sc8 : nullptr;
+        L.p.cand = cand;
+        L.p.cand_cnt = cnt + 0;
+        L.p.cand_cap = 65536;
+        L.p.err = (int *)(cnt + 1);
+        L.p.dump_h = h_out;
+        L.p.dump_e = e_out;
+        L.p.orig_r = R->orig;
+        L.p.orig_s = S->orig;
+        rc = launch_tc_join(L, st, false, fp8);
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    dev_free(ws, st);
+    if (!rc && e != cudaSuccess) rc = cuda_fail(e, "dl_debug_scores");
+    return rc;
+}
+
 int dl_result_count(const dl_result *r, int64_t *n)
 {
     if (!r || !n) {

@@ -235,6 +235,7 @@ __global__ void __launch_bounds__(320, 1)
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int kc = p.kc, stages = p.stages, a_slots = p.a_slots;
     constexpr uint32_t kStageBytes = BN * 128;
+    constexpr int kChunkCols = FP8 ? 128 : 64;   // columns per 128-byte K chunk
     constexpr uint32_t kTmemCols = 2 * BN;
     constexpr int HC = BN / 2;               // columns of a tile each epilogue warp owns
     constexpr int kSubW = HC / 32;           // 32-column chunks per warp per tile
@@ -305,8 +306,8 @@ __global__ void __launch_bounds__(320, 1)
                     break;
                 }
                 mbar_arrive_expect_tx(a_full + slot, a_bytes);
-                for (int c = 0; c < kc; ++c)
-                    tma_load_2d(sA + slot * a_bytes + c * 16384, &tmA, a_full + slot, c * 64, un.x * 128);
+                for (int c = 0; c < kc; ++c)   // a K chunk is 128 bytes: 64 BF16 or 128 FP8 columns
+                    tma_load_2d(sA + slot * a_bytes + c * 16384, &tmA, a_full + slot, c * kChunkCols, un.x * 128);
                 a_pend[slot] = true;
                 a_pend_par[slot] = use & 1;
                 for (int n = un.y; n < un.z && ok; ++n) {
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(320, 1)
                             break;
                         }
                         mbar_arrive_expect_tx(full + stage, kStageBytes);
-                        tma_load_2d(sB + stage * kStageBytes, &tmB, full + stage, c * 64, n * BN);
+                        tma_load_2d(sB + stage * kStageBytes, &tmB, full + stage, c * kChunkCols, n * BN);
                         pend[stage] = true;
                         pend_par[stage] = phase;
                         if (++stage == (uint32_t)stages) {
@@ -511,6 +512,18 @@ __global__ void __launch_bounds__(320, 1)
                 const float4 cs0 = cst[2 * piece], cs1 = cst[2 * piece + 1];
                 const float eh0 = __fmaf_ru(rp.z, cs0.x, __fmaf_ru(rp.w, cs0.y, cs0.z));
                 const float eh1 = __fmaf_ru(rp.z, cs1.x, __fmaf_ru(rp.w, cs1.y, cs1.z));
+                if (p.dump_h) {   // diagnostics: every pair's h and bound, at caller row order
+#pragma unroll
+                    for (int j = 0; j < 64; ++j) {
+                        const int c = colw + piece * 64 + j;
+                        if (r < p.nR && c < p.nS) {
+                            const float h = FP8 ? __uint_as_float(v[j]) : __uint_as_float(v[j]) + nbeta[piece * 64 + j];
+                            const size_t o = (size_t)p.orig_r[r] * p.nS + p.orig_s[c];
+                            p.dump_h[o] = h;
+                            p.dump_e[o] = j < 32 ? eh0 : eh1;
+                        }
+                    }
+                }
                 float tr0, tr1;
                 if constexpr (TOPK) {   // candidate iff h + E (+ canonical slack rp.x) >= the best threshold
                     const float th = fmaxf(theta, theta_row);

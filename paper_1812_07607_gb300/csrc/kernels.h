@@ -20,6 +20,9 @@ struct TcParams {
     const float4 *rowpar;    // [m_tiles*128] {alpha_acc, alpha_rej, rq, nqt}
     const float *beta;       // S: RN32(||x||^2/2), +inf padding
     const float4 *cstat;     // S: per 32-column chunk {P1, P2, P3, min beta}
+    float *dump_h;           // diagnostics: h of every pair [nR][nS] in caller order (NULL: off)
+    float *dump_e;           // diagnostics: the bound E of every pair
+    const int32_t *orig_r, *orig_s;   // diagnostics: caller row of each store row
     const float *sc_r;       // FP8: per-row power-of-two scales of R (NULL for BF16)
     const float *sc_s;       // FP8: per-row scales of S
     uint2 *cand;             // candidates: {r, c | 0x80000000 if a band pair, else a proven match}

@@ -34,6 +34,7 @@ EXPORTS = [
     "dl_result_stats", "dl_result_free", "dl_last_error", "dl_version", "dl_kernel_launches",
     "dl_sim_join_noalloc", "dl_batch_join", "dl_result_request_pairs", "dl_result_request_topk",
     "dl_server_create", "dl_submit", "dl_poll", "dl_cancel", "dl_server_get_stats", "dl_server_destroy",
+    "dl_debug_scores",
 ]
 
 
@@ -119,6 +120,8 @@ def load(path: str | None = None):
     L.dl_server_destroy.argtypes = [vp]
     for name in ("dl_server_create", "dl_submit", "dl_poll", "dl_cancel", "dl_server_get_stats", "dl_server_destroy"):
         getattr(L, name).restype = ctypes.c_int
+    L.dl_debug_scores.argtypes = [vp, vp, i32, vp, vp, vp]
+    L.dl_debug_scores.restype = ctypes.c_int
     L.dl_last_error.restype = ctypes.c_char_p
     L.dl_version.restype = ctypes.c_char_p
     L.dl_kernel_launches.restype = i64
@@ -422,3 +425,13 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def debug_scores(R: Store, S: Store, precision="bf16", stream=None):
+    """(h~, E) as torch [|R|, |S|] float32 CUDA tensors: the kernel's h approximation and its bound."""
+    import torch
+    h = torch.empty(R.n, S.n, dtype=torch.float32, device="cuda")
+    e = torch.empty(R.n, S.n, dtype=torch.float32, device="cuda")
+    _check(load().dl_debug_scores(R.handle, S.handle, PRECISIONS[precision], h.data_ptr(), e.data_ptr(),
+                                  _stream_handle(stream)), "dl_debug_scores")
+    return h, e

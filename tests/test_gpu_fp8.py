@@ -91,3 +91,23 @@ def test_fp8_bench_workload_equals_bf16(dl):
     b.free()
     assert set(zip(ra.tolist(), sa.tolist())) == set(zip(rb.tolist(), sb.tolist()))
     print("fp8 band pairs", stb["band_pairs"], "fp64", stb["fp64_pairs"])
+
+
+def test_fp8_signed_multichunk_equals_exact_fp32(dl):
+    """Signed unit-norm embeddings at d = 256 / 512 / 1024 (2-8 FP8 K chunks): FP8 set == exact FP32 set."""
+    import torch
+    g = W.rng(7300)
+    for d, n in ((256, 6000), (512, 6000), (1024, 3000)):
+        # jitter of norm ~0.15: same-centroid pairs sit near 0.21 apart, right at eps
+        sig = 0.15 / np.sqrt(d)
+        R, c = W.unit_mixture(g, n, d, 256, sig)
+        S, _ = W.unit_mixture(g, n, d, 256, sig, centroids=c)
+        Rs = dl.Store(torch.arange(n).cuda(), torch.from_numpy(R).cuda())
+        Ss = dl.Store(torch.arange(n).cuda() + 10**9, torch.from_numpy(S).cuda())
+        sets = {}
+        for prec in ("fp8", "fp32"):
+            r = dl.sim_join(Rs, Ss, 0.21, precision=prec)
+            a, b = r.pairs_host()
+            r.free()
+            sets[prec] = set(zip(a.tolist(), b.tolist()))
+        assert len(sets["fp32"]) > 100 and sets["fp8"] == sets["fp32"], (d, len(sets["fp8"] ^ sets["fp32"]))
