@@ -91,66 +91,47 @@ __device__ __forceinline__ void flush_stage(const TcParams &p, uint2 *stg, uint3
     scnt = 0;
 }
 
-// Slow path for a 64-column piece that a chunk bound could not reject: for each
-// 32-column half that some lane could not reject, compute h = fl(A - beta) for
-// the pairs (r, col0 + j), classify them against the half's (accept, reject)
-// thresholds, and buffer every proven match and band pair. Warp-collective;
-// rarely taken.
+// Pair-by-pair path for one 32-column chunk. The rows (lanes) whose chunk bound failed are
+// taken one at a time: the row's 32 values pass through the warp's shared-memory exchange
+// slot so that lane j classifies column c0 + j, with h = fl(A - beta_j) (FP8: v already
+// holds h). A pair with h >= tau_rej of its row -- a proven match (h >= tau_acc) or a band
+// pair -- is buffered as a candidate, its position given by a ballot prefix. Warp-collective.
 template <bool FP8>
-__device__ __forceinline__ uint32_t slow_piece(const TcParams &p, const uint32_t (&v)[64], const float *nb, float rx,
-                                              float ry, float eh0, float eh1, bool hit0, bool hit1, int r, int col0,
-                                              uint2 *stg, uint32_t scnt)
+__device__ __forceinline__ uint32_t slow_chunk(const TcParams &p, const uint32_t (&v)[64], int o, const float *bt,
+                                               float tau_acc, float tau_rej, bool hit, int r, int c0, float *xch,
+                                               uint2 *stg, uint32_t scnt)
 {
     const unsigned lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
+    const int c = c0 + (int)lane;                        // this lane's column
+    const float bl = FP8 ? 0.f : bt[o + lane];
+    const bool cvalid = c < p.nS;
+    unsigned hm = __ballot_sync(0xffffffffu, hit);
+    while (hm) {
+        const int k = __ffs(hm) - 1;
+        hm &= hm - 1u;
+        if ((int)lane == k) {
+            float4 *x4 = reinterpret_cast<float4 *>(xch);
 #pragma unroll
-    for (int hh = 0; hh < 2; ++hh) {
-        if (!__any_sync(0xffffffffu, hh ? hit1 : hit0)) continue;
-        const float eh = hh ? eh1 : eh0;
-        const float tau_acc = __fadd_ru(rx, eh);
-        const float tau_rej = __fsub_rd(ry, eh);
-        const int c0 = col0 + hh * 32;
-        uint32_t am = 0, bm = 0;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const float h = FP8 ? __uint_as_float(v[hh * 32 + j]) : __uint_as_float(v[hh * 32 + j]) + nb[hh * 32 + j];
-            const bool a = h >= tau_acc;
-            const bool b = !a && (h >= tau_rej);
-            am |= (a ? 1u : 0u) << j;
-            bm |= (b ? 1u : 0u) << j;
+            for (int i = 0; i < 8; ++i)
+                x4[i] = make_float4(__uint_as_float(v[o + 4 * i]), __uint_as_float(v[o + 4 * i + 1]),
+                                    __uint_as_float(v[o + 4 * i + 2]), __uint_as_float(v[o + 4 * i + 3]));
         }
-        uint32_t vm = 0xffffffffu;
-        const int rem = p.nS - c0;
-        if (rem < 32) vm = rem <= 0 ? 0u : ((1u << rem) - 1u);
-        if (p.upper) {
-            const int k = r - c0;   // columns j <= k are not pairs (need c > r)
-            if (k >= 31)
-                vm = 0u;
-            else if (k >= 0)
-                vm &= ~((2u << k) - 1u);
-        }
-        if (r >= p.nR) vm = 0u;
-        am &= vm;
-        bm &= vm;
-        while (__any_sync(0xffffffffu, (am | bm) != 0u)) {
-            const bool has_a = am != 0u;
-            const bool has = has_a || bm != 0u;
-            int j = 0;
-            if (has_a) {
-                j = __ffs(am) - 1;
-                am &= am - 1u;
-            } else if (has) {
-                j = __ffs(bm) - 1;
-                bm &= bm - 1u;
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, has);
-            if (scnt + __popc(m) > kStageCap) flush_stage(p, stg, scnt);
-            if (has)
-                stg[scnt + __popc(m & lt)] = make_uint2((uint32_t)r, (uint32_t)(c0 + j) | (has_a ? 0u : kBandFlag));
-            scnt += __popc(m);
+        __syncwarp();
+        const float a = xch[lane];
+        __syncwarp();   // every lane has read the slot before the next row overwrites it
+        const float h = FP8 ? a : a - bl;
+        const float ta = __shfl_sync(0xffffffffu, tau_acc, k);
+        const float tr = __shfl_sync(0xffffffffu, tau_rej, k);
+        const int rk = __shfl_sync(0xffffffffu, r, k);
+        const bool cand = cvalid && h >= tr && (!p.upper || c > rk);   // upper mode: pairs with c > r only
+        const unsigned cm = __ballot_sync(0xffffffffu, cand);
+        if (cm) {
+            if (scnt + __popc(cm) > (uint32_t)kStageCap) flush_stage(p, stg, scnt);
+            if (cand) stg[scnt + __popc(cm & lt)] = make_uint2((uint32_t)rk, (uint32_t)c | (h >= ta ? 0u : kBandFlag));
+            scnt += __popc(cm);
         }
     }
-    (void)lane;
     return scnt;
 }
 
@@ -203,7 +184,7 @@ __device__ __noinline__ float2 topk_insert(const TcParams &p, size_t sidx, int r
 
 // Top-k slow path for a 64-column piece some lane could not reject: each lane
 // walks its own row's columns whose upper bound reaches its theta.
-__device__ __forceinline__ void slow_topk(const TcParams &p, const uint32_t (&v)[64], const float *nb, float eh0,
+__device__ __forceinline__ void slow_topk(const TcParams &p, const uint32_t (&v)[64], const float *bt, float eh0,
                                           float eh1, bool hit0, bool hit1, int r, int col0, size_t sidx,
                                           float &theta, int &cnt, float theta_row)
 {
@@ -215,7 +196,7 @@ __device__ __forceinline__ void slow_topk(const TcParams &p, const uint32_t (&v)
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
             const int c = col0 + hh * 32 + j;
-            const float h = __uint_as_float(v[hh * 32 + j]) + nb[hh * 32 + j];
+            const float h = __uint_as_float(v[hh * 32 + j]) - bt[hh * 32 + j];
             const float U = __fadd_ru(h, eh);
             if (c < p.nS && U >= fmaxf(theta, theta_row)) {
                 const float2 st = topk_insert(p, sidx, r, c, U, __fsub_rd(h, eh), theta, cnt, theta_row);
@@ -224,6 +205,26 @@ __device__ __forceinline__ void slow_topk(const TcParams &p, const uint32_t (&v)
             }
         }
     }
+}
+
+// Maximum of v[o .. o+31] with three-input max.f32 (17 instructions, depth 4).
+__device__ __forceinline__ float fmax3(float a, float b, float c)
+{
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+__device__ __forceinline__ float max_tree32(const uint32_t (&v)[64], int o)
+{
+    float m[11];
+#pragma unroll
+    for (int i = 0; i < 10; ++i)
+        m[i] = fmax3(__uint_as_float(v[o + 3 * i]), __uint_as_float(v[o + 3 * i + 1]), __uint_as_float(v[o + 3 * i + 2]));
+    m[10] = fmaxf(__uint_as_float(v[o + 30]), __uint_as_float(v[o + 31]));
+    const float a = fmax3(m[0], m[1], m[2]), b = fmax3(m[3], m[4], m[5]), c = fmax3(m[6], m[7], m[8]);
+    const float e = fmaxf(m[9], m[10]);
+    return fmaxf(fmax3(a, b, c), e);
 }
 
 template <int BN, bool TOPK, bool FP8>
@@ -242,8 +243,8 @@ __global__ void __launch_bounds__(320, 1)
     const uint32_t a_bytes = (uint32_t)kc * 16384;
     uint8_t *sA = smem;                                    // a_slots x kc x [128 rows x 128 B]
     uint8_t *sB = smem + a_slots * a_bytes;                // stages x [BN rows x 128 B]
-    float *s_nbeta = reinterpret_cast<float *>(sB + stages * kStageBytes);   // 8 warps x 2 x HC: -beta
-    float4 *s_cst = reinterpret_cast<float4 *>(s_nbeta + 8 * 2 * HC);       // 8 warps x 2 x kSubW chunk stats
+    float *s_beta = reinterpret_cast<float *>(sB + stages * kStageBytes);    // 8 warps x 2 x HC: beta
+    float4 *s_cst = reinterpret_cast<float4 *>(s_beta + 8 * 2 * HC);       // 8 warps x 2 x kSubW chunk stats
     uint2 *s_stage = reinterpret_cast<uint2 *>(s_cst + 8 * 2 * kSubW);       // 8 warps x kStageCap candidates
     float *s_sx = reinterpret_cast<float *>(s_stage + 8 * kStageCap);        // FP8: 8 warps x 2 x HC column scales
     uint64_t *bars = reinterpret_cast<uint64_t *>(s_sx + (FP8 ? 8 * 2 * HC : 0));
@@ -256,6 +257,7 @@ __global__ void __launch_bounds__(320, 1)
     uint64_t *done = bars + 24;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 25);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 26);
+    float *s_xch = reinterpret_cast<float *>(bars + 28);   // [8 warps x 32] row exchange slots (16-byte aligned)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -405,10 +407,11 @@ __global__ void __launch_bounds__(320, 1)
         const int quad = warp & 3;         // TMEM lanes this warp may access: 32*quad .. +31
         const int half = e >> 2;           // which half of the tile's columns
         const uint32_t lane_base = static_cast<uint32_t>(quad * 32) << 16;
-        float *my_nb = s_nbeta + e * (2 * HC);
+        float *my_bt = s_beta + e * (2 * HC);
         float *my_sx = s_sx + e * (2 * HC);   // FP8 only
         float4 *my_cs = s_cst + e * (2 * kSubW);
         uint2 *my_stg = s_stage + e * kStageCap;
+        float *my_xch = s_xch + e * 32;
         uint32_t scnt = 0;
         constexpr int kPer = HC / 32;      // -beta values a lane stages per tile (4 or 2)
         TileIter cur, nxt;
@@ -416,34 +419,22 @@ __global__ void __launch_bounds__(320, 1)
         nxt = cur;
         nxt.next(p);
 
-        auto stage_regs = [&](const TileIter &it, float (&nb)[kPer], float (&sx)[kPer], float4 &cs) {
-            if (it.valid) {
-                const int c0 = it.n * BN + half * HC;
-#pragma unroll
-                for (int q = 0; q < kPer; ++q) nb[q] = -__ldg(p.beta + c0 + lane * kPer + q);
-                if constexpr (FP8) {
-#pragma unroll
-                    for (int q = 0; q < kPer; ++q) sx[q] = __ldg(p.sc_s + c0 + lane * kPer + q);
-                }
-                if (lane < kSubW) cs = __ldg(p.cstat + (c0 >> 5) + lane);
+        auto stage_async = [&](const TileIter &it, int s) {
+            if (!it.valid) return;
+            const int c0 = it.n * BN + half * HC;
+            if constexpr (kPer == 4) {
+                cp_async_16(my_bt + s * HC + lane * 4, p.beta + c0 + lane * 4);
+                if constexpr (FP8) cp_async_16(my_sx + s * HC + lane * 4, p.sc_s + c0 + lane * 4);
+            } else {
+                cp_async_8(my_bt + s * HC + lane * 2, p.beta + c0 + lane * 2);
+                if constexpr (FP8) cp_async_8(my_sx + s * HC + lane * 2, p.sc_s + c0 + lane * 2);
             }
+            if (lane < kSubW) cp_async_16(my_cs + s * kSubW + lane, p.cstat + (c0 >> 5) + lane);
+            cp_async_commit();
         };
-        auto stage_store = [&](int s, const float (&nb)[kPer], const float (&sx)[kPer], const float4 &cs) {
-#pragma unroll
-            for (int q = 0; q < kPer; ++q) my_nb[s * HC + lane * kPer + q] = nb[q];
-            if constexpr (FP8) {
-#pragma unroll
-                for (int q = 0; q < kPer; ++q) my_sx[s * HC + lane * kPer + q] = sx[q];
-            }
-            if (lane < kSubW) my_cs[s * kSubW + lane] = cs;
-            __syncwarp();
-        };
-        {
-            float nb[kPer], sx[kPer];
-            float4 cs = make_float4(0.f, 0.f, 0.f, 0.f);
-            stage_regs(cur, nb, sx, cs);
-            stage_store(0, nb, sx, cs);
-        }
+        stage_async(cur, 0);
+        cp_async_wait_all();
+        __syncwarp();
 
         uint32_t t = 0;
         bool ok = true;
@@ -468,9 +459,7 @@ __global__ void __launch_bounds__(320, 1)
                     }
                 }
             }
-            float nbn[kPer], sxn[kPer];
-            float4 csn = make_float4(0.f, 0.f, 0.f, 0.f);
-            stage_regs(nxt, nbn, sxn, csn);   // prefetch the next tile's -beta (latency hidden by this tile)
+            stage_async(nxt, (t & 1) ^ 1);   // prefetch the next tile's -beta (latency hidden by this tile)
 
             if constexpr (TOPK) {
                 theta_row = __int_as_float(0xff800000);
@@ -484,7 +473,7 @@ __global__ void __launch_bounds__(320, 1)
             }
             tc_fence_after();
             const uint32_t tbase = tmem_base + lane_base + b * BN + half * HC;
-            const float *nbeta = my_nb + slot * HC;
+            const float *beta = my_bt + slot * HC;
             const float *sxs = my_sx + slot * HC;
             const float4 *cst = my_cs + slot * kSubW;
             const int colw = cur.n * BN + half * HC;   // first column this warp owns in the tile
@@ -495,14 +484,14 @@ __global__ void __launch_bounds__(320, 1)
                     // h = fma(acc, s_q s_x, -beta): one rounding (s_q s_x is an exact power of two);
                     // the values in v become h, and the chunk bound below uses beta_min = 0.
                     const float4 *sx4 = reinterpret_cast<const float4 *>(sxs + piece * 64);
-                    const float4 *nb4 = reinterpret_cast<const float4 *>(nbeta + piece * 64);
+                    const float4 *bt4 = reinterpret_cast<const float4 *>(beta + piece * 64);
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
-                        const float4 sx = sx4[i], nb = nb4[i];
+                        const float4 sx = sx4[i], bt = bt4[i];
                         const float2 a = __ffma2_rn(make_float2(__uint_as_float(v[4 * i]), __uint_as_float(v[4 * i + 1])),
-                                                    make_float2(sq * sx.x, sq * sx.y), make_float2(nb.x, nb.y));
+                                                    make_float2(sq * sx.x, sq * sx.y), make_float2(-bt.x, -bt.y));
                         const float2 b = __ffma2_rn(make_float2(__uint_as_float(v[4 * i + 2]), __uint_as_float(v[4 * i + 3])),
-                                                    make_float2(sq * sx.z, sq * sx.w), make_float2(nb.z, nb.w));
+                                                    make_float2(sq * sx.z, sq * sx.w), make_float2(-bt.z, -bt.w));
                         v[4 * i] = __float_as_uint(a.x);
                         v[4 * i + 1] = __float_as_uint(a.y);
                         v[4 * i + 2] = __float_as_uint(b.x);
@@ -517,7 +506,7 @@ __global__ void __launch_bounds__(320, 1)
                     for (int j = 0; j < 64; ++j) {
                         const int c = colw + piece * 64 + j;
                         if (r < p.nR && c < p.nS) {
-                            const float h = FP8 ? __uint_as_float(v[j]) : __uint_as_float(v[j]) + nbeta[piece * 64 + j];
+                            const float h = FP8 ? __uint_as_float(v[j]) : __uint_as_float(v[j]) - beta[piece * 64 + j];
                             const size_t o = (size_t)p.orig_r[r] * p.nS + p.orig_s[c];
                             p.dump_h[o] = h;
                             p.dump_e[o] = j < 32 ? eh0 : eh1;
@@ -535,34 +524,21 @@ __global__ void __launch_bounds__(320, 1)
                 }
                 // Whole-chunk reject: with beta_j >= beta_min(chunk), every h_j = fl(A_j - beta_j)
                 // is <= fl_ru(max_j A_j - beta_min); rows are in norm order, so beta_min is tight.
-                float m0[16], m1[16];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    m0[i] = fmaxf(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
-                    m1[i] = fmaxf(__uint_as_float(v[32 + 2 * i]), __uint_as_float(v[32 + 2 * i + 1]));
-                }
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    m0[i] = fmaxf(m0[2 * i], m0[2 * i + 1]);
-                    m1[i] = fmaxf(m1[2 * i], m1[2 * i + 1]);
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    m0[i] = fmaxf(m0[2 * i], m0[2 * i + 1]);
-                    m1[i] = fmaxf(m1[2 * i], m1[2 * i + 1]);
-                }
-                const float mx0 = fmaxf(fmaxf(m0[0], m0[1]), fmaxf(m0[2], m0[3]));
-                const float mx1 = fmaxf(fmaxf(m1[0], m1[1]), fmaxf(m1[2], m1[3]));
+                const float mx0 = max_tree32(v, 0), mx1 = max_tree32(v, 32);
                 const bool hit0 = (FP8 ? mx0 : __fsub_ru(mx0, cs0.w)) >= tr0;
                 const bool hit1 = (FP8 ? mx1 : __fsub_ru(mx1, cs1.w)) >= tr1;
                 if constexpr (TOPK) {
                     if (hit0 || hit1)
-                        slow_topk(p, v, nbeta + piece * 64, __fadd_ru(eh0, rp.x), __fadd_ru(eh1, rp.x), hit0, hit1, r,
+                        slow_topk(p, v, beta + piece * 64, __fadd_ru(eh0, rp.x), __fadd_ru(eh1, rp.x), hit0, hit1, r,
                                   colw + piece * 64, sidx, theta, tcnt, theta_row);
                 } else {
-                    if (__any_sync(0xffffffffu, hit0 || hit1))
-                        scnt = slow_piece<FP8>(p, v, nbeta + piece * 64, rp.x, rp.y, eh0, eh1, hit0, hit1, r,
-                                               colw + piece * 64, my_stg, scnt);
+                    if (__any_sync(0xffffffffu, hit0 || hit1)) {
+                        const int c0 = colw + piece * 64;
+                        scnt = slow_chunk<FP8>(p, v, 0, beta + piece * 64, __fadd_ru(rp.x, eh0), __fsub_rd(rp.y, eh0),
+                                               hit0, r, c0, my_xch, my_stg, scnt);
+                        scnt = slow_chunk<FP8>(p, v, 32, beta + piece * 64, __fadd_ru(rp.x, eh1), __fsub_rd(rp.y, eh1),
+                                               hit1, r, c0 + 32, my_xch, my_stg, scnt);
+                    }
                 }
             };
 
@@ -590,7 +566,8 @@ __global__ void __launch_bounds__(320, 1)
                 }
             }
             // publish the next tile's -beta into the other slot (this warp's own copy)
-            stage_store(slot ^ 1, nbn, sxn, csn);
+            cp_async_wait_all();
+            __syncwarp();
             cur = nxt;
             nxt.next(p);
             ++t;
@@ -611,9 +588,9 @@ __global__ void __launch_bounds__(320, 1)
 
 static size_t tc_extra_bytes(int BN, bool fp8)
 {
-    // per epilogue warp: 2 x BN/2 floats of -beta (and of the FP8 column scales), 2 x BN/64
-    // chunk stats, the candidate buffer; then 27 barrier / flag words
-    return (size_t)8 * (2 * (BN / 2) * 4 * (fp8 ? 2 : 1) + 2 * (BN / 64) * 16 + kStageCap * 8) + 27 * 8;
+    // per epilogue warp: 2 x BN/2 floats of beta (and of the FP8 column scales), 2 x BN/64
+    // chunk stats, the candidate buffer; then 27 barrier / flag words and 8 x 32 exchange floats
+    return (size_t)8 * (2 * (BN / 2) * 4 * (fp8 ? 2 : 1) + 2 * (BN / 64) * 16 + kStageCap * 8) + 27 * 8 + 8 * 32 * 4 + 16;
 }
 
 static size_t tc_smem_bytes(int BN, int kc, int stages, int a_slots, bool fp8)

@@ -241,3 +241,13 @@ def request_mix(g: np.random.Generator, n_requests: int, mu: float, sigma: float
         else:
             out.append({"kind": "eps", "nq": int(sizes[i]), "k": 0, "selectivity": float(sel[i])})
     return out
+
+
+def sample_rows(n: int, k: int, seed: int) -> np.ndarray:
+    """k distinct row indices of [0, n), ascending, drawn with a seeded permutation."""
+    return np.sort(rng(seed).choice(n, size=min(k, n), replace=False)).astype(np.int64)
+
+
+# Row sample of the 1,048,576 x 1,048,576 d=512 join whose exact pair set is stored as a digest.
+UNIT_MIXTURE_SAMPLE_SEED = SEED_BASE + 103
+UNIT_MIXTURE_SAMPLE_ROWS = 16384
