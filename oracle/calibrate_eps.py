@@ -10,6 +10,9 @@ selectivity instead and this script turns that into a value:
   * self_clustered_262k: 512 seeded rows against all 262,144 rows; eps^2 sits
     in the gap that makes the mean number of other rows within eps equal 20.
   * rxs_unit_mixture_1m: 64 seeded R rows against all of S; mean 10 per row.
+  * batch_store_2m / serve_store_4m (request workloads): 256 fresh query rows against a
+    seeded 65,536-row sample of the store; the pooled distances give a
+    (selectivity, eps) table, selectivity = the fraction of store rows within eps.
 
 eps is then placed so that fl(eps*eps) lies strictly inside the chosen gap of
 the sampled canonical distances (the gap's midpoint), keeping every sampled
@@ -105,6 +108,18 @@ def calibrate(name: str) -> tuple[str, float, dict]:
         key = f"rxs_unit_mixture_1m:{W.SEED_BASE + 2}:1048576:512:4096"
         per_row = (sm <= eps * eps).sum(axis=1)
         return key, eps, {"sample_rows": 64, "mean_matches": float(per_row.mean())}
+    if name in ("batch_store_2m", "serve_store_4m"):
+        st = getattr(W, name)()
+        g = W.rng(W.SEED_BASE + 104)
+        cols = np.sort(g.choice(st.X.shape[0], size=65536, replace=False))
+        Q = st.queries(256, W.SEED_BASE + 105)
+        sm = smallest_per_row(Q, np.ascontiguousarray(st.X[cols]), keep=2000)
+        vals = np.sort(sm.ravel())
+        table = []
+        for sel in np.geomspace(1e-5, 5.5e-3, 40):
+            rank = int(round(sel * len(cols) * Q.shape[0]))
+            table.append([float(sel), eps_in_gap(vals, max(1, rank))])
+        return None, None, {"extra": {f"{name}:selectivity_eps": table}}
     raise KeyError(name)
 
 
@@ -115,7 +130,8 @@ def main(names):
             table = json.load(f)
     for n in names:
         key, eps, info = calibrate(n)
-        table[key] = eps
+        if key is not None:
+            table[key] = eps
         table.update(info.pop("extra", {}))
         print(n, key, repr(eps), info, file=sys.stderr)
         with open(OUT, "w") as f:
@@ -124,4 +140,5 @@ def main(names):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["rxs_histograms_2k", "self_clustered_262k", "rxs_unit_mixture_1m"])
+    main(sys.argv[1:] or ["rxs_histograms_2k", "self_clustered_262k", "rxs_unit_mixture_1m", "batch_store_2m",
+                          "serve_store_4m"])

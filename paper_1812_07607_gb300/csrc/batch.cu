@@ -55,8 +55,8 @@ __global__ void k_batch_expand(const ReqDev *__restrict__ reqs, int n, int64_t t
 }
 
 // Candidates -> decisions in place (rejected entries get column 0xffffffff) and
-// per-request counts. One thread per entry: band entries are rechecked by
-// their own thread (sequential FP32 with its bound, canonical FP64 if needed);
+// per-request counts. One thread per entry; the warp rechecks its band entries
+// together, one after another (FP32 with its bound, canonical FP64 if needed);
 // counts are aggregated per warp over lanes of the same request.
 __global__ void __launch_bounds__(256)
     k_batch_decide(uint2 *__restrict__ cand, const unsigned long long *__restrict__ cand_cnt, unsigned long long cap,
@@ -76,13 +76,18 @@ __global__ void __launch_bounds__(256)
         const bool band = valid && (e.y & kBandFlag);
         bool acc = valid && !band;
         bool f64 = false;
-        if (band) {
-            const double e2 = row_e2[r];
-            float ta, tr;
-            fp32_thresholds(e2, d, &ta, &tr);
-            acc = lane_exact_decide(Q + (size_t)r * d, S + (size_t)c * d, d, e2, ta, tr, &f64);
+        const unsigned bm = __ballot_sync(0xffffffffu, band);
+        if (bm) {
+            double e2 = 0.0;
+            float ta = 0.f, tr = 0.f;
+            if (band) {
+                e2 = row_e2[r];
+                fp32_thresholds(e2, d, &ta, &tr);
+            }
+            const bool dec = warp_band_decide(bm, Q + (size_t)r * d, S + (size_t)c * d, d, e2, ta, tr, &f64);
+            if (band) acc = dec;
         }
-        const unsigned bm = __ballot_sync(0xffffffffu, band), fm = __ballot_sync(0xffffffffu, f64);
+        const unsigned fm = __ballot_sync(0xffffffffu, f64);
         if (lane == 0) {
             if (bm) atomicAdd(n_band, (unsigned long long)__popc(bm));
             if (fm) atomicAdd(n_fp64, (unsigned long long)__popc(fm));

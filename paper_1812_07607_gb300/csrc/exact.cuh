@@ -19,22 +19,45 @@ __device__ __forceinline__ void fp32_thresholds(double e2, int d, float *t_acc, 
     *t_rej = __double2float_ru(e2 * (1.0 + 2.0 * g64) * (1.0 + g32) * (1.0 + 8.881784197001252e-16) + abs32);
 }
 
-// Exact decision for the pair (q, x), taken by the whole warp (same answer in
-// every lane): FP32 first, the canonical FP64 sum only when FP32 cannot decide.
-__device__ __forceinline__ bool warp_exact_decide(const float *__restrict__ q, const float *__restrict__ x, int d,
-                                                  double e2, float t_acc, float t_rej,
-                                                  unsigned long long *__restrict__ n_fp64)
+// FP32 squared distance of (q, x) computed by the whole warp: each lane sums a slice
+// (16-byte loads when d % 4 == 0: store rows are then 16-byte aligned), then a shuffle
+// tree. Every lane returns the sum. The (d+8) 2^-24 bound of fp32_thresholds holds for
+// any summation order.
+__device__ __forceinline__ float warp_sq32(const float *__restrict__ q, const float *__restrict__ x, int d)
 {
     const unsigned lane = threadIdx.x & 31;
     float s = 0.f;
-    for (int k = lane; k < d; k += 32) {
-        const float t = __ldg(q + k) - __ldg(x + k);
-        s = fmaf(t, t, s);
+    if ((d & 3) == 0) {
+        const float4 *q4 = reinterpret_cast<const float4 *>(q);
+        const float4 *x4 = reinterpret_cast<const float4 *>(x);
+        for (int k = lane; k < (d >> 2); k += 32) {
+            const float4 a = __ldg(q4 + k), b = __ldg(x4 + k);
+            float t = a.x - b.x;
+            s = fmaf(t, t, s);
+            t = a.y - b.y;
+            s = fmaf(t, t, s);
+            t = a.z - b.z;
+            s = fmaf(t, t, s);
+            t = a.w - b.w;
+            s = fmaf(t, t, s);
+        }
+    } else {
+        for (int k = lane; k < d; k += 32) {
+            const float t = __ldg(q + k) - __ldg(x + k);
+            s = fmaf(t, t, s);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (s <= t_acc) return true;
-    if (s > t_rej) return false;
+    return s;
+}
+
+// The canonical FP64 sum of (q, x) by the whole warp: lane l forms the term of dimension
+// k0 + l, then every lane adds the 32 terms in ascending k with __dadd_rn, so the sum is
+// exactly the sequential definition's. Every lane returns it.
+__device__ __forceinline__ double warp_canonical64(const float *__restrict__ q, const float *__restrict__ x, int d)
+{
+    const unsigned lane = threadIdx.x & 31;
     double sum = 0.0;
     for (int k0 = 0; k0 < d; k0 += 32) {
         double pk = 0.0;
@@ -46,31 +69,57 @@ __device__ __forceinline__ bool warp_exact_decide(const float *__restrict__ q, c
         const int lim = min(32, d - k0);
         for (int l = 0; l < lim; ++l) sum = __dadd_rn(sum, __shfl_sync(0xffffffffu, pk, l));
     }
-    if (lane == 0) atomicAdd(n_fp64, 1ULL);
+    return sum;
+}
+
+// Exact decision for the pair (q, x), taken by the whole warp (same answer in
+// every lane): FP32 first, the canonical FP64 sum only when FP32 cannot decide.
+__device__ __forceinline__ bool warp_exact_decide(const float *__restrict__ q, const float *__restrict__ x, int d,
+                                                  double e2, float t_acc, float t_rej,
+                                                  unsigned long long *__restrict__ n_fp64)
+{
+    const float s = warp_sq32(q, x, d);
+    if (s <= t_acc) return true;
+    if (s > t_rej) return false;
+    const double sum = warp_canonical64(q, x, d);
+    if ((threadIdx.x & 31) == 0) atomicAdd(n_fp64, 1ULL);
     return sum <= e2;
 }
 
-// Exact decision for one pair by ONE thread: sequential FP32 FMA chain (bound
-// (d+8) 2^-24 D, the same as the warp version's), then the canonical FP64 sum
-// only when FP32 cannot decide. For lists where most entries are band pairs.
-__device__ __forceinline__ bool lane_exact_decide(const float *__restrict__ q, const float *__restrict__ x, int d,
-                                                  double e2, float t_acc, float t_rej, bool *used_fp64)
+// Exact decisions for the band entries among a warp's 32 candidate entries: each lane in
+// bm holds a band pair (q, x) with its own squared threshold e2 and FP32 thresholds; the
+// warp settles them one after another (warp_sq32, then warp_canonical64 when FP32 cannot
+// decide). Returns this lane's decision (false for lanes not in bm); *used_fp64 is set in
+// the lanes whose pair needed the FP64 sum.
+__device__ __forceinline__ bool warp_band_decide(unsigned bm, const float *q, const float *x, int d, double e2,
+                                                 float t_acc, float t_rej, bool *used_fp64)
 {
-    float s = 0.f;
-    for (int k = 0; k < d; ++k) {
-        const float t = __ldg(q + k) - __ldg(x + k);
-        s = fmaf(t, t, s);
-    }
+    const unsigned lane = threadIdx.x & 31;
+    bool mine = false;
     *used_fp64 = false;
-    if (s <= t_acc) return true;
-    if (s > t_rej) return false;
-    *used_fp64 = true;
-    double sum = 0.0;
-    for (int k = 0; k < d; ++k) {
-        const double t = __dsub_rn((double)__ldg(q + k), (double)__ldg(x + k));
-        sum = __dadd_rn(sum, __dmul_rn(t, t));
+    while (bm) {
+        const int k = __ffs(bm) - 1;
+        bm &= bm - 1u;
+        const float *qk = reinterpret_cast<const float *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(q), k));
+        const float *xk = reinterpret_cast<const float *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(x), k));
+        const float s = warp_sq32(qk, xk, d);
+        const float ta = __shfl_sync(0xffffffffu, t_acc, k);
+        const float tr = __shfl_sync(0xffffffffu, t_rej, k);
+        bool dec;
+        if (s <= ta) {
+            dec = true;
+        } else if (s > tr) {
+            dec = false;
+        } else {
+            const double e2k = __shfl_sync(0xffffffffu, e2, k);
+            dec = warp_canonical64(qk, xk, d) <= e2k;
+            if ((int)lane == k) *used_fp64 = true;
+        }
+        if ((int)lane == k) mine = dec;
     }
-    return sum <= e2;
+    return mine;
 }
 
 // Warp-aggregated atomicAdd of `v` to counter[key]: lanes with equal keys are

@@ -3,7 +3,8 @@
 // A band pair is one whose low-precision distance could not be placed on one
 // side of eps^2 by the error bound. K6 settles it exactly:
 //   1. FP32, one warp per pair: D32 = sum_k fl(q_k - x_k)^2 (lane partial FMA
-//      chains + a shuffle tree), bound |D32 - D| <= (d+8) 2^-24 D + tiny; if that
+//      chains over 16-byte slices + a shuffle tree), bound |D32 - D| <= (d+8) 2^-24 D
+//      + tiny; if that
 //      decides the pair against the canonical-FP64 slack, done;
 //   2. otherwise the canonical FP64 value itself: k ascending,
 //      t = (double)q_k - (double)x_k, s = s + t*t, every operation rounded to
@@ -33,9 +34,9 @@ __global__ void __launch_bounds__(256)
 }
 
 // Candidates of the tensor-core kernel -> id pairs. Each warp takes 32 entries:
-// proven matches are emitted as they are, each band entry is rechecked by its
-// own lane (sequential FP32 with its bound, canonical FP64 if needed), then the
-// warp emits the survivors.
+// proven matches are emitted as they are, the band entries are rechecked by the
+// whole warp one after another (vector loads of both rows, FP32 with its bound,
+// canonical FP64 if needed), then the warp emits the survivors.
 __global__ void __launch_bounds__(256)
     k_finalize(const uint2 *__restrict__ cand, const unsigned long long *__restrict__ cand_cnt,
                unsigned long long cand_cap, const float *__restrict__ R, const float *__restrict__ S, int d, double e2,
@@ -55,8 +56,12 @@ __global__ void __launch_bounds__(256)
         const bool band = valid && (e.y & kBandFlag);
         bool acc = valid && !band;
         bool f64 = false;
-        if (band) acc = lane_exact_decide(R + (size_t)r * d, S + (size_t)c * d, d, e2, t_acc, t_rej, &f64);
-        const unsigned bm = __ballot_sync(0xffffffffu, band), fm = __ballot_sync(0xffffffffu, f64);
+        const unsigned bm = __ballot_sync(0xffffffffu, band);
+        if (bm) {
+            const bool dec = warp_band_decide(bm, R + (size_t)r * d, S + (size_t)c * d, d, e2, t_acc, t_rej, &f64);
+            if (band) acc = dec;
+        }
+        const unsigned fm = __ballot_sync(0xffffffffu, f64);
         if (lane == 0) {
             if (bm) atomicAdd(n_band, (unsigned long long)__popc(bm));
             if (fm) atomicAdd(n_fp64, (unsigned long long)__popc(fm));

@@ -159,18 +159,68 @@ def self_clustered_262k(seed: int = SEED_BASE + 1, n: int = 262144, d: int = 128
     return JoinWorkload("self_clustered_262k", X, None, ids, None, eps)
 
 
+def clustered_queries(n: int, seed_q: int, store_seed: int, d: int, n_centroids: int, sigma: float,
+                      alpha: float = 0.5) -> np.ndarray:
+    """Fresh query patches for a clustered store: new jitters of the store's own centroids.
+
+    The store generator draws its centroids first from rng(store_seed), so they are
+    re-drawn here the same way; the jitter follows clustered_histograms.
+    """
+    cents = rng(store_seed).dirichlet(np.full(d, alpha, dtype=np.float64), size=n_centroids)
+    g = rng(seed_q)
+    out = np.empty((n, d), dtype=np.float32)
+    chunk = 65536
+    for r0 in range(0, n, chunk):
+        r1 = min(n, r0 + chunk)
+        c = cents[g.integers(0, n_centroids, size=r1 - r0)]
+        x = np.clip(c + g.normal(0.0, sigma, size=(r1 - r0, d)), 0.0, None)
+        s = x.sum(axis=1, keepdims=True)
+        bad = s[:, 0] <= 0.0
+        x[bad] = c[bad]
+        s[bad] = 1.0
+        out[r0:r1] = (x / s).astype(np.float32)
+    return out
+
+
 def self_clustered_queries(n: int, seed_q: int, seed: int = SEED_BASE + 1, d: int = 128,
                            n_centroids: int = 8192, sigma: float = 0.01) -> np.ndarray:
     """Fresh query patches for the 262,144-patch store: new jitters of the store's own centroids."""
-    cents = rng(seed).dirichlet(np.full(d, 0.5, dtype=np.float64), size=n_centroids)
-    g = rng(seed_q)
-    c = cents[g.integers(0, n_centroids, size=n)]
-    x = np.clip(c + g.normal(0.0, sigma, size=(n, d)), 0.0, None)
-    s = x.sum(axis=1, keepdims=True)
-    bad = s[:, 0] <= 0.0
-    x[bad] = c[bad]
-    s[bad] = 1.0
-    return (x / s).astype(np.float32)
+    return clustered_queries(n, seed_q, seed, d, n_centroids, sigma)
+
+
+@dataclass
+class StoreWorkload:
+    name: str
+    X: np.ndarray            # float32 [n, d]
+    ids: np.ndarray          # int64 [n]
+    seed: int
+    n_centroids: int
+    sigma: float
+
+    @property
+    def d(self) -> int:
+        return int(self.X.shape[1])
+
+    def queries(self, n: int, seed_q: int) -> np.ndarray:
+        return clustered_queries(n, seed_q, self.seed, self.d, self.n_centroids, self.sigma)
+
+    def eps_table(self):
+        """(selectivity, eps) pairs calibrated by the oracle on this store."""
+        return eps_table()[f"{self.name}:selectivity_eps"]
+
+
+def batch_store_2m(seed: int = SEED_BASE + 3, n: int = 2097152, d: int = 128, n_centroids: int = 65536,
+                   sigma: float = 0.01) -> StoreWorkload:
+    """Shared store of the batched-requests workload: 2,097,152 d=128 clustered histograms."""
+    X, _ = clustered_histograms(rng(seed), n, d, n_centroids, sigma)
+    return StoreWorkload("batch_store_2m", X, patch_ids(rng(seed + 1000), n), seed, n_centroids, sigma)
+
+
+def serve_store_4m(seed: int = SEED_BASE + 4, n: int = 4194304, d: int = 256, n_centroids: int = 131072,
+                   sigma: float = 0.01) -> StoreWorkload:
+    """Device-resident store of the serving workload: 4,194,304 d=256 clustered histograms."""
+    X, _ = clustered_histograms(rng(seed), n, d, n_centroids, sigma)
+    return StoreWorkload("serve_store_4m", X, patch_ids(rng(seed + 1000), n), seed, n_centroids, sigma)
 
 
 def rxs_unit_mixture_1m(seed: int = SEED_BASE + 2, n: int = 1048576, d: int = 512,
