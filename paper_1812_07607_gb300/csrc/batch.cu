@@ -233,12 +233,26 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
     int rc = DL_OK;
     std::vector<void *> frees;
     std::vector<dl_store *> stores;
+    // opts.timing: events at [0] start, [1]/[2] around the epsilon contraction, [3] after the
+    // exact decisions, [4] after the scatter, [5] end (after the top-k part)
+    cudaEvent_t bev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (o.timing)
+        for (auto &ev : bev) cudaEventCreate(&ev);
+    auto mark = [&](int i) {
+        if (bev[i]) cudaEventRecord(bev[i], st);
+    };
     auto cleanup = [&]() {
         cudaStreamSynchronize(st);   // nothing of this call may still run when its scratch is released
         for (auto *s : stores) dl_store_destroy(s);
         for (void *p : frees) dev_free(p, st);
         cudaStreamSynchronize(st);
+        for (auto &ev : bev)
+            if (ev) {
+                cudaEventDestroy(ev);
+                ev = nullptr;
+            }
     };
+    mark(0);
     // ---- query rows on the device (host inputs are uploaded once)
     const int64_t *dq_ids = q_ids;
     const float *dq = q_feats;
@@ -401,7 +415,9 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
                 L.p.cand_cap = (unsigned long long)cap;
                 L.p.err = (int *)(cnt + 3);
                 if (tune_trial) cudaEventRecord(tev[0], st);
+                mark(1);
                 rc = launch_tc_join(L, st);
+                mark(2);
                 if (tune_trial) cudaEventRecord(tev[1], st);
             }
             if (!rc) {
@@ -410,6 +426,7 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
                 count_launch(2);
                 e = cudaGetLastError();
                 if (e != cudaSuccess) rc = cuda_fail(e, "k_batch_decide launch");
+                mark(3);
             }
             unsigned long long hc[4] = {0, 0, 0, 0};
             std::vector<unsigned long long> hreq(n_req, 0);
@@ -454,6 +471,7 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
                 e = cudaGetLastError();
                 if (e != cudaSuccess) rc = cuda_fail(e, "k_batch_scatter launch");
             }
+            mark(4);
             if (!rc) {
                 std::lock_guard<std::mutex> lk(const_cast<dl_store *>(S)->mu);
                 const_cast<dl_store *>(S)->hint_band = (int64_t)hc[0];
@@ -496,12 +514,26 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
             return rc;
         }
     }
+    mark(5);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         dev_free(tk_block, st);
         dev_free(pair_block, st);
         cleanup();
         return cuda_fail(e, "dl_batch_join");
+    }
+    if (o.timing) {
+        auto span = [&](int a, int b) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, bev[a], bev[b]) != cudaSuccess) {
+                cudaGetLastError();   // an event that was never recorded (that part did not run)
+                ms = 0.f;
+            }
+            return ms;
+        };
+        stats.ms_main = span(1, 2);
+        stats.ms_recheck = span(2, 4);
+        stats.ms_total = span(0, 5);
     }
     cleanup();
     dl_result *res = new dl_result();

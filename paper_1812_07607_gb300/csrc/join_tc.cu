@@ -91,11 +91,15 @@ __device__ __forceinline__ void flush_stage(const TcParams &p, uint2 *stg, uint3
     scnt = 0;
 }
 
-// Pair-by-pair path for one 32-column chunk. The rows (lanes) whose chunk bound failed are
-// taken one at a time: the row's 32 values pass through the warp's shared-memory exchange
-// slot so that lane j classifies column c0 + j, with h = fl(A - beta_j) (FP8: v already
-// holds h). A pair with h >= tau_rej of its row -- a proven match (h >= tau_acc) or a band
-// pair -- is buffered as a candidate, its position given by a ballot prefix. Warp-collective.
+// Pair-by-pair path for one 32-column chunk, for pairs (r, c0 + j) with h = fl(A - beta_j)
+// (FP8: v already holds h). A pair with h >= tau_rej of its row -- a proven match
+// (h >= tau_acc) or a band pair -- becomes a candidate. Warp-collective; `hit` marks the
+// lanes (rows) whose chunk bound failed, the others have no candidate in this chunk.
+//  * Few such rows: they are taken one at a time, the row's 32 values passing through the
+//    warp's shared-memory exchange slot so that lane j classifies column c0 + j; the
+//    candidates' buffer positions come from a ballot prefix.
+//  * Many such rows: every lane classifies its own row's 32 columns into a bit mask, a
+//    warp prefix sum of the mask counts places each lane's candidates.
 template <bool FP8>
 __device__ __forceinline__ uint32_t slow_chunk(const TcParams &p, const uint32_t (&v)[64], int o, const float *bt,
                                                float tau_acc, float tau_rej, bool hit, int r, int c0, float *xch,
@@ -103,10 +107,69 @@ __device__ __forceinline__ uint32_t slow_chunk(const TcParams &p, const uint32_t
 {
     const unsigned lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
+    unsigned hm = __ballot_sync(0xffffffffu, hit);
+    if (__popc(hm) > 3) {
+        uint32_t cm = 0, am = 0;
+        if (hit) {
+            const float4 *bt4 = reinterpret_cast<const float4 *>(bt + o);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float4 b4 = FP8 ? make_float4(0.f, 0.f, 0.f, 0.f) : bt4[q];
+                const float bq[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int j = 4 * q + i;
+                    const float h = FP8 ? __uint_as_float(v[o + j]) : __uint_as_float(v[o + j]) - bq[i];
+                    cm |= (h >= tau_rej ? 1u : 0u) << j;
+                    am |= (h >= tau_acc ? 1u : 0u) << j;
+                }
+            }
+            const int rem = p.nS - c0;   // columns past the store
+            if (rem < 32) cm &= rem <= 0 ? 0u : ((1u << rem) - 1u);
+            if (p.upper) {   // upper mode: only pairs with c > r
+                const int k = r - c0;
+                if (k >= 31)
+                    cm = 0u;
+                else if (k >= 0)
+                    cm &= ~((2u << k) - 1u);
+            }
+        }
+        const uint32_t nl = __popc(cm);
+        uint32_t incl = nl;
+#pragma unroll
+        for (int sft = 1; sft < 32; sft <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, sft);
+            if ((int)lane >= sft) incl += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total == 0) return scnt;
+        uint2 *dst;
+        unsigned long long lim;
+        if (total <= (uint32_t)kStageCap) {
+            if (scnt + total > (uint32_t)kStageCap) flush_stage(p, stg, scnt);
+            dst = stg + scnt;
+            lim = ~0ULL;
+            scnt += total;
+        } else {   // more than a buffer: reserve the space in the global list directly
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(p.cand_cnt, (unsigned long long)total);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            dst = p.cand + base;
+            lim = base < p.cand_cap ? p.cand_cap - base : 0ULL;
+        }
+        unsigned long long k = incl - nl;
+        while (cm) {
+            const int j = __ffs(cm) - 1;
+            cm &= cm - 1u;
+            if (k < lim)
+                dst[k] = make_uint2((uint32_t)r, (uint32_t)(c0 + j) | (((am >> j) & 1u) ? 0u : kBandFlag));
+            ++k;
+        }
+        return scnt;
+    }
     const int c = c0 + (int)lane;                        // this lane's column
     const float bl = FP8 ? 0.f : bt[o + lane];
     const bool cvalid = c < p.nS;
-    unsigned hm = __ballot_sync(0xffffffffu, hit);
     while (hm) {
         const int k = __ffs(hm) - 1;
         hm &= hm - 1u;
