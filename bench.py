@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-baselines", action="store_true", help="skip the plain-FP32 and CPU legs")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-requests leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-precision", action="store_true", help="skip the d=512 BF16 / FP8 leg")
     ap.add_argument("--serving-seconds", type=float, default=4.0)
     ap.add_argument("--serving-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
     return ap.parse_args()
@@ -174,68 +175,78 @@ def cpu_oracle_rate(wl, budget_s: float):
     return pairs / dt / 1e9, {"rows": rows, "pairs": pairs, "seconds": round(dt, 3)}
 
 
-def batch_leg(dl, store, n_store, n_req=256, seed=SEED_BATCH):
-    """Many eps / top-k requests of uneven sizes in one dl_batch_join (the batching config's mix).
+def batch_leg(dl, seed=SEED_BATCH, n_req=4096, reps=2):
+    """The batching config: 4,096 eps / top-k requests in ONE dl_batch_join on the 2,097,152 x 128 store.
 
     Request sizes lognormal(5, 1.5) clipped to [1, 8192]; 70% eps-joins at a selectivity
-    uniform in [0.05%, 0.5%] of the store, 30% top-k with k = 10; queries are fresh jitters of
-    the store's centroids. Returns throughput in pairs evaluated per second.
+    uniform in [0.05%, 0.5%] of the store (eps from the oracle-calibrated table), 30% top-k
+    with k = 10; queries are fresh jitters of the store's centroids, resident on the device.
+    Throughput counts pairs evaluated (query rows x store rows) per second of the whole call.
     """
     import torch
     from paper_1812_07607_gb300 import workloads as W
+    st = W.batch_store_2m()
     g = W.rng(seed)
     reqs = W.request_mix(g, n_req, 5.0, 1.5, 8192, topk_frac=0.3, ks=(10,), sel_lo=5e-4, sel_hi=5e-3)
-    table = W.eps_table()["self_clustered_262k:selectivity_eps"]
+    table = st.eps_table()
     off = 0
     for r in reqs:
         r["q_begin"] = off
         off += r["nq"]
         if r["kind"] == "eps":
             r["eps"] = W.eps_for_selectivity(table, r["selectivity"])
-    Q = W.self_clustered_queries(off, seed + 1)
-    qid = np.arange(off, dtype=np.int64)
+    Q = st.queries(off, seed + 1)
+    store = dl.Store(torch.from_numpy(st.ids).cuda(), torch.from_numpy(st.X).cuda())
     Qd = torch.from_numpy(Q).cuda()
-    qd = torch.from_numpy(qid).cuda()
-    times, st, out_pairs = [], None, 0
-    for i in range(4):
+    qd = torch.arange(off, dtype=torch.int64).cuda()
+    times, stats, out_pairs = [], None, 0
+    warm = 4   # the tile autotuner's four trial calls (the first also sizes the candidate list)
+    for i in range(warm + reps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = dl.batch_join(store, qd, Qd, reqs)
+        res = dl.batch_join(store, qd, Qd, reqs, timing=True)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        st = res.stats()
+        stats = res.stats()
         out_pairs = res.count()
         res.free()
-        if i > 0:
+        if i >= warm:
             times.append(dt)
+    store.close()
     t = statistics.median(times)
-    pairs = off * n_store
+    pairs = off * st.X.shape[0]
     return {"value": pairs / t / 1e9, "unit": UNIT, "ms_per_batch": 1e3 * t, "requests": n_req,
-            "requests_per_s": n_req / t, "query_rows": off, "pairs_out": out_pairs,
-            "band_pairs": st["band_pairs"], "fp64_pairs": st["fp64_pairs"],
-            "config": "262,144 x 128 store; 256 requests, sizes lognormal(5,1.5) in [1,8192]; "
-                      "70% eps at selectivity U[0.05%,0.5%], 30% top-k k=10"}
+            "requests_per_s": n_req / t, "query_rows": off, "pairs_evaluated": pairs, "pairs_out": out_pairs,
+            "band_pairs": stats["band_pairs"], "fp64_pairs": stats["fp64_pairs"],
+            "ms_eps_contraction": stats["ms_main"], "ms_eps_decide_scatter": stats["ms_recheck"],
+            "ms_device_total": stats["ms_total"],
+            "config": "batch_store_2m: 2,097,152 x 128 store; 4,096 requests in one call, sizes lognormal(5,1.5) "
+                      "in [1,8192]; 70% eps at selectivity U[0.05%,0.5%], 30% top-k k=10; device inputs"}
 
 
-def serving_leg(dl, store, n_store, seconds=4.0, rate=2000.0, seed=SEED_SERVE):
-    """Poisson arrivals into the request loop; p50/p99 submit-to-ready latency and throughput.
+def serving_leg(dl, seconds=4.0, rate=2000.0, seed=SEED_SERVE):
+    """The serving config: Poisson arrivals into the request loop over the 4,194,304 x 256 store.
 
-    Mix of the serving config: 70% eps-joins (selectivity U[0.05%, 0.5%]) and 30% top-k with
-    k uniform over {1, 10, 100}; query sizes lognormal(4, 1.5) clipped to [1, 4096].
+    70% eps-joins (selectivity U[0.05%, 0.5%]) and 30% top-k with k uniform over
+    {1, 10, 100}; query sizes lognormal(4, 1.5) clipped to [1, 4096]; submit-to-ready
+    latency p50/p99 and completed requests per second at the offered rate.
     """
     import threading
+
+    import torch
     from paper_1812_07607_gb300 import workloads as W
+    sw = W.serve_store_4m()
     g = W.rng(seed)
     n = int(seconds * rate)
     reqs = W.request_mix(g, n, 4.0, 1.5, 4096, topk_frac=0.3, ks=(1, 10, 100), sel_lo=5e-4, sel_hi=5e-3)
-    table = W.eps_table()["self_clustered_262k:selectivity_eps"]
+    table = sw.eps_table()
     arrivals = np.cumsum(g.exponential(1.0 / rate, size=n))
     total = sum(r["nq"] for r in reqs)
-    Q = W.self_clustered_queries(total, seed + 1)
-    sv = dl.Server(store, mem_budget_bytes=32 << 30, slots=3, max_batch_rows=65536)
+    Q = sw.queries(total, seed + 1)
+    store = dl.Store(torch.from_numpy(sw.ids).cuda(), torch.from_numpy(sw.X).cuda())
+    sv = dl.Server(store, mem_budget_bytes=64 << 30, slots=3, max_batch_rows=65536)
     tickets = []
     lock = threading.Lock()
-    done_pairs = [0]
 
     def submitter():
         off = 0
@@ -272,14 +283,49 @@ def serving_leg(dl, store, n_store, seconds=4.0, rate=2000.0, seed=SEED_SERVE):
     th.join()
     st = sv.stats()
     sv.close()
-    pairs = total * n_store
+    store.close()
+    pairs = total * sw.X.shape[0]
     return {"offered_req_per_s": rate, "requests": n, "seconds": wall, "completed": st["completed"],
             "req_per_s": st["completed"] / wall, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "max_ms": st["max_ms"], "pairs_per_s_G": pairs / wall / 1e9, "batches": st["batches"],
             "mean_batch_requests": st["mean_batch_requests"],
-            "config": "262,144 x 128 store resident; Poisson arrivals; 70% eps at selectivity "
+            "config": "serve_store_4m: 4,194,304 x 256 store resident; Poisson arrivals; 70% eps at selectivity "
                       "U[0.05%,0.5%] / 30% top-k k in {1,10,100}; sizes lognormal(4,1.5) in [1,4096]; "
-                      "3 stream slots"}
+                      "3 stream slots; results stay on the device until polled"}
+
+
+def precision_leg(dl, reps=2):
+    """The precision config: the 1,048,576 x 1,048,576 d=512 unit-norm R x S join, BF16 and FP8 e4m3."""
+    import torch
+    from paper_1812_07607_gb300 import workloads as W
+    wl = W.rxs_unit_mixture_1m()
+    n = wl.R.shape[0]
+    S = dl.Store(torch.arange(n).cuda(), torch.from_numpy(wl.S).cuda())
+    R = dl.Store(torch.arange(n).cuda(), torch.from_numpy(wl.R).cuda())
+    out = {"config": "rxs_unit_mixture_1m: 1,048,576 x 1,048,576, d=512 unit-norm, 4,096-component mixture; "
+                     "exact pair set (parity: 16,384 sampled rows against the oracle digest)",
+           "pairs_evaluated": n * n}
+    for prec in ("bf16", "fp8"):
+        ts, st = [], None
+        warm = 4 if prec == "bf16" else 1   # BF16: the tile autotuner's four trial calls
+        for i in range(warm + reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = dl.sim_join(R, S, wl.eps, precision=prec, timing=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            st = res.stats()
+            res.free()
+            if i >= warm:
+                ts.append(dt)
+        t = statistics.median(ts)
+        out[prec] = {"value": n * n / t / 1e9, "unit": UNIT, "ms": 1e3 * t, "ms_main": st["ms_main"],
+                     "ms_recheck": st["ms_recheck"], "band_pairs": st["band_pairs"], "fp64_pairs": st["fp64_pairs"],
+                     "pairs_out": st["pairs_out"], "tile_n": st["tile_n"],
+                     "main_tflops": 2.0 * 512 * n * n / (st["ms_main"] / 1e3) / 1e12}
+    R.close()
+    S.close()
+    return out
 
 
 def run_reference(args):
@@ -353,6 +399,8 @@ def run_ours(args):
         res.free()
         return st
 
+    for _ in range(4):   # setup: the tile autotuner's trial calls for this shape class
+        one_step()
     for _ in range(args.warmup):
         one_step()
     barrier()
@@ -431,10 +479,13 @@ def run_ours(args):
 
     batch = None
     if rank == 0 and not args.no_batch:
-        batch = batch_leg(dl, store, n)
+        batch = batch_leg(dl)
     serving = None
     if rank == 0 and not args.no_serving:
-        serving = serving_leg(dl, store, n, seconds=args.serving_seconds, rate=args.serving_rate)
+        serving = serving_leg(dl, seconds=args.serving_seconds, rate=args.serving_rate)
+    precision = None
+    if rank == 0 and not args.no_precision:
+        precision = precision_leg(dl)
 
     cpu = None
     if rank == 0 and not args.no_baselines:
@@ -462,6 +513,7 @@ def run_ours(args):
             "plain_fp32_gpu": plain,
             "batch": batch,
             "serving": serving,
+            "precision": precision,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

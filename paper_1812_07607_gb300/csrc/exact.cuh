@@ -86,37 +86,81 @@ __device__ __forceinline__ bool warp_exact_decide(const float *__restrict__ q, c
     return sum <= e2;
 }
 
-// Exact decisions for the band entries among a warp's 32 candidate entries: each lane in
-// bm holds a band pair (q, x) with its own squared threshold e2 and FP32 thresholds; the
-// warp settles them one after another (warp_sq32, then warp_canonical64 when FP32 cannot
-// decide). Returns this lane's decision (false for lanes not in bm); *used_fp64 is set in
+// Exact decisions for the band entries among a warp's 32 candidate entries. Each lane in
+// bm holds a band pair (q, x) with its own squared threshold e2 and FP32 thresholds. Four
+// pairs are settled at a time, one per 8-lane group: the group sums the pair's FP32
+// squared distance over 16-byte slices (a shuffle tree within the group; the (d+8) 2^-24
+// bound holds for any order) and compares it with the pair's thresholds. The pairs that
+// FP32 cannot decide are then settled one by one by the whole warp with the canonical
+// FP64 sum. Returns this lane's decision (false for lanes not in bm); *used_fp64 is set in
 // the lanes whose pair needed the FP64 sum.
 __device__ __forceinline__ bool warp_band_decide(unsigned bm, const float *q, const float *x, int d, double e2,
                                                  float t_acc, float t_rej, bool *used_fp64)
 {
     const unsigned lane = threadIdx.x & 31;
-    bool mine = false;
-    *used_fp64 = false;
-    while (bm) {
-        const int k = __ffs(bm) - 1;
-        bm &= bm - 1u;
+    const unsigned below = (1u << lane) - 1u;
+    const int grp = (int)(lane >> 3), gl = (int)(lane & 7);
+    bool mine = false, und = false;
+    unsigned rem = bm;
+    while (rem) {
+        const unsigned pos = __fns(rem, 0, grp + 1);   // this group's entry: the (grp+1)-th pending lane
+        const bool have = pos < 32u;
+        const int k = have ? (int)pos : 0;
         const float *qk = reinterpret_cast<const float *>(
             __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(q), k));
         const float *xk = reinterpret_cast<const float *>(
             __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(x), k));
-        const float s = warp_sq32(qk, xk, d);
+        float s = 0.f;
+        if (have) {
+            if ((d & 3) == 0) {
+                const float4 *q4 = reinterpret_cast<const float4 *>(qk);
+                const float4 *x4 = reinterpret_cast<const float4 *>(xk);
+                for (int i = gl; i < (d >> 2); i += 8) {
+                    const float4 a = __ldg(q4 + i), b = __ldg(x4 + i);
+                    float t = a.x - b.x;
+                    s = fmaf(t, t, s);
+                    t = a.y - b.y;
+                    s = fmaf(t, t, s);
+                    t = a.z - b.z;
+                    s = fmaf(t, t, s);
+                    t = a.w - b.w;
+                    s = fmaf(t, t, s);
+                }
+            } else {
+                for (int i = gl; i < d; i += 8) {
+                    const float t = __ldg(qk + i) - __ldg(xk + i);
+                    s = fmaf(t, t, s);
+                }
+            }
+        }
+        s += __shfl_xor_sync(0xffffffffu, s, 4);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
         const float ta = __shfl_sync(0xffffffffu, t_acc, k);
         const float tr = __shfl_sync(0xffffffffu, t_rej, k);
-        bool dec;
-        if (s <= ta) {
-            dec = true;
-        } else if (s > tr) {
-            dec = false;
-        } else {
-            const double e2k = __shfl_sync(0xffffffffu, e2, k);
-            dec = warp_canonical64(qk, xk, d) <= e2k;
-            if ((int)lane == k) *used_fp64 = true;
+        const unsigned accm = __ballot_sync(0xffffffffu, have && gl == 0 && s <= ta);
+        const unsigned undm = __ballot_sync(0xffffffffu, have && gl == 0 && !(s <= ta) && !(s > tr));
+        if ((rem >> lane) & 1u) {   // an entry of this round: rank r among the pending lanes
+            const int r = __popc(rem & below);
+            if (r < 4) {
+                mine = ((accm >> (8 * r)) & 1u) != 0u;
+                und = ((undm >> (8 * r)) & 1u) != 0u;
+            }
         }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) rem &= rem - 1u;   // the four settled entries leave the set
+    }
+    *used_fp64 = und;
+    unsigned um = __ballot_sync(0xffffffffu, und);
+    while (um) {
+        const int k = __ffs(um) - 1;
+        um &= um - 1u;
+        const float *qk = reinterpret_cast<const float *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(q), k));
+        const float *xk = reinterpret_cast<const float *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(x), k));
+        const double e2k = __shfl_sync(0xffffffffu, e2, k);
+        const bool dec = warp_canonical64(qk, xk, d) <= e2k;
         if ((int)lane == k) mine = dec;
     }
     return mine;

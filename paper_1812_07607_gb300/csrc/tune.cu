@@ -1,11 +1,12 @@
 // tune.cu -- on-line autotuner for the tensor-core tile width.
 //
 // A tuning key is a shape class: (device SMs, padded d, join kind, log2 |R|,
-// log2 |S|). The first calls of a class each run one candidate tile width
-// (256, then 128) with CUDA-event timing of the tensor-core kernel; from then
-// on the faster one (by kernel milliseconds per 10^9 pairs) is used. Decisions
-// are kept for the process and, when the environment variable DL_TUNE_CACHE
-// names a file, loaded from and appended to it as lines "key BN".
+// log2 |S|). The first calls of a class run the candidate tile widths in turn
+// (256, 128, 256, 128) with CUDA-event timing of the tensor-core kernel; each
+// candidate's best (smallest kernel milliseconds per 10^9 pairs) of its two trials
+// counts, so a cold first call does not decide. From then on the faster one is
+// used. Decisions are kept for the process and, when the environment variable
+// DL_TUNE_CACHE names a file, loaded from and appended to it as lines "key BN".
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -21,10 +22,12 @@ namespace {
 
 constexpr int kCandidates[] = {256, 128};
 constexpr int kNumCandidates = 2;
+constexpr int kRounds = 2;   // trials per candidate
+constexpr int kTrials = kNumCandidates * kRounds;
 
 struct Entry {
-    double ms_per_gpair[kNumCandidates] = {0.0, 0.0};
-    int tried = 0;      // candidates measured so far
+    double ms_per_gpair[kNumCandidates] = {0.0, 0.0};   // best trial so far
+    int tried = 0;      // trials measured so far
     int chosen = 0;     // 0 until decided
 };
 
@@ -62,7 +65,7 @@ void load_locked()
     while (std::fscanf(f, "%95s %d", key, &bn) == 2) {
         Entry &e = g_tab[key];
         e.chosen = bn;
-        e.tried = kNumCandidates;
+        e.tried = kTrials;
     }
     std::fclose(f);
 }
@@ -90,7 +93,7 @@ int tune_pick(int dp, int kind, int64_t nR, int64_t nS, bool *trial)
         return e.chosen;
     }
     *trial = true;
-    return kCandidates[e.tried < kNumCandidates ? e.tried : 0];
+    return kCandidates[e.tried % kNumCandidates];
 }
 
 // Record a measured candidate; decides the class once every candidate has been timed.
@@ -100,9 +103,12 @@ void tune_record(int dp, int kind, int64_t nR, int64_t nS, int bn, double kernel
     std::lock_guard<std::mutex> lk(g_mu);
     const std::string key = make_key(dp, kind, nR, nS);
     Entry &e = g_tab[key];
-    if (e.chosen || e.tried >= kNumCandidates || kCandidates[e.tried] != bn) return;
-    e.ms_per_gpair[e.tried++] = kernel_ms / (pairs / 1e9);
-    if (e.tried == kNumCandidates) {
+    if (e.chosen || e.tried >= kTrials || kCandidates[e.tried % kNumCandidates] != bn) return;
+    const int c = e.tried % kNumCandidates;
+    const double v = kernel_ms / (pairs / 1e9);
+    if (e.tried < kNumCandidates || v < e.ms_per_gpair[c]) e.ms_per_gpair[c] = v;
+    ++e.tried;
+    if (e.tried == kTrials) {
         int best = 0;
         for (int i = 1; i < kNumCandidates; ++i)
             if (e.ms_per_gpair[i] < e.ms_per_gpair[best]) best = i;

@@ -249,7 +249,7 @@ def test_self_clustered_262k_full_size_sampled(dl, orc):
 
 
 def test_autotuner_tries_both_tiles_and_persists(tmp_path):
-    """Tile width autotuner: first calls of a shape class try 256 then 128, then the faster sticks."""
+    """Tile width autotuner: first calls of a shape class try 256, 128, 256, 128; then the faster sticks."""
     import os
     import subprocess
     import sys
@@ -262,7 +262,7 @@ wl = W.rxs_histograms_2k()
 R = dl.Store(torch.from_numpy(wl.r_ids).cuda(), torch.from_numpy(wl.R).cuda())
 S = dl.Store(torch.from_numpy(wl.s_ids).cuda(), torch.from_numpy(wl.S).cuda())
 tiles = []
-for _ in range(4):
+for _ in range(6):
     r = dl.sim_join(R, S, wl.eps)
     tiles.append(r.stats()["tile_n"])
     r.free()
@@ -273,9 +273,9 @@ print(tiles)
     out = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stderr
     tiles = eval(out.stdout.strip().splitlines()[-1])
-    assert tiles[:2] == [256, 128] and tiles[2] == tiles[3] and tiles[2] in (128, 256)
+    assert tiles[:4] == [256, 128, 256, 128] and tiles[4] == tiles[5] and tiles[4] in (128, 256)
     lines = cache.read_text().split()
-    assert len(lines) == 2 and int(lines[1]) == tiles[2]
+    assert len(lines) == 2 and int(lines[1]) == tiles[4]
     # a new process starts from the cache
     out = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=300)
-    assert eval(out.stdout.strip().splitlines()[-1]) == [tiles[2]] * 4
+    assert eval(out.stdout.strip().splitlines()[-1]) == [tiles[4]] * 6
