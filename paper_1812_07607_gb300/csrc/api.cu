@@ -378,7 +378,9 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
     if (!rc) rc = check_device(Sx);
     if (rc) return rc;
     int prec = o.precision;
-    if (prec == DL_PREC_AUTO) prec = (R->dp <= 512) ? DL_PREC_BF16 : DL_PREC_FP32;
+    // AUTO: BF16 while its R tile fits in shared memory (d <= 512), else the FP8 tensor-core
+    // path (d <= 1024, always within the domain); both give the exact set.
+    if (prec == DL_PREC_AUTO) prec = (R->dp <= 512) ? DL_PREC_BF16 : DL_PREC_FP8E4M3;
     if (prec != DL_PREC_BF16 && prec != DL_PREC_FP8E4M3 && prec != DL_PREC_FP32 && prec != DL_PREC_FP32_PLAIN) {
         set_error("dl_sim_join: bad precision %d", prec);
         return DL_EINVAL;

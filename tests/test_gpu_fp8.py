@@ -111,3 +111,16 @@ def test_fp8_signed_multichunk_equals_exact_fp32(dl):
             r.free()
             sets[prec] = set(zip(a.tolist(), b.tolist()))
         assert len(sets["fp32"]) > 100 and sets["fp8"] == sets["fp32"], (d, len(sets["fp8"] ^ sets["fp32"]))
+
+
+def test_auto_precision_uses_fp8_above_512(dl, orc):
+    """d in (512, 1024]: the BF16 R tile does not fit in shared memory, so AUTO takes FP8 (still exact)."""
+    g = W.rng(7400)
+    R = W.dirichlet_histograms(g, 300, 768)
+    S = W.dirichlet_histograms(g, 700, 768)
+    D = orc.dist_block(R, S)
+    eps = math.sqrt(float(np.quantile(D, 0.01)))
+    got, st, rid, sid = gpu_pairs(dl, R, S, eps, "auto")
+    assert st["precision"] == dl.DL_PREC_FP8E4M3
+    want = oracle_pairs(orc, R, S, eps, oracle.MODE_RXS, rid, sid)
+    assert got == want
