@@ -69,22 +69,31 @@ static void hpool_put(void *p, size_t bytes)
 
 // ------------------------------------------------------------------ unit lists
 // Work units of the tensor-core kernel: (R tile m, S tiles [nb, ne)). For a
-// self-join only tiles holding some column c > row r are listed.
+// self-join only tiles holding some column c > row r are listed. Units are ordered
+// S-range-major (all R tiles of one range of L S tiles, then the next range), and the
+// kernel hands them out round-robin, so the CTAs running at the same time share the
+// same S tiles: each S range is read from HBM about once per wave and served from L2
+// to every CTA, while each CTA reads only its own R tile. (R-major order would stream
+// a different S range into every CTA, which makes a store larger than L2 HBM-bound.)
 static std::mutex g_units_mu;
 static std::map<std::tuple<int, int64_t, int64_t, int, int, int>, std::pair<int4 *, int>> g_units;
+
+static int first_upper_tile(int m, int BN, bool upper)
+{
+    if (!upper) return 0;
+    const long long num = (long long)m * 128 + 2 - BN;
+    return num <= 0 ? 0 : (int)((num + BN - 1) / BN);
+}
 
 static void build_units(int64_t nR, int64_t nS, bool upper, int BN, int L, std::vector<int4> *v)
 {
     const int mt = (int)((nR + 127) / 128), nt = (int)((nS + BN - 1) / BN);
     v->clear();
-    for (int m = 0; m < mt; ++m) {
-        int nf = 0;
-        if (upper) {
-            const long long num = (long long)m * 128 + 2 - BN;
-            nf = num <= 0 ? 0 : (int)((num + BN - 1) / BN);
+    for (int nb0 = 0; nb0 < nt; nb0 += L)
+        for (int m = 0; m < mt; ++m) {
+            const int lo = std::max(nb0, first_upper_tile(m, BN, upper)), hi = std::min(nb0 + L, nt);
+            if (lo < hi) v->push_back(make_int4(m, lo, hi, 0));
         }
-        for (int nb = nf; nb < nt; nb += L) v->push_back(make_int4(m, nb, std::min(nb + L, nt), 0));
-    }
 }
 
 static int get_units(int64_t nR, int64_t nS, bool upper, int BN, int sms, const int4 **d_units, int *n_units)
@@ -92,17 +101,13 @@ static int get_units(int64_t nR, int64_t nS, bool upper, int BN, int sms, const 
     int dev = 0;
     cudaGetDevice(&dev);
     const int mt = (int)((nR + 127) / 128), nt = (int)((nS + BN - 1) / BN);
-    int L = 16;
+    // the longest ranges (fewest R re-reads) that still give every SM four units
+    int L = 64;
     while (L > 1) {
         long long cnt = 0;
-        for (int m = 0; m < mt; ++m) {
-            int nf = 0;
-            if (upper) {
-                const long long num = (long long)m * 128 + 2 - BN;
-                nf = num <= 0 ? 0 : (int)((num + BN - 1) / BN);
-            }
-            cnt += (nt - nf + L - 1) / L;
-        }
+        for (int nb0 = 0; nb0 < nt; nb0 += L)
+            for (int m = 0; m < mt; ++m)
+                if (std::max(nb0, first_upper_tile(m, BN, upper)) < std::min(nb0 + L, nt)) ++cnt;
         if (cnt >= 4LL * sms) break;
         L >>= 1;
     }

@@ -122,15 +122,16 @@ __global__ void __launch_bounds__(256)
 
 static size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Units of the epsilon pass: every row tile against every S tile (no self pairs).
+// Units of the epsilon pass: every row tile against every S tile (no self pairs), in
+// S-range-major order so that the CTAs running together share S tiles through L2.
 static int batch_units(int64_t nR, int64_t nS, int BN, int sms, std::vector<int4> *v)
 {
     const int mt = (int)((nR + 127) / 128), nt = (int)((nS + BN - 1) / BN);
-    int L = 16;
+    int L = 64;
     while (L > 1 && (int64_t)mt * ((nt + L - 1) / L) < 4LL * sms) L >>= 1;
     v->clear();
-    for (int m = 0; m < mt; ++m)
-        for (int nb = 0; nb < nt; nb += L) v->push_back(make_int4(m, nb, std::min(nb + L, nt), 0));
+    for (int nb = 0; nb < nt; nb += L)
+        for (int m = 0; m < mt; ++m) v->push_back(make_int4(m, nb, std::min(nb + L, nt), 0));
     return DL_OK;
 }
 
@@ -359,7 +360,9 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
         int64_t cap;
         {
             std::lock_guard<std::mutex> lk(const_cast<dl_store *>(S)->mu);
-            cap = std::max<int64_t>(1 << 20, S->hint_band + S->hint_band / 4);
+            // candidates per evaluated pair from the last batch against this store, with headroom
+            const double want = S->hint_batch_rate * (double)ne * (double)S->n;
+            cap = std::max<int64_t>(1 << 20, (int64_t)(want * 1.3) + (1 << 16));
         }
         for (int attempt = 0;; ++attempt) {
             void *ws = nullptr;
@@ -474,7 +477,7 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
             mark(4);
             if (!rc) {
                 std::lock_guard<std::mutex> lk(const_cast<dl_store *>(S)->mu);
-                const_cast<dl_store *>(S)->hint_band = (int64_t)hc[0];
+                const_cast<dl_store *>(S)->hint_batch_rate = (double)hc[0] / ((double)ne * (double)S->n);
             }
             if (!rc && tune_trial && attempt == 0) {
                 float ms = 0.f;

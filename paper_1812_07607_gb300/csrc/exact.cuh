@@ -113,18 +113,29 @@ __device__ __forceinline__ bool warp_band_decide(unsigned bm, const float *q, co
         float s = 0.f;
         if (have) {
             if ((d & 3) == 0) {
+                // four 16-byte slices of each row in flight per lane (zero past the row: adds 0)
                 const float4 *q4 = reinterpret_cast<const float4 *>(qk);
                 const float4 *x4 = reinterpret_cast<const float4 *>(xk);
-                for (int i = gl; i < (d >> 2); i += 8) {
-                    const float4 a = __ldg(q4 + i), b = __ldg(x4 + i);
-                    float t = a.x - b.x;
-                    s = fmaf(t, t, s);
-                    t = a.y - b.y;
-                    s = fmaf(t, t, s);
-                    t = a.z - b.z;
-                    s = fmaf(t, t, s);
-                    t = a.w - b.w;
-                    s = fmaf(t, t, s);
+                const int n4 = d >> 2;
+                for (int i0 = gl; i0 < n4; i0 += 32) {
+                    float4 a[4], b[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int i = i0 + 8 * u;
+                        a[u] = i < n4 ? __ldg(q4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        b[u] = i < n4 ? __ldg(x4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        float t = a[u].x - b[u].x;
+                        s = fmaf(t, t, s);
+                        t = a[u].y - b[u].y;
+                        s = fmaf(t, t, s);
+                        t = a[u].z - b[u].z;
+                        s = fmaf(t, t, s);
+                        t = a[u].w - b[u].w;
+                        s = fmaf(t, t, s);
+                    }
                 }
             } else {
                 for (int i = gl; i < d; i += 8) {

@@ -90,6 +90,7 @@ struct Store {
     float nq_max = 0.f;      // largest ||x||^2 of the store (FP32 sum; used only inside slack terms)
     int64_t hint_pairs = 0;  // last output size seen with this store as R (capacity hint)
     int64_t hint_band = 0;
+    double hint_batch_rate = 0.0;   // batch calls: candidates per evaluated pair last seen against this store
 };
 
 // Create a store; gather == NULL orders rows by norm, else store row i is caller row gather[i].

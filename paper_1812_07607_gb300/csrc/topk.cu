@@ -374,8 +374,10 @@ static int topk_units(int64_t nQ, int64_t nS, int BN, int splits, const int4 **d
     if (it == g_tku.end()) {
         const int mt = (int)((nQ + 127) / 128), nt = (int)((nS + BN - 1) / BN);
         std::vector<int4> v;
-        for (int m = 0; m < mt; ++m)
-            for (int s = 0; s < splits; ++s) {
+        // split-major: the CTAs running together walk the same S range (shared through L2),
+        // and later splits of a row start from the threshold its earlier splits published
+        for (int s = 0; s < splits; ++s)
+            for (int m = 0; m < mt; ++m) {
                 const int nb = (int)((int64_t)nt * s / splits), ne = (int)((int64_t)nt * (s + 1) / splits);
                 if (ne > nb) v.push_back(make_int4(m, nb, ne, s));
             }
