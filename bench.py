@@ -224,18 +224,32 @@ def batch_leg(dl, seed=SEED_BATCH, n_req=4096, reps=2):
                       "in [1,8192]; 70% eps at selectivity U[0.05%,0.5%], 30% top-k k=10; device inputs"}
 
 
-def serving_leg(dl, seconds=4.0, rate=2000.0, seed=SEED_SERVE):
+def serving_leg(dl, seconds=4.0, rates=(2000.0, 1000.0, 500.0), seed=SEED_SERVE):
     """The serving config: Poisson arrivals into the request loop over the 4,194,304 x 256 store.
 
     70% eps-joins (selectivity U[0.05%, 0.5%]) and 30% top-k with k uniform over
     {1, 10, 100}; query sizes lognormal(4, 1.5) clipped to [1, 4096]; submit-to-ready
-    latency p50/p99 and completed requests per second at the offered rate.
+    latency p50/p99 and completed requests per second at each offered rate (the first
+    rate is the serving config's; the others are the sweep below it).
     """
-    import threading
-
     import torch
     from paper_1812_07607_gb300 import workloads as W
     sw = W.serve_store_4m()
+    store = dl.Store(torch.from_numpy(sw.ids).cuda(), torch.from_numpy(sw.X).cuda())
+    out = None
+    sweep = []
+    for i, rate in enumerate(rates):
+        r = _serve_once(dl, W, sw, store, seconds, rate, seed + 10 * i)
+        sweep.append({k: r[k] for k in ("offered_req_per_s", "req_per_s", "p50_ms", "p99_ms", "max_ms", "batches")})
+        if out is None:
+            out = r
+    store.close()
+    out["sweep"] = sweep
+    return out
+
+
+def _serve_once(dl, W, sw, store, seconds, rate, seed):
+    import threading
     g = W.rng(seed)
     n = int(seconds * rate)
     reqs = W.request_mix(g, n, 4.0, 1.5, 4096, topk_frac=0.3, ks=(1, 10, 100), sel_lo=5e-4, sel_hi=5e-3)
@@ -243,7 +257,6 @@ def serving_leg(dl, seconds=4.0, rate=2000.0, seed=SEED_SERVE):
     arrivals = np.cumsum(g.exponential(1.0 / rate, size=n))
     total = sum(r["nq"] for r in reqs)
     Q = sw.queries(total, seed + 1)
-    store = dl.Store(torch.from_numpy(sw.ids).cuda(), torch.from_numpy(sw.X).cuda())
     sv = dl.Server(store, mem_budget_bytes=64 << 30, slots=3, max_batch_rows=65536)
     tickets = []
     lock = threading.Lock()
@@ -283,7 +296,6 @@ def serving_leg(dl, seconds=4.0, rate=2000.0, seed=SEED_SERVE):
     th.join()
     st = sv.stats()
     sv.close()
-    store.close()
     pairs = total * sw.X.shape[0]
     return {"offered_req_per_s": rate, "requests": n, "seconds": wall, "completed": st["completed"],
             "req_per_s": st["completed"] / wall, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
@@ -482,7 +494,7 @@ def run_ours(args):
         batch = batch_leg(dl)
     serving = None
     if rank == 0 and not args.no_serving:
-        serving = serving_leg(dl, seconds=args.serving_seconds, rate=args.serving_rate)
+        serving = serving_leg(dl, seconds=args.serving_seconds, rates=(args.serving_rate, 1000.0, 500.0))
     precision = None
     if rank == 0 and not args.no_precision:
         precision = precision_leg(dl)
