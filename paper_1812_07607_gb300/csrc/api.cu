@@ -245,7 +245,7 @@ static int run_pass(const PassCfg &c, PassOut *po)
                 L.p.beta = S->beta;
                 L.p.cstat = fp8 ? S->cstat8 : S->cstat;
                 L.p.sc_r = fp8 ? R->sc8 : nullptr;
-                L.p.sc_s = fp8 ? S->sc8 : nullptr;
+                L.p.sc_s = fp8 ? S->scc8 : nullptr;
                 L.p.cand = band;                 // candidates share the band buffer and counter
                 L.p.cand_cnt = cnt + 1;
                 L.p.cand_cap = (unsigned long long)c.band_cap;
@@ -570,7 +570,7 @@ int dl_debug_scores(const dl_store *R, const dl_store *S, int32_t precision, flo
         L.p.beta = S->beta;
         L.p.cstat = fp8 ? S->cstat8 : S->cstat;
         L.p.sc_r = fp8 ? R->sc8 : nullptr;
-        L.p.sc_s = fp8 ? S->sc8 : nullptr;
+        L.p.sc_s = fp8 ? S->scc8 : nullptr;
         L.p.cand = cand;
         L.p.cand_cnt = cnt + 0;
         L.p.cand_cap = 65536;

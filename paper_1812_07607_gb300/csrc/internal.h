@@ -82,9 +82,10 @@ struct Store {
     int32_t dp8 = 0;         // d rounded up to a multiple of 128 (one 128-byte swizzle row per K chunk)
     void *fp8_block = nullptr;
     uint8_t *x8 = nullptr;   // [n][dp8] e4m3 codes of x / s
-    float *sc8 = nullptr;    // [n_pad] s (1 in padding)
+    float *sc8 = nullptr;    // [n_pad] s of each row: its 32-row chunk's scale (1 in padding)
+    float *scc8 = nullptr;   // [n_pad/32] the chunk scales (power of two)
     float2 *rowb8 = nullptr; // [n] {||x - s x8|| up, ||s x8|| up}
-    float4 *cstat8 = nullptr;// [n_pad/32] {P1, P2 (FP8), P3, 0}
+    float4 *cstat8 = nullptr;// [n_pad/32] {P1, P2 (FP8), P3, beta_min}
     TmapCache tmaps8[3];     // FP8 boxes
     std::mutex mu;           // guards tmaps and hints
     float nq_max = 0.f;      // largest ||x||^2 of the store (FP32 sum; used only inside slack terms)

@@ -91,8 +91,9 @@ __device__ __forceinline__ void flush_stage(const TcParams &p, uint2 *stg, uint3
     scnt = 0;
 }
 
-// Pair-by-pair path for one 32-column chunk, for pairs (r, c0 + j) with h = fl(A - beta_j)
-// (FP8: v already holds h). A pair with h >= tau_rej of its row -- a proven match
+// Pair-by-pair path for one 32-column chunk, for pairs (r, c0 + j) with h = fl(A s - beta_j)
+// (s = 1 for BF16; for FP8 the exact power of two s_q s_chunk, so one rounding). A pair with
+// h >= tau_rej of its row -- a proven match
 // (h >= tau_acc) or a band pair -- becomes a candidate. Warp-collective; `hit` marks the
 // lanes (rows) whose chunk bound failed, the others have no candidate in this chunk.
 //  * Few such rows: they are taken one at a time, the row's 32 values passing through the
@@ -102,8 +103,8 @@ __device__ __forceinline__ void flush_stage(const TcParams &p, uint2 *stg, uint3
 //    warp prefix sum of the mask counts places each lane's candidates.
 template <bool FP8>
 __device__ __forceinline__ uint32_t slow_chunk(const TcParams &p, const uint32_t (&v)[64], int o, const float *bt,
-                                               float tau_acc, float tau_rej, bool hit, int r, int c0, float *xch,
-                                               uint2 *stg, uint32_t scnt)
+                                               float sc, float tau_acc, float tau_rej, bool hit, int r, int c0,
+                                               float *xch, uint2 *stg, uint32_t scnt)
 {
     const unsigned lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
@@ -114,12 +115,12 @@ __device__ __forceinline__ uint32_t slow_chunk(const TcParams &p, const uint32_t
             const float4 *bt4 = reinterpret_cast<const float4 *>(bt + o);
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const float4 b4 = FP8 ? make_float4(0.f, 0.f, 0.f, 0.f) : bt4[q];
+                const float4 b4 = bt4[q];
                 const float bq[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int j = 4 * q + i;
-                    const float h = FP8 ? __uint_as_float(v[o + j]) : __uint_as_float(v[o + j]) - bq[i];
+                    const float h = __fmaf_rn(__uint_as_float(v[o + j]), sc, -bq[i]);
                     cm |= (h >= tau_rej ? 1u : 0u) << j;
                     am |= (h >= tau_acc ? 1u : 0u) << j;
                 }
@@ -168,7 +169,7 @@ __device__ __forceinline__ uint32_t slow_chunk(const TcParams &p, const uint32_t
         return scnt;
     }
     const int c = c0 + (int)lane;                        // this lane's column
-    const float bl = FP8 ? 0.f : bt[o + lane];
+    const float bl = bt[o + lane];
     const bool cvalid = c < p.nS;
     while (hm) {
         const int k = __ffs(hm) - 1;
@@ -183,7 +184,7 @@ __device__ __forceinline__ uint32_t slow_chunk(const TcParams &p, const uint32_t
         __syncwarp();
         const float a = xch[lane];
         __syncwarp();   // every lane has read the slot before the next row overwrites it
-        const float h = FP8 ? a : a - bl;
+        const float h = __fmaf_rn(a, __shfl_sync(0xffffffffu, sc, k), -bl);
         const float ta = __shfl_sync(0xffffffffu, tau_acc, k);
         const float tr = __shfl_sync(0xffffffffu, tau_rej, k);
         const int rk = __shfl_sync(0xffffffffu, r, k);
@@ -309,8 +310,8 @@ __global__ void __launch_bounds__(320, 1)
     float *s_beta = reinterpret_cast<float *>(sB + stages * kStageBytes);    // 8 warps x 2 x HC: beta
     float4 *s_cst = reinterpret_cast<float4 *>(s_beta + 8 * 2 * HC);       // 8 warps x 2 x kSubW chunk stats
     uint2 *s_stage = reinterpret_cast<uint2 *>(s_cst + 8 * 2 * kSubW);       // 8 warps x kStageCap candidates
-    float *s_sx = reinterpret_cast<float *>(s_stage + 8 * kStageCap);        // FP8: 8 warps x 2 x HC column scales
-    uint64_t *bars = reinterpret_cast<uint64_t *>(s_sx + (FP8 ? 8 * 2 * HC : 0));
+    float *s_sx = reinterpret_cast<float *>(s_stage + 8 * kStageCap);        // FP8: 8 warps x 2 x kSubW chunk scales
+    uint64_t *bars = reinterpret_cast<uint64_t *>(s_sx + (FP8 ? 8 * 2 * kSubW : 0));
     uint64_t *full = bars;                    // [8]
     uint64_t *empty = bars + 8;               // [8]
     uint64_t *a_full = bars + 16;             // [2]
@@ -471,7 +472,7 @@ __global__ void __launch_bounds__(320, 1)
         const int half = e >> 2;           // which half of the tile's columns
         const uint32_t lane_base = static_cast<uint32_t>(quad * 32) << 16;
         float *my_bt = s_beta + e * (2 * HC);
-        float *my_sx = s_sx + e * (2 * HC);   // FP8 only
+        float *my_sx = s_sx + e * (2 * kSubW);   // FP8 only
         float4 *my_cs = s_cst + e * (2 * kSubW);
         uint2 *my_stg = s_stage + e * kStageCap;
         float *my_xch = s_xch + e * 32;
@@ -487,10 +488,10 @@ __global__ void __launch_bounds__(320, 1)
             const int c0 = it.n * BN + half * HC;
             if constexpr (kPer == 4) {
                 cp_async_16(my_bt + s * HC + lane * 4, p.beta + c0 + lane * 4);
-                if constexpr (FP8) cp_async_16(my_sx + s * HC + lane * 4, p.sc_s + c0 + lane * 4);
+                if (FP8 && lane == kSubW) cp_async_16(my_sx + s * kSubW, p.sc_s + (c0 >> 5));   // 4 chunk scales
             } else {
                 cp_async_8(my_bt + s * HC + lane * 2, p.beta + c0 + lane * 2);
-                if constexpr (FP8) cp_async_8(my_sx + s * HC + lane * 2, p.sc_s + c0 + lane * 2);
+                if (FP8 && lane == kSubW) cp_async_8(my_sx + s * kSubW, p.sc_s + (c0 >> 5));    // 2 chunk scales
             }
             if (lane < kSubW) cp_async_16(my_cs + s * kSubW + lane, p.cstat + (c0 >> 5) + lane);
             cp_async_commit();
@@ -537,30 +538,14 @@ __global__ void __launch_bounds__(320, 1)
             tc_fence_after();
             const uint32_t tbase = tmem_base + lane_base + b * BN + half * HC;
             const float *beta = my_bt + slot * HC;
-            const float *sxs = my_sx + slot * HC;
+            const float *sxs = my_sx + slot * kSubW;
             const float4 *cst = my_cs + slot * kSubW;
             const int colw = cur.n * BN + half * HC;   // first column this warp owns in the tile
 
             // 64 columns [piece*64, piece*64+64) of this warp's half, values in v
             auto process64 = [&](uint32_t (&v)[64], int piece) {
-                if constexpr (FP8) {
-                    // h = fma(acc, s_q s_x, -beta): one rounding (s_q s_x is an exact power of two);
-                    // the values in v become h, and the chunk bound below uses beta_min = 0.
-                    const float4 *sx4 = reinterpret_cast<const float4 *>(sxs + piece * 64);
-                    const float4 *bt4 = reinterpret_cast<const float4 *>(beta + piece * 64);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float4 sx = sx4[i], bt = bt4[i];
-                        const float2 a = __ffma2_rn(make_float2(__uint_as_float(v[4 * i]), __uint_as_float(v[4 * i + 1])),
-                                                    make_float2(sq * sx.x, sq * sx.y), make_float2(-bt.x, -bt.y));
-                        const float2 b = __ffma2_rn(make_float2(__uint_as_float(v[4 * i + 2]), __uint_as_float(v[4 * i + 3])),
-                                                    make_float2(sq * sx.z, sq * sx.w), make_float2(-bt.z, -bt.w));
-                        v[4 * i] = __float_as_uint(a.x);
-                        v[4 * i + 1] = __float_as_uint(a.y);
-                        v[4 * i + 2] = __float_as_uint(b.x);
-                        v[4 * i + 3] = __float_as_uint(b.y);
-                    }
-                }
+                // FP8: h = fl(A s_q s_chunk - beta), one rounding (the scale product is an exact power of two)
+                const float sc0 = FP8 ? sq * sxs[2 * piece] : 1.0f, sc1 = FP8 ? sq * sxs[2 * piece + 1] : 1.0f;
                 const float4 cs0 = cst[2 * piece], cs1 = cst[2 * piece + 1];
                 const float eh0 = __fmaf_ru(rp.z, cs0.x, __fmaf_ru(rp.w, cs0.y, cs0.z));
                 const float eh1 = __fmaf_ru(rp.z, cs1.x, __fmaf_ru(rp.w, cs1.y, cs1.z));
@@ -569,7 +554,7 @@ __global__ void __launch_bounds__(320, 1)
                     for (int j = 0; j < 64; ++j) {
                         const int c = colw + piece * 64 + j;
                         if (r < p.nR && c < p.nS) {
-                            const float h = FP8 ? __uint_as_float(v[j]) : __uint_as_float(v[j]) - beta[piece * 64 + j];
+                            const float h = __fmaf_rn(__uint_as_float(v[j]), j < 32 ? sc0 : sc1, -beta[piece * 64 + j]);
                             const size_t o = (size_t)p.orig_r[r] * p.nS + p.orig_s[c];
                             p.dump_h[o] = h;
                             p.dump_e[o] = j < 32 ? eh0 : eh1;
@@ -585,11 +570,12 @@ __global__ void __launch_bounds__(320, 1)
                     tr0 = __fsub_rd(rp.y, eh0);
                     tr1 = __fsub_rd(rp.y, eh1);
                 }
-                // Whole-chunk reject: with beta_j >= beta_min(chunk), every h_j = fl(A_j - beta_j)
-                // is <= fl_ru(max_j A_j - beta_min); rows are in norm order, so beta_min is tight.
+                // Whole-chunk reject: with beta_j >= beta_min(chunk) and one scale s > 0 per chunk,
+                // every h_j = fl(A_j s - beta_j) is <= fl_ru(max_j A_j * s - beta_min); rows are in
+                // norm order, so beta_min is tight.
                 const float mx0 = max_tree32(v, 0), mx1 = max_tree32(v, 32);
-                const bool hit0 = (FP8 ? mx0 : __fsub_ru(mx0, cs0.w)) >= tr0;
-                const bool hit1 = (FP8 ? mx1 : __fsub_ru(mx1, cs1.w)) >= tr1;
+                const bool hit0 = __fmaf_ru(mx0, sc0, -cs0.w) >= tr0;
+                const bool hit1 = __fmaf_ru(mx1, sc1, -cs1.w) >= tr1;
                 if constexpr (TOPK) {
                     if (hit0 || hit1)
                         slow_topk(p, v, beta + piece * 64, __fadd_ru(eh0, rp.x), __fadd_ru(eh1, rp.x), hit0, hit1, r,
@@ -597,10 +583,10 @@ __global__ void __launch_bounds__(320, 1)
                 } else {
                     if (__any_sync(0xffffffffu, hit0 || hit1)) {
                         const int c0 = colw + piece * 64;
-                        scnt = slow_chunk<FP8>(p, v, 0, beta + piece * 64, __fadd_ru(rp.x, eh0), __fsub_rd(rp.y, eh0),
-                                               hit0, r, c0, my_xch, my_stg, scnt);
-                        scnt = slow_chunk<FP8>(p, v, 32, beta + piece * 64, __fadd_ru(rp.x, eh1), __fsub_rd(rp.y, eh1),
-                                               hit1, r, c0 + 32, my_xch, my_stg, scnt);
+                        scnt = slow_chunk<FP8>(p, v, 0, beta + piece * 64, sc0, __fadd_ru(rp.x, eh0),
+                                               __fsub_rd(rp.y, eh0), hit0, r, c0, my_xch, my_stg, scnt);
+                        scnt = slow_chunk<FP8>(p, v, 32, beta + piece * 64, sc1, __fadd_ru(rp.x, eh1),
+                                               __fsub_rd(rp.y, eh1), hit1, r, c0 + 32, my_xch, my_stg, scnt);
                     }
                 }
             };
@@ -651,9 +637,10 @@ __global__ void __launch_bounds__(320, 1)
 
 static size_t tc_extra_bytes(int BN, bool fp8)
 {
-    // per epilogue warp: 2 x BN/2 floats of beta (and of the FP8 column scales), 2 x BN/64
-    // chunk stats, the candidate buffer; then 27 barrier / flag words and 8 x 32 exchange floats
-    return (size_t)8 * (2 * (BN / 2) * 4 * (fp8 ? 2 : 1) + 2 * (BN / 64) * 16 + kStageCap * 8) + 27 * 8 + 8 * 32 * 4 + 16;
+    // per epilogue warp: 2 x BN/2 floats of beta, 2 x BN/64 chunk stats, the candidate buffer and
+    // (FP8) 2 x BN/64 chunk scales; then 27 barrier / flag words and 8 x 32 exchange floats
+    return (size_t)8 * (2 * (BN / 2) * 4 + 2 * (BN / 64) * 16 + kStageCap * 8 + (fp8 ? 2 * (BN / 64) * 4 : 0)) + 27 * 8 +
+           8 * 32 * 4 + 16;
 }
 
 static size_t tc_smem_bytes(int BN, int kc, int stages, int a_slots, bool fp8)

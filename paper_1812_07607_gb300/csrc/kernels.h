@@ -24,7 +24,7 @@ struct TcParams {
     float *dump_e;           // diagnostics: the bound E of every pair
     const int32_t *orig_r, *orig_s;   // diagnostics: caller row of each store row
     const float *sc_r;       // FP8: per-row power-of-two scales of R (NULL for BF16)
-    const float *sc_s;       // FP8: per-row scales of S
+    const float *sc_s;       // FP8: per-32-row-chunk scales of S
     uint2 *cand;             // candidates: {r, c | 0x80000000 if a band pair, else a proven match}
     unsigned long long *cand_cnt;
     unsigned long long cand_cap;

@@ -287,12 +287,15 @@ __global__ void __launch_bounds__(256) k_gather_rows(const float *__restrict__ s
 }
 
 // ------------------------------------------------------------------ FP8 copy
-// One warp per row: s = the power of two with max|x| / s <= 448 (the largest
-// finite e4m3), codes = RN_e4m3(x / s) (x / s is exact), and FP64 upper bounds
-// of ||x - s*dec(codes)|| and ||s*dec(codes)||.
-__global__ void __launch_bounds__(256) k1_fp8(const float *__restrict__ x32, int64_t n, int d, int dp8,
-                                              uint8_t *__restrict__ x8, float *__restrict__ sc8,
-                                              float2 *__restrict__ rowb8)
+// Every 32-row chunk shares one power-of-two scale s: the largest over its rows of the
+// power of two s_row with max|x| / s_row <= 448 (the largest finite e4m3). Codes are
+// RN_e4m3(x / s) (x / s is exact, and max|x| / s <= 448 still holds in every row). One
+// scale per chunk lets the epilogue bound a whole chunk from its raw accumulators:
+// h_j = fl(A_j s_q s - beta_j) <= fl_ru(max_j A_j * s_q s - beta_min).
+
+// One warp per row: the row's own scale s_row.
+__global__ void __launch_bounds__(256) k1_fp8_row_scale(const float *__restrict__ x32, int64_t n, int d,
+                                                        float *__restrict__ sc8)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row = (int64_t)blockIdx.x * 8 + warp;
@@ -311,6 +314,37 @@ __global__ void __launch_bounds__(256) k1_fp8(const float *__restrict__ x32, int
         sc = ldexpf(1.0f, c);
         while (mx / sc > 448.0f) sc *= 2.0f;
     }
+    if (lane == 0) sc8[row] = sc;
+}
+
+// One warp per 32-row chunk: the chunk scale (the largest row scale), written to the chunk
+// table and to every row of the chunk (1 on padding rows).
+__global__ void __launch_bounds__(256) k1_fp8_chunk_scale(int64_t n, int64_t n_pad, float *__restrict__ sc8,
+                                                          float *__restrict__ scc8)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t chunk = (int64_t)blockIdx.x * 8 + warp;
+    if (chunk * 32 >= n_pad) return;
+    const int64_t row = chunk * 32 + lane;
+    float sc = row < n ? sc8[row] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sc = fmaxf(sc, __shfl_xor_sync(0xffffffffu, sc, o));
+    if (sc == 0.f) sc = 1.0f;
+    sc8[row] = row < n ? sc : 1.0f;
+    if (lane == 0) scc8[chunk] = sc;
+}
+
+// One warp per row: codes with the row's (chunk) scale, and FP64 upper bounds of
+// ||x - s*dec(codes)|| and ||s*dec(codes)||.
+__global__ void __launch_bounds__(256) k1_fp8(const float *__restrict__ x32, int64_t n, int d, int dp8,
+                                              const float *__restrict__ sc8, uint8_t *__restrict__ x8,
+                                              float2 *__restrict__ rowb8)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * 8 + warp;
+    if (row >= n) return;
+    const float *xr = x32 + row * d;
+    const float sc = sc8[row];
     uint8_t *br = x8 + row * dp8;
     double s2 = 0.0, s3 = 0.0;
     for (int k = lane; k < dp8; k += 32) {
@@ -330,15 +364,13 @@ __global__ void __launch_bounds__(256) k1_fp8(const float *__restrict__ x32, int
     if (lane == 0) {
         const double fac = 1.0 + (double)(dp8 + 4) * 2.220446049250313e-16;
         const double grow = 1.0 + 8.881784197001252e-16;
-        sc8[row] = sc;
         rowb8[row] = make_float2(__double2float_ru(sqrt(s2 * fac) * grow), __double2float_ru(sqrt(s3 * fac) * grow));
     }
 }
 
-// Per 32-row chunk: {max ||x||, max r8 + (gamma_tc8 + 1.01u) max ||x~8||, P3 (as BF16), 0}.
+// Per 32-row chunk: {max ||x||, max r8 + (gamma_tc8 + 1.01u) max ||x~8||, P3 (as BF16), beta_min}.
 __global__ void __launch_bounds__(256) k1_fp8_stats(const float2 *__restrict__ rowb8, const float4 *__restrict__ cstat,
-                                                    int64_t n, int64_t n_pad, float g2, float *__restrict__ sc8,
-                                                    float4 *__restrict__ cstat8)
+                                                    int64_t n, int64_t n_pad, float g2, float4 *__restrict__ cstat8)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t chunk = (int64_t)blockIdx.x * 8 + warp;
@@ -349,8 +381,6 @@ __global__ void __launch_bounds__(256) k1_fp8_stats(const float2 *__restrict__ r
         const float2 rb = rowb8[row];
         rq = rb.x;
         nqt = rb.y;
-    } else {
-        sc8[row] = 1.0f;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -359,7 +389,7 @@ __global__ void __launch_bounds__(256) k1_fp8_stats(const float2 *__restrict__ r
     }
     if (lane == 0) {
         const float4 c = cstat[chunk];
-        cstat8[chunk] = make_float4(c.x, __fmaf_ru(g2, nqt, rq), c.z, 0.f);
+        cstat8[chunk] = make_float4(c.x, __fmaf_ru(g2, nqt, rq), c.z, c.w);
     }
 }
 
@@ -370,21 +400,29 @@ int ensure_fp8(Store *s, cudaStream_t st)
     const int dp8 = (s->d + 127) / 128 * 128;
     const size_t b_x = align256((size_t)s->n * dp8), b_sc = align256(sizeof(float) * s->n_pad),
                  b_rb = align256(sizeof(float2) * std::max<int64_t>(s->n, 1)),
-                 b_cs = align256(sizeof(float4) * (s->n_pad / 32));
+                 b_cs = align256(sizeof(float4) * (s->n_pad / 32)), b_scc = align256(sizeof(float) * (s->n_pad / 32));
     void *blk = nullptr;
-    int rc = dev_alloc(&blk, b_x + b_sc + b_rb + b_cs, st);
+    int rc = dev_alloc(&blk, b_x + b_sc + b_rb + b_cs + b_scc, st);
     if (rc) return rc;
     char *p = (char *)blk;
     uint8_t *x8 = (uint8_t *)p;
     float *sc8 = (float *)(p + b_x);
     float2 *rowb8 = (float2 *)(p + b_x + b_sc);
     float4 *cstat8 = (float4 *)(p + b_x + b_sc + b_rb);
+    float *scc8 = (float *)(p + b_x + b_sc + b_rb + b_cs);
+    const unsigned chunk_blocks = (unsigned)((s->n_pad / 32 + 7) / 8);
     if (s->n > 0) {
-        k1_fp8<<<(unsigned)((s->n + 7) / 8), 256, 0, st>>>(s->x32, s->n, s->d, dp8, x8, sc8, rowb8);
+        k1_fp8_row_scale<<<(unsigned)((s->n + 7) / 8), 256, 0, st>>>(s->x32, s->n, s->d, sc8);
+        count_launch();
+    }
+    k1_fp8_chunk_scale<<<chunk_blocks, 256, 0, st>>>(s->n, s->n_pad, sc8, scc8);
+    count_launch();
+    if (s->n > 0) {
+        k1_fp8<<<(unsigned)((s->n + 7) / 8), 256, 0, st>>>(s->x32, s->n, s->d, dp8, sc8, x8, rowb8);
         count_launch();
     }
     const float g2 = f32_ru(gamma_tc8(dp8) + 1.01 * kU32);
-    k1_fp8_stats<<<(unsigned)((s->n_pad / 32 + 7) / 8), 256, 0, st>>>(rowb8, s->cstat, s->n, s->n_pad, g2, sc8, cstat8);
+    k1_fp8_stats<<<chunk_blocks, 256, 0, st>>>(rowb8, s->cstat, s->n, s->n_pad, g2, cstat8);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -395,6 +433,7 @@ int ensure_fp8(Store *s, cudaStream_t st)
     s->dp8 = dp8;
     s->x8 = x8;
     s->sc8 = sc8;
+    s->scc8 = scc8;
     s->rowb8 = rowb8;
     s->cstat8 = cstat8;
     s->fp8_block = blk;

@@ -36,7 +36,12 @@ def enc_bf16(X):
 
 
 def enc_fp8(X):
-    """Host rebuild of the library's FP8 copy: power-of-two row scale s with max|x|/s <= 448, RN e4m3."""
+    """Host rebuild of the library's FP8 copy: power-of-two scale s with max|x|/s <= 448, RN e4m3.
+
+    The library shares one scale per 32-row chunk (the largest row scale of the chunk); the FP8
+    cases below give every row max|x| = 1, so every row scale, hence every chunk scale, is 2^-8
+    and the per-row rebuild here is exact.
+    """
     import torch
     mx = np.abs(X).max(axis=1, keepdims=True).astype(np.float32)
     m, e = np.frexp(mx / np.float32(448.0))
@@ -64,6 +69,9 @@ def test_bound_and_accumulation_margin(dl, prec, d, kind):
     import torch
     g = W.rng(9000 + d + (kind == "signed") + 17 * (prec == "fp8"))
     R, S = _data(kind, d, 320, g), _data(kind, d, 2500, g)
+    if prec == "fp8":   # one scale for every row (see enc_fp8)
+        R = (R / np.abs(R).max(axis=1, keepdims=True)).astype(np.float32)
+        S = (S / np.abs(S).max(axis=1, keepdims=True)).astype(np.float32)
     Rs = dl.Store(torch.arange(R.shape[0]).cuda(), torch.from_numpy(R).cuda())
     Ss = dl.Store(torch.arange(S.shape[0]).cuda(), torch.from_numpy(S).cuda())
     h, e = dl.debug_scores(Rs, Ss, prec)
