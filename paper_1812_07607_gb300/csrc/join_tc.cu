@@ -14,9 +14,11 @@
 //               once per unit into one of one or two A slots; S tiles stream
 //               through a ring of stages, one 64-column K-chunk of BN rows per
 //               stage (128-byte swizzle).
-//   warp 1      MMA issuer: 4 x tcgen05.mma (K=16 each) per stage into one of two
-//               TMEM accumulators (128 lanes x BN FP32 columns each), then
-//               tcgen05.commit to free the stage / publish the accumulator.
+//   warp 1      MMA issuer: 4 x tcgen05.mma (K=16 each) per stage into one of the
+//               512 / BN TMEM accumulators (128 lanes x BN FP32 columns each: two
+//               of 256 or four of 128 columns, so a narrower tile leaves the
+//               MMA more tiles of slack before it needs a released accumulator),
+//               then tcgen05.commit to free the stage / publish the accumulator.
 //   warps 2-9   epilogue, two warps per TMEM lane quadrant, each owning half of
 //               the tile's columns: tcgen05.ld 64 columns at a time, then a max
 //               tree over the raw accumulators of each 32-column chunk and one
@@ -301,7 +303,8 @@ __global__ void __launch_bounds__(320, 1)
     const int kc = p.kc, stages = p.stages, a_slots = p.a_slots;
     constexpr uint32_t kStageBytes = BN * 128;
     constexpr int kChunkCols = FP8 ? 128 : 64;   // columns per 128-byte K chunk
-    constexpr uint32_t kTmemCols = 2 * BN;
+    constexpr int kAcc = 512 / BN;              // TMEM accumulators: 2 of 256 or 4 of 128 columns
+    constexpr uint32_t kTmemCols = 512;
     constexpr int HC = BN / 2;               // columns of a tile each epilogue warp owns
     constexpr int kSubW = HC / 32;           // 32-column chunks per warp per tile
     const uint32_t a_bytes = (uint32_t)kc * 16384;
@@ -316,12 +319,12 @@ __global__ void __launch_bounds__(320, 1)
     uint64_t *empty = bars + 8;               // [8]
     uint64_t *a_full = bars + 16;             // [2]
     uint64_t *a_empty = bars + 18;            // [2]
-    uint64_t *acc_full = bars + 20;           // [2]
-    uint64_t *acc_empty = bars + 22;          // [2]
-    uint64_t *done = bars + 24;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 25);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 26);
-    float *s_xch = reinterpret_cast<float *>(bars + 28);   // [8 warps x 32] row exchange slots (16-byte aligned)
+    uint64_t *acc_full = bars + 20;           // [kAcc <= 4]
+    uint64_t *acc_empty = bars + 24;          // [kAcc <= 4]
+    uint64_t *done = bars + 28;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 29);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 30);
+    float *s_xch = reinterpret_cast<float *>(bars + 32);   // [8 warps x 32] row exchange slots (16-byte aligned)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -334,6 +337,8 @@ __global__ void __launch_bounds__(320, 1)
         for (int s = 0; s < 2; ++s) {
             mbar_init(a_full + s, 1);
             mbar_init(a_empty + s, 1);
+        }
+        for (int s = 0; s < kAcc; ++s) {
             mbar_init(acc_full + s, 1);
             mbar_init(acc_empty + s, 8);
         }
@@ -421,8 +426,8 @@ __global__ void __launch_bounds__(320, 1)
                 tc_fence_after();
                 const uint32_t a_base = smem_u32(sA + slot * a_bytes);
                 for (int n = un.y; n < un.z && ok; ++n) {
-                    const uint32_t b = t & 1;
-                    if (!mbar_wait(acc_empty + b, ((t >> 1) & 1) ^ 1, abort_flag)) {
+                    const uint32_t b = t % kAcc;
+                    if (!mbar_wait(acc_empty + b, ((t / kAcc) & 1) ^ 1, abort_flag)) {
                         ok = false;
                         break;
                     }
@@ -529,9 +534,9 @@ __global__ void __launch_bounds__(320, 1)
                 theta_row = __int_as_float(0xff800000);
                 if (r < p.nR) theta_row = float_from_order_code(__ldcg(p.tk_row_theta + r));
             }
-            const uint32_t b = t & 1;
+            const uint32_t b = t % kAcc;
             const int slot = t & 1;
-            if (!mbar_wait(acc_full + b, (t >> 1) & 1, abort_flag)) {
+            if (!mbar_wait(acc_full + b, (t / kAcc) & 1, abort_flag)) {
                 ok = false;
                 break;
             }
@@ -638,9 +643,9 @@ __global__ void __launch_bounds__(320, 1)
 static size_t tc_extra_bytes(int BN, bool fp8)
 {
     // per epilogue warp: 2 x BN/2 floats of beta, 2 x BN/64 chunk stats, the candidate buffer and
-    // (FP8) 2 x BN/64 chunk scales; then 27 barrier / flag words and 8 x 32 exchange floats
-    return (size_t)8 * (2 * (BN / 2) * 4 + 2 * (BN / 64) * 16 + kStageCap * 8 + (fp8 ? 2 * (BN / 64) * 4 : 0)) + 27 * 8 +
-           8 * 32 * 4 + 16;
+    // (FP8) 2 x BN/64 chunk scales; then 32 barrier / flag words and 8 x 32 exchange floats
+    return (size_t)8 * (2 * (BN / 2) * 4 + 2 * (BN / 64) * 16 + kStageCap * 8 + (fp8 ? 2 * (BN / 64) * 4 : 0)) + 32 * 8 +
+           8 * 32 * 4;
 }
 
 static size_t tc_smem_bytes(int BN, int kc, int stages, int a_slots, bool fp8)
