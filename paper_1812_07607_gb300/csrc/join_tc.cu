@@ -203,8 +203,9 @@ __device__ __forceinline__ uint32_t slow_chunk(const TcParams &p, const uint32_t
 
 // ---------------------------------------------------------------- top-k epilogue
 // A slot's state is (theta, list fill) in registers plus, in global memory, a
-// min-heap of the k largest lower bounds L = fl_rd(h - E) seen so far (theta is
-// its minimum: at least k columns have h >= theta) and the list of every column
+// min-heap of the k largest lower bounds L = fl_rd(h - E) seen so far above the row's
+// published threshold (theta is its minimum: at least k columns have h >= theta) and
+// the list of every column
 // whose upper bound U = fl_ru(h + E) reached theta when it was seen. Every true
 // top-k column has U >= h >= the k-th largest h >= theta, so it is in the list.
 // Returns the new (theta, fill) packed in a float2.
@@ -214,7 +215,6 @@ __device__ __noinline__ float2 topk_insert(const TcParams &p, size_t sidx, int r
     uint2 *list = p.tk_list + sidx * (size_t)p.tk_cap;
     if (cnt >= p.tk_cap) {   // compact: drop columns whose upper bound fell below the best threshold
         const float th = fmaxf(theta, float_from_order_code(__ldcg(p.tk_row_theta + r)));
-        (void)theta_row;
         int w = 0;
         for (int i = 0; i < cnt; ++i) {
             const uint2 e = list[i];
@@ -227,7 +227,11 @@ __device__ __noinline__ float2 topk_insert(const TcParams &p, size_t sidx, int r
         }
     }
     list[cnt++] = make_uint2((uint32_t)c, __float_as_uint(U));
-    if (L > theta) {
+    // The heap only needs lower bounds above every threshold already known for the row: a
+    // bound at or below the row's threshold can raise neither this slot's threshold past it
+    // nor the k-th largest bound that finalize takes over all heaps (which stays <= the
+    // row's k-th largest h either way), so it is not inserted.
+    if (L > fmaxf(theta, theta_row)) {
         float *heap = p.tk_heap + sidx * (size_t)p.tk_k;
         const int k = p.tk_k;
         int i = 0;

@@ -531,8 +531,22 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
                 L.p.tk_theta = theta;
                 L.p.tk_row_theta = row_theta;
                 L.p.tk_overflow = ovf;
+                // Units are split-major, so the first mt units are every row tile's first split.
+                // Running those alone first publishes each row's threshold before the other
+                // splits start: their slots then admit only columns that can still reach the
+                // top k (fewer list entries and heap inserts, most visibly for large k).
+                const int first = (splits > 1 && n_units > mt) ? (int)mt : n_units;
+                L.p.n_units = first;
+                L.grid = std::min(first, sms);
                 rc = launch_tc_join(L, st, true);
                 ++launches;
+                if (!rc && first < n_units) {
+                    L.p.units = units + first;
+                    L.p.n_units = n_units - first;
+                    L.grid = std::min(n_units - first, sms);
+                    rc = launch_tc_join(L, st, true);
+                    ++launches;
+                }
             }
             if (!rc) {
                 const int grid = (int)std::min<int64_t>((nQ + 3) / 4, (int64_t)sms * 16);
