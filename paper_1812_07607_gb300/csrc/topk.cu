@@ -535,7 +535,8 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
                 // Running those alone first publishes each row's threshold before the other
                 // splits start: their slots then admit only columns that can still reach the
                 // top k (fewer list entries and heap inserts, most visibly for large k).
-                const int first = (splits > 1 && n_units > mt) ? (int)mt : n_units;
+                // (only when the first splits alone still fill most of the GPU)
+                const int first = (splits > 1 && n_units > mt && 2 * mt >= sms) ? (int)mt : n_units;
                 L.p.n_units = first;
                 L.grid = std::min(first, sms);
                 rc = launch_tc_join(L, st, true);
