@@ -59,7 +59,8 @@ typedef enum dl_precision {
     DL_PREC_AUTO = 0,       /* BF16 tensor-core path when d <= 512, else FP8 e4m3 (ε-join);
                                top-k: BF16 when d <= 512, else FP32 */
     DL_PREC_BF16 = 1,       /* -2 q.x on tcgen05 tensor cores in BF16, FP32 accumulate; exact result */
-    DL_PREC_FP8E4M3 = 2,    /* as BF16 but FP8 e4m3 with per-row scales; exact result */
+    DL_PREC_FP8E4M3 = 2,    /* as BF16 but FP8 e4m3 with power-of-two scales (per 32-row chunk of
+                               each store); exact result */
     DL_PREC_FP32 = 3,       /* FP32 SIMT distances + bound + FP64 recheck; exact result */
     DL_PREC_FP32_PLAIN = 4  /* plain FP32 SIMT join D32 <= (float)(eps*eps): the comparison
                                baseline, NOT exact near the threshold */

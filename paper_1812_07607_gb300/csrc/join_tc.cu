@@ -3,35 +3,36 @@
 // The nested-loop join of Sec. 5 evaluates every pair (q, x). With
 //   D(q, x) = ||q||^2 + ||x||^2 - 2 q.x
 // the only pair-wise term is the dot product, a dense contraction. This kernel
-// computes A = Q~ X~^T on the tcgen05 tensor cores (BF16 in, FP32 accumulate in
-// TMEM) and classifies every pair in a fused epilogue against per-row
-// thresholds that carry a proven error bound, so that each pair is either a
-// proven match, a proven non-match, or an undecided "band" pair that the
-// recheck kernel settles exactly.
+// computes A = Q~ X~^T on the tcgen05 tensor cores (BF16 or FP8 e4m3 in, FP32
+// accumulate in TMEM) and classifies every pair in a fused epilogue against per-row
+// thresholds that carry a proven error bound, so that each pair is either a proven
+// match, a proven non-match, or an undecided "band" pair that the recheck settles
+// exactly. With h = q.x - ||x||^2/2 the epilogue works on h~ = fl(A s - beta)
+// (s = 1 for BF16; for FP8 the exact power of two s_q s_chunk).
 //
 // Per CTA (persistent, one per SM, 320 threads, warp-specialised):
-//   warp 0      TMA producer: the 128-row R tile (all d/64 K-chunks) is loaded
-//               once per unit into one of one or two A slots; S tiles stream
-//               through a ring of stages, one 64-column K-chunk of BN rows per
-//               stage (128-byte swizzle).
-//   warp 1      MMA issuer: 4 x tcgen05.mma (K=16 each) per stage into one of the
-//               512 / BN TMEM accumulators (128 lanes x BN FP32 columns each: two
-//               of 256 or four of 128 columns, so a narrower tile leaves the
-//               MMA more tiles of slack before it needs a released accumulator),
-//               then tcgen05.commit to free the stage / publish the accumulator.
-//   warps 2-9   epilogue, two warps per TMEM lane quadrant, each owning half of
-//               the tile's columns: tcgen05.ld 64 columns at a time, then a max
-//               tree over the raw accumulators of each 32-column chunk and one
-//               compare of fl_ru(max A - min beta of the chunk) against the
-//               row's reject threshold (about one issue slot per pair; store
-//               rows are in norm order so a chunk's betas are nearly equal).
-//               Only chunks that this bound cannot reject compute
-//               h = fl(A - beta) per pair (against -beta each warp stages in
-//               shared memory a tile ahead) and classify them exactly; proven
-//               matches and band pairs go to a per-warp shared-memory buffer as
-//               (r, c) candidates, flushed to the global candidate list with one
-//               atomic per flush. k_finalize turns them into id pairs.
-// A unit is (R tile m, S tiles [nb, ne)); units are handed out round-robin.
+//   warp 0      TMA producer: the 128-row R tile (all K chunks of 128 bytes: 64 BF16
+//               or 128 FP8 columns) is loaded once per unit into one of one or two A
+//               slots; S tiles stream through a ring of stages, one K chunk of BN
+//               rows per stage (128-byte swizzle).
+//   warp 1      MMA issuer: 4 x tcgen05.mma (K = 32 bytes each) per stage into one of
+//               the 512 / BN TMEM accumulators (128 lanes x BN FP32 columns each: two
+//               of 256 or four of 128 columns), then tcgen05.commit to free the stage
+//               and to publish the accumulator.
+//   warps 2-9   epilogue, two warps per TMEM lane quadrant, each owning half of the
+//               tile's columns. Per 64-column piece: tcgen05.ld, then a three-input max
+//               tree over the raw accumulators of each 32-column chunk and one compare
+//               of fl_ru(max A * s - beta_min of the chunk) against the row's reject
+//               threshold (about half an issue slot per pair; store rows are in norm
+//               order so a chunk's betas are nearly equal). Only chunks that this
+//               bound cannot reject are classified pair by pair (slow_chunk): proven
+//               matches and band pairs go to a per-warp shared-memory buffer as (r, c)
+//               candidates, flushed to the global candidate list with one atomic per
+//               flush. The column data (beta, chunk stats, FP8 chunk scales) of the
+//               next tile is staged with cp.async while the current one is processed.
+//               k_finalize turns the candidates into id pairs.
+// A unit is (R tile m, S tiles [nb, ne)); units are handed out round-robin, in the
+// S-range-major order their builders produce.
 #include <cuda.h>
 
 #include "kernels.h"
@@ -486,7 +487,7 @@ __global__ void __launch_bounds__(320, 1)
         uint2 *my_stg = s_stage + e * kStageCap;
         float *my_xch = s_xch + e * 32;
         uint32_t scnt = 0;
-        constexpr int kPer = HC / 32;      // -beta values a lane stages per tile (4 or 2)
+        constexpr int kPer = HC / 32;      // beta values a lane stages per tile (4 or 2)
         TileIter cur, nxt;
         cur.start(p);
         nxt = cur;
@@ -532,7 +533,7 @@ __global__ void __launch_bounds__(320, 1)
                     }
                 }
             }
-            stage_async(nxt, (t & 1) ^ 1);   // prefetch the next tile's -beta (latency hidden by this tile)
+            stage_async(nxt, (t & 1) ^ 1);   // the next tile's column data lands while this one is processed
 
             if constexpr (TOPK) {
                 theta_row = __int_as_float(0xff800000);
@@ -623,7 +624,7 @@ __global__ void __launch_bounds__(320, 1)
                     p.tk_cnt[sidx] = tcnt;
                 }
             }
-            // publish the next tile's -beta into the other slot (this warp's own copy)
+            // the next tile's column data is in the other slot
             cp_async_wait_all();
             __syncwarp();
             cur = nxt;

@@ -6,8 +6,9 @@ tests/golden/unit_mixture_1m_sample16k.json (written by the committed script bes
 it, which calls only the oracle). Here the GPU path computes
 
   * the sample rows x S join, in BF16 and FP8 (the digest must match exactly), and
-  * the whole 1M x 1M join in BF16 in one launch, restricted afterwards to the sample
-    rows (the digest must match again: the full-size launch decides those rows exactly).
+  * the whole 1M x 1M join in one launch, in BF16 and in FP8, restricted afterwards to the
+    sample rows (the digest must match again: the full-size launch decides those rows
+    exactly).
 
 The input generator's output is pinned by hashes in the same file, so a platform
 whose generator draws differ is reported as such and not as a join mismatch.
@@ -82,13 +83,14 @@ def test_unit_mixture_1m_sample_rows_bf16_fp8(dl, c3):
         _check(P, dg, gold, prec)
 
 
-def test_unit_mixture_1m_full_launch_bf16(dl, c3):
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_unit_mixture_1m_full_launch(dl, c3, prec):
     import torch
     wl, rows, Rs, gold = c3
     n = wl.R.shape[0]
     S = dl.Store(torch.arange(n).cuda(), torch.from_numpy(wl.S).cuda())
     R = dl.Store(torch.arange(n).cuda(), torch.from_numpy(wl.R).cuda())
-    res = dl.sim_join(R, S, wl.eps, precision="bf16")
+    res = dl.sim_join(R, S, wl.eps, precision=prec)
     a, b = res.pairs_host()
     st = res.stats()
     res.free()
@@ -97,7 +99,7 @@ def test_unit_mixture_1m_full_launch_bf16(dl, c3):
     pos[rows] = np.arange(rows.shape[0])
     keep = pos[a] >= 0
     P, dg = _digest(pos[a[keep]], b[keep])
-    _check(P, dg, gold, "full launch")
+    _check(P, dg, gold, f"full launch {prec}")
     # the whole result: about 10 matches per row, no duplicates
     assert 5 * n < a.shape[0] < 20 * n
     key = a * n + b
