@@ -70,19 +70,24 @@ def test_batch_2m_store_4096_requests_sampled(dl):
         res = dl.batch_join(store, torch.from_numpy(qid).cuda(), torch.from_numpy(Q).cuda(), reqs)
         stats = res.stats()
         assert stats["pairs_evaluated"] == nq_total * st.X.shape[0]
+        rows_of = {}
+        for i, q in jobs_e:
+            rows_of.setdefault(i, []).append(q)
         got_e, got_k = {}, {}
         for i in picks.tolist():
             if reqs[i]["kind"] == "eps":
                 a, b = res.request_pairs(i)
-                key = (a << 35) | b   # query ids < 2^24, store ids < 2^35
-                assert np.unique(key).shape[0] == key.shape[0]   # no duplicate pairs
-                got_e[i] = (a, b)
+                order = np.argsort(a, kind="stable")   # group the request's pairs by query row
+                a, b = a[order], b[order]
+                for q in rows_of.get(i, []):
+                    lo, hi = np.searchsorted(a, qid[q], "left"), np.searchsorted(a, qid[q], "right")
+                    got_e[(i, q)] = np.sort(b[lo:hi])
             else:
                 got_k[i] = res.request_topk(i)
         res.free()
         for (i, q), idx in zip(jobs_e, want_e.get()):
-            a, b = got_e[i]
-            got = np.sort(b[a == qid[q]])
+            got = got_e[(i, q)]
+            assert np.unique(got).shape[0] == got.shape[0]   # no duplicate pairs
             assert np.array_equal(got, np.sort(st.ids[idx])), (i, q, got.shape, idx.shape)
         for (i, q), (idx, d2) in zip(jobs_k, want_k.get()):
             ids, dd = got_k[i]
