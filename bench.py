@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-requests leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-precision", action="store_true", help="skip the d=512 BF16 / FP8 leg")
+    ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES), default=None,
+                    help="run one small profiling case three times and print its timings (no bench line)")
     ap.add_argument("--serving-seconds", type=float, default=4.0)
     ap.add_argument("--serving-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
     return ap.parse_args()
@@ -536,8 +538,54 @@ def run_ours(args):
     return 0
 
 
+def _case_fp8_unit_d512():
+    """65,536 x 65,536 d=512 unit-norm R x S join in FP8 e4m3 (the precision config's rows at a
+    size that a full ncu capture handles)."""
+    import torch
+    from paper_1812_07607_gb300 import dl, workloads as W
+    dl.load()
+    g = W.rng(5)
+    R, c = W.unit_mixture(g, 65536, 512, 4096, 0.02)
+    T, _ = W.unit_mixture(g, 65536, 512, 4096, 0.02, centroids=c)
+    Rs = dl.Store(torch.arange(65536).cuda(), torch.from_numpy(R).cuda())
+    Ts = dl.Store(torch.arange(65536).cuda(), torch.from_numpy(T).cuda())
+    return lambda: dl.sim_join(Rs, Ts, 0.55, precision="fp8", timing=True)
+
+
+def _case_dense_d256():
+    """16,384 fresh queries x the first 1,048,576 rows of the serving store (d=256), eps at
+    0.5% selectivity: a candidate-dense join (BF16, tile 256)."""
+    import torch
+    from paper_1812_07607_gb300 import dl, workloads as W
+    dl.load()
+    sw = W.serve_store_4m(n=1048576)
+    Q = sw.queries(16384, 7)
+    S = dl.Store(torch.from_numpy(sw.ids).cuda(), torch.from_numpy(sw.X).cuda())
+    Qs = dl.Store(torch.arange(16384).cuda(), torch.from_numpy(Q).cuda())
+    eps = W.eps_for_selectivity(W.eps_table()["serve_store_4m:selectivity_eps"], 5e-3)
+    return lambda: dl.sim_join(Qs, S, eps, precision="bf16", timing=True, tile_n=256)
+
+
+PROFILE_CASES = {"fp8_unit_d512_65536": _case_fp8_unit_d512, "dense_d256_16384x1m": _case_dense_d256}
+
+
+def run_profile_case(name):
+    from paper_1812_07607_gb300 import build as B
+    B.build()
+    call = PROFILE_CASES[name]()
+    for _ in range(3):
+        r = call()
+        st = r.stats()
+        r.free()
+        print(json.dumps({"case": name, "ms_main": st["ms_main"], "ms_recheck": st["ms_recheck"],
+                          "band_pairs": st["band_pairs"], "pairs_out": st["pairs_out"]}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        return run_profile_case(args.profile_case)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
