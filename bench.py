@@ -450,7 +450,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         s2 = dl.Store(h_ids, h_feats, stream=stream)
         res = dl.sim_join(s2, None, wl.eps, precision=args.precision, stream=stream)
-        r_ids, s_ids = res.pairs_host()
+        r_ids, s_ids = res.pairs_host(copy=False)   # the pairs in pinned host memory
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) * 1e3
         d2h = r_ids.nbytes + s_ids.nbytes + 32

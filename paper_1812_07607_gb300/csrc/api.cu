@@ -317,6 +317,11 @@ static int run_pass(const PassCfg &c, PassOut *po)
     return rc;
 }
 
+// Output and band pairs per evaluated pair of the last completed join (any store): the first
+// join of a new store sizes its buffers from them.
+static std::mutex g_rate_mu;
+static double g_rate_out = 0.0, g_rate_band = 0.0;
+
 static int check_device(const dl_store *s)
 {
     int dev = -1;
@@ -433,11 +438,19 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
     c.timing = o.timing != 0 || tune_trial;
     c.st = (cudaStream_t)o.cuda_stream;
     const bool fixed = o.out_capacity > 0;
+    const double n_pairs = self ? 0.5 * (double)R->n * (double)R->n : (double)R->n * (double)Sx->n;
     {
         std::lock_guard<std::mutex> lk(const_cast<dl_store *>(R)->mu);
-        c.cap = fixed ? o.out_capacity : std::max<int64_t>(1 << 16, R->hint_pairs + R->hint_pairs / 4);
+        int64_t hp = R->hint_pairs, hb = R->hint_band;
+        if (hp == 0 && hb == 0) {   // a store's first join: the process-wide rates of the last join
+            // (a short first call costs a re-run; capped so that an outlier cannot claim GBs)
+            std::lock_guard<std::mutex> lr(g_rate_mu);
+            hp = (int64_t)std::min(g_rate_out * n_pairs, (double)(1 << 26));
+            hb = (int64_t)std::min(g_rate_band * n_pairs, (double)(1 << 26));
+        }
+        c.cap = fixed ? o.out_capacity : std::max<int64_t>(1 << 16, hp + hp / 4);
         // the BF16 path's candidate list holds proven matches and band pairs
-        const int64_t want = ((prec == DL_PREC_BF16 || prec == DL_PREC_FP8E4M3) ? R->hint_pairs : 0) + R->hint_band;
+        const int64_t want = ((prec == DL_PREC_BF16 || prec == DL_PREC_FP8E4M3) ? hp : 0) + hb;
         c.band_cap = std::max<int64_t>(1 << 16, want + want / 4);
     }
 
@@ -472,6 +485,11 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
         std::lock_guard<std::mutex> lk(const_cast<dl_store *>(R)->mu);
         const_cast<dl_store *>(R)->hint_pairs = (int64_t)po.out_cnt;
         const_cast<dl_store *>(R)->hint_band = (int64_t)po.band_only;
+    }
+    if (n_pairs > 0) {
+        std::lock_guard<std::mutex> lr(g_rate_mu);
+        g_rate_out = (double)po.out_cnt / n_pairs;
+        g_rate_band = (double)po.band_only / n_pairs;
     }
     if (tune_trial && reruns == 0)
         tune_record(R->dp, self ? 1 : 0, R->n, Sx->n, BN, po.ms_main,

@@ -230,17 +230,21 @@ class Result:
         _check(load().dl_result_stats(self._h, ctypes.byref(st)), "dl_result_stats")
         return {f: getattr(st, f) for f, _ in dl_join_stats._fields_}
 
-    def pairs_host(self):
-        """(r_ids, s_ids) as int64 numpy arrays (copied out of the result)."""
+    def pairs_host(self, copy: bool = True):
+        """(r_ids, s_ids) as int64 numpy arrays.
+
+        copy=False returns views of the result's pinned host buffer: no host-side copy, valid
+        until free() (the views do not keep the result alive).
+        """
         a, b, n = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int64()
         _check(load().dl_result_pairs(self._h, DL_MEM_HOST, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)),
                "dl_result_pairs")
         n = int(n.value)
         if n == 0:
             return np.empty(0, np.int64), np.empty(0, np.int64)
-        ra = np.ctypeslib.as_array(ctypes.cast(a, ctypes.POINTER(ctypes.c_int64)), shape=(n,)).copy()
-        sa = np.ctypeslib.as_array(ctypes.cast(b, ctypes.POINTER(ctypes.c_int64)), shape=(n,)).copy()
-        return ra, sa
+        ra = np.ctypeslib.as_array(ctypes.cast(a, ctypes.POINTER(ctypes.c_int64)), shape=(n,))
+        sa = np.ctypeslib.as_array(ctypes.cast(b, ctypes.POINTER(ctypes.c_int64)), shape=(n,))
+        return (ra.copy(), sa.copy()) if copy else (ra, sa)
 
     def pairs_device(self):
         """(r_ids, s_ids) as torch int64 CUDA tensors viewing the result's memory."""
