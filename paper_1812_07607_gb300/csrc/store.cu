@@ -93,8 +93,9 @@ int device_sm_count()
 // One warp per row. Computes, from the FP32 row x:
 //   nq64  = sum x_k^2 in FP64 (products exact, rounding only in the sum),
 //   the BF16 copy x~ = RN_bf16(x) (zero padded to dp),
-//   upper bounds of ||x - x~||, ||x~||, ||x|| (FP64 sums, inflated by the sum
-//   and sqrt rounding, rounded up to FP32),
+//   upper bounds of ||x - x~|| and ||x~|| (FP32 sums of squares rounded up at every
+//   step, square roots rounded up), and of ||x|| (from the FP64 sum, inflated by the
+//   sum and sqrt rounding),
 //   beta = RN32(nq64 / 2) and an upper bound of |beta - ||x||^2 / 2|,
 // and flags rows with a non-finite value or |x_k| > 2^40.
 __global__ void __launch_bounds__(256) k1_norm_quant(const float *__restrict__ x32, int64_t n, int d, int dp,
@@ -107,24 +108,26 @@ __global__ void __launch_bounds__(256) k1_norm_quant(const float *__restrict__ x
     if (row >= n) return;
     const float *xr = x32 + row * d;
     __nv_bfloat16 *br = xb + row * dp;
-    double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    double s1 = 0.0;
+    float s2 = 0.f, s3 = 0.f;   // rounded up at every step: upper bounds of the exact sums
     bool bad = false;
     for (int k = lane; k < dp; k += 32) {
         const float v = (k < d) ? __ldg(xr + k) : 0.0f;
         if (!(fabsf(v) <= 1099511627776.0f)) bad = true;  // also catches NaN
         const __nv_bfloat16 b = __float2bfloat16_rn(v);
         br[k] = b;
-        const double dv = (double)v, db = (double)__bfloat162float(b);
-        const double e = dv - db;   // exact: x~ shares x's leading bits
+        const float fb = __bfloat162float(b);
+        const float e = v - fb;   // exact: x~ shares x's leading bits
+        const double dv = (double)v;
         s1 = __dadd_rn(s1, __dmul_rn(dv, dv));
-        s2 = __dadd_rn(s2, __dmul_rn(e, e));
-        s3 = __dadd_rn(s3, __dmul_rn(db, db));
+        s2 = __fmaf_ru(e, e, s2);
+        s3 = __fmaf_ru(fb, fb, s3);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         s1 = __dadd_rn(s1, __shfl_xor_sync(0xffffffffu, s1, o));
-        s2 = __dadd_rn(s2, __shfl_xor_sync(0xffffffffu, s2, o));
-        s3 = __dadd_rn(s3, __shfl_xor_sync(0xffffffffu, s3, o));
+        s2 = __fadd_ru(s2, __shfl_xor_sync(0xffffffffu, s2, o));
+        s3 = __fadd_ru(s3, __shfl_xor_sync(0xffffffffu, s3, o));
     }
     bad = __any_sync(0xffffffffu, bad);
     if (lane == 0) {
@@ -133,8 +136,8 @@ __global__ void __launch_bounds__(256) k1_norm_quant(const float *__restrict__ x
         const double fac = 1.0 + (double)(dp + 4) * 2.220446049250313e-16;
         const double grow = 1.0 + 8.881784197001252e-16;   // 1 + 2^-50 covers the sqrt / product roundings
         nq64[row] = s1;
-        const float rq = __double2float_ru(sqrt(s2 * fac) * grow);
-        const float nqt = __double2float_ru(sqrt(s3 * fac) * grow);
+        const float rq = __fsqrt_ru(s2);
+        const float nqt = __fsqrt_ru(s3);
         const float nx = __double2float_ru(sqrt(s1 * fac) * grow);
         const double h = 0.5 * s1;
         const float bt = __double2float_rn(h);
@@ -200,22 +203,37 @@ static size_t align256(size_t x);
 __global__ void __launch_bounds__(256) k_sort_keys(const float *__restrict__ x, int64_t n, int d,
                                                    float *__restrict__ keys, unsigned *__restrict__ minmax)
 {
+    __shared__ unsigned s_min[8], s_max[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row = (int64_t)blockIdx.x * 8 + warp;
-    if (row >= n) return;
-    const float *xr = x + row * d;
-    float s = 0.f;
-    for (int k = lane; k < d; k += 32) {
-        const float v = __ldg(xr + k);
-        s = fmaf(v, v, s);
-    }
+    unsigned kmin = 0xffffffffu, kmax = 0u;
+    if (row < n) {
+        const float *xr = x + row * d;
+        float s = 0.f;
+        for (int k = lane; k < d; k += 32) {
+            const float v = __ldg(xr + k);
+            s = fmaf(v, v, s);
+        }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) {
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (!(s <= 3.0e38f)) s = 3.0e38f;   // non-finite rows are rejected later; keep the key ordered
-        keys[row] = s;
-        atomicMin(minmax + 0, __float_as_uint(s));   // non-negative floats order like their bits
-        atomicMax(minmax + 1, __float_as_uint(s));
+        if (lane == 0) keys[row] = s;
+        kmin = kmax = __float_as_uint(s);   // non-negative floats order like their bits
+    }
+    if (lane == 0) {
+        s_min[warp] = kmin;
+        s_max[warp] = kmax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {   // one atomic pair per block of eight rows
+        for (int w = 1; w < 8; ++w) {
+            kmin = min(kmin, s_min[w]);
+            kmax = max(kmax, s_max[w]);
+        }
+        if (kmin != 0xffffffffu) {
+            atomicMin(minmax + 0, kmin);
+            atomicMax(minmax + 1, kmax);
+        }
     }
 }
 
@@ -334,8 +352,9 @@ __global__ void __launch_bounds__(256) k1_fp8_chunk_scale(int64_t n, int64_t n_p
     if (lane == 0) scc8[chunk] = sc;
 }
 
-// One warp per row: codes with the row's (chunk) scale, and FP64 upper bounds of
-// ||x - s*dec(codes)|| and ||s*dec(codes)||.
+// One warp per row: codes with the row's (chunk) scale, and upper bounds of
+// ||x - s*dec(codes)|| and ||s*dec(codes)|| (FP32 sums of squares rounded up at every step,
+// square roots rounded up).
 __global__ void __launch_bounds__(256) k1_fp8(const float *__restrict__ x32, int64_t n, int d, int dp8,
                                               const float *__restrict__ sc8, uint8_t *__restrict__ x8,
                                               float2 *__restrict__ rowb8)
@@ -346,26 +365,22 @@ __global__ void __launch_bounds__(256) k1_fp8(const float *__restrict__ x32, int
     const float *xr = x32 + row * d;
     const float sc = sc8[row];
     uint8_t *br = x8 + row * dp8;
-    double s2 = 0.0, s3 = 0.0;
+    float s2 = 0.f, s3 = 0.f;
     for (int k = lane; k < dp8; k += 32) {
         const float v = (k < d) ? __ldg(xr + k) : 0.0f;
         const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(v / sc, __NV_SATFINITE, __NV_E4M3);
         br[k] = (uint8_t)q;
-        const float dec = __half2float(__half(__nv_cvt_fp8_to_halfraw(q, __NV_E4M3))) * sc;
-        const double e = (double)v - (double)dec;
-        s2 = __dadd_rn(s2, __dmul_rn(e, e));
-        s3 = __dadd_rn(s3, __dmul_rn((double)dec, (double)dec));
+        const float dec = __half2float(__half(__nv_cvt_fp8_to_halfraw(q, __NV_E4M3))) * sc;   // exact
+        const float e = v - dec;   // exact: |e| is below half an e4m3 step of v / s, times s
+        s2 = __fmaf_ru(e, e, s2);
+        s3 = __fmaf_ru(dec, dec, s3);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        s2 = __dadd_rn(s2, __shfl_xor_sync(0xffffffffu, s2, o));
-        s3 = __dadd_rn(s3, __shfl_xor_sync(0xffffffffu, s3, o));
+        s2 = __fadd_ru(s2, __shfl_xor_sync(0xffffffffu, s2, o));
+        s3 = __fadd_ru(s3, __shfl_xor_sync(0xffffffffu, s3, o));
     }
-    if (lane == 0) {
-        const double fac = 1.0 + (double)(dp8 + 4) * 2.220446049250313e-16;
-        const double grow = 1.0 + 8.881784197001252e-16;
-        rowb8[row] = make_float2(__double2float_ru(sqrt(s2 * fac) * grow), __double2float_ru(sqrt(s3 * fac) * grow));
-    }
+    if (lane == 0) rowb8[row] = make_float2(__fsqrt_ru(s2), __fsqrt_ru(s3));
 }
 
 // Per 32-row chunk: {max ||x||, max r8 + (gamma_tc8 + 1.01u) max ||x~8||, P3 (as BF16), beta_min}.
