@@ -78,3 +78,25 @@ def test_randomized_configurations(dl, orc, case):
     eps = math.sqrt(float(np.quantile(D, q))) if D.size else 0.1
     mode = ["upper", "full"][int(g.integers(0, 2))]
     check(dl, orc, R, S, eps, self_mode=mode, precs=(prec,))
+
+
+@pytest.mark.parametrize("case", range(12))
+def test_randomized_topk(dl, orc, case):
+    """12 seeded top-k configurations: ids and canonical distances equal the oracle's."""
+    import torch
+    g = W.rng(8300 + case)
+    n = int(g.integers(1, 400))
+    m = int(g.integers(1, 900))
+    d = int(g.integers(1, 300))
+    k = int(g.choice([1, 2, 7, 10, 33, 100, 200]))
+    Q, S = _draw(g, n, d), _draw(g, m, d)
+    sid = np.arange(m, dtype=np.int64) * 7 + 1
+    Qs = dl.Store(torch.arange(n).cuda(), torch.from_numpy(Q).cuda())
+    Ss = dl.Store(torch.from_numpy(sid).cuda(), torch.from_numpy(S).cuda())
+    res = dl.topk_join(Qs, Ss, k)
+    ids, d2 = res.topk_host()
+    res.free()
+    oi, od = orc.topk(Q, S, k)
+    want_ids = np.where(oi >= 0, sid[np.maximum(oi, 0)], -1)
+    assert np.array_equal(ids, want_ids), (n, m, d, k)
+    assert np.array_equal(d2, np.where(oi >= 0, od, -1.0)), (n, m, d, k)
