@@ -23,6 +23,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 
 CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11"]
+LIBS = ["-lm"]
 
 _lib = None
 
@@ -30,7 +31,7 @@ _lib = None
 def build(src: str = _SRC, out: str = _LIB_PATH, extra=()) -> str:
     """Compile oracle.c into a shared library (gcc, no FMA contraction)."""
     os.makedirs(os.path.dirname(out), exist_ok=True)
-    cmd = ["gcc", *CFLAGS, *extra, "-o", out, src]
+    cmd = ["gcc", *CFLAGS, *extra, "-o", out, src, *LIBS]
     subprocess.run(cmd, check=True)
     return out
 
@@ -60,6 +61,11 @@ def load(path: str | None = None):
     lib.oracle_dist_block.restype = None
     lib.oracle_dist_block.argtypes = [f32p, ctypes.c_int64, ctypes.c_int64, f32p, ctypes.c_int64,
                                       ctypes.c_int32, f64p]
+    lib.oracle_normalize.restype = ctypes.c_int64
+    lib.oracle_normalize.argtypes = [f32p, ctypes.c_int64, ctypes.c_int32, f32p]
+    lib.oracle_cosine_join.restype = ctypes.c_int64
+    lib.oracle_cosine_join.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int32,
+                                       ctypes.c_double, ctypes.c_int32, i64p, i64p, ctypes.c_int64]
     lib.oracle_topk.restype = ctypes.c_int32
     lib.oracle_topk.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int32,
                                 ctypes.c_int32, i64p, f64p]
@@ -116,6 +122,36 @@ class Oracle:
             out_s = np.empty(cap, dtype=np.int64)
             n = self.lib.oracle_join(Rp, R.shape[0], Sp, nS, d, float(eps), mode,
                                      out_r.ctypes.data_as(i64), out_s.ctypes.data_as(i64), cap)
+            if n <= cap:
+                return np.stack([out_r[:n], out_s[:n]], axis=1)
+            cap = int(n)
+
+    def normalize(self, X):
+        """Unit-normalized copy (the cosine metric's rows); raises on a zero-norm row."""
+        X, Xp = _f32(X)
+        out = np.empty_like(X)
+        bad = self.lib.oracle_normalize(Xp, X.shape[0], X.shape[1], out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        if bad:
+            raise ValueError(f"{bad} rows have a zero norm")
+        return out
+
+    def cosine_join(self, Rn, Sn=None, c: float = 1.0, mode: int | None = None) -> np.ndarray:
+        """Row-index pairs with canonical D(q^, x^) <= fl64(2 - 2c) on normalized rows."""
+        Rn, Rp = _f32(Rn)
+        if mode is None:
+            mode = MODE_RXS if Sn is not None else MODE_SELF_UPPER
+        if Sn is None:
+            Sn, Sp, nS = Rn, Rp, Rn.shape[0]
+        else:
+            Sn, Sp = _f32(Sn)
+            nS = Sn.shape[0]
+        i64 = ctypes.POINTER(ctypes.c_int64)
+        cap = 1 << 16
+        while True:
+            out_r = np.empty(cap, dtype=np.int64)
+            out_s = np.empty(cap, dtype=np.int64)
+            n = self.lib.oracle_cosine_join(Rp, Rn.shape[0], Sp, nS, Rn.shape[1], float(c), mode,
+                                            out_r.ctypes.data_as(i64), out_s.ctypes.data_as(i64), cap)
             if n <= cap:
                 return np.stack([out_r[:n], out_s[:n]], axis=1)
             cap = int(n)

@@ -23,13 +23,19 @@
  *   - top-k ties are broken by the smaller row index of the store side;
  *   - "exact" means the canonical FP64 value below: for k = 0..d-1 ascending,
  *     t = (double)q_k - (double)x_k, s = s + t*t, each operation rounded to
- *     nearest, no fused multiply-add (build with -ffp-contract=off).
+ *     nearest, no fused multiply-add (build with -ffp-contract=off);
+ *   - cosine similarity (a further metric; the paper names only Euclidean
+ *     queries) is taken on unit-normalized rows: n = fl32(sqrt(sum_k x_k^2)),
+ *     the sum in FP64 with k ascending, x^_k = fl32(x_k / n); a pair matches
+ *     iff the canonical D(q^, x^) <= fl64(2 - 2c), the L2 form of cos >= c for
+ *     unit vectors. Rows with a zero norm have no direction and are rejected.
  *
  * Parity pins (tests/test_oracle_pins.py): exact rational brute force, integer
  * grid and one-hot closed forms, symmetry, zero self-distance, monotonicity in
  * eps, union and permutation laws, top-k/join consistency, and a mutation test
  * that plants mistakes in a copy of this file.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -122,4 +128,56 @@ int32_t oracle_topk(const float *Q, int64_t nQ, const float *S, int64_t nS, int3
     }
     free(c);
     return 0;
+}
+
+/*
+ * Unit-normalized copy of X [n][d] (the cosine metric's rows): n_i =
+ * fl32(sqrt(sum_k x_k^2)) with the sum in FP64, k ascending, each step rounded
+ * to nearest; out_k = fl32(x_k / n_i). Returns the number of rows with a zero
+ * norm (their output row is left zero).
+ */
+int64_t oracle_normalize(const float *X, int64_t n, int32_t d, float *out)
+{
+    int64_t bad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const float *x = X + i * (int64_t)d;
+        float *o = out + i * (int64_t)d;
+        double s = 0.0;
+        for (int32_t k = 0; k < d; ++k) s = s + (double)x[k] * (double)x[k];
+        const float nr = (float)sqrt(s);
+        if (!(nr > 0.0f)) {
+            ++bad;
+            for (int32_t k = 0; k < d; ++k) o[k] = 0.0f;
+            continue;
+        }
+        for (int32_t k = 0; k < d; ++k) o[k] = x[k] / nr;
+    }
+    return bad;
+}
+
+/*
+ * Cosine-similarity join on normalized rows: the nested loop of oracle_join with
+ * the predicate canonical D(q^, x^) <= fl64(2 - 2c).
+ */
+int64_t oracle_cosine_join(const float *Rn, int64_t nR, const float *Sn, int64_t nS, int32_t d,
+                           double c, int32_t mode, int64_t *out_r, int64_t *out_s, int64_t cap)
+{
+    const double e2 = 2.0 - 2.0 * c;
+    const float *T = (mode == 0) ? Sn : Rn;
+    const int64_t nT = (mode == 0) ? nS : nR;
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < nR; ++i) {
+        int64_t j0 = (mode == 1) ? i + 1 : 0;
+        for (int64_t j = j0; j < nT; ++j) {
+            double s = oracle_sqdist(Rn + i * (int64_t)d, T + j * (int64_t)d, d);
+            if (s <= e2) {
+                if (cnt < cap) {
+                    out_r[cnt] = i;
+                    out_s[cnt] = j;
+                }
+                ++cnt;
+            }
+        }
+    }
+    return cnt;
 }

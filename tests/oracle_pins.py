@@ -11,7 +11,10 @@ disagrees with something the paper or the mathematics fixes:
     integer grids scaled by 2^-3 (exact in every format);
   * invariants: self-join symmetry, zero self-distance, monotonicity in eps,
     eps=0 gives exact duplicates, eps=inf gives every pair, permutation and
-    union laws, top-k ordering and top-k/join consistency.
+    union laws, top-k ordering and top-k/join consistency;
+  * the cosine metric: the normalized rows against exact rational arithmetic
+    (round-to-nearest quotients, unit norm within the rounding bound, invariance
+    under power-of-two scaling) and the cosine join against the exact cosine.
 
 The same suite runs against deliberately broken copies of the oracle
 (tests/test_oracle_mutants.py) to show that a plausible slip fails a pin.
@@ -279,6 +282,83 @@ def pin_topk_small_store_and_join_consistency(orc):
         assert set(idx[i].tolist()) <= row
 
 
+def _rn32(q: Fraction) -> Fraction:
+    """The float32 nearest to the rational q (ties to even), as a rational (exact search)."""
+    f = np.float32(float(q))   # within an ulp; then step to the exact nearest
+    best = None
+    for cand in (np.nextafter(f, np.float32(-np.inf)), f, np.nextafter(f, np.float32(np.inf))):
+        c = Fraction(float(cand))
+        key = (abs(c - q), int(np.frombuffer(np.float32(cand).tobytes(), dtype=np.uint32)[0]) & 1)
+        if best is None or key < best[0]:
+            best = (key, c)
+    return best[1]
+
+
+def pin_normalize_exact_properties(orc):
+    """Unit-normalized rows: RN quotients, unit norm within 5u, power-of-two scaling, zero rows."""
+    # rows whose norm is exact (Pythagorean), so each output is the RN of an exact quotient
+    X = np.array([[3, 4, 0], [0, -5, 12], [8, 0, 15], [-2, 3, 6]], dtype=np.float32)
+    N = orc.normalize(X)
+    for i, norm in enumerate((5, 13, 17, 7)):
+        for k in range(3):
+            assert Fraction(float(N[i, k])) == _rn32(Fraction(int(X[i, k]), norm)), (i, k)
+    g = _g(19)
+    for d in (1, 2, 5, 16, 77):
+        Y = W.mixed_magnitude_rows(g, 20, d) if d < 77 else W.dirichlet_histograms(g, 20, d)
+        Y = Y[np.abs(Y).max(axis=1) > 0]
+        M = orc.normalize(Y)
+        for i in range(M.shape[0]):
+            s = sum(Fraction(float(v)) ** 2 for v in M[i].tolist())
+            assert abs(s - 1) <= Fraction(5, 2**24), (d, i, float(s))
+        for e in (-20, 3, 17):   # scaling by 2^e changes nothing
+            assert np.array_equal(orc.normalize((Y.astype(np.float64) * 2.0 ** e).astype(np.float32)), M), (d, e)
+    one_hot = W.one_hot_rows(g, 10, 6) * np.float32(-3.5)
+    assert np.array_equal(orc.normalize(one_hot), -np.abs(one_hot) / np.float32(3.5))
+    try:
+        orc.normalize(np.zeros((2, 4), np.float32))
+        raise AssertionError("a zero row must be rejected")
+    except ValueError:
+        pass
+
+
+def pin_cosine_join_matches_exact(orc):
+    """The cosine join equals the exact set on its rows, and agrees with the exact cosine."""
+    g = _g(20)
+    checked = 0
+    for d, nR, nS in ((3, 15, 19), (8, 21, 17)):
+        R = orc.normalize(W.mixed_magnitude_rows(g, nR, d))
+        S = orc.normalize(W.mixed_magnitude_rows(g, nS, d))
+        M = exact_matrix(R, S)
+        vals = sorted({v for row in M for v in row})
+        for rank in (len(vals) // 5, len(vals) // 2):
+            a, b = vals[rank], vals[rank + 1]
+            c = (2.0 - float((a + b) / 2)) / 2.0
+            t = Fraction(2.0 - 2.0 * c)
+            if not (a < t < b):
+                continue
+            want = {(i, j) for i in range(nR) for j in range(nS) if M[i][j] <= t}
+            assert pair_set(orc.cosine_join(R, S, c, MODE_RXS)) == want, (d, rank)
+            checked += 1
+    assert checked >= 2
+    # against the exact cosine of the raw rows (margin for the normalization rounding)
+    Rraw = W.dirichlet_histograms(g, 30, 6)
+    Sraw = W.dirichlet_histograms(g, 40, 6)
+    c = 0.8
+    got = pair_set(orc.cosine_join(orc.normalize(Rraw), orc.normalize(Sraw), c, MODE_RXS))
+    margin = Fraction(1, 10**5)
+    for i in range(30):
+        for j in range(40):
+            q = [Fraction(v) for v in Rraw[i].astype(np.float64).tolist()]
+            x = [Fraction(v) for v in Sraw[j].astype(np.float64).tolist()]
+            dot = sum(a * b for a, b in zip(q, x))
+            nq, nx = sum(a * a for a in q), sum(b * b for b in x)
+            hi, lo = (Fraction(c) + margin) ** 2, (Fraction(c) - margin) ** 2
+            if dot > 0 and dot * dot >= hi * nq * nx:
+                assert (i, j) in got, (i, j)
+            if dot <= 0 or dot * dot <= lo * nq * nx:
+                assert (i, j) not in got, (i, j)
+
+
 ALL_PINS = [
     pin_sqdist_within_rounding_of_exact,
     pin_join_matches_exact_rational,
@@ -288,5 +368,7 @@ ALL_PINS = [
     pin_monotone_in_eps,
     pin_permutation_and_union,
     pin_topk_matches_exact_order,
+    pin_normalize_exact_properties,
+    pin_cosine_join_matches_exact,
     pin_topk_small_store_and_join_consistency,
 ]

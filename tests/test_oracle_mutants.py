@@ -32,6 +32,9 @@ MUTANTS = {
     "topk_descending": ("if (x->d2 < y->d2) return -1;\n    if (x->d2 > y->d2) return 1;",
                         "if (x->d2 < y->d2) return 1;\n    if (x->d2 > y->d2) return -1;"),
     "topk_keep_k": ("int64_t keep = (k < nS) ? k : nS;", "int64_t keep = k;"),
+    "cosine_threshold_halved": ("const double e2 = 2.0 - 2.0 * c;", "const double e2 = 2.0 - c;"),
+    "norm_not_rooted": ("const float nr = (float)sqrt(s);", "const float nr = (float)s;"),
+    "norm_multiplies": ("o[k] = x[k] / nr;", "o[k] = x[k] * nr;"),
 }
 
 
