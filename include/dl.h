@@ -52,7 +52,10 @@ typedef enum dl_status {
 } dl_status;
 
 typedef enum dl_metric {
-    DL_METRIC_L2 = 0      /* squared Euclidean distance compared with eps^2 (Sec. 3.2) */
+    DL_METRIC_L2 = 0,     /* squared Euclidean distance compared with eps^2 (Sec. 3.2) */
+    DL_METRIC_COSINE = 1  /* cosine similarity on stores made by dl_store_normalize: eps is the
+                             threshold c in [-1, 1] and a pair matches iff the canonical D of
+                             the normalized rows is <= fl64(2 - 2c) (cos >= c for unit rows) */
 } dl_metric;
 
 typedef enum dl_precision {
@@ -111,6 +114,17 @@ void dl_join_opts_default(dl_join_opts *o);
 int dl_store_create(dl_store **out, const int64_t *ids, const float *feats, int64_t n, int32_t d,
                     int32_t where, void *cuda_stream);
 
+/*
+ * A new store holding the unit-normalized rows of `in`, for the cosine metric (a metric
+ * beyond the paper's Euclidean queries): same ids and the same caller row order, row
+ * x^ = fl32(x_k / n) with n = fl32(sqrt(sum_k x_k^2)), the sum in FP64 with k ascending and
+ * every addition rounded to nearest. The normalized FP32 rows are the ground truth of every
+ * cosine join on the new store. A row with a zero norm has no direction: DL_EINVAL and *out
+ * stays NULL. `in` is unchanged and may be destroyed afterwards. cuda_stream as for
+ * dl_store_create; the call returns when the new store is ready.
+ */
+int dl_store_normalize(const dl_store *in, dl_store **out, void *cuda_stream);
+
 /* Free a store. Joins that use it must have completed. NULL is accepted. */
 int dl_store_destroy(dl_store *s);
 
@@ -125,7 +139,8 @@ int dl_store_shape(const dl_store *s, int64_t *n, int32_t *d);
  * Epsilon-similarity join (Sec. 5 nested-loop semantics, Sec. 3.2 predicate):
  * every pair (r in R, s in S) with canonical D(r, s) <= eps*eps, as id pairs.
  * S == NULL is a self-join of R, in opts->self_mode. eps must be >= 0 and not
- * NaN; eps = +inf returns every pair. metric must be DL_METRIC_L2. opts may be
+ * NaN; eps = +inf returns every pair. With DL_METRIC_COSINE, eps is the cosine
+ * threshold c in [-1, 1] and both stores must come from dl_store_normalize. opts may be
  * NULL (defaults). On success *out holds the result (free with
  * dl_result_free); on DL_EOVERFLOW *out is also set so that the required
  * count can be read. The pair order is unspecified (the result is a set).
@@ -136,7 +151,9 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
 /*
  * Top-k join (Sec. 6.2 q1 generalised to k): for every row of Q, the min(k, |S|)
  * rows of S with the smallest canonical D, ordered by (D, S row index); ties
- * beyond the k-th are not returned. 1 <= k <= 1024.
+ * beyond the k-th are not returned. 1 <= k <= 1024. With DL_METRIC_COSINE (both
+ * stores from dl_store_normalize) these are the k most similar rows, and the
+ * distances returned are the canonical D of the normalized rows (2 - 2 cos).
  */
 int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric, int32_t k,
                  const dl_join_opts *opts, dl_result **out);

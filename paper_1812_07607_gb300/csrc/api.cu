@@ -361,12 +361,26 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
         set_error("dl_sim_join: R is NULL");
         return DL_EINVAL;
     }
-    if (metric != DL_METRIC_L2) {
+    double e2 = 0.0;   // the squared-L2 threshold the join decides against
+    if (metric == DL_METRIC_L2) {
+        if (std::isnan(eps) || eps < 0.0) {
+            set_error("dl_sim_join: eps must be >= 0 (got %g)", eps);
+            return DL_EINVAL;
+        }
+        e2 = eps * eps;
+    } else if (metric == DL_METRIC_COSINE) {
+        // eps is the cosine threshold c: on unit-normalized rows cos >= c is D <= 2 - 2c
+        if (!(eps >= -1.0 && eps <= 1.0)) {
+            set_error("dl_sim_join: the cosine threshold must lie in [-1, 1] (got %g)", eps);
+            return DL_EINVAL;
+        }
+        if (!R->unit || (S && !S->unit)) {
+            set_error("dl_sim_join: the cosine metric needs stores made by dl_store_normalize");
+            return DL_EINVAL;
+        }
+        e2 = 2.0 - 2.0 * eps;
+    } else {
         set_error("dl_sim_join: unsupported metric %d", metric);
-        return DL_EINVAL;
-    }
-    if (std::isnan(eps) || eps < 0.0) {
-        set_error("dl_sim_join: eps must be >= 0 (got %g)", eps);
         return DL_EINVAL;
     }
     dl_join_opts o;
@@ -416,7 +430,6 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
     }
 
     const int d = R->d;
-    const double e2 = eps * eps;
     PassCfg c;
     c.R = R;
     c.S = Sx;
@@ -426,7 +439,7 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
     c.BN = BN;
     c.e2 = e2;
     if (prec == DL_PREC_FP32_PLAIN) {
-        const float ef = (float)eps;
+        const float ef = (float)std::sqrt(e2);
         c.t_acc = ef * ef;
         c.t_rej = c.t_acc;
     } else {

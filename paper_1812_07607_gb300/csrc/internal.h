@@ -92,6 +92,7 @@ struct Store {
     int64_t hint_pairs = 0;  // last output size seen with this store as R (capacity hint)
     int64_t hint_band = 0;
     double hint_batch_rate = 0.0;   // batch calls: candidates per evaluated pair last seen against this store
+    bool unit = false;       // rows are the unit-normalized rows of another store (cosine metric)
 };
 
 // Create a store; gather == NULL orders rows by norm, else store row i is caller row gather[i].

@@ -707,6 +707,43 @@ int store_create_impl(dl_store **out, const int64_t *ids, const float *feats, in
     return DL_OK;
 }
 
+// ------------------------------------------------------------------ cosine metric
+// One warp per store row: the unit-normalized row, written at the caller's row index.
+//   n = fl32(sqrt(sum_k x_k^2)), the sum in FP64 with k ascending and each addition
+//   rounded to nearest (the products of two floats are exact in FP64); x^_k = fl32(x_k / n).
+// A row whose norm is zero has no direction: it is flagged and left zero.
+__global__ void __launch_bounds__(256) k_normalize_rows(const float *__restrict__ x32, const int64_t *__restrict__ ids,
+                                                        const int32_t *__restrict__ orig, int64_t n, int d,
+                                                        float *__restrict__ out, int64_t *__restrict__ out_ids,
+                                                        int *__restrict__ err)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * 8 + warp;
+    if (row >= n) return;
+    const float *xr = x32 + row * d;
+    double s = 0.0;
+    for (int k0 = 0; k0 < d; k0 += 32) {
+        const int k = k0 + lane;
+        double sq = 0.0;
+        if (k < d) {
+            const double v = (double)__ldg(xr + k);
+            sq = __dmul_rn(v, v);
+        }
+        const int lim = min(32, d - k0);
+        for (int l = 0; l < lim; ++l) s = __dadd_rn(s, __shfl_sync(0xffffffffu, sq, l));
+    }
+    const float nr = __double2float_rn(__dsqrt_rn(s));
+    const int64_t dst = orig[row];
+    float *o = out + dst * d;
+    if (!(nr > 0.0f)) {
+        for (int k = lane; k < d; k += 32) o[k] = 0.0f;
+        if (lane == 0) atomicOr(err, 1);
+    } else {
+        for (int k = lane; k < d; k += 32) o[k] = __fdiv_rn(__ldg(xr + k), nr);
+    }
+    if (lane == 0) out_ids[dst] = ids[row];
+}
+
 }  // namespace dl
 
 using namespace dl;
@@ -717,6 +754,59 @@ int dl_store_create(dl_store **out, const int64_t *ids, const float *feats, int6
                     void *cuda_stream)
 {
     return store_create_impl(out, ids, feats, n, d, where, cuda_stream, nullptr);
+}
+
+int dl_store_normalize(const dl_store *in, dl_store **out, void *cuda_stream)
+{
+    clear_error();
+    if (!in || !out) {
+        set_error("dl_store_normalize: NULL argument");
+        return DL_EINVAL;
+    }
+    *out = nullptr;
+    int dev = -1;
+    DL_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != in->device) {
+        set_error("dl_store_normalize: store lives on device %d but device %d is current", in->device, dev);
+        return DL_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int64_t n = in->n;
+    const int d = in->d;
+    void *tmp = nullptr;
+    const size_t b_x = align256(sizeof(float) * (size_t)std::max<int64_t>(n, 1) * d);
+    const size_t b_ids = align256(sizeof(int64_t) * (size_t)std::max<int64_t>(n, 1));
+    int rc = dev_alloc(&tmp, b_x + b_ids + 256, st);
+    if (rc) return rc;
+    float *xn = (float *)tmp;
+    int64_t *idn = (int64_t *)((char *)tmp + b_x);
+    int *d_err = (int *)((char *)tmp + b_x + b_ids);
+    cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess && n > 0) {
+        k_normalize_rows<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(in->x32, in->ids, in->orig, n, d, xn, idn, d_err);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    int h_err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        dev_free(tmp, st);
+        return cuda_fail(e, "dl_store_normalize");
+    }
+    if (h_err) {
+        dev_free(tmp, st);
+        set_error("dl_store_normalize: a row has a zero norm (no direction for the cosine metric)");
+        return DL_EINVAL;
+    }
+    dl_store *s = nullptr;
+    rc = store_create_impl(&s, idn, xn, n, d, DL_MEM_DEVICE, cuda_stream, nullptr);
+    cudaStreamSynchronize(st);
+    dev_free(tmp, st);
+    if (rc) return rc;
+    s->unit = true;
+    *out = s;
+    return DL_OK;
 }
 
 int dl_store_destroy(dl_store *s)

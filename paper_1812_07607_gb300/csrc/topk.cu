@@ -680,7 +680,12 @@ extern "C" int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric
         set_error("dl_topk_join: NULL store");
         return DL_EINVAL;
     }
-    if (metric != DL_METRIC_L2) {
+    if (metric == DL_METRIC_COSINE) {   // the most similar rows are the nearest normalized rows
+        if (!Q->unit || !S->unit) {
+            set_error("dl_topk_join: the cosine metric needs stores made by dl_store_normalize");
+            return DL_EINVAL;
+        }
+    } else if (metric != DL_METRIC_L2) {
         set_error("dl_topk_join: unsupported metric %d", metric);
         return DL_EINVAL;
     }

@@ -21,7 +21,8 @@ DL_OK, DL_EINVAL, DL_ENOMEM, DL_EOVERFLOW, DL_EAGAIN, DL_ETIMEOUT, DL_ECUDA, DL_
 STATUS_NAMES = {0: "DL_OK", 1: "DL_EINVAL", 2: "DL_ENOMEM", 3: "DL_EOVERFLOW", 4: "DL_EAGAIN",
                 5: "DL_ETIMEOUT", 6: "DL_ECUDA", 7: "DL_ECANCELED", 8: "DL_ENOMEM_ADMIT",
                 9: "DL_EFAILED", 10: "DL_EUNSUPPORTED"}
-DL_METRIC_L2 = 0
+DL_METRIC_L2, DL_METRIC_COSINE = 0, 1
+METRICS = {"l2": DL_METRIC_L2, "cosine": DL_METRIC_COSINE}
 DL_PREC_AUTO, DL_PREC_BF16, DL_PREC_FP8E4M3, DL_PREC_FP32, DL_PREC_FP32_PLAIN = range(5)
 PRECISIONS = {"auto": 0, "bf16": 1, "fp8": 2, "fp32": 3, "fp32_plain": 4}
 DL_MEM_HOST, DL_MEM_DEVICE = 0, 1
@@ -34,7 +35,7 @@ EXPORTS = [
     "dl_result_stats", "dl_result_free", "dl_last_error", "dl_version", "dl_kernel_launches",
     "dl_sim_join_noalloc", "dl_batch_join", "dl_result_request_pairs", "dl_result_request_topk",
     "dl_server_create", "dl_submit", "dl_poll", "dl_cancel", "dl_server_get_stats", "dl_server_destroy",
-    "dl_debug_scores",
+    "dl_debug_scores", "dl_store_normalize",
 ]
 
 
@@ -95,6 +96,8 @@ def load(path: str | None = None):
     L.dl_store_create.argtypes = [pp, vp, vp, i64, i32, i32, vp]
     L.dl_store_destroy.argtypes = [vp]
     L.dl_store_shape.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)]
+    L.dl_store_normalize.argtypes = [vp, pp, vp]
+    L.dl_store_normalize.restype = ctypes.c_int
     L.dl_sim_join.argtypes = [vp, vp, i32, f64, ctypes.POINTER(dl_join_opts), pp]
     L.dl_topk_join.argtypes = [vp, vp, i32, i32, ctypes.POINTER(dl_join_opts), pp]
     L.dl_result_count.argtypes = [vp, ctypes.POINTER(i64)]
@@ -198,6 +201,15 @@ class Store:
     def handle(self):
         return self._h
 
+    def normalized(self, stream=None) -> "Store":
+        """dl_store_normalize: a new store of the unit-normalized rows (for metric="cosine")."""
+        h = ctypes.c_void_p()
+        _check(load().dl_store_normalize(self._h, ctypes.byref(h), _stream_handle(stream)), "dl_store_normalize")
+        out = Store.__new__(Store)
+        out._h = h
+        out.n, out.d = self.n, self.d
+        return out
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             load().dl_store_destroy(self._h)
@@ -296,11 +308,12 @@ def make_opts(precision="auto", self_mode="upper", out_capacity=0, stream=None, 
 
 
 def sim_join(R: Store, S: Store | None, eps: float, precision="auto", self_mode="upper", out_capacity=0,
-             stream=None, tile_n=0, timing=False, allow_overflow=False) -> Result:
-    """dl_sim_join: every pair with canonical squared L2 distance <= eps^2."""
+             stream=None, tile_n=0, timing=False, allow_overflow=False, metric="l2") -> Result:
+    """dl_sim_join: every pair with canonical squared L2 distance <= eps^2, or with
+    metric="cosine" (stores from Store.normalized()) every pair with cosine >= eps."""
     o = make_opts(precision, self_mode, out_capacity, stream, tile_n, timing)
     h = ctypes.c_void_p()
-    rc = load().dl_sim_join(R.handle, None if S is None else S.handle, DL_METRIC_L2, float(eps),
+    rc = load().dl_sim_join(R.handle, None if S is None else S.handle, METRICS[metric], float(eps),
                             ctypes.byref(o), ctypes.byref(h))
     if rc == DL_EOVERFLOW and allow_overflow:
         return Result(h)
@@ -310,11 +323,11 @@ def sim_join(R: Store, S: Store | None, eps: float, precision="auto", self_mode=
     return Result(h)
 
 
-def topk_join(Q: Store, S: Store, k: int, precision="auto", stream=None, timing=False) -> Result:
+def topk_join(Q: Store, S: Store, k: int, precision="auto", stream=None, timing=False, metric="l2") -> Result:
     """dl_topk_join: the k nearest store rows of every query row, by (canonical D, row)."""
     o = make_opts(precision, "upper", 0, stream, 0, timing)
     h = ctypes.c_void_p()
-    rc = load().dl_topk_join(Q.handle, S.handle, DL_METRIC_L2, int(k), ctypes.byref(o), ctypes.byref(h))
+    rc = load().dl_topk_join(Q.handle, S.handle, METRICS[metric], int(k), ctypes.byref(o), ctypes.byref(h))
     _check(rc, "dl_topk_join")
     return Result(h)
 
