@@ -69,6 +69,23 @@ def load(path: str | None = None):
     lib.oracle_topk.restype = ctypes.c_int32
     lib.oracle_topk.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int32,
                                 ctypes.c_int32, i64p, f64p]
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    lib.oracle_l1dist.restype = ctypes.c_double
+    lib.oracle_l1dist.argtypes = [f32p, f32p, ctypes.c_int32]
+    lib.oracle_chi2dist.restype = ctypes.c_double
+    lib.oracle_chi2dist.argtypes = [f32p, f32p, ctypes.c_int32]
+    lib.oracle_hist_join.restype = ctypes.c_int64
+    lib.oracle_hist_join.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_double, ctypes.c_int32, i64p, i64p, ctypes.c_int64]
+    lib.oracle_hist_dist_block.restype = None
+    lib.oracle_hist_dist_block.argtypes = [f32p, ctypes.c_int64, ctypes.c_int64, f32p, ctypes.c_int64,
+                                           ctypes.c_int32, ctypes.c_int32, f64p]
+    lib.oracle_color_hist.restype = ctypes.c_int64
+    lib.oracle_color_hist.argtypes = [u8p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, i32p, ctypes.c_int64,
+                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, f32p]
+    lib.oracle_components.restype = ctypes.c_int64
+    lib.oracle_components.argtypes = [ctypes.c_int64, i64p, i64p, ctypes.c_int64, i64p]
     if path == _LIB_PATH:
         _lib = lib
     return lib
@@ -80,6 +97,8 @@ def _f32(a):
 
 
 MODE_RXS, MODE_SELF_UPPER, MODE_SELF_FULL = 0, 1, 2
+METRIC_L1, METRIC_CHI2 = 1, 2
+DEDUP_ALL, DEDUP_FILTER_MATCH, DEDUP_MATCH_FILTER = 0, 1, 2
 
 
 class Oracle:
@@ -155,6 +174,94 @@ class Oracle:
             if n <= cap:
                 return np.stack([out_r[:n], out_s[:n]], axis=1)
             cap = int(n)
+
+    def hist_dist(self, q, x, metric: int) -> float:
+        q, qp = _f32(q)
+        x, xp = _f32(x)
+        f = self.lib.oracle_l1dist if metric == METRIC_L1 else self.lib.oracle_chi2dist
+        return float(f(qp, xp, int(q.shape[-1])))
+
+    def hist_dist_block(self, R, S, metric: int) -> np.ndarray:
+        R, Rp = _f32(R)
+        S, Sp = _f32(S)
+        out = np.empty((R.shape[0], S.shape[0]), dtype=np.float64)
+        self.lib.oracle_hist_dist_block(Rp, 0, R.shape[0], Sp, S.shape[0], R.shape[1], int(metric),
+                                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return out
+
+    def hist_join(self, R, S=None, eps: float = 0.0, metric: int = METRIC_L1, mode: int | None = None) -> np.ndarray:
+        """Row-index pairs with canonical L1 (metric 1) or chi-square (metric 2) distance <= eps."""
+        R, Rp = _f32(R)
+        if mode is None:
+            mode = MODE_RXS if S is not None else MODE_SELF_UPPER
+        if S is None:
+            S, Sp, nS = R, Rp, R.shape[0]
+        else:
+            S, Sp = _f32(S)
+            nS = S.shape[0]
+        i64 = ctypes.POINTER(ctypes.c_int64)
+        cap = 1 << 16
+        while True:
+            out_r = np.empty(cap, dtype=np.int64)
+            out_s = np.empty(cap, dtype=np.int64)
+            n = self.lib.oracle_hist_join(Rp, R.shape[0], Sp, nS, R.shape[1], int(metric), float(eps), mode,
+                                          out_r.ctypes.data_as(i64), out_s.ctypes.data_as(i64), cap)
+            if n <= cap:
+                return np.stack([out_r[:n], out_s[:n]], axis=1)
+            cap = int(n)
+
+    def color_hist(self, frames, boxes, bins) -> np.ndarray:
+        """Histograms [nb, br*bg*bb] of the boxes {frame, x0, y0, x1, y1} of frames [nF, H, W, 3] (uint8)."""
+        frames = np.ascontiguousarray(frames, dtype=np.uint8)
+        boxes = np.ascontiguousarray(boxes, dtype=np.int32).reshape(-1, 5)
+        br, bg, bb = (int(b) for b in bins)
+        out = np.empty((boxes.shape[0], br * bg * bb), dtype=np.float32)
+        rc = self.lib.oracle_color_hist(frames.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), frames.shape[0],
+                                        frames.shape[1], frames.shape[2],
+                                        boxes.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), boxes.shape[0],
+                                        br, bg, bb, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        if rc < 0:
+            raise MemoryError("oracle_color_hist: allocation failed")
+        if rc > 0:
+            raise ValueError(f"box {rc - 1} is invalid")
+        return out
+
+    def components(self, n: int, pairs) -> tuple[np.ndarray, int]:
+        """(label int64 [n], number of components): label = smallest row index of the component."""
+        pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int64).reshape(-1, 2))
+        a = np.ascontiguousarray(pairs[:, 0])
+        b = np.ascontiguousarray(pairs[:, 1])
+        label = np.empty(n, dtype=np.int64)
+        i64 = ctypes.POINTER(ctypes.c_int64)
+        c = self.lib.oracle_components(int(n), a.ctypes.data_as(i64), b.ctypes.data_as(i64), a.shape[0],
+                                       label.ctypes.data_as(i64))
+        if c < 0:
+            raise ValueError("an edge names a row outside [0, n)")
+        return label, int(c)
+
+    def dedup(self, X, eps: float, labels=None, target: int = 0, plan: int = DEDUP_ALL):
+        """q4 (Sec. 6.2, Sec. 7.5): (component label per row, number of distinct objects).
+
+        DEDUP_ALL: components of the epsilon self-join of every row.
+        DEDUP_FILTER_MATCH: keep the rows whose label is `target`, join them, count their
+          components; the other rows get label -1.
+        DEDUP_MATCH_FILTER: join every row, then count the components holding at least
+          one row whose label is `target`.
+        """
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        n = X.shape[0]
+        if plan == DEDUP_FILTER_MATCH:
+            keep = np.flatnonzero(np.asarray(labels) == target)
+            pairs = keep[self.join(X[keep], None, eps, MODE_SELF_UPPER)] if keep.size else np.empty((0, 2), np.int64)
+            lab, _ = self.components(n, pairs)
+            out = np.full(n, -1, dtype=np.int64)
+            out[keep] = lab[keep]
+            return out, int(np.unique(lab[keep]).size)
+        lab, c = self.components(n, self.join(X, None, eps, MODE_SELF_UPPER))
+        if plan == DEDUP_ALL:
+            return lab, c
+        hit = np.asarray(labels) == target
+        return lab, int(np.unique(lab[hit]).size)
 
     def topk(self, Q, S, k: int):
         """(idx int64 [nQ, k], d2 float64 [nQ, k]); unused slots are -1."""

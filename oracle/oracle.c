@@ -29,6 +29,18 @@
  *     the sum in FP64 with k ascending, x^_k = fl32(x_k / n); a pair matches
  *     iff the canonical D(q^, x^) <= fl64(2 - 2c), the L2 form of cos >= c for
  *     unit vectors. Rows with a zero norm have no direction and are rejected.
+ *   - L1 and chi-square histogram distances (the other further metrics): for
+ *     k ascending, t = (double)q_k - (double)x_k, s = s + |t| (L1), or
+ *     u = (double)q_k + (double)x_k and, where u > 0, s = s + (t*t)/u
+ *     (chi-square, no factor 1/2); every operation rounded to nearest. A pair
+ *     matches iff s <= eps (these distances are not squared).
+ *   - colour histograms (Sec. 4.1 transformers): a patch is a box of a frame of
+ *     8-bit interleaved RGB pixels; channel value v falls in bin floor(v*b/256)
+ *     of its channel's b bins, the joint bin is (r*bg + g)*bb + b, and the
+ *     histogram is count / (pixels in the box), one FP32 division per bin.
+ *   - q4 deduplication (Sec. 6.2 q4, Sec. 7.5): the distinct objects are the
+ *     connected components of the self-join's pairs; each row is labelled with
+ *     the smallest row index of its component.
  *
  * Parity pins (tests/test_oracle_pins.py): exact rational brute force, integer
  * grid and one-hot closed forms, symmetry, zero self-distance, monotonicity in
@@ -180,4 +192,134 @@ int64_t oracle_cosine_join(const float *Rn, int64_t nR, const float *Sn, int64_t
         }
     }
     return cnt;
+}
+
+/* Canonical L1 distance: k ascending, FP64, each operation rounded to nearest. */
+double oracle_l1dist(const float *q, const float *x, int32_t d)
+{
+    double s = 0.0;
+    for (int32_t k = 0; k < d; ++k) {
+        double t = (double)q[k] - (double)x[k];
+        s = s + fabs(t);
+    }
+    return s;
+}
+
+/* Canonical chi-square distance sum_k (q_k - x_k)^2 / (q_k + x_k); bins with q_k + x_k == 0 add nothing. */
+double oracle_chi2dist(const float *q, const float *x, int32_t d)
+{
+    double s = 0.0;
+    for (int32_t k = 0; k < d; ++k) {
+        double t = (double)q[k] - (double)x[k];
+        double u = (double)q[k] + (double)x[k];
+        if (u > 0.0) s = s + (t * t) / u;
+    }
+    return s;
+}
+
+/*
+ * Nested-loop join with a histogram distance: metric 1 = L1, 2 = chi-square;
+ * a pair matches iff its distance <= eps. Modes and output as in oracle_join.
+ */
+int64_t oracle_hist_join(const float *R, int64_t nR, const float *S, int64_t nS, int32_t d, int32_t metric,
+                         double eps, int32_t mode, int64_t *out_r, int64_t *out_s, int64_t cap)
+{
+    const float *T = (mode == 0) ? S : R;
+    const int64_t nT = (mode == 0) ? nS : nR;
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < nR; ++i) {
+        int64_t j0 = (mode == 1) ? i + 1 : 0;
+        for (int64_t j = j0; j < nT; ++j) {
+            const float *q = R + i * (int64_t)d, *x = T + j * (int64_t)d;
+            double s = (metric == 1) ? oracle_l1dist(q, x, d) : oracle_chi2dist(q, x, d);
+            if (s <= eps) {
+                if (cnt < cap) {
+                    out_r[cnt] = i;
+                    out_s[cnt] = j;
+                }
+                ++cnt;
+            }
+        }
+    }
+    return cnt;
+}
+
+/* Histogram distances of rows [r0, r1) of R against every row of S, row-major. */
+void oracle_hist_dist_block(const float *R, int64_t r0, int64_t r1, const float *S, int64_t nS, int32_t d,
+                            int32_t metric, double *out)
+{
+    for (int64_t i = r0; i < r1; ++i)
+        for (int64_t j = 0; j < nS; ++j) {
+            const float *q = R + i * (int64_t)d, *x = S + j * (int64_t)d;
+            out[(i - r0) * nS + j] = (metric == 1) ? oracle_l1dist(q, x, d) : oracle_chi2dist(q, x, d);
+        }
+}
+
+/*
+ * Colour-histogram transformer (Sec. 4.1). frames is [nF][H][W][3] 8-bit RGB;
+ * box i is boxes[5i..5i+4] = {frame, x0, y0, x1, y1}, the half-open pixel
+ * rectangle [x0, x1) x [y0, y1). out is [nb][br*bg*bb]. Returns 0, or the
+ * 1-based index of the first invalid box (out of the frame, empty, or more
+ * than 2^24 pixels, where the count would not convert to FP32 exactly).
+ */
+int64_t oracle_color_hist(const uint8_t *frames, int64_t nF, int32_t H, int32_t W, const int32_t *boxes,
+                          int64_t nb, int32_t br, int32_t bg, int32_t bb, float *out)
+{
+    const int32_t d = br * bg * bb;
+    int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * (size_t)d);
+    if (!cnt) return -1;
+    for (int64_t i = 0; i < nb; ++i) {
+        const int32_t *bx = boxes + 5 * i;
+        const int64_t f = bx[0];
+        const int32_t x0 = bx[1], y0 = bx[2], x1 = bx[3], y1 = bx[4];
+        if (f < 0 || f >= nF || x0 < 0 || y0 < 0 || x1 > W || y1 > H || x0 >= x1 || y0 >= y1 ||
+            (int64_t)(x1 - x0) * (y1 - y0) > (1 << 24)) {
+            free(cnt);
+            return i + 1;
+        }
+        for (int32_t k = 0; k < d; ++k) cnt[k] = 0;
+        for (int32_t y = y0; y < y1; ++y)
+            for (int32_t x = x0; x < x1; ++x) {
+                const uint8_t *px = frames + ((f * H + y) * (int64_t)W + x) * 3;
+                const int32_t r = (px[0] * br) >> 8, g = (px[1] * bg) >> 8, b = (px[2] * bb) >> 8;
+                cnt[(r * bg + g) * bb + b] += 1;
+            }
+        const float area = (float)((int64_t)(x1 - x0) * (y1 - y0));
+        for (int32_t k = 0; k < d; ++k) out[i * d + k] = (float)cnt[k] / area;
+    }
+    free(cnt);
+    return 0;
+}
+
+/*
+ * Connected components of the graph on rows 0..n-1 with edges (a[e], b[e]):
+ * label[i] = the smallest row index of i's component. Plain label propagation:
+ * every row starts with its own index, each pass gives both ends of every edge
+ * the smaller of their labels, until a pass changes nothing. Returns the
+ * number of components, or -1 if an edge names a row outside [0, n).
+ */
+int64_t oracle_components(int64_t n, const int64_t *a, const int64_t *b, int64_t m, int64_t *label)
+{
+    for (int64_t e = 0; e < m; ++e)
+        if (a[e] < 0 || a[e] >= n || b[e] < 0 || b[e] >= n) return -1;
+    for (int64_t i = 0; i < n; ++i) label[i] = i;
+    int changed = 1;
+    while (changed) {
+        changed = 0;
+        for (int64_t e = 0; e < m; ++e) {
+            const int64_t la = label[a[e]], lb = label[b[e]];
+            const int64_t lo = (la < lb) ? la : lb;
+            if (label[a[e]] != lo) {
+                label[a[e]] = lo;
+                changed = 1;
+            }
+            if (label[b[e]] != lo) {
+                label[b[e]] = lo;
+                changed = 1;
+            }
+        }
+    }
+    int64_t c = 0;
+    for (int64_t i = 0; i < n; ++i) c += (label[i] == i);
+    return c;
 }

@@ -120,6 +120,7 @@ class JoinWorkload:
     r_ids: np.ndarray        # int64 [nR]
     s_ids: np.ndarray | None
     eps: float
+    groups: np.ndarray | None = None   # int64 [nR]: the object (centroid) each row is a view of
 
     @property
     def d(self) -> int:
@@ -152,11 +153,11 @@ def self_clustered_262k(seed: int = SEED_BASE + 1, n: int = 262144, d: int = 128
                         eps: float | None = None) -> JoinWorkload:
     """Self-join of 262,144 d=128 histograms: 8,192 Dirichlet centroids + N(0, 0.01^2) jitter."""
     g = rng(seed)
-    X, _ = clustered_histograms(g, n, d, n_centroids, sigma)
+    X, groups = clustered_histograms(g, n, d, n_centroids, sigma)
     ids = patch_ids(g, n)
     if eps is None:
         eps = eps_table().get(f"self_clustered_262k:{seed}:{n}:{d}:{n_centroids}")
-    return JoinWorkload("self_clustered_262k", X, None, ids, None, eps)
+    return JoinWorkload("self_clustered_262k", X, None, ids, None, eps, groups)
 
 
 def clustered_queries(n: int, seed_q: int, store_seed: int, d: int, n_centroids: int, sigma: float,
@@ -301,3 +302,77 @@ def sample_rows(n: int, k: int, seed: int) -> np.ndarray:
 # Row sample of the 1,048,576 x 1,048,576 d=512 join whose exact pair set is stored as a digest.
 UNIT_MIXTURE_SAMPLE_SEED = SEED_BASE + 103
 UNIT_MIXTURE_SAMPLE_ROWS = 16384
+
+
+# ---------------------------------------------------------------------------------------------
+# detector output for q4 and raw frames for the colour-histogram transformer
+# ---------------------------------------------------------------------------------------------
+
+def object_labels(g: np.random.Generator, groups: np.ndarray, n_groups: int,
+                  classes=(0.45, 0.45, 0.10), flip: float = 0.08) -> np.ndarray:
+    """Detector labels of patches (q4): each object has a class (0 person, 1 vehicle, 2 other);
+    each patch shows its object's class, except with probability `flip`, where the detector
+    reports a uniformly drawn class instead. int32 [n]."""
+    cls = g.choice(len(classes), size=n_groups, p=np.asarray(classes, dtype=np.float64))
+    lab = cls[groups].astype(np.int32)
+    f = g.random(len(groups)) < flip
+    lab[f] = g.integers(0, len(classes), size=int(f.sum()), dtype=np.int32)
+    return lab
+
+
+def traffic_frames(g: np.random.Generator, n_frames: int, H: int = 1080, W: int = 1920,
+                   block: int = 24, noise: int = 6) -> np.ndarray:
+    """8-bit RGB frames [n, H, W, 3] (interleaved, row-major): piecewise-constant colour blocks
+    (road, vehicles, sky stand-ins) plus uniform integer noise in [-noise, noise], clipped."""
+    out = np.empty((n_frames, H, W, 3), dtype=np.uint8)
+    bh, bw = -(-H // block), -(-W // block)
+    for f in range(n_frames):
+        base = g.integers(0, 256, size=(bh, bw, 3), dtype=np.int16)
+        img = np.repeat(np.repeat(base, block, axis=0), block, axis=1)[:H, :W]
+        img = img + g.integers(-noise, noise + 1, size=(H, W, 3), dtype=np.int16)
+        np.clip(img, 0, 255, out=img)
+        out[f] = img.astype(np.uint8)
+    return out
+
+
+DETECTOR_BOX_SIDES = np.array([16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512], dtype=np.int64)
+DETECTOR_BOX_WEIGHTS = np.array([4, 6, 8, 9, 9, 8, 6, 4, 3, 2, 1], dtype=np.float64)
+
+
+def detector_boxes(g: np.random.Generator, n_frames: int, H: int, W: int, per_frame: int) -> np.ndarray:
+    """Object-detector boxes {frame, x0, y0, x1, y1} (int32 [n_frames * per_frame, 5], half-open):
+    sides from a discrete log-spaced mix (16 to 512 pixels, small boxes most common), each
+    jittered by up to a quarter, aspect 1:2 to 2:1, placed uniformly inside the frame."""
+    n = n_frames * per_frame
+    p = DETECTOR_BOX_WEIGHTS / DETECTOR_BOX_WEIGHTS.sum()
+    side = g.choice(DETECTOR_BOX_SIDES, size=n, p=p)
+    w = side + g.integers(-(side // 4), side // 4 + 1)
+    h = (w * g.integers(2, 9, size=n)) // 4
+    w = np.clip(w, 1, W)
+    h = np.clip(h, 1, H)
+    x0 = g.integers(0, W - w + 1)
+    y0 = g.integers(0, H - h + 1)
+    f = np.repeat(np.arange(n_frames, dtype=np.int64), per_frame)
+    return np.stack([f, x0, y0, x0 + w, y0 + h], axis=1).astype(np.int32)
+
+
+@dataclass
+class FrameWorkload:
+    name: str
+    frames: np.ndarray       # uint8 [n_frames, H, W, 3]
+    boxes: np.ndarray        # int32 [n_boxes, 5]
+    bins: tuple              # (br, bg, bb)
+
+    @property
+    def pixels(self) -> int:
+        b = self.boxes.astype(np.int64)
+        return int(((b[:, 3] - b[:, 1]) * (b[:, 4] - b[:, 2])).sum())
+
+
+def traffic_boxes_1080p(seed: int = SEED_BASE + 5, n_frames: int = 64, per_frame: int = 64,
+                        bins=(8, 4, 4)) -> FrameWorkload:
+    """64 1080p frames with 64 detector boxes each, histograms of (8, 4, 4) = 128 bins."""
+    g = rng(seed)
+    frames = traffic_frames(g, n_frames)
+    boxes = detector_boxes(g, n_frames, frames.shape[1], frames.shape[2], per_frame)
+    return FrameWorkload("traffic_boxes_1080p", frames, boxes, tuple(bins))

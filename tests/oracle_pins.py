@@ -14,7 +14,14 @@ disagrees with something the paper or the mathematics fixes:
     union laws, top-k ordering and top-k/join consistency;
   * the cosine metric: the normalized rows against exact rational arithmetic
     (round-to-nearest quotients, unit norm within the rounding bound, invariance
-    under power-of-two scaling) and the cosine join against the exact cosine.
+    under power-of-two scaling) and the cosine join against the exact cosine;
+  * the L1 and chi-square histogram distances against exact rationals, their
+    one-hot and histogram-intersection closed forms, symmetry and chi2 <= L1;
+  * the colour-histogram transformer against the hand-derived fixture
+    tests/golden/color_hist_small.txt, the uniform-binning definition at every
+    8-bit value, count conservation, box additivity and pixel-order invariance;
+  * connected components against scipy's graph routine and closed forms (paths,
+    isolated rows), and the q4 plans on a hand-built example.
 
 The same suite runs against deliberately broken copies of the oracle
 (tests/test_oracle_mutants.py) to show that a plausible slip fails a pin.
@@ -28,6 +35,7 @@ from fractions import Fraction
 
 import numpy as np
 
+import oracle
 from oracle import MODE_RXS, MODE_SELF_FULL, MODE_SELF_UPPER
 from paper_1812_07607_gb300 import workloads as W
 
@@ -359,6 +367,279 @@ def pin_cosine_join_matches_exact(orc):
                 assert (i, j) not in got, (i, j)
 
 
+# ----------------------------------------------------------------------------------------
+# L1 / chi-square histogram distances
+# ----------------------------------------------------------------------------------------
+
+def exact_l1(q, x) -> Fraction:
+    return sum((abs(Fraction(a) - Fraction(b)) for a, b in zip(q.tolist(), x.tolist())), Fraction(0))
+
+
+def exact_chi2(q, x) -> Fraction:
+    s = Fraction(0)
+    for a, b in zip(q.tolist(), x.tolist()):
+        fa, fb = Fraction(a), Fraction(b)
+        if fa + fb > 0:
+            s += (fa - fb) ** 2 / (fa + fb)
+    return s
+
+
+def _nonneg_rows(g, n, d):
+    return np.abs(W.mixed_magnitude_rows(g, n, d)).astype(np.float32)
+
+
+def pin_hist_dist_within_rounding_of_exact(orc):
+    """|L1_64 - L1| <= (d+2) 2^-53 L1 and |chi2_64 - chi2| <= (d+6) 2^-53 chi2 (standard bounds)."""
+    g = _g(31)
+    for d in (1, 2, 5, 16, 33):
+        for gen in (_nonneg_rows, lambda g, n, d: W.dirichlet_histograms(g, n, d)):
+            X = gen(g, 5, d)
+            for i in range(X.shape[0]):
+                for j in range(X.shape[0]):
+                    for metric, ex, slack in ((oracle.METRIC_L1, exact_l1, d + 2), (oracle.METRIC_CHI2, exact_chi2, d + 6)):
+                        D = ex(X[i], X[j])
+                        got = orc.hist_dist(X[i], X[j], metric)
+                        if D == 0:
+                            assert got == 0.0, (metric, d, i, j, got)
+                        else:
+                            assert abs(Fraction(got) - D) <= Fraction(slack, 2**53) * D, (metric, d, i, j, got, float(D))
+
+
+def _thr_between(values, lo_rank: int):
+    """A threshold strictly inside a wide gap of the exact values (no distance near it)."""
+    vals = sorted(set(values))
+    for r in range(max(0, lo_rank), len(vals) - 1):
+        a, b = vals[r], vals[r + 1]
+        if b - a > Fraction(1, 10**6) * max(b, Fraction(1, 10**30)):
+            t = float((a + b) / 2)
+            if a < Fraction(t) < b:
+                return t, Fraction(t)
+    raise AssertionError("no usable gap")
+
+
+def pin_hist_join_matches_exact_rational(orc):
+    """The L1 / chi-square joins (all modes) equal the exact-rational nested loop on tiny inputs."""
+    g = _g(32)
+    for metric, ex in ((oracle.METRIC_L1, exact_l1), (oracle.METRIC_CHI2, exact_chi2)):
+        for d, nR, nS in ((1, 7, 9), (6, 13, 11), (12, 9, 14)):
+            R = _nonneg_rows(g, nR, d) if d != 12 else W.dirichlet_histograms(g, nR, d)
+            S = _nonneg_rows(g, nS, d) if d != 12 else W.dirichlet_histograms(g, nS, d)
+            M = [[ex(R[i], S[j]) for j in range(nS)] for i in range(nR)]
+            vals = [v for row in M for v in row]
+            for rank in (0, len(vals) // 5, len(vals) // 2):
+                t, ft = _thr_between(vals, rank)
+                want = {(i, j) for i in range(nR) for j in range(nS) if M[i][j] <= ft}
+                assert pair_set(orc.hist_join(R, S, t, metric, MODE_RXS)) == want, (metric, d, rank)
+            MS = [[ex(R[i], R[j]) for j in range(nR)] for i in range(nR)]
+            t, ft = _thr_between([MS[i][j] for i in range(nR) for j in range(nR) if i != j], nR)
+            up = {(i, j) for i in range(nR) for j in range(i + 1, nR) if MS[i][j] <= ft}
+            full = {(i, j) for i in range(nR) for j in range(nR) if MS[i][j] <= ft}
+            assert pair_set(orc.hist_join(R, None, t, metric, MODE_SELF_UPPER)) == up, (metric, d)
+            assert pair_set(orc.hist_join(R, None, t, metric, MODE_SELF_FULL)) == full, (metric, d)
+
+
+def pin_hist_closed_forms(orc):
+    """One-hot rows, histogram intersection, chi2(h, 0) = sum h, symmetry, chi2 <= L1."""
+    d = 10
+    E = np.eye(d, dtype=np.float32)
+    for metric in (oracle.METRIC_L1, oracle.METRIC_CHI2):
+        for i in range(d):
+            for j in range(d):
+                assert orc.hist_dist(E[i], E[j], metric) == (0.0 if i == j else 2.0), (metric, i, j)
+        # distinct one-hot rows are exactly 2 apart: the inclusive threshold 2 keeps every pair
+        assert len(orc.hist_join(E, None, 2.0, metric, MODE_SELF_UPPER)) == d * (d - 1) // 2
+        assert len(orc.hist_join(E, None, float(np.nextafter(2.0, 0.0)), metric, MODE_SELF_UPPER)) == 0
+    g = _g(33)
+    # histograms on the 2^-10 grid summing to exactly 1: every FP64 step is exact
+    for _ in range(40):
+        a = g.multinomial(1024, g.dirichlet(np.full(d, 0.7))).astype(np.float32) / np.float32(1024)
+        b = g.multinomial(1024, g.dirichlet(np.full(d, 0.7))).astype(np.float32) / np.float32(1024)
+        inter = float(np.minimum(a, b).astype(np.float64).sum())
+        assert orc.hist_dist(a, b, oracle.METRIC_L1) == 2.0 - 2.0 * inter
+        assert orc.hist_dist(a, np.zeros(d, np.float32), oracle.METRIC_CHI2) == 1.0
+        assert orc.hist_dist(np.zeros(d, np.float32), b, oracle.METRIC_CHI2) == 1.0
+    X = np.concatenate([_nonneg_rows(g, 6, 9), W.dirichlet_histograms(g, 6, 9)])
+    for i in range(X.shape[0]):
+        for j in range(X.shape[0]):
+            l1 = orc.hist_dist(X[i], X[j], oracle.METRIC_L1)
+            c2 = orc.hist_dist(X[i], X[j], oracle.METRIC_CHI2)
+            assert l1 == orc.hist_dist(X[j], X[i], oracle.METRIC_L1)
+            assert c2 == orc.hist_dist(X[j], X[i], oracle.METRIC_CHI2)
+            assert c2 <= l1 * (1 + 30 * 2.0**-53), (i, j, c2, l1)
+
+
+# ----------------------------------------------------------------------------------------
+# colour-histogram transformer
+# ----------------------------------------------------------------------------------------
+
+HIST_GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "color_hist_small.txt")
+
+
+def read_hist_golden(path=HIST_GOLDEN):
+    frames = boxes = None
+    cases, bins = [], None
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if not line:
+            continue
+        tok = line.split()
+        if tok[0] == "frames":
+            nF, H, Wd = map(int, tok[1:4])
+            frames = np.zeros((nF, H, Wd, 3), dtype=np.uint8)
+            boxes = []
+        elif tok[0] == "pixels":
+            f, y = int(tok[1]), int(tok[2])
+            for x, px in enumerate(tok[4:]):
+                frames[f, y, x] = [int(v) for v in px.split(",")]
+        elif tok[0] == "box":
+            boxes.append([int(v) for v in tok[1:6]])
+        elif tok[0] == "bins":
+            bins = tuple(int(v) for v in tok[1:4])
+            cases.append((bins, {}))
+        elif tok[0] == "counts":
+            cases[-1][1][int(tok[1])] = [int(v) for v in tok[3:]]
+    return frames, np.array(boxes, dtype=np.int32), cases
+
+
+def pin_color_hist_golden_fixture(orc):
+    """The hand-derived fixture: every box's histogram is its hand count over its area."""
+    frames, boxes, cases = read_hist_golden()
+    for bins, counts in cases:
+        got = orc.color_hist(frames, boxes, bins)
+        for b, cnt in counts.items():
+            x0, y0, x1, y1 = boxes[b, 1:]
+            area = np.float32((x1 - x0) * (y1 - y0))
+            want = np.array(cnt, dtype=np.float32) / area
+            assert np.array_equal(got[b], want), (bins, b, got[b], want)
+
+
+def pin_color_hist_binning_definition(orc):
+    """Each 8-bit value lands in the bin j with j*256/b <= v < (j+1)*256/b, channel by channel."""
+    v = np.arange(256, dtype=np.uint8)
+    for b in (1, 2, 3, 5, 7, 8, 16, 256):
+        for ch, bins in ((0, (b, 1, 1)), (1, (1, b, 1)), (2, (1, 1, b))):
+            frames = np.zeros((1, 1, 256, 3), dtype=np.uint8)
+            frames[0, 0, :, ch] = v
+            boxes = np.array([[0, x, 0, x + 1, 1] for x in range(256)], dtype=np.int32)
+            got = orc.color_hist(frames, boxes, bins)
+            for x in range(256):
+                j = [jj for jj in range(b) if Fraction(jj * 256, b) <= x < Fraction((jj + 1) * 256, b)]
+                assert len(j) == 1
+                want = np.zeros(b, dtype=np.float32)
+                want[j[0]] = 1.0
+                assert np.array_equal(got[x], want), (b, ch, x)
+
+
+def pin_color_hist_invariants(orc):
+    """Counts sum to the area, adjacent boxes add up, pixel order inside a frame does not matter,
+    a one-colour frame is one-hot at its colour's bin."""
+    g = _g(34)
+    nF, H, Wd = 3, 13, 21
+    frames = g.integers(0, 256, size=(nF, H, Wd, 3), dtype=np.uint8)
+    bins = (4, 3, 2)
+    boxes = []
+    for _ in range(30):
+        f = int(g.integers(0, nF))
+        x0, y0 = int(g.integers(0, Wd - 2)), int(g.integers(0, H - 1))
+        x1, y1 = int(g.integers(x0 + 2, Wd + 1)), int(g.integers(y0 + 1, H + 1))
+        xm = (x0 + x1) // 2
+        boxes += [[f, x0, y0, x1, y1], [f, x0, y0, xm, y1], [f, xm, y0, x1, y1]]
+    boxes = np.array(boxes, dtype=np.int32)
+    h = orc.color_hist(frames, boxes, bins).astype(np.float64)
+    area = ((boxes[:, 3] - boxes[:, 1]) * (boxes[:, 4] - boxes[:, 2])).astype(np.float64)
+    cnt = np.rint(h * area[:, None])
+    assert np.all(np.abs(h * area[:, None] - cnt) <= 1e-5 * area[:, None])
+    assert np.array_equal(cnt.sum(axis=1), area)
+    for t in range(0, len(boxes), 3):
+        assert np.array_equal(cnt[t], cnt[t + 1] + cnt[t + 2]), t
+    whole = np.array([[f, 0, 0, Wd, H] for f in range(nF)], dtype=np.int32)
+    perm = frames.reshape(nF, H * Wd, 3)[:, g.permutation(H * Wd)].reshape(nF, H, Wd, 3)
+    assert np.array_equal(orc.color_hist(frames, whole, bins), orc.color_hist(perm, whole, bins))
+    one = np.zeros((1, H, Wd, 3), dtype=np.uint8)
+    one[...] = (200, 90, 130)        # bins: 200 -> 3 of 4, 90 -> 1 of 3, 130 -> 1 of 2
+    got = orc.color_hist(one, np.array([[0, 0, 0, Wd, H]], dtype=np.int32), bins)[0]
+    want = np.zeros(24, dtype=np.float32)
+    want[(3 * 3 + 1) * 2 + 1] = 1.0
+    assert np.array_equal(got, want)
+    for bad in ([1, 0, 0, 1, 1], [0, 0, 0, 0, 1], [0, 0, 0, Wd + 1, 1], [0, -1, 0, 1, 1], [0, 0, 2, 1, 2]):
+        try:
+            orc.color_hist(one, np.array([bad], dtype=np.int32), bins)
+        except ValueError:
+            continue
+        raise AssertionError(f"invalid box accepted: {bad}")
+
+
+# ----------------------------------------------------------------------------------------
+# connected components and q4 deduplication
+# ----------------------------------------------------------------------------------------
+
+def _min_label_partition(n, pairs):
+    """Components from scipy's graph routine, relabelled by the smallest member."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+    pairs = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
+    A = sp.coo_matrix((np.ones(len(pairs)), (pairs[:, 0], pairs[:, 1])), shape=(n, n))
+    nc, lab = connected_components(A, directed=False)
+    first = np.full(nc, n, dtype=np.int64)
+    np.minimum.at(first, lab, np.arange(n))
+    return first[lab], nc
+
+
+def pin_components_match_library(orc):
+    """Random graphs (with self-loops and repeated edges) against scipy's connected components."""
+    g = _g(35)
+    for n, m in ((1, 0), (7, 0), (10, 4), (50, 30), (300, 250), (400, 900)):
+        pairs = g.integers(0, n, size=(m, 2)) if m else np.empty((0, 2), np.int64)
+        if m:
+            pairs = np.concatenate([pairs, pairs[: m // 5], np.stack([pairs[:3, 0], pairs[:3, 0]], 1)])
+        lab, c = orc.components(n, pairs)
+        want, nc = _min_label_partition(n, pairs)
+        assert c == nc and np.array_equal(lab, want), (n, m)
+        assert np.all(lab <= np.arange(n)) and np.array_equal(lab[lab], lab)
+        if len(pairs):
+            assert np.array_equal(lab[pairs[:, 0]], lab[pairs[:, 1]])
+
+
+def pin_components_closed_forms(orc):
+    """A path listed back to front is one component labelled 0; no edges leave every row alone."""
+    n = 64
+    path = np.array([[i, i + 1] for i in range(n - 2, -1, -1)], dtype=np.int64)
+    lab, c = orc.components(n, path)
+    assert c == 1 and np.all(lab == 0)
+    lab, c = orc.components(n, path[:, ::-1])
+    assert c == 1 and np.all(lab == 0)
+    lab, c = orc.components(n, np.empty((0, 2), np.int64))
+    assert c == n and np.array_equal(lab, np.arange(n))
+    # two interleaved paths: evens and odds
+    ev = np.array([[i, i + 2] for i in range(n - 4, -1, -2)], dtype=np.int64)
+    od = ev + 1
+    lab, c = orc.components(n, np.concatenate([od, ev]))
+    assert c == 2 and np.array_equal(lab, np.arange(n) % 2)
+    try:
+        orc.components(3, np.array([[0, 3]]))
+    except ValueError:
+        pass
+    else:
+        raise AssertionError("an edge outside [0, n) was accepted")
+
+
+def pin_dedup_plans_hand_example(orc):
+    """q4's two plan orders (Sec. 7.5) on a hand-built line of rows: 0-1 and 1-2 match, 0-2 do not."""
+    X = np.array([[0.0], [1.0], [2.0], [10.0], [20.0], [21.0]], dtype=np.float32)
+    P, C = 1, 2
+    labels = np.array([P, C, P, P, C, C], dtype=np.int32)
+    lab, c = orc.dedup(X, 1.0, plan=oracle.DEDUP_ALL)
+    assert c == 3 and lab.tolist() == [0, 0, 0, 3, 4, 4]
+    lab, c = orc.dedup(X, 1.0, labels, P, oracle.DEDUP_FILTER_MATCH)
+    assert c == 3 and lab.tolist() == [0, -1, 2, 3, -1, -1]
+    lab, c = orc.dedup(X, 1.0, labels, P, oracle.DEDUP_MATCH_FILTER)
+    assert c == 2 and lab.tolist() == [0, 0, 0, 3, 4, 4]
+    lab, c = orc.dedup(X, 1.0, labels, C, oracle.DEDUP_MATCH_FILTER)
+    assert c == 2
+    lab, c = orc.dedup(X, 1.0, labels, 7, oracle.DEDUP_FILTER_MATCH)
+    assert c == 0 and np.all(lab == -1)
+
+
 ALL_PINS = [
     pin_sqdist_within_rounding_of_exact,
     pin_join_matches_exact_rational,
@@ -371,4 +652,13 @@ ALL_PINS = [
     pin_normalize_exact_properties,
     pin_cosine_join_matches_exact,
     pin_topk_small_store_and_join_consistency,
+    pin_hist_dist_within_rounding_of_exact,
+    pin_hist_join_matches_exact_rational,
+    pin_hist_closed_forms,
+    pin_color_hist_golden_fixture,
+    pin_color_hist_binning_definition,
+    pin_color_hist_invariants,
+    pin_components_match_library,
+    pin_components_closed_forms,
+    pin_dedup_plans_hand_example,
 ]

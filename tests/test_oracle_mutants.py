@@ -2,7 +2,8 @@
 
 Every mutant is a one-line edit of oracle/oracle.c (a dropped term, a wrong sign
 or index, a transposed operand, a strict instead of inclusive comparison, a
-missing tie-break ...). It is compiled to a temporary library with the same
+missing tie-break ...). Mutants are chosen so that every index they compute stays
+inside its buffer. It is compiled to a temporary library with the same
 flags as the real oracle and the full pin suite runs against it: at least one
 pin must fail. Runs on the CPU only.
 """
@@ -35,6 +36,19 @@ MUTANTS = {
     "cosine_threshold_halved": ("const double e2 = 2.0 - 2.0 * c;", "const double e2 = 2.0 - c;"),
     "norm_not_rooted": ("const float nr = (float)sqrt(s);", "const float nr = (float)s;"),
     "norm_multiplies": ("o[k] = x[k] / nr;", "o[k] = x[k] * nr;"),
+    "l1_abs_dropped": ("s = s + fabs(t);", "s = s + t;"),
+    "chi2_no_division": ("if (u > 0.0) s = s + (t * t) / u;", "if (u > 0.0) s = s + (t * t);"),
+    "chi2_divides_by_q": ("double u = (double)q[k] + (double)x[k];", "double u = (double)q[k];"),
+    "hist_join_strict": ("if (s <= eps)", "if (s < eps)"),
+    "hist_channels_swapped": ("r = (px[0] * br) >> 8, g = (px[1] * bg) >> 8, b = (px[2] * bb) >> 8;",
+                              "r = (px[2] * br) >> 8, g = (px[1] * bg) >> 8, b = (px[0] * bb) >> 8;"),
+    "hist_row_stride": ("((f * H + y) * (int64_t)W + x) * 3", "((f * H + y) * (int64_t)H + x) * 3"),
+    "hist_area_width_only": ("const float area = (float)((int64_t)(x1 - x0) * (y1 - y0));",
+                             "const float area = (float)((int64_t)(x1 - x0));"),
+    "hist_joint_index_transposed": ("cnt[(r * bg + g) * bb + b] += 1;", "cnt[(g * br + r) * bb + b] += 1;"),
+    "components_max_label": ("const int64_t lo = (la < lb) ? la : lb;", "const int64_t lo = (la > lb) ? la : lb;"),
+    "components_one_pass": ("while (changed) {", "if (changed) {"),
+    "components_count_inverted": ("c += (label[i] == i);", "c += (label[i] != i);"),
 }
 
 
