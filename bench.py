@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-requests leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-precision", action="store_true", help="skip the d=512 BF16 / FP8 leg")
+    ap.add_argument("--no-rows", action="store_true",
+                    help="skip the colour-histogram, L1 / chi-square and dedup leg")
     ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES), default=None,
                     help="run one small profiling case three times and print its timings (no bench line)")
     ap.add_argument("--serving-seconds", type=float, default=4.0)
@@ -342,6 +344,112 @@ def precision_leg(dl, reps=2):
     return out
 
 
+def _event_ms(fn, reps, flush=None):
+    """Median CUDA-event time (ms) of fn() on the current stream over reps calls after one warm call;
+    flush() (outside the events) runs before each timed call."""
+    import torch
+    st = torch.cuda.current_stream()
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def rows_leg(dl, sm_mhz=None, reps=5):
+    """The further rows: the colour-histogram transformer, the L1 / chi-square self-joins and q4
+    deduplication, each on its own seeded workload at full size (parity in the GPU tests)."""
+    import torch
+    from paper_1812_07607_gb300 import workloads as W
+    pk = peaks()
+    mhz = sm_mhz or 2070.0
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    scratch = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    flush = lambda: scratch.fill_(1)   # noqa: E731  (512 MiB > L2)
+    out = {"clock_mhz_for_alu_peaks": mhz}
+
+    wl = W.traffic_boxes_1080p()
+    fr = torch.from_numpy(wl.frames).cuda()
+    bx = torch.from_numpy(wl.boxes).cuda()
+    d = wl.bins[0] * wl.bins[1] * wl.bins[2]
+    h = torch.empty((len(wl.boxes), d), dtype=torch.float32, device="cuda")
+    kms = []
+
+    def hist_call():
+        tm = {}
+        dl.color_hist(fr, bx, wl.bins, out=h, timing=tm)
+        kms.append(tm["count_ms"])
+
+    ms = _event_ms(hist_call, reps, flush)
+    kern = statistics.median(kms[1:])
+    byt = 3 * wl.pixels + 4 * h.numel()
+    out["color_hist"] = {
+        "config": f"traffic_boxes_1080p: {fr.shape[0]} frames 1920x1080 RGB8, {len(wl.boxes)} detector boxes, "
+                  f"bins {wl.bins} (d={d}); L2 flushed between calls",
+        "ms_call": ms, "ms_count_kernel": kern, "patches_per_s": len(wl.boxes) / (ms / 1e3), "pixels": wl.pixels,
+        "call_GBps": byt / (ms / 1e3) / 1e9,
+        "roofline": {"bound": "hbm", "achieved": byt / (kern / 1e3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": byt / (kern / 1e3) / 1e9 / pk["hbm_gbs"], "kernel": "k_hist_count",
+                     "algorithmic": f"3 B/pixel x {wl.pixels} + 4 B x {h.numel()} bins = {byt} B per launch"}}
+    del fr, bx, h
+
+    X, thr = W.hist_clustered_64k()
+    n = X.shape[0]
+    Xs = dl.Store(torch.arange(n, device="cuda"), torch.from_numpy(X).cuda())
+    P = n * (n - 1) // 2
+    for metric, unit_ops, lanes, what in (("l1", 2, 128, "FP32 add (sub, add |t|) per term, 128 lanes/SM"),
+                                          ("chi2", 1, 16, "one MUFU reciprocal per term, 16 lanes/SM")):
+        st = {}
+
+        def call():
+            r = dl.sim_join(Xs, None, thr[metric], metric=metric, timing=True)
+            st.update(r.stats())
+            r.free()
+
+        ms = _event_ms(call, 3)
+        ops = unit_ops * X.shape[1] * P
+        kern_ms = st["ms_main"]
+        peak = sms * lanes * mhz * 1e6
+        out[metric] = {"config": f"hist_clustered_64k: {n} x d=128 clustered histograms, self-join, "
+                                 f"eps={thr[metric]:.6g} (20 matches per row)",
+                       "value": P / (ms / 1e3) / 1e9, "unit": "Gpairs/s", "ms": ms, "ms_main": kern_ms,
+                       "pairs_out": st["pairs_out"], "band_pairs": st["band_pairs"], "fp64_pairs": st["fp64_pairs"],
+                       "roofline": {"bound": "alu", "achieved": ops / (kern_ms / 1e3) / 1e12,
+                                    "peak": peak / 1e12, "unit": "Tops/s", "frac": ops / (kern_ms / 1e3) / peak,
+                                    "algorithmic": f"{unit_ops} x d x {P} pairs ({what}), at {mhz:.0f} MHz"}}
+    Xs.close()
+
+    wl2 = W.self_clustered_262k()
+    labels = torch.from_numpy(W.object_labels(W.rng(W.SEED_BASE + 107), wl2.groups, 8192)).cuda()
+    S = dl.Store(torch.from_numpy(wl2.r_ids).cuda(), torch.from_numpy(wl2.R).cuda())
+    dd = {"config": "self_clustered_262k + object labels (0 person / 1 vehicle / 2 other per object, 8% "
+                    "detector flips); target label 0; eps of the store (mean 20 matches)"}
+    for plan in ("all", "filter_match", "match_filter"):
+        cnt = []
+        ms = _event_ms(lambda: cnt.append(dl.dedup(S, wl2.eps, labels, 0, plan=plan)[1]), 3)
+        dd[plan] = {"ms": ms, "distinct": cnt[-1]}
+    r = dl.sim_join(S, None, wl2.eps)
+    a, b = (torch.as_tensor(v) for v in r.pairs_device())
+    ids = torch.from_numpy(wl2.r_ids).cuda()
+    srt, perm = torch.sort(ids)
+    ra, rb = perm[torch.searchsorted(srt, a)], perm[torch.searchsorted(srt, b)]
+    ms = _event_ms(lambda: dl.components(wl2.R.shape[0], ra, rb), reps)
+    dd["components"] = {"ms": ms, "edges": int(ra.numel()), "edges_per_s": ra.numel() / (ms / 1e3)}
+    r.free()
+    S.close()
+    out["dedup"] = dd
+    del scratch
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -500,6 +608,9 @@ def run_ours(args):
     precision = None
     if rank == 0 and not args.no_precision:
         precision = precision_leg(dl)
+    rows = None
+    if rank == 0 and not args.no_rows:
+        rows = rows_leg(dl, clocks.get("sm_mhz"))
 
     cpu = None
     if rank == 0 and not args.no_baselines:
@@ -528,6 +639,7 @@ def run_ours(args):
             "batch": batch,
             "serving": serving,
             "precision": precision,
+            "next_rows": rows,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
@@ -566,15 +678,45 @@ def _case_dense_d256():
     return lambda: dl.sim_join(Qs, S, eps, precision="bf16", timing=True, tile_n=256)
 
 
-PROFILE_CASES = {"fp8_unit_d512_65536": _case_fp8_unit_d512, "dense_d256_16384x1m": _case_dense_d256}
+def _case_color_hist_1080p():
+    """The colour-histogram transformer on the full traffic_boxes_1080p workload (400 MB of frames)."""
+    import torch
+    from paper_1812_07607_gb300 import dl, workloads as W
+    dl.load()
+    wl = W.traffic_boxes_1080p()
+    fr = torch.from_numpy(wl.frames).cuda()
+    bx = torch.from_numpy(wl.boxes).cuda()
+    out = torch.empty((len(wl.boxes), 128), dtype=torch.float32, device="cuda")
+    return lambda: dl.color_hist(fr, bx, wl.bins, out=out)
+
+
+def _case_l1_16k():
+    """L1 self-join of the first 16,384 rows of hist_clustered_64k (CUDA-core kernel k8_simt_join<1>)."""
+    import torch
+    from paper_1812_07607_gb300 import dl, workloads as W
+    dl.load()
+    X, thr = W.hist_clustered_64k()
+    Xs = dl.Store(torch.arange(16384).cuda(), torch.from_numpy(X[:16384]).cuda())
+    return lambda: dl.sim_join(Xs, None, thr["l1"], metric="l1", timing=True)
+
+
+PROFILE_CASES = {"fp8_unit_d512_65536": _case_fp8_unit_d512, "dense_d256_16384x1m": _case_dense_d256,
+                 "color_hist_1080p": _case_color_hist_1080p, "l1_hist_16384": _case_l1_16k}
 
 
 def run_profile_case(name):
     from paper_1812_07607_gb300 import build as B
     B.build()
     call = PROFILE_CASES[name]()
+    import torch
     for _ in range(3):
+        t0 = time.perf_counter()
         r = call()
+        torch.cuda.synchronize()
+        dt = 1e3 * (time.perf_counter() - t0)
+        if not hasattr(r, "stats"):
+            print(json.dumps({"case": name, "ms_call": dt}), flush=True)
+            continue
         st = r.stats()
         r.free()
         print(json.dumps({"case": name, "ms_main": st["ms_main"], "ms_recheck": st["ms_recheck"],

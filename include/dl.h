@@ -53,9 +53,14 @@ typedef enum dl_status {
 
 typedef enum dl_metric {
     DL_METRIC_L2 = 0,     /* squared Euclidean distance compared with eps^2 (Sec. 3.2) */
-    DL_METRIC_COSINE = 1  /* cosine similarity on stores made by dl_store_normalize: eps is the
+    DL_METRIC_COSINE = 1, /* cosine similarity on stores made by dl_store_normalize: eps is the
                              threshold c in [-1, 1] and a pair matches iff the canonical D of
                              the normalized rows is <= fl64(2 - 2c) (cos >= c for unit rows) */
+    DL_METRIC_L1 = 2,     /* histogram L1 distance: canonical FP64 sum_k |q_k - x_k| <= eps
+                             (k ascending, every step rounded to nearest); epsilon-join only */
+    DL_METRIC_CHI2 = 3    /* chi-square histogram distance on non-negative features: canonical FP64
+                             sum over bins with q_k + x_k > 0 of (q_k - x_k)^2 / (q_k + x_k) <= eps
+                             (no factor 1/2); epsilon-join only */
 } dl_metric;
 
 typedef enum dl_precision {
@@ -131,6 +136,58 @@ int dl_store_destroy(dl_store *s);
 /* Number of rows and dimension of a store. */
 int dl_store_shape(const dl_store *s, int64_t *n, int32_t *d);
 
+/*
+ * Colour-histogram transformer (Sec. 4.1 "Transformers": colour histogram features
+ * for image matching), the producer of the stores' features.
+ *   frames  device, uint8 [n_frames][H][W][3], interleaved RGB, row-major, 16-byte aligned;
+ *   boxes   device, int32 [n_boxes][5] = {frame, x0, y0, x1, y1}: the half-open pixel
+ *           rectangle [x0, x1) x [y0, y1) of that frame;
+ *   br, bg, bb  bins per channel, each in [1, 256], d = br*bg*bb <= 1024;
+ *   out     device, float32 [n_boxes][d], row-major (caller-owned);
+ *   count_ms  host, may be NULL: receives the CUDA-event time of the pixel-counting kernel.
+ * Channel value v falls in bin floor(v*b/256) of that channel; the joint bin is
+ * (r_bin*bg + g_bin)*bb + b_bin; out = count / (pixels of the box), each a correctly
+ * rounded FP32 division. Errors: DL_EINVAL for bad sizes or alignment and for any
+ * invalid box (outside its frame, empty, or more than 2^24 pixels), in which case
+ * out is unspecified. The call synchronizes cuda_stream to report invalid boxes.
+ */
+int dl_color_hist(const uint8_t *frames, int64_t n_frames, int32_t H, int32_t W, const int32_t *boxes,
+                  int64_t n_boxes, int32_t br, int32_t bg, int32_t bb, float *out, float *count_ms,
+                  void *cuda_stream);
+
+/* ---------------------------------------------------------------------------------
+ * q4 deduplication (Sec. 6.2 q4, Sec. 7.5 and Table 1).
+ * ------------------------------------------------------------------------------- */
+
+/*
+ * Connected components of the graph on rows 0..n-1 whose edges are (pair_a[e], pair_b[e]),
+ * e < m (device int64 arrays of row indices; self-loops and repeats allowed). label
+ * (device int64 [n], caller-owned) receives, for every row, the smallest row index of its
+ * component; *n_components (host, may be NULL) the number of components. n must be below
+ * 2^31. DL_EINVAL when an edge names a row outside [0, n). Synchronizes cuda_stream.
+ */
+int dl_components(int64_t n, const int64_t *pair_a, const int64_t *pair_b, int64_t m, int64_t *label,
+                  int64_t *n_components, void *cuda_stream);
+
+typedef enum dl_dedup_plan {
+    DL_DEDUP_ALL = 0,           /* components of the self-join of every row */
+    DL_DEDUP_FILTER_MATCH = 1,  /* keep the rows labelled `target`, join them, count their components
+                                   (Table 1 "Patch, Filter, Match"); other rows get component -1 */
+    DL_DEDUP_MATCH_FILTER = 2   /* join every row, count the components holding at least one row
+                                   labelled `target` (Table 1 "Patch, Match, Filter") */
+} dl_dedup_plan;
+
+/*
+ * Count distinct objects (q4): the epsilon self-join of X (metric and eps as in
+ * dl_sim_join; opts->self_mode and out_capacity are ignored), then its connected
+ * components. labels: device int32 [n] per caller row (required by the two label plans).
+ * comp: device int64 [n], per caller row the smallest caller row of its component (or -1,
+ * see the plan). *n_distinct (host): the number of distinct objects under the plan.
+ * Synchronizes opts->cuda_stream. Errors as dl_sim_join.
+ */
+int dl_dedup(const dl_store *X, int32_t metric, double eps, const int32_t *labels, int32_t target, int32_t plan,
+             const dl_join_opts *opts, int64_t *comp, int64_t *n_distinct);
+
 /* ---------------------------------------------------------------------------------
  * Joins.
  * ------------------------------------------------------------------------------- */
@@ -140,7 +197,10 @@ int dl_store_shape(const dl_store *s, int64_t *n, int32_t *d);
  * every pair (r in R, s in S) with canonical D(r, s) <= eps*eps, as id pairs.
  * S == NULL is a self-join of R, in opts->self_mode. eps must be >= 0 and not
  * NaN; eps = +inf returns every pair. With DL_METRIC_COSINE, eps is the cosine
- * threshold c in [-1, 1] and both stores must come from dl_store_normalize. opts may be
+ * threshold c in [-1, 1] and both stores must come from dl_store_normalize. With
+ * DL_METRIC_L1 / DL_METRIC_CHI2 the predicate is the histogram distance <= eps; these
+ * run with DL_PREC_FP32 (AUTO picks it) or DL_PREC_FP32_PLAIN (BF16 / FP8 give
+ * DL_EUNSUPPORTED), and CHI2 gives DL_EINVAL when a feature is negative. opts may be
  * NULL (defaults). On success *out holds the result (free with
  * dl_result_free); on DL_EOVERFLOW *out is also set so that the required
  * count can be read. The pair order is unspecified (the result is a set).

@@ -10,6 +10,10 @@ selectivity instead and this script turns that into a value:
   * self_clustered_262k: 512 seeded rows against all 262,144 rows; eps^2 sits
     in the gap that makes the mean number of other rows within eps equal 20.
   * rxs_unit_mixture_1m: 64 seeded R rows against all of S; mean 10 per row.
+  * hist_clustered_64k (L1 / chi-square self-joins): 256 seeded rows against
+    all 65,536 rows per metric; the threshold sits in the gap that gives a mean of
+    20 other rows per row (these distances are not squared, so the threshold is
+    the gap's midpoint itself).
   * batch_store_2m / serve_store_4m (request workloads): 256 fresh query rows against a
     seeded 65,536-row sample of the store; the pooled distances give a
     (selectivity, eps) table, selectivity = the fraction of store rows within eps.
@@ -39,23 +43,34 @@ OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
 
 
 def _block_smallest(args):
-    R, S, keep, excl = args
-    D = oracle.default().dist_block(R, S)
+    R, S, keep, excl = args[:4]
+    metric = args[4] if len(args) > 4 else 0
+    D = oracle.default().dist_block(R, S) if metric == 0 else oracle.default().hist_dist_block(R, S, metric)
     if excl is not None:
         D[np.arange(D.shape[0]), excl] = np.inf
     keep = min(keep, D.shape[1] - 1)
     return np.sort(np.partition(D, keep, axis=1)[:, :keep + 1], axis=1)
 
 
-def smallest_per_row(R, S, keep, excl=None, procs=None, block=8):
+def smallest_per_row(R, S, keep, excl=None, procs=None, block=8, metric=0):
     procs = procs or min(8, os.cpu_count() or 1)
     jobs = []
     for r0 in range(0, R.shape[0], block):
         r1 = min(R.shape[0], r0 + block)
-        jobs.append((R[r0:r1], S, keep, None if excl is None else excl[r0:r1]))
+        jobs.append((R[r0:r1], S, keep, None if excl is None else excl[r0:r1], metric))
     with mp.get_context("spawn").Pool(procs) as pool:
         parts = pool.map(_block_smallest, jobs)
     return np.concatenate(parts, axis=0)
+
+
+def thr_in_gap(sorted_vals: np.ndarray, rank: int) -> float:
+    """An unsquared threshold strictly between sorted_vals[rank-1] and the next larger value."""
+    a = sorted_vals[rank - 1]
+    b = sorted_vals[np.searchsorted(sorted_vals, a, side="right")]
+    t = 0.5 * (a + b)
+    if not (a < t < b):
+        raise RuntimeError(f"gap too narrow at rank {rank}: {a!r} {b!r}")
+    return t
 
 
 def eps_in_gap(sorted_vals: np.ndarray, rank: int) -> float:
@@ -108,6 +123,16 @@ def calibrate(name: str) -> tuple[str, float, dict]:
         key = f"rxs_unit_mixture_1m:{W.SEED_BASE + 2}:1048576:512:4096"
         per_row = (sm <= eps * eps).sum(axis=1)
         return key, eps, {"sample_rows": 64, "mean_matches": float(per_row.mean())}
+    if name == "hist_clustered_64k":
+        X, _ = W.hist_clustered_64k()
+        g = W.rng(W.SEED_BASE + 106)
+        rows = np.sort(g.choice(X.shape[0], size=256, replace=False))
+        extra = {}
+        for mname, metric in (("l1", oracle.METRIC_L1), ("chi2", oracle.METRIC_CHI2)):
+            sm = smallest_per_row(X[rows], X, keep=400, excl=rows, metric=metric)
+            vals = np.sort(sm.ravel())
+            extra[f"hist_clustered_64k:{mname}:{W.SEED_BASE + 6}"] = thr_in_gap(vals, 20 * len(rows))
+        return None, None, {"extra": extra}
     if name in ("batch_store_2m", "serve_store_4m"):
         st = getattr(W, name)()
         g = W.rng(W.SEED_BASE + 104)
@@ -141,4 +166,4 @@ def main(names):
 
 if __name__ == "__main__":
     main(sys.argv[1:] or ["rxs_histograms_2k", "self_clustered_262k", "rxs_unit_mixture_1m", "batch_store_2m",
-                          "serve_store_4m"])
+                          "serve_store_4m", "hist_clustered_64k"])

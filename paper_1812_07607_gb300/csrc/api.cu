@@ -137,7 +137,9 @@ struct PassCfg {
     bool self, mirror;
     int prec;
     int BN;
-    double e2;
+    double e2;              // squared-L2 threshold (metric 0), or the L1 / chi-square threshold eps
+    int metric;             // 0 squared L2 (and cosine), 1 L1, 2 chi-square
+    const int64_t *ids;     // ids written for both sides (self-join only; NULL: the store's ids)
     float t_acc, t_rej;     // FP32 thresholds (exact: recheck/SIMT; plain: SIMT only)
     int64_t cap, band_cap;
     bool timing;
@@ -196,8 +198,8 @@ static int run_pass(const PassCfg &c, PassOut *po)
     if (c.timing) cudaEventRecord(ev[0], st);
 
     JoinOut jo;
-    jo.r_ids = R->ids;
-    jo.s_ids = S->ids;
+    jo.r_ids = c.ids ? c.ids : R->ids;
+    jo.s_ids = c.ids ? c.ids : S->ids;
     jo.out_r = po->out_r;
     jo.out_s = po->out_s;
     jo.out_cnt = cnt + 0;
@@ -263,6 +265,7 @@ static int run_pass(const PassCfg &c, PassOut *po)
             sp.upper = c.self ? 1 : 0;
             sp.tiles_m = 0;
             sp.exact = (c.prec == DL_PREC_FP32) ? 1 : 0;
+            sp.metric = c.metric;
             sp.t_acc = c.t_acc;
             sp.t_rej = c.t_rej;
             sp.out = jo;
@@ -273,6 +276,10 @@ static int run_pass(const PassCfg &c, PassOut *po)
         if (!rc && (c.prec == DL_PREC_BF16 || c.prec == DL_PREC_FP8E4M3)) {
             rc = launch_finalize(band, cnt + 1, (unsigned long long)c.band_cap, R->x32, S->x32, d, c.e2, c.t_acc,
                                  c.t_rej, jo, cnt + 3, cnt + 2, sms * 8, st);
+            ++launches;
+        } else if (!rc && c.prec == DL_PREC_FP32 && c.metric != 0) {
+            rc = launch_hist_recheck(c.metric, band, cnt + 1, (unsigned long long)c.band_cap, R->x32, S->x32, d, c.e2,
+                                     jo, cnt + 3, sms * 8, st);
             ++launches;
         } else if (!rc && c.prec == DL_PREC_FP32) {
             rc = launch_recheck(band, cnt + 1, (unsigned long long)c.band_cap, R->x32, S->x32, d, c.e2, c.t_acc, c.t_rej,
@@ -285,7 +292,7 @@ static int run_pass(const PassCfg &c, PassOut *po)
         cudaEventRecord(ev[2], st);
     }
     if (!rc && c.mirror) {
-        rc = launch_diag(R->ids, nR, po->out_r, po->out_s, cnt + 0, (unsigned long long)c.cap, st);
+        rc = launch_diag(c.ids ? c.ids : R->ids, nR, po->out_r, po->out_s, cnt + 0, (unsigned long long)c.cap, st);
         ++launches;
     }
     if (c.timing) cudaEventRecord(ev[3], st);
@@ -348,10 +355,13 @@ void dl_join_opts_default(dl_join_opts *o)
     o->self_mode = DL_SELF_UPPER;
 }
 
-int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps, const dl_join_opts *opts,
-                dl_result **out)
+}  // extern "C"
+
+namespace dl {
+
+int sim_join_impl(const dl_store *R, const dl_store *S, int32_t metric, double eps, const dl_join_opts *opts,
+                  dl_result **out, const int64_t *emit_ids)
 {
-    clear_error();
     if (!out) {
         set_error("dl_sim_join: out is NULL");
         return DL_EINVAL;
@@ -379,10 +389,17 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
             return DL_EINVAL;
         }
         e2 = 2.0 - 2.0 * eps;
+    } else if (metric == DL_METRIC_L1 || metric == DL_METRIC_CHI2) {
+        if (std::isnan(eps) || eps < 0.0) {
+            set_error("dl_sim_join: eps must be >= 0 (got %g)", eps);
+            return DL_EINVAL;
+        }
+        e2 = eps;   // histogram distances are compared unsquared
     } else {
         set_error("dl_sim_join: unsupported metric %d", metric);
         return DL_EINVAL;
     }
+    const int hmetric = (metric == DL_METRIC_L1) ? 1 : (metric == DL_METRIC_CHI2) ? 2 : 0;
     dl_join_opts o;
     if (opts)
         o = *opts;
@@ -403,8 +420,23 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
     if (rc) return rc;
     int prec = o.precision;
     // AUTO: BF16 while its R tile fits in shared memory (d <= 512), else the FP8 tensor-core
-    // path (d <= 1024, always within the domain); both give the exact set.
-    if (prec == DL_PREC_AUTO) prec = (R->dp <= 512) ? DL_PREC_BF16 : DL_PREC_FP8E4M3;
+    // path (d <= 1024, always within the domain); both give the exact set. The histogram
+    // distances are not contractions: they run on the CUDA cores (FP32 + bound + FP64).
+    if (prec == DL_PREC_AUTO) prec = hmetric ? DL_PREC_FP32 : (R->dp <= 512) ? DL_PREC_BF16 : DL_PREC_FP8E4M3;
+    if (hmetric && (prec == DL_PREC_BF16 || prec == DL_PREC_FP8E4M3)) {
+        set_error("dl_sim_join: L1 and chi-square run on DL_PREC_FP32 (or FP32_PLAIN), not on tensor cores");
+        return DL_EUNSUPPORTED;
+    }
+    if (hmetric == 2) {
+        bool ok = false;
+        rc = store_nonneg(const_cast<dl_store *>(R), (cudaStream_t)o.cuda_stream, &ok);
+        if (!rc && ok && !self) rc = store_nonneg(const_cast<dl_store *>(Sx), (cudaStream_t)o.cuda_stream, &ok);
+        if (rc) return rc;
+        if (!ok) {
+            set_error("dl_sim_join: the chi-square distance needs non-negative features");
+            return DL_EINVAL;
+        }
+    }
     if (prec != DL_PREC_BF16 && prec != DL_PREC_FP8E4M3 && prec != DL_PREC_FP32 && prec != DL_PREC_FP32_PLAIN) {
         set_error("dl_sim_join: bad precision %d", prec);
         return DL_EINVAL;
@@ -438,10 +470,22 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
     c.prec = prec;
     c.BN = BN;
     c.e2 = e2;
-    if (prec == DL_PREC_FP32_PLAIN) {
+    c.metric = hmetric;
+    c.ids = emit_ids;
+    if (prec == DL_PREC_FP32_PLAIN && hmetric) {
+        c.t_acc = (float)eps;
+        c.t_rej = c.t_acc;
+    } else if (prec == DL_PREC_FP32_PLAIN) {
         const float ef = (float)std::sqrt(e2);
         c.t_acc = ef * ef;
         c.t_rej = c.t_acc;
+    } else if (hmetric) {
+        // |D32 - D| <= g32 D + abs32 for the SIMT evaluation, |D64 - D| <= g64 D for the canonical sum
+        const double g64 = (hmetric == 1) ? gamma64(d) : gamma64(d + 4);
+        const double g32 = (hmetric == 1) ? (d + 4) * 1.1920928955078125e-07 : (d + 16) * 1.1920928955078125e-07;
+        const double abs32 = (hmetric == 1) ? d * 7.52316384526264e-37 : d * 2.168404344971009e-19;   // d 2^-120, d 2^-62
+        c.t_acc = f32_rd(eps * (1.0 - g64) * (1.0 - g32) * (1.0 - 8.881784197001252e-16) - abs32);
+        c.t_rej = f32_ru(eps * (1.0 + 2.0 * g64) * (1.0 + g32) * (1.0 + 8.881784197001252e-16) + abs32);
     } else {
         const double g64 = gamma64(d), g32 = gamma32(d);
         const double abs32 = (double)(d + 8) * 1.401298464324817e-45 * 2.0;
@@ -533,6 +577,17 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
         return DL_EOVERFLOW;
     }
     return DL_OK;
+}
+
+}  // namespace dl
+
+extern "C" {
+
+int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps, const dl_join_opts *opts,
+                dl_result **out)
+{
+    clear_error();
+    return sim_join_impl(R, S, metric, eps, opts, out, nullptr);
 }
 
 int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric, int32_t k, const dl_join_opts *opts,

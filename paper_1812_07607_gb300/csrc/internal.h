@@ -93,11 +93,20 @@ struct Store {
     int64_t hint_band = 0;
     double hint_batch_rate = 0.0;   // batch calls: candidates per evaluated pair last seen against this store
     bool unit = false;       // rows are the unit-normalized rows of another store (cosine metric)
+    int nonneg = 0;          // 0 not checked yet, 1 every feature >= 0, 2 some feature < 0 (chi-square)
 };
 
 // Create a store; gather == NULL orders rows by norm, else store row i is caller row gather[i].
 int store_create_impl(dl_store **out, const int64_t *ids, const float *feats, int64_t n, int32_t d, int32_t where,
                       void *cuda_stream, const int32_t *gather);
+
+// Whether every feature of the store is >= 0 (checked once, on first use, then cached).
+int store_nonneg(Store *s, cudaStream_t st, bool *ok);
+
+// The epsilon-join behind dl_sim_join; emit_ids (self-join only, device, [n] in store order)
+// replaces the ids written to the output when not NULL.
+int sim_join_impl(const dl_store *R, const dl_store *S, int32_t metric, double eps, const dl_join_opts *opts,
+                  dl_result **out, const int64_t *emit_ids);
 
 // Build (or fetch from the store's cache) a 2-D BF16 tensor map over the store's
 // BF16 copy with a box of 64 columns x box_rows rows and the 128-byte swizzle.

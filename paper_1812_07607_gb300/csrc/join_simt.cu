@@ -2,7 +2,10 @@
 //
 // The nested-loop join of Sec. 5 evaluated directly as D32 = sum_k fl(q_k - x_k)^2
 // with an FMA chain per pair, register-tiled 8x8 pairs per thread over a
-// 128 x 128 pair tile staged through shared memory in 32-wide K slices.
+// 128 x 128 pair tile staged through shared memory in 32-wide K slices. The same
+// tiling evaluates the histogram distances (L1, chi-square), which are not
+// contractions and so stay on the CUDA cores; their thresholds carry their own
+// FP32 bounds and their band pairs go to k_hist_recheck.
 //
 //   plain (DL_PREC_FP32_PLAIN): accept iff D32 <= fl32(eps)^2 -- the usual FP32
 //     GPU join, the throughput baseline; not exact near the threshold.
@@ -20,6 +23,30 @@ constexpr int kSimtK = 32;
 
 __device__ __forceinline__ long long tri_start(int m, int T) { return (long long)m * T - (long long)m * (m - 1) / 2; }
 
+// One distance term of metric M for the pair (a, b) of feature values, added to acc:
+//   M = 0: squared L2, acc += (a - b)^2 (one FMA);
+//   M = 1: L1, acc += |a - b|;
+//   M = 2: chi-square on non-negative features, acc += (a - b)^2 / (a + b) with the
+//          reciprocal from rcp.approx (relative error <= 2^-23), 0 when a + b is 0 or
+//          subnormal (then the exact term is at most a + b < 2^-126).
+template <int M>
+__device__ __forceinline__ void dist_term(float a, float b, float &acc)
+{
+    const float t = a - b;
+    if constexpr (M == 0) {
+        acc = fmaf(t, t, acc);
+    } else if constexpr (M == 1) {
+        acc += fabsf(t);
+    } else {
+        const float u = a + b;
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(u));
+        const float term = (t * t) * r;
+        acc += (u >= 1.17549435e-38f) ? term : 0.f;
+    }
+}
+
+template <int M>
 __global__ void __launch_bounds__(256) k8_simt_join(const SimtParams p)
 {
     __shared__ __align__(16) float As[kSimtK][kSimtTile + 4];
@@ -73,10 +100,7 @@ __global__ void __launch_bounds__(256) k8_simt_join(const SimtParams p)
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float t = a[i] - b[j];
-                    acc[i][j] = fmaf(t, t, acc[i][j]);
-                }
+                for (int j = 0; j < 8; ++j) dist_term<M>(a[i], b[j], acc[i][j]);
         }
         __syncthreads();
     }
@@ -117,13 +141,18 @@ int launch_simt_join(SimtParams p, cudaStream_t st)
             set_error("self-join too large for the SIMT path");
             return DL_EUNSUPPORTED;
         }
-        k8_simt_join<<<(unsigned)blocks, 256, 0, st>>>(p);
+        if (p.metric == 1) k8_simt_join<1><<<(unsigned)blocks, 256, 0, st>>>(p);
+        else if (p.metric == 2) k8_simt_join<2><<<(unsigned)blocks, 256, 0, st>>>(p);
+        else k8_simt_join<0><<<(unsigned)blocks, 256, 0, st>>>(p);
     } else {
         if (tm > 65535) {
             set_error("R too large for the SIMT path grid");
             return DL_EUNSUPPORTED;
         }
-        k8_simt_join<<<dim3((unsigned)tn, (unsigned)tm), 256, 0, st>>>(p);
+        const dim3 grid((unsigned)tn, (unsigned)tm);
+        if (p.metric == 1) k8_simt_join<1><<<grid, 256, 0, st>>>(p);
+        else if (p.metric == 2) k8_simt_join<2><<<grid, 256, 0, st>>>(p);
+        else k8_simt_join<0><<<grid, 256, 0, st>>>(p);
     }
     count_launch();
     cudaError_t e = cudaGetLastError();

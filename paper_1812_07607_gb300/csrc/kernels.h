@@ -62,10 +62,16 @@ struct SimtParams {
     int upper;          // self-join: only c > r
     int tiles_m;        // filled by the launcher
     int exact;          // 0 plain, 1 exact (band output)
+    int metric;         // 0 squared L2, 1 L1, 2 chi-square (distances compared with t_acc / t_rej)
     float t_acc, t_rej; // exact thresholds; plain uses t_acc only
     JoinOut out;
 };
 int launch_simt_join(SimtParams p, cudaStream_t st);
+// Exact decision of the histogram-distance band pairs (metric 1 L1, 2 chi-square): the
+// canonical FP64 distance compared with eps (recheck.cu).
+int launch_hist_recheck(int metric, const uint2 *band, const unsigned long long *band_cnt, unsigned long long band_cap,
+                        const float *R, const float *S, int d, double eps, const JoinOut &out,
+                        unsigned long long *n_fp64, int grid, cudaStream_t st);
 
 // ---- K6 recheck and small per-join kernels (recheck.cu)
 int launch_recheck(const uint2 *band, const unsigned long long *band_cnt, unsigned long long band_cap, const float *R,

@@ -70,6 +70,47 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Band pairs of the histogram distances: the canonical FP64 value itself, one pair per
+// lane (the band is a relative width of about (d + 10) 2^-22 around eps, so few pairs
+// reach it): k ascending, t = (double)q_k - (double)x_k, then s = s + |t| (L1), or
+// u = (double)q_k + (double)x_k and, where u > 0, s = s + (t*t)/u (chi-square), every
+// operation rounded to nearest with no contraction, compared with eps.
+template <int M>
+__global__ void __launch_bounds__(256)
+    k_hist_recheck(const uint2 *__restrict__ band, const unsigned long long *__restrict__ band_cnt,
+                   unsigned long long band_cap, const float *__restrict__ R, const float *__restrict__ S, int d,
+                   double eps, JoinOut out, unsigned long long *__restrict__ n_fp64)
+{
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned long long n = min(*band_cnt, band_cap);
+    const unsigned long long w0 = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    for (unsigned long long base = w0 * 32; base < n; base += nw * 32) {
+        const unsigned long long i = base + lane;
+        const bool valid = i < n;
+        const uint2 pr = valid ? band[i] : make_uint2(0u, 0u);
+        bool acc = false;
+        if (valid) {
+            const float *q = R + (size_t)pr.x * d, *x = S + (size_t)pr.y * d;
+            double s = 0.0;
+            for (int k = 0; k < d; ++k) {
+                const double a = (double)__ldg(q + k), b = (double)__ldg(x + k);
+                const double t = __dsub_rn(a, b);
+                if constexpr (M == 1) {
+                    s = __dadd_rn(s, fabs(t));
+                } else {
+                    const double u = __dadd_rn(a, b);
+                    if (u > 0.0) s = __dadd_rn(s, __ddiv_rn(__dmul_rn(t, t), u));
+                }
+            }
+            acc = s <= eps;
+        }
+        const unsigned vm = __ballot_sync(0xffffffffu, valid);
+        if (lane == 0 && vm) atomicAdd(n_fp64, (unsigned long long)__popc(vm));
+        warp_emit(out, acc, false, (int)pr.x, (int)pr.y);
+    }
+}
+
 // Per-row thresholds of the tensor-core epilogue for one join:
 //   alpha_acc = RU32((||q||^2_up - e2 (1 - g64)) / 2)   accept iff h >= alpha_acc + E
 //   alpha_rej = RD32((||q||^2_dn - e2 (1 + 2 g64)) / 2) reject iff h <  alpha_rej - E
@@ -126,6 +167,20 @@ int launch_recheck(const uint2 *band, const unsigned long long *band_cnt, unsign
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k6_recheck launch");
+    return DL_OK;
+}
+
+int launch_hist_recheck(int metric, const uint2 *band, const unsigned long long *band_cnt, unsigned long long band_cap,
+                        const float *R, const float *S, int d, double eps, const JoinOut &out,
+                        unsigned long long *n_fp64, int grid, cudaStream_t st)
+{
+    if (metric == 1)
+        k_hist_recheck<1><<<grid, 256, 0, st>>>(band, band_cnt, band_cap, R, S, d, eps, out, n_fp64);
+    else
+        k_hist_recheck<2><<<grid, 256, 0, st>>>(band, band_cnt, band_cap, R, S, d, eps, out, n_fp64);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_hist_recheck launch");
     return DL_OK;
 }
 

@@ -744,6 +744,49 @@ __global__ void __launch_bounds__(256) k_normalize_rows(const float *__restrict_
     if (lane == 0) out_ids[dst] = ids[row];
 }
 
+// ------------------------------------------------------------------ chi-square domain
+__global__ void __launch_bounds__(256) k_any_negative(const float *__restrict__ x, int64_t n, int *flag)
+{
+    bool neg = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        neg |= __ldg(x + i) < 0.f;
+    if (__any_sync(0xffffffffu, neg) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+int store_nonneg(Store *s, cudaStream_t st, bool *ok)
+{
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->nonneg) {
+            *ok = s->nonneg == 1;
+            return DL_OK;
+        }
+    }
+    const int64_t n = s->n * (int64_t)s->d;
+    int h = 0;
+    if (n > 0) {
+        void *tmp = nullptr;
+        int rc = dev_alloc(&tmp, 16, st);
+        if (rc) return rc;
+        int *flag = (int *)tmp;
+        cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+        if (e == cudaSuccess) {
+            const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)device_sm_count() * 8);
+            k_any_negative<<<grid, 256, 0, st>>>(s->x32, n, flag);
+            count_launch();
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        dev_free(tmp, st);
+        if (e != cudaSuccess) return cuda_fail(e, "store_nonneg");
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->nonneg = h ? 2 : 1;
+    *ok = !h;
+    return DL_OK;
+}
+
 }  // namespace dl
 
 using namespace dl;

@@ -21,8 +21,10 @@ DL_OK, DL_EINVAL, DL_ENOMEM, DL_EOVERFLOW, DL_EAGAIN, DL_ETIMEOUT, DL_ECUDA, DL_
 STATUS_NAMES = {0: "DL_OK", 1: "DL_EINVAL", 2: "DL_ENOMEM", 3: "DL_EOVERFLOW", 4: "DL_EAGAIN",
                 5: "DL_ETIMEOUT", 6: "DL_ECUDA", 7: "DL_ECANCELED", 8: "DL_ENOMEM_ADMIT",
                 9: "DL_EFAILED", 10: "DL_EUNSUPPORTED"}
-DL_METRIC_L2, DL_METRIC_COSINE = 0, 1
-METRICS = {"l2": DL_METRIC_L2, "cosine": DL_METRIC_COSINE}
+DL_METRIC_L2, DL_METRIC_COSINE, DL_METRIC_L1, DL_METRIC_CHI2 = 0, 1, 2, 3
+METRICS = {"l2": DL_METRIC_L2, "cosine": DL_METRIC_COSINE, "l1": DL_METRIC_L1, "chi2": DL_METRIC_CHI2}
+DL_DEDUP_ALL, DL_DEDUP_FILTER_MATCH, DL_DEDUP_MATCH_FILTER = 0, 1, 2
+DEDUP_PLANS = {"all": DL_DEDUP_ALL, "filter_match": DL_DEDUP_FILTER_MATCH, "match_filter": DL_DEDUP_MATCH_FILTER}
 DL_PREC_AUTO, DL_PREC_BF16, DL_PREC_FP8E4M3, DL_PREC_FP32, DL_PREC_FP32_PLAIN = range(5)
 PRECISIONS = {"auto": 0, "bf16": 1, "fp8": 2, "fp32": 3, "fp32_plain": 4}
 DL_MEM_HOST, DL_MEM_DEVICE = 0, 1
@@ -35,7 +37,7 @@ EXPORTS = [
     "dl_result_stats", "dl_result_free", "dl_last_error", "dl_version", "dl_kernel_launches",
     "dl_sim_join_noalloc", "dl_batch_join", "dl_result_request_pairs", "dl_result_request_topk",
     "dl_server_create", "dl_submit", "dl_poll", "dl_cancel", "dl_server_get_stats", "dl_server_destroy",
-    "dl_debug_scores", "dl_store_normalize",
+    "dl_debug_scores", "dl_store_normalize", "dl_color_hist", "dl_components", "dl_dedup",
 ]
 
 
@@ -123,6 +125,12 @@ def load(path: str | None = None):
     L.dl_server_destroy.argtypes = [vp]
     for name in ("dl_server_create", "dl_submit", "dl_poll", "dl_cancel", "dl_server_get_stats", "dl_server_destroy"):
         getattr(L, name).restype = ctypes.c_int
+    L.dl_color_hist.argtypes = [vp, i64, i32, i32, vp, i64, i32, i32, i32, vp, ctypes.POINTER(ctypes.c_float), vp]
+    L.dl_color_hist.restype = ctypes.c_int
+    L.dl_components.argtypes = [i64, vp, vp, i64, vp, ctypes.POINTER(i64), vp]
+    L.dl_components.restype = ctypes.c_int
+    L.dl_dedup.argtypes = [vp, i32, f64, vp, i32, i32, ctypes.POINTER(dl_join_opts), vp, ctypes.POINTER(i64)]
+    L.dl_dedup.restype = ctypes.c_int
     L.dl_debug_scores.argtypes = [vp, vp, i32, vp, vp, vp]
     L.dl_debug_scores.restype = ctypes.c_int
     L.dl_last_error.restype = ctypes.c_char_p
@@ -307,10 +315,63 @@ def make_opts(precision="auto", self_mode="upper", out_capacity=0, stream=None, 
     return o
 
 
+def color_hist(frames, boxes, bins, out=None, stream=None, timing=None):
+    """dl_color_hist: float32 [n_boxes, br*bg*bb] histograms of the boxes {frame, x0, y0, x1, y1}
+    of frames (a CUDA uint8 tensor [n_frames, H, W, 3]); boxes is a CUDA int32 tensor [n, 5].
+    A dict passed as `timing` receives the counting kernel's event time ("count_ms")."""
+    import torch
+    assert frames.is_cuda and frames.dtype == torch.uint8 and frames.dim() == 4 and frames.shape[3] == 3
+    frames = frames.contiguous()
+    boxes = boxes.contiguous().to(device=frames.device, dtype=torch.int32)
+    br, bg, bb = (int(b) for b in bins)
+    nb = int(boxes.shape[0])
+    if out is None:
+        out = torch.empty((nb, br * bg * bb), dtype=torch.float32, device=frames.device)
+    nF, H, W, _ = frames.shape
+    ms = ctypes.c_float(0.0)
+    rc = load().dl_color_hist(frames.data_ptr(), nF, H, W, boxes.data_ptr(), nb, br, bg, bb, out.data_ptr(),
+                              ctypes.byref(ms) if timing is not None else None, _stream_handle(stream))
+    _check(rc, "dl_color_hist")
+    if timing is not None:
+        timing["count_ms"] = float(ms.value)
+    return out
+
+
+def components(n: int, a, b, stream=None):
+    """dl_components: (label int64 CUDA tensor [n], number of components) of the edges (a[e], b[e])."""
+    import torch
+    a = a.contiguous().to(dtype=torch.int64)
+    b = b.contiguous().to(device=a.device, dtype=torch.int64)
+    label = torch.empty(n, dtype=torch.int64, device=a.device)
+    c = ctypes.c_int64()
+    rc = load().dl_components(int(n), a.data_ptr(), b.data_ptr(), int(a.numel()), label.data_ptr(), ctypes.byref(c),
+                              _stream_handle(stream))
+    _check(rc, "dl_components")
+    return label, int(c.value)
+
+
+def dedup(X: Store, eps: float, labels=None, target: int = 0, plan="all", metric="l2", precision="auto",
+          stream=None):
+    """dl_dedup (q4): (component per caller row as an int64 CUDA tensor, number of distinct objects)."""
+    import torch
+    o = make_opts(precision, "upper", 0, stream, 0, False)
+    comp = torch.empty(X.n, dtype=torch.int64, device="cuda")
+    lab_ptr = None
+    if labels is not None:
+        labels = labels.contiguous().to(device="cuda", dtype=torch.int32)
+        lab_ptr = labels.data_ptr()
+    c = ctypes.c_int64()
+    rc = load().dl_dedup(X.handle, METRICS[metric], float(eps), lab_ptr, int(target), DEDUP_PLANS[plan],
+                         ctypes.byref(o), comp.data_ptr(), ctypes.byref(c))
+    _check(rc, "dl_dedup")
+    return comp, int(c.value)
+
+
 def sim_join(R: Store, S: Store | None, eps: float, precision="auto", self_mode="upper", out_capacity=0,
              stream=None, tile_n=0, timing=False, allow_overflow=False, metric="l2") -> Result:
-    """dl_sim_join: every pair with canonical squared L2 distance <= eps^2, or with
-    metric="cosine" (stores from Store.normalized()) every pair with cosine >= eps."""
+    """dl_sim_join: every pair with canonical squared L2 distance <= eps^2; with
+    metric="cosine" (stores from Store.normalized()) every pair with cosine >= eps; with
+    metric="l1" / "chi2" every pair whose histogram distance is <= eps."""
     o = make_opts(precision, self_mode, out_capacity, stream, tile_n, timing)
     h = ctypes.c_void_p()
     rc = load().dl_sim_join(R.handle, None if S is None else S.handle, METRICS[metric], float(eps),

@@ -160,6 +160,18 @@ def self_clustered_262k(seed: int = SEED_BASE + 1, n: int = 262144, d: int = 128
     return JoinWorkload("self_clustered_262k", X, None, ids, None, eps, groups)
 
 
+def hist_clustered_64k(seed: int = SEED_BASE + 6, n: int = 65536, d: int = 128, n_centroids: int = 2048,
+                       sigma: float = 0.01):
+    """Self-join store of the histogram metrics (L1, chi-square): 65,536 d=128 clustered
+    histograms (2,048 Dirichlet(0.5) centroids + N(0, 0.01^2) jitter, clipped, renormalised;
+    clipping leaves exact zero bins). Returns (features, {metric: eps}) with eps from the
+    oracle-calibrated table (about 20 other rows within eps per row)."""
+    g = rng(seed)
+    X, _ = clustered_histograms(g, n, d, n_centroids, sigma)
+    tab = eps_table()
+    return X, {m: tab.get(f"hist_clustered_64k:{m}:{seed}") for m in ("l1", "chi2")}
+
+
 def clustered_queries(n: int, seed_q: int, store_seed: int, d: int, n_centroids: int, sigma: float,
                       alpha: float = 0.5) -> np.ndarray:
     """Fresh query patches for a clustered store: new jitters of the store's own centroids.
