@@ -427,6 +427,47 @@ def rows_leg(dl, sm_mhz=None, reps=5):
                                     "algorithmic": f"{unit_ops} x d x {P} pairs ({what}), at {mhz:.0f} MHz"}}
     Xs.close()
 
+    # the exact pruned join on tracked objects: dense join, store clustering (one-time), pruned join
+    wt = W.tracked_objects_262k()
+    nt_ = wt.R.shape[0]
+    St = dl.Store(torch.from_numpy(wt.r_ids).cuda(), torch.from_numpy(wt.R).cuda())
+    Pt = nt_ * (nt_ - 1) // 2
+    dst, pst = {}, {}
+
+    def dense_call():
+        r = dl.sim_join(St, None, wt.eps, precision="bf16", timing=True)
+        dst.update(r.stats())
+        r.free()
+
+    for _ in range(4):   # the tile autotuner's trial calls
+        dense_call()
+    ms_dense = _event_ms(dense_call, 3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Ct = St.clustered(1024, iters=5)
+    torch.cuda.synchronize()
+    ms_cluster = 1e3 * (time.perf_counter() - t0)
+
+    def pruned_call():
+        r = dl.sim_join(Ct, None, wt.eps, precision="bf16", timing=True, prune=True)
+        pst.update(r.stats())
+        r.free()
+
+    ms_pruned = _event_ms(pruned_call, 3)
+    assert pst["pairs_out"] == dst["pairs_out"]
+    out["pruned_join"] = {
+        "config": f"tracked_objects_262k: {nt_} x d=128 histograms of 256 tracked objects, self-join, "
+                  f"eps={wt.eps:.6g} (100 matches per row); store clustered by 5 k-means iterations, 1,024 centres",
+        "dense": {"value": Pt / (ms_dense / 1e3) / 1e9, "unit": "Gpairs/s", "ms": ms_dense,
+                  "ms_main": dst["ms_main"], "pairs_out": dst["pairs_out"]},
+        "pruned": {"value": Pt / (ms_pruned / 1e3) / 1e9, "unit": "Gpairs/s (pairs of the join / time)",
+                   "ms": ms_pruned, "ms_main": pst["ms_main"], "pairs_out": pst["pairs_out"],
+                   "tile_pairs": pst["tile_pairs"], "tile_pairs_kept": pst["tile_pairs_kept"]},
+        "cluster_store_ms": ms_cluster,
+        "speedup": ms_dense / ms_pruned}
+    Ct.close()
+    St.close()
+
     wl2 = W.self_clustered_262k()
     labels = torch.from_numpy(W.object_labels(W.rng(W.SEED_BASE + 107), wl2.groups, 8192)).cuda()
     S = dl.Store(torch.from_numpy(wl2.r_ids).cuda(), torch.from_numpy(wl2.R).cuda())

@@ -97,6 +97,9 @@ typedef struct dl_join_opts {
     void *cuda_stream;      /* cudaStream_t the work is ordered on */
     int32_t tile_n;         /* 0: autotuned; else the tensor-core tile width (128 or 256) */
     int32_t timing;         /* 1: record CUDA events around each kernel (dl_result_stats) */
+    int32_t prune;          /* 1: the exact pruned epsilon-join (tensor-core precisions, L2 and
+                               cosine): tile pairs whose bounding balls lie farther apart than
+                               eps are skipped; best on stores from dl_store_cluster */
 } dl_join_opts;
 
 /* Fill `o` with defaults: AUTO precision, upper self mode, auto capacity, NULL stream. */
@@ -129,6 +132,16 @@ int dl_store_create(dl_store **out, const int64_t *ids, const float *feats, int6
  * dl_store_create; the call returns when the new store is ready.
  */
 int dl_store_normalize(const dl_store *in, dl_store **out, void *cuda_stream);
+
+/*
+ * A copy of `in` (same rows, ids and caller rows) in a clustered row order, for the pruned
+ * join (opts.prune; Sec. 5 and Sec. 7.3: the on-the-fly index join). The rows are grouped by
+ * `iters` iterations of k-means with `n_clusters` centres, started from store rows spread
+ * pseudo-randomly (row c * 1000003 mod n for centre c); each assignment step is the exact top-1 join of the rows against the centres. The
+ * order changes no join result, only how many tile pairs the pruned join can skip.
+ * Synchronizes cuda_stream. DL_EINVAL for n_clusters < 1 or iters outside [0, 100].
+ */
+int dl_store_cluster(const dl_store *in, int32_t n_clusters, int32_t iters, dl_store **out, void *cuda_stream);
 
 /* Free a store. Joins that use it must have completed. NULL is accepted. */
 int dl_store_destroy(dl_store *s);
@@ -384,6 +397,8 @@ typedef struct dl_join_stats {
     float ms_recheck;           /* device time of the recheck kernel (opts.timing) */
     float ms_total;             /* device time of all kernels of the call (opts.timing) */
     int32_t kernels_launched;   /* kernels this call launched */
+    int64_t tile_pairs;         /* opts.prune: tile pairs of the join (0 without pruning) */
+    int64_t tile_pairs_kept;    /* opts.prune: tile pairs that survived the ball test */
 } dl_join_stats;
 
 int dl_result_stats(const dl_result *r, dl_join_stats *st);

@@ -14,6 +14,8 @@ selectivity instead and this script turns that into a value:
     all 65,536 rows per metric; the threshold sits in the gap that gives a mean of
     20 other rows per row (these distances are not squared, so the threshold is
     the gap's midpoint itself).
+  * tracked_objects_262k (pruned join): 256 seeded rows against all 262,144 rows;
+    eps sits in the gap that gives a mean of 100 other rows within eps per row.
   * batch_store_2m / serve_store_4m (request workloads): 256 fresh query rows against a
     seeded 65,536-row sample of the store; the pooled distances give a
     (selectivity, eps) table, selectivity = the fraction of store rows within eps.
@@ -123,6 +125,15 @@ def calibrate(name: str) -> tuple[str, float, dict]:
         key = f"rxs_unit_mixture_1m:{W.SEED_BASE + 2}:1048576:512:4096"
         per_row = (sm <= eps * eps).sum(axis=1)
         return key, eps, {"sample_rows": 64, "mean_matches": float(per_row.mean())}
+    if name == "tracked_objects_262k":
+        wl = W.tracked_objects_262k(eps=0.0)
+        g = W.rng(W.SEED_BASE + 108)
+        rows = np.sort(g.choice(wl.R.shape[0], size=256, replace=False))
+        sm = smallest_per_row(wl.R[rows], wl.R, keep=1000, excl=rows)
+        vals = np.sort(sm.ravel())
+        eps = eps_in_gap(vals, 100 * len(rows))
+        key = f"tracked_objects_262k:{W.SEED_BASE + 7}:262144:128:256"
+        return key, eps, {"sample_rows": 256, "mean_matches": float((sm <= eps * eps).sum(axis=1).mean())}
     if name == "hist_clustered_64k":
         X, _ = W.hist_clustered_64k()
         g = W.rng(W.SEED_BASE + 106)
@@ -166,4 +177,4 @@ def main(names):
 
 if __name__ == "__main__":
     main(sys.argv[1:] or ["rxs_histograms_2k", "self_clustered_262k", "rxs_unit_mixture_1m", "batch_store_2m",
-                          "serve_store_4m", "hist_clustered_64k"])
+                          "serve_store_4m", "hist_clustered_64k", "tracked_objects_262k"])

@@ -23,7 +23,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdlsimjoin.so")
 
-SOURCES = ["store.cu", "api.cu", "join_tc.cu", "join_simt.cu", "recheck.cu", "topk.cu", "noalloc.cu", "batch.cu", "server.cu", "tune.cu", "hist.cu", "cc.cu"]
+SOURCES = ["store.cu", "api.cu", "join_tc.cu", "join_simt.cu", "recheck.cu", "topk.cu", "noalloc.cu", "batch.cu", "server.cu", "tune.cu", "hist.cu", "cc.cu", "prune.cu"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off,-O2",

@@ -140,6 +140,9 @@ struct PassCfg {
     double e2;              // squared-L2 threshold (metric 0), or the L1 / chi-square threshold eps
     int metric;             // 0 squared L2 (and cosine), 1 L1, 2 chi-square
     const int64_t *ids;     // ids written for both sides (self-join only; NULL: the store's ids)
+    const int4 *units = nullptr;   // work units of the pruned join
+    int n_units = 0;
+    bool pruned = false;           // the pruned join (units may be empty: every tile pair skipped)
     float t_acc, t_rej;     // FP32 thresholds (exact: recheck/SIMT; plain: SIMT only)
     int64_t cap, band_cap;
     bool timing;
@@ -228,7 +231,12 @@ static int run_pass(const PassCfg &c, PassOut *po)
                 rc = fp8 ? get_tmap8(const_cast<dl_store *>(S), c.BN, &tmB) : get_tmap(const_cast<dl_store *>(S), c.BN, &tmB);
             const int4 *units = nullptr;
             int n_units = 0;
-            if (!rc) rc = get_units(nR, nS, c.self, c.BN, sms, &units, &n_units);
+            if (!rc && c.units) {
+                units = c.units;
+                n_units = c.n_units;
+            } else if (!rc && !c.pruned) {
+                rc = get_units(nR, nS, c.self, c.BN, sms, &units, &n_units);
+            }
             if (!rc && n_units > 0) {
                 TcLaunch L;
                 std::memset(&L.p, 0, sizeof L.p);
@@ -451,7 +459,8 @@ int sim_join_impl(const dl_store *R, const dl_store *S, int32_t metric, double e
     }
     bool tune_trial = false;
     int BN = o.tile_n;
-    if (BN == 0) BN = (prec == DL_PREC_BF16) ? tune_pick(R->dp, self ? 1 : 0, R->n, Sx->n, &tune_trial) : 256;
+    if (BN == 0)
+        BN = (prec == DL_PREC_BF16 && !o.prune) ? tune_pick(R->dp, self ? 1 : 0, R->n, Sx->n, &tune_trial) : 256;
     if (prec == DL_PREC_FP8E4M3 && R->d > 1024) {
         set_error("dl_sim_join: FP8 path supports d <= 1024");
         return DL_EUNSUPPORTED;
@@ -511,6 +520,24 @@ int sim_join_impl(const dl_store *R, const dl_store *S, int32_t metric, double e
         c.band_cap = std::max<int64_t>(1 << 16, want + want / 4);
     }
 
+    int4 *prune_u = nullptr;
+    int64_t tiles_total = 0, tiles_kept = 0;
+    if (o.prune && (prec == DL_PREC_BF16 || prec == DL_PREC_FP8E4M3) && hmetric == 0) {
+        int pn = 0;
+        rc = prune_units(R, Sx, self, BN, e2, c.st, &prune_u, &pn, &tiles_total, &tiles_kept);
+        if (rc) return rc;
+        c.units = prune_u;
+        c.n_units = pn;
+        c.pruned = true;
+    }
+    struct UnitsGuard {
+        int4 *p;
+        cudaStream_t st;
+        ~UnitsGuard()
+        {
+            if (p) dev_free(p, st);
+        }
+    } units_guard{prune_u, c.st};
     PassOut po;
     int reruns = 0;
     for (int attempt = 0;; ++attempt) {
@@ -571,6 +598,8 @@ int sim_join_impl(const dl_store *R, const dl_store *S, int32_t metric, double e
     s.ms_recheck = po.ms_recheck;
     s.ms_total = po.ms_total;
     s.kernels_launched = po.launches * (reruns + 1);
+    s.tile_pairs = tiles_total;
+    s.tile_pairs_kept = tiles_kept;
     *out = res;
     if (fixed && po.out_cnt > (unsigned long long)c.cap) {
         set_error("dl_sim_join: %llu pairs exceed out_capacity %lld", po.out_cnt, (long long)c.cap);

@@ -17,13 +17,13 @@
 //                 loads plus the next 4-byte word (a pixel may straddle the
 //                 segment's end). Every segment starts at the same byte phase
 //                 (48 is a multiple of 3), so the 16 pixel positions inside it
-//                 are compile-time offsets of one of three phases. Runs of equal
-//                 bins are counted in registers and added to the CTA's
-//                 shared-memory histogram with one predicated reduction per run
-//                 (no branches; power-of-two bin counts take shifts instead of
-//                 multiplies); each item ends with one global atomic per
-//                 non-zero bin, and the last item of a box to finish writes
-//                 its histogram, counts / area.
+//                 are compile-time offsets of one of three phases. Each pixel
+//                 adds 1 to its bin in its lane's copy of the CTA's shared
+//                 histogram (up to 32 interleaved copies, so that the lanes of
+//                 a warp never share a bank); power-of-two bin counts take a
+//                 mask, one multiply and a shift. Each item ends with one
+//                 global atomic per non-zero bin, and the last item of a box
+//                 to finish writes its histogram, counts / area.
 #include "kernels.h"
 
 namespace dl {
@@ -33,6 +33,7 @@ namespace {
 constexpr int kHistThreads = 256;
 constexpr int kItemSegs = 2048;     // segments (16 pixels each) per work item
 constexpr int kPlanThreads = 1024;
+constexpr int kMaxSmemHist = 32768; // bytes of interleaved shared histogram copies per CTA
 
 struct HistParams {
     const uint8_t *frames;
@@ -51,6 +52,7 @@ struct HistParams {
     unsigned long long *next_item;  // work counter
     int *bad;                       // set to 1 + box index of an invalid box
     int *box_done;                  // [nb] items of the box counted so far
+    int lcopies;                    // log2 of the shared histogram copies (>= 2)
     float *out;
 };
 
@@ -142,39 +144,30 @@ __device__ __forceinline__ int pixel_bin(uint32_t v, const BinSpec &b)
     }
 }
 
-// Count the pixels of a segment whose first pixel starts at byte PHI of the 13-word window
-// (words 0..11: the segment; word 12: the next segment's first word); bit i of `valid` says
-// whether pixel i belongs to the box row. Runs of equal bins are counted in a register: a
-// pixel whose bin differs from the run's adds the run to the shared histogram (a predicated
-// reduction; an empty first run adds 0) and starts a new run. Invalid pixels take the run's
-// bin and add nothing.
+// Direct form: every valid pixel adds 1 to its bin in this lane's copy of the histogram
+// (2^lc interleaved copies, copy = lane mod 2^lc, word = bin * 2^lc + copy). With 32 copies
+// every lane of a warp owns one bank, so a warp's reductions never conflict, whatever bins
+// its pixels fall in.
 template <int PHI, bool GATHER>
-__device__ __forceinline__ void seg_count(const uint32_t (&w)[13], uint32_t valid, const BinSpec &b, unsigned *sh)
+__device__ __forceinline__ void seg_count_direct(const uint32_t (&w)[13], uint32_t valid, const BinSpec &b,
+                                                 unsigned *sh_lane, int lc)
 {
-    int prev = 0;
-    unsigned run = 0;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        const int o = PHI + 3 * i;       // compile-time after unrolling
+        const int o = PHI + 3 * i;
         const int wi = o >> 2, sft = (o & 3) * 8;
         const uint32_t v = sft ? __funnelshift_r(w[wi], w[wi + 1], sft) : w[wi];
-        const bool ok = (valid >> i) & 1u;
-        const int bin = ok ? pixel_bin<GATHER>(v, b) : prev;
-        const bool change = bin != prev;
-        red_shared_if(sh + prev, run, change);
-        run = (change ? 0u : run) + (ok ? 1u : 0u);
-        prev = bin;
+        red_shared_if(sh_lane + (pixel_bin<GATHER>(v, b) << lc), 1u, (valid >> i) & 1u);
     }
-    red_shared_if(sh + prev, run, run != 0u);
 }
 
 template <bool GATHER>
 __device__ __forceinline__ void seg_count_phase(int phi, const uint32_t (&w)[13], uint32_t valid, const BinSpec &b,
-                                                unsigned *sh)
+                                                unsigned *sh, int lc)
 {
-    if (phi == 0) seg_count<0, GATHER>(w, valid, b, sh);
-    else if (phi == 1) seg_count<1, GATHER>(w, valid, b, sh);
-    else seg_count<2, GATHER>(w, valid, b, sh);
+    if (phi == 0) seg_count_direct<0, GATHER>(w, valid, b, sh, lc);
+    else if (phi == 1) seg_count_direct<1, GATHER>(w, valid, b, sh, lc);
+    else seg_count_direct<2, GATHER>(w, valid, b, sh, lc);
 }
 
 __device__ __forceinline__ uint32_t byte_at(const uint8_t *base, int64_t a, int64_t lo, int64_t hi)
@@ -185,16 +178,18 @@ __device__ __forceinline__ uint32_t byte_at(const uint8_t *base, int64_t a, int6
 template <bool GATHER>
 __global__ void __launch_bounds__(kHistThreads, 4) k_hist_count(HistParams p)
 {
-    extern __shared__ unsigned sh_hist[];   // [d]
+    extern __shared__ __align__(16) unsigned sh_hist[];   // [d][2^lcopies]
     __shared__ long long s_item[2];          // this item and the next one (fetched while this one runs)
     __shared__ bool s_last;
     BinSpec bs;
     bs.br = p.br, bs.bg = p.bg, bs.bb = p.bb, bs.gbb = p.bg * p.bb;
     bs.M = p.gM, bs.K = p.gK, bs.S = p.gS;
+    const int lc = p.lcopies;
     const int64_t total_items = p.item_off[p.nb];
     if (threadIdx.x == 0) s_item[0] = (long long)atomicAdd(p.next_item, 1ull);
+    for (int k = threadIdx.x; k < (p.d << lc) / 4; k += kHistThreads)
+        reinterpret_cast<uint4 *>(sh_hist)[k] = make_uint4(0u, 0u, 0u, 0u);
     for (int it = 0;; ++it) {
-        for (int k = threadIdx.x; k < p.d; k += kHistThreads) sh_hist[k] = 0u;
         __syncthreads();
         const int64_t item = s_item[it & 1];
         if (item >= total_items) break;
@@ -263,12 +258,19 @@ __global__ void __launch_bounds__(kHistThreads, 4) k_hist_count(HistParams p)
                            (byte_at(p.frames, b + 2, s, e) << 16) | (byte_at(p.frames, b + 3, s, e) << 24);
                 }
             }
-            seg_count_phase<GATHER>(phi, w, valid, bs, sh_hist);
+            seg_count_phase<GATHER>(phi, w, valid, bs, sh_hist + (threadIdx.x & ((1 << lc) - 1)), lc);
         }
         __syncthreads();
         unsigned *gc = p.counts + box * p.d;
         for (int k = threadIdx.x; k < p.d; k += kHistThreads) {
-            const unsigned c = sh_hist[k];
+            unsigned c = 0;
+            for (int q0 = 0; q0 < (1 << lc); q0 += 4) {
+                const int q = (q0 + 4 * k) & ((1 << lc) - 1);   // rotated start: neighbouring bins read other banks
+                uint4 *cell = reinterpret_cast<uint4 *>(sh_hist + (k << lc) + q);
+                const uint4 t = *cell;
+                *cell = make_uint4(0u, 0u, 0u, 0u);   // leaves the copies zeroed for the next item
+                c += t.x + t.y + t.z + t.w;
+            }
             if (c) atomicAdd(gc + k, c);
         }
         // the box's last item to finish turns its counts into the histogram
@@ -391,7 +393,9 @@ int color_hist_impl(const uint8_t *frames, int64_t n_frames, int32_t H, int32_t 
     }
     if (e == cudaSuccess) {
         int sms = device_sm_count();
-        const size_t smem = (size_t)d * 4;
+        p.lcopies = 5;
+        while (p.lcopies > 2 && ((size_t)d << p.lcopies) * 4 > (size_t)kMaxSmemHist) --p.lcopies;
+        const size_t smem = ((size_t)d << p.lcopies) * 4;
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hist_count<true>, kHistThreads, smem);
         if (e == cudaSuccess && count_ms) {

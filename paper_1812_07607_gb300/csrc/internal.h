@@ -87,6 +87,13 @@ struct Store {
     float2 *rowb8 = nullptr; // [n] {||x - s x8|| up, ||s x8|| up}
     float4 *cstat8 = nullptr;// [n_pad/32] {P1, P2 (FP8), P3, beta_min}
     TmapCache tmaps8[3];     // FP8 boxes
+    struct BallCache {       // bounding balls of the pruned join's tiles, per tile height
+        int rows = 0;
+        void *blk = nullptr;
+        const float *centre = nullptr;   // [kMaxSeg][d][tiles]: ball u's centre coordinate k of each tile
+        const float *radius = nullptr;   // [tiles][kMaxSeg]
+        const int *nseg = nullptr;       // [tiles] balls of each tile
+    } balls[2];
     std::mutex mu;           // guards tmaps and hints
     float nq_max = 0.f;      // largest ||x||^2 of the store (FP32 sum; used only inside slack terms)
     int64_t hint_pairs = 0;  // last output size seen with this store as R (capacity hint)
@@ -94,6 +101,7 @@ struct Store {
     double hint_batch_rate = 0.0;   // batch calls: candidates per evaluated pair last seen against this store
     bool unit = false;       // rows are the unit-normalized rows of another store (cosine metric)
     int nonneg = 0;          // 0 not checked yet, 1 every feature >= 0, 2 some feature < 0 (chi-square)
+    int32_t *clabel = nullptr;   // [n] cluster of each store row (stores from dl_store_cluster), else NULL
 };
 
 // Create a store; gather == NULL orders rows by norm, else store row i is caller row gather[i].
@@ -107,6 +115,11 @@ int store_nonneg(Store *s, cudaStream_t st, bool *ok);
 // replaces the ids written to the output when not NULL.
 int sim_join_impl(const dl_store *R, const dl_store *S, int32_t metric, double eps, const dl_join_opts *opts,
                   dl_result **out, const int64_t *emit_ids);
+
+// Work units of the pruned join: the (R tile, S tile) pairs whose bounding balls may hold a
+// pair within eps (prune.cu). *d_units is device memory from dev_alloc (NULL when none).
+int prune_units(const dl_store *R, const dl_store *S, bool upper, int BN, double e2, cudaStream_t st, int4 **d_units,
+                int *n_units, int64_t *tiles_total, int64_t *tiles_kept);
 
 // Build (or fetch from the store's cache) a 2-D BF16 tensor map over the store's
 // BF16 copy with a box of 64 columns x box_rows rows and the 128-byte swizzle.

@@ -860,6 +860,9 @@ int dl_store_destroy(dl_store *s)
     if (prev != s->device) cudaSetDevice(s->device);
     dev_free(s->ids, 0);   // ids is the base of the store's single allocation
     if (s->fp8_block) dev_free(s->fp8_block, 0);
+    if (s->clabel) dev_free(s->clabel, 0);
+    for (auto &b : s->balls)
+        if (b.blk) dev_free(b.blk, 0);
     if (prev != s->device) cudaSetDevice(prev);
     delete s;
     return DL_OK;

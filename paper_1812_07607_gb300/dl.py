@@ -37,7 +37,7 @@ EXPORTS = [
     "dl_result_stats", "dl_result_free", "dl_last_error", "dl_version", "dl_kernel_launches",
     "dl_sim_join_noalloc", "dl_batch_join", "dl_result_request_pairs", "dl_result_request_topk",
     "dl_server_create", "dl_submit", "dl_poll", "dl_cancel", "dl_server_get_stats", "dl_server_destroy",
-    "dl_debug_scores", "dl_store_normalize", "dl_color_hist", "dl_components", "dl_dedup",
+    "dl_debug_scores", "dl_store_normalize", "dl_color_hist", "dl_components", "dl_dedup", "dl_store_cluster",
 ]
 
 
@@ -50,7 +50,7 @@ class DLError(RuntimeError):
 class dl_join_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("self_mode", ctypes.c_int32),
                 ("out_capacity", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
-                ("tile_n", ctypes.c_int32), ("timing", ctypes.c_int32)]
+                ("tile_n", ctypes.c_int32), ("timing", ctypes.c_int32), ("prune", ctypes.c_int32)]
 
 
 class dl_join_stats(ctypes.Structure):
@@ -58,7 +58,8 @@ class dl_join_stats(ctypes.Structure):
                 ("band_pairs", ctypes.c_int64), ("fp64_pairs", ctypes.c_int64),
                 ("reruns", ctypes.c_int64), ("precision", ctypes.c_int32), ("tile_n", ctypes.c_int32),
                 ("ms_main", ctypes.c_float), ("ms_recheck", ctypes.c_float), ("ms_total", ctypes.c_float),
-                ("kernels_launched", ctypes.c_int32)]
+                ("kernels_launched", ctypes.c_int32), ("tile_pairs", ctypes.c_int64),
+                ("tile_pairs_kept", ctypes.c_int64)]
 
 
 class dl_request(ctypes.Structure):
@@ -125,6 +126,8 @@ def load(path: str | None = None):
     L.dl_server_destroy.argtypes = [vp]
     for name in ("dl_server_create", "dl_submit", "dl_poll", "dl_cancel", "dl_server_get_stats", "dl_server_destroy"):
         getattr(L, name).restype = ctypes.c_int
+    L.dl_store_cluster.argtypes = [vp, i32, i32, pp, vp]
+    L.dl_store_cluster.restype = ctypes.c_int
     L.dl_color_hist.argtypes = [vp, i64, i32, i32, vp, i64, i32, i32, i32, vp, ctypes.POINTER(ctypes.c_float), vp]
     L.dl_color_hist.restype = ctypes.c_int
     L.dl_components.argtypes = [i64, vp, vp, i64, vp, ctypes.POINTER(i64), vp]
@@ -218,6 +221,16 @@ class Store:
         out.n, out.d = self.n, self.d
         return out
 
+    def clustered(self, n_clusters: int, iters: int = 4, stream=None) -> "Store":
+        """dl_store_cluster: the same rows in a k-means-grouped order (for sim_join(prune=True))."""
+        h = ctypes.c_void_p()
+        _check(load().dl_store_cluster(self._h, int(n_clusters), int(iters), ctypes.byref(h), _stream_handle(stream)),
+               "dl_store_cluster")
+        out = Store.__new__(Store)
+        out._h = h
+        out.n, out.d = self.n, self.d
+        return out
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             load().dl_store_destroy(self._h)
@@ -303,7 +316,8 @@ class Result:
             pass
 
 
-def make_opts(precision="auto", self_mode="upper", out_capacity=0, stream=None, tile_n=0, timing=False):
+def make_opts(precision="auto", self_mode="upper", out_capacity=0, stream=None, tile_n=0, timing=False,
+              prune=False):
     o = dl_join_opts()
     load().dl_join_opts_default(ctypes.byref(o))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -312,6 +326,7 @@ def make_opts(precision="auto", self_mode="upper", out_capacity=0, stream=None, 
     o.cuda_stream = _stream_handle(stream)
     o.tile_n = int(tile_n)
     o.timing = 1 if timing else 0
+    o.prune = 1 if prune else 0
     return o
 
 
@@ -368,11 +383,11 @@ def dedup(X: Store, eps: float, labels=None, target: int = 0, plan="all", metric
 
 
 def sim_join(R: Store, S: Store | None, eps: float, precision="auto", self_mode="upper", out_capacity=0,
-             stream=None, tile_n=0, timing=False, allow_overflow=False, metric="l2") -> Result:
+             stream=None, tile_n=0, timing=False, allow_overflow=False, metric="l2", prune=False) -> Result:
     """dl_sim_join: every pair with canonical squared L2 distance <= eps^2; with
     metric="cosine" (stores from Store.normalized()) every pair with cosine >= eps; with
     metric="l1" / "chi2" every pair whose histogram distance is <= eps."""
-    o = make_opts(precision, self_mode, out_capacity, stream, tile_n, timing)
+    o = make_opts(precision, self_mode, out_capacity, stream, tile_n, timing, prune)
     h = ctypes.c_void_p()
     rc = load().dl_sim_join(R.handle, None if S is None else S.handle, METRICS[metric], float(eps),
                             ctypes.byref(o), ctypes.byref(h))

@@ -172,6 +172,20 @@ def hist_clustered_64k(seed: int = SEED_BASE + 6, n: int = 65536, d: int = 128, 
     return X, {m: tab.get(f"hist_clustered_64k:{m}:{seed}") for m in ("l1", "chi2")}
 
 
+def tracked_objects_262k(seed: int = SEED_BASE + 7, n: int = 262144, d: int = 128, n_objects: int = 256,
+                         sigma: float = 0.003, eps: float | None = None) -> JoinWorkload:
+    """Self-join store of the pruned join: 262,144 d=128 patch histograms of 256 tracked objects
+    (about 1,024 views each, as a pedestrian or vehicle seen over many frames; q4), each view its
+    object's Dirichlet(0.5) histogram plus N(0, 0.003^2) jitter, clipped and renormalised.
+    eps from the oracle-calibrated table: a mean of 100 other rows within eps per row."""
+    g = rng(seed)
+    X, groups = clustered_histograms(g, n, d, n_objects, sigma)
+    ids = patch_ids(g, n)
+    if eps is None:
+        eps = eps_table().get(f"tracked_objects_262k:{seed}:{n}:{d}:{n_objects}")
+    return JoinWorkload("tracked_objects_262k", X, None, ids, None, eps, groups)
+
+
 def clustered_queries(n: int, seed_q: int, store_seed: int, d: int, n_centroids: int, sigma: float,
                       alpha: float = 0.5) -> np.ndarray:
     """Fresh query patches for a clustered store: new jitters of the store's own centroids.
