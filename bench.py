@@ -741,7 +741,19 @@ def _case_l1_16k():
     return lambda: dl.sim_join(Xs, None, thr["l1"], metric="l1", timing=True)
 
 
+def _case_pruned_tracked():
+    """The pruned self-join of tracked_objects_262k on its clustered store (1,024 centres, 5 iterations)."""
+    import torch
+    from paper_1812_07607_gb300 import dl, workloads as W
+    dl.load()
+    wt = W.tracked_objects_262k()
+    St = dl.Store(torch.from_numpy(wt.r_ids).cuda(), torch.from_numpy(wt.R).cuda())
+    Ct = St.clustered(1024, iters=5)
+    return lambda: dl.sim_join(Ct, None, wt.eps, precision="bf16", timing=True, prune=True)
+
+
 PROFILE_CASES = {"fp8_unit_d512_65536": _case_fp8_unit_d512, "dense_d256_16384x1m": _case_dense_d256,
+                 "pruned_tracked_262k": _case_pruned_tracked,
                  "color_hist_1080p": _case_color_hist_1080p, "l1_hist_16384": _case_l1_16k}
 
 
