@@ -68,3 +68,28 @@ def test_no_cpu_fallback():
     with pytest.raises(dl.DLError) as ei:
         dl.Store(np.arange(4, dtype=np.int64), np.ones((4, 8), np.float32))
     assert ei.value.status == dl.DL_ECUDA
+
+
+def test_further_rows_validation_without_gpu(lib):
+    """The further rows' entry points reject bad arguments before any CUDA work."""
+    from paper_1812_07607_gb300 import dl
+    h = ctypes.c_void_p()
+    c = ctypes.c_int64()
+    ms = ctypes.c_float()
+    # colour histograms: bin counts outside [1, 256] or d > 1024, negative sizes, NULL inputs
+    for bins in ((0, 1, 1), (257, 1, 1), (16, 16, 8)):
+        assert lib.dl_color_hist(None, 1, 8, 8, None, 1, *bins, None, None, None) == dl.DL_EINVAL
+    assert lib.dl_color_hist(None, -1, 8, 8, None, 1, 4, 4, 4, None, None, None) == dl.DL_EINVAL
+    assert lib.dl_color_hist(None, 1, 8, 8, None, 3, 4, 4, 4, None, ctypes.byref(ms), None) == dl.DL_EINVAL
+    assert lib.dl_color_hist(None, 1, 8, 8, None, 0, 4, 4, 4, None, None, None) == dl.DL_OK   # no boxes: no work
+    # components: negative sizes, n >= 2^31, NULL arrays; an empty graph needs no GPU
+    assert lib.dl_components(-1, None, None, 0, None, ctypes.byref(c), None) == dl.DL_EINVAL
+    assert lib.dl_components(1 << 31, None, None, 0, None, ctypes.byref(c), None) == dl.DL_EINVAL
+    assert lib.dl_components(5, None, None, 3, None, ctypes.byref(c), None) == dl.DL_EINVAL
+    assert lib.dl_components(0, None, None, 0, None, ctypes.byref(c), None) == dl.DL_OK and c.value == 0
+    # dedup and clustering: NULL stores and bad plans / cluster counts
+    assert lib.dl_dedup(None, 0, 0.1, None, 0, 0, None, None, ctypes.byref(c)) == dl.DL_EINVAL
+    assert lib.dl_store_cluster(None, 4, 2, ctypes.byref(h), None) == dl.DL_EINVAL
+    # the new metrics are part of the join's metric enum; an unknown metric is rejected
+    assert lib.dl_sim_join(None, None, 2, 0.1, None, ctypes.byref(h)) == dl.DL_EINVAL
+    assert lib.dl_last_error()
