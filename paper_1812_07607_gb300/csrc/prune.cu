@@ -114,18 +114,27 @@ __global__ void __launch_bounds__(256)
     bool keep = false;
     if (t < nt) {
         const int nb = nS_seg[t];
-        for (int u = 0; u < na && !keep; ++u)
-            for (int v = 0; v < nb && !keep; ++v) {
-                const float *a = cm + u * d;
-                const float *b = cS + (int64_t)v * d * nt + t;
-                float s = 0.f;
-                for (int k = 0; k < d; ++k) {
-                    const float w = a[k] - __ldg(b + (int64_t)k * nt);
-                    s = fmaf(w, w, s);
-                }
-                const float lower = sqrtf(s) * (1.0f - 1e-4f) - rR[m * kMaxSeg + u] - rS[t * kMaxSeg + v];
-                keep = !(lower > 0.f && lower * lower > e2_up);
+        for (int v = 0; v < nb && !keep; ++v) {
+            // one pass over S ball v's centre serves every ball of the R tile
+            float su[kMaxSeg] = {0.f, 0.f, 0.f, 0.f};
+            const float *b = cS + (int64_t)v * d * nt + t;
+#pragma unroll 8
+            for (int k = 0; k < d; ++k) {
+                const float bv = __ldg(b + (int64_t)k * nt);
+#pragma unroll
+                for (int u = 0; u < kMaxSeg; ++u)
+                    if (u < na) {
+                        const float w = cm[u * d + k] - bv;
+                        su[u] = fmaf(w, w, su[u]);
+                    }
             }
+#pragma unroll
+            for (int u = 0; u < kMaxSeg; ++u)
+                if (u < na) {
+                    const float lower = sqrtf(su[u]) * (1.0f - 1e-4f) - rR[m * kMaxSeg + u] - rS[t * kMaxSeg + v];
+                    keep |= !(lower > 0.f && lower * lower > e2_up);
+                }
+        }
     }
     const unsigned word = __ballot_sync(0xffffffffu, keep);
     const int ntw = (nt + 31) >> 5;
