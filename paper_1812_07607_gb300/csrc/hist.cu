@@ -30,8 +30,8 @@ namespace dl {
 
 namespace {
 
-constexpr int kHistThreads = 256;
-constexpr int kItemSegs = 2048;     // segments (16 pixels each) per work item
+constexpr int kHistThreads = 128;
+constexpr int kItemSegs = 1024;     // segments (16 pixels each) per work item
 constexpr int kPlanThreads = 1024;
 constexpr int kMaxSmemHist = 32768; // bytes of interleaved shared histogram copies per CTA
 
@@ -176,7 +176,7 @@ __device__ __forceinline__ uint32_t byte_at(const uint8_t *base, int64_t a, int6
 }
 
 template <bool GATHER>
-__global__ void __launch_bounds__(kHistThreads, 4) k_hist_count(HistParams p)
+__global__ void __launch_bounds__(kHistThreads, 8) k_hist_count(HistParams p)
 {
     extern __shared__ __align__(16) unsigned sh_hist[];   // [d][2^lcopies]
     __shared__ long long s_item[2];          // this item and the next one (fetched while this one runs)
