@@ -169,7 +169,7 @@ int dl_color_hist(const uint8_t *frames, int64_t n_frames, int32_t H, int32_t W,
                   void *cuda_stream);
 
 /* ---------------------------------------------------------------------------------
- * q4 deduplication (Sec. 6.2 q4, Sec. 7.5 and Table 1).
+ * q4 deduplication (Sec. 6.2 q4, Sec. 7.4.3 and Table 1).
  * ------------------------------------------------------------------------------- */
 
 /*

@@ -240,7 +240,7 @@ class Oracle:
         return label, int(c)
 
     def dedup(self, X, eps: float, labels=None, target: int = 0, plan: int = DEDUP_ALL):
-        """q4 (Sec. 6.2, Sec. 7.5): (component label per row, number of distinct objects).
+        """q4 (Sec. 6.2, Sec. 7.4.3): (component label per row, number of distinct objects).
 
         DEDUP_ALL: components of the epsilon self-join of every row.
         DEDUP_FILTER_MATCH: keep the rows whose label is `target`, join them, count their

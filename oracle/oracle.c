@@ -38,7 +38,7 @@
  *     8-bit interleaved RGB pixels; channel value v falls in bin floor(v*b/256)
  *     of its channel's b bins, the joint bin is (r*bg + g)*bb + b, and the
  *     histogram is count / (pixels in the box), one FP32 division per bin.
- *   - q4 deduplication (Sec. 6.2 q4, Sec. 7.5): the distinct objects are the
+ *   - q4 deduplication (Sec. 6.2 q4, Sec. 7.4.3): the distinct objects are the
  *     connected components of the self-join's pairs; each row is labelled with
  *     the smallest row index of its component.
  *

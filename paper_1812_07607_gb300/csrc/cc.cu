@@ -1,4 +1,4 @@
-// cc.cu -- q4 deduplication (Sec. 6.2 q4, Sec. 7.5): connected components of the
+// cc.cu -- q4 deduplication (Sec. 6.2 q4, Sec. 7.4.3): connected components of the
 // epsilon self-join's pairs, and the two plan orders of Table 1.
 //
 // Components are found by concurrent union-find over a parent array:

@@ -624,7 +624,7 @@ def pin_components_closed_forms(orc):
 
 
 def pin_dedup_plans_hand_example(orc):
-    """q4's two plan orders (Sec. 7.5) on a hand-built line of rows: 0-1 and 1-2 match, 0-2 do not."""
+    """q4's two plan orders (Sec. 7.4.3) on a hand-built line of rows: 0-1 and 1-2 match, 0-2 do not."""
     X = np.array([[0.0], [1.0], [2.0], [10.0], [20.0], [21.0]], dtype=np.float32)
     P, C = 1, 2
     labels = np.array([P, C, P, P, C, C], dtype=np.int32)
