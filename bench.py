@@ -179,6 +179,37 @@ def cpu_oracle_rate(wl, budget_s: float):
     return pairs / dt / 1e9, {"rows": rows, "pairs": pairs, "seconds": round(dt, 3)}
 
 
+def cpu_oracle_rows(W):
+    """The FP64 CPU oracle (one thread) on bounded samples of the further rows' workloads, in
+    the units of their GPU figures. Inputs come from the generators only."""
+    import oracle
+    orc = oracle.default()
+    out = {"cores": 1, "kind": "oracle"}
+    wl = W.traffic_boxes_1080p()
+    boxes = wl.boxes[:512]
+    px = int(((boxes[:, 3] - boxes[:, 1]).astype(np.int64) * (boxes[:, 4] - boxes[:, 2])).sum())
+    t0 = time.perf_counter()
+    orc.color_hist(wl.frames, boxes, wl.bins)
+    dt = time.perf_counter() - t0
+    out["color_hist"] = {"value": (3 * px + 4 * 128 * len(boxes)) / dt / 1e9, "unit": "GB/s",
+                         "sample": f"the first {len(boxes)} boxes ({px} pixels), {dt:.3f} s"}
+    X, thr = W.hist_clustered_64k()
+    for name, metric in (("l1", oracle.METRIC_L1), ("chi2", oracle.METRIC_CHI2)):
+        t0 = time.perf_counter()
+        orc.hist_join(X[:16], X, thr[name], metric, oracle.MODE_RXS)
+        dt = time.perf_counter() - t0
+        out[name] = {"value": 16 * X.shape[0] / dt / 1e9, "unit": "Gpairs/s",
+                     "sample": f"16 rows x all {X.shape[0]} rows, {dt:.3f} s"}
+    wl2 = W.self_clustered_262k()
+    Y = np.ascontiguousarray(wl2.R[:4096])
+    t0 = time.perf_counter()
+    _, c = orc.dedup(Y, wl2.eps)
+    dt = time.perf_counter() - t0
+    out["dedup"] = {"value": 4096 / dt, "unit": "rows/s", "distinct": c,
+                    "sample": f"the first 4,096 rows: self-join (8.4 M pairs) and components, {dt:.3f} s"}
+    return out
+
+
 def batch_leg(dl, seed=SEED_BATCH, n_req=4096, reps=2):
     """The batching config: 4,096 eps / top-k requests in ONE dl_batch_join on the 2,097,152 x 128 store.
 
@@ -488,6 +519,10 @@ def rows_leg(dl, sm_mhz=None, reps=5):
     S.close()
     out["dedup"] = dd
     del scratch
+    try:
+        out["cpu_baseline"] = cpu_oracle_rows(W)
+    except Exception as exc:   # the CPU figures are context; never lose the GPU ones for them
+        out["cpu_baseline"] = {"error": repr(exc)[:200]}
     return out
 
 
