@@ -686,7 +686,10 @@ def run_ours(args):
         precision = precision_leg(dl)
     rows = None
     if rank == 0 and not args.no_rows:
-        rows = rows_leg(dl, clocks.get("sm_mhz"))
+        try:
+            rows = rows_leg(dl, clocks.get("sm_mhz"))
+        except Exception as exc:   # a failing further row must not cost the bench line
+            rows = {"error": repr(exc)[:300]}
 
     cpu = None
     if rank == 0 and not args.no_baselines:
