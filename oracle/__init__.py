@@ -84,6 +84,9 @@ def load(path: str | None = None):
     lib.oracle_color_hist.restype = ctypes.c_int64
     lib.oracle_color_hist.argtypes = [u8p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, i32p, ctypes.c_int64,
                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, f32p]
+    lib.oracle_hist_topk.restype = ctypes.c_int32
+    lib.oracle_hist_topk.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_int32, i64p, f64p]
     lib.oracle_components.restype = ctypes.c_int64
     lib.oracle_components.argtypes = [ctypes.c_int64, i64p, i64p, ctypes.c_int64, i64p]
     if path == _LIB_PATH:
@@ -209,6 +212,19 @@ class Oracle:
             if n <= cap:
                 return np.stack([out_r[:n], out_s[:n]], axis=1)
             cap = int(n)
+
+    def hist_topk(self, Q, S, k: int, metric: int = METRIC_L1):
+        """(idx int64 [nQ, k], dist float64 [nQ, k]) by (L1 or chi-square distance, store row); unused slots -1."""
+        Q, Qp = _f32(Q)
+        S, Sp = _f32(S)
+        idx = np.empty((Q.shape[0], k), dtype=np.int64)
+        dist = np.empty((Q.shape[0], k), dtype=np.float64)
+        rc = self.lib.oracle_hist_topk(Qp, Q.shape[0], Sp, S.shape[0], Q.shape[1], int(metric), int(k),
+                                       idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                       dist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        if rc != 0:
+            raise MemoryError("oracle_hist_topk: allocation failed")
+        return idx, dist
 
     def color_hist(self, frames, boxes, bins) -> np.ndarray:
         """Histograms [nb, br*bg*bb] of the boxes {frame, x0, y0, x1, y1} of frames [nF, H, W, 3] (uint8)."""

@@ -33,7 +33,8 @@
  *     k ascending, t = (double)q_k - (double)x_k, s = s + |t| (L1), or
  *     u = (double)q_k + (double)x_k and, where u > 0, s = s + (t*t)/u
  *     (chi-square, no factor 1/2); every operation rounded to nearest. A pair
- *     matches iff s <= eps (these distances are not squared).
+ *     matches iff s <= eps (these distances are not squared); their top-k orders
+ *     by (distance, store row) as the L2 top-k does.
  *   - colour histograms (Sec. 4.1 transformers): a patch is a box of a frame of
  *     8-bit interleaved RGB pixels; channel value v falls in bin floor(v*b/256)
  *     of its channel's b bins, the joint bin is (r*bg + g)*bb + b, and the
@@ -322,4 +323,32 @@ int64_t oracle_components(int64_t n, const int64_t *a, const int64_t *b, int64_t
     int64_t c = 0;
     for (int64_t i = 0; i < n; ++i) c += (label[i] == i);
     return c;
+}
+
+/*
+ * Top-k with a histogram distance (metric 1 = L1, 2 = chi-square): for every query row,
+ * the store rows ordered by (canonical distance, store row index), first min(k, nS) kept;
+ * entries past that are -1 / -1.0. Returns 0, or -1 when the scratch allocation fails.
+ */
+int32_t oracle_hist_topk(const float *Q, int64_t nQ, const float *S, int64_t nS, int32_t d, int32_t metric,
+                         int32_t k, int64_t *out_idx, double *out_d)
+{
+    oracle_cand *c = (oracle_cand *)malloc(sizeof(oracle_cand) * (size_t)(nS > 0 ? nS : 1));
+    if (!c) return -1;
+    const int64_t keep = (k < nS) ? k : nS;
+    for (int64_t i = 0; i < nQ; ++i) {
+        const float *q = Q + i * (int64_t)d;
+        for (int64_t j = 0; j < nS; ++j) {
+            const float *x = S + j * (int64_t)d;
+            c[j].d2 = (metric == 1) ? oracle_l1dist(q, x, d) : oracle_chi2dist(q, x, d);
+            c[j].j = j;
+        }
+        qsort(c, (size_t)nS, sizeof(oracle_cand), cand_cmp);
+        for (int64_t t = 0; t < k; ++t) {
+            out_idx[i * k + t] = (t < keep) ? c[t].j : -1;
+            out_d[i * k + t] = (t < keep) ? c[t].d2 : -1.0;
+        }
+    }
+    free(c);
+    return 0;
 }

@@ -468,6 +468,28 @@ def pin_hist_closed_forms(orc):
             assert c2 <= l1 * (1 + 30 * 2.0**-53), (i, j, c2, l1)
 
 
+def pin_hist_topk_order_ties_and_join(orc):
+    """Histogram top-k: exact rational order where values are well separated, ties (duplicate
+    rows) by the smaller store row, -1 past |S|, and the join's matches as a prefix."""
+    g = _g(36)
+    for metric, ex in ((oracle.METRIC_L1, exact_l1), (oracle.METRIC_CHI2, exact_chi2)):
+        Q = W.dirichlet_histograms(g, 4, 7)
+        S = W.dirichlet_histograms(g, 12, 7)
+        S[9] = S[2]                      # a duplicate: equal distances, row 2 first
+        k = 15
+        idx, dist = orc.hist_topk(Q, S, k, metric)
+        for i in range(Q.shape[0]):
+            exact = [ex(Q[i], S[j]) for j in range(S.shape[0])]
+            order = sorted(range(S.shape[0]), key=lambda j: (exact[j], j))
+            assert idx[i, :12].tolist() == order, (metric, i)
+            assert np.all(idx[i, 12:] == -1) and np.all(dist[i, 12:] == -1.0)
+            assert np.all(np.diff(dist[i, :12]) >= 0)
+            assert idx[i].tolist().index(2) < idx[i].tolist().index(9)
+            t = float(dist[i, 5])
+            m = orc.hist_join(Q[i:i + 1], S, t, metric, MODE_RXS)
+            assert set(m[:, 1].tolist()) == set(idx[i, :len(m)].tolist())
+
+
 # ----------------------------------------------------------------------------------------
 # colour-histogram transformer
 # ----------------------------------------------------------------------------------------
@@ -655,6 +677,7 @@ ALL_PINS = [
     pin_hist_dist_within_rounding_of_exact,
     pin_hist_join_matches_exact_rational,
     pin_hist_closed_forms,
+    pin_hist_topk_order_ties_and_join,
     pin_color_hist_golden_fixture,
     pin_color_hist_binning_definition,
     pin_color_hist_invariants,
