@@ -87,6 +87,11 @@ def load(path: str | None = None):
     lib.oracle_hist_topk.restype = ctypes.c_int32
     lib.oracle_hist_topk.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                      ctypes.c_int32, i64p, f64p]
+    lib.oracle_dot.restype = ctypes.c_double
+    lib.oracle_dot.argtypes = [f32p, f32p, ctypes.c_int32]
+    lib.oracle_ip_join.restype = ctypes.c_int64
+    lib.oracle_ip_join.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
+                                   ctypes.c_int32, i64p, i64p, ctypes.c_int64]
     lib.oracle_components.restype = ctypes.c_int64
     lib.oracle_components.argtypes = [ctypes.c_int64, i64p, i64p, ctypes.c_int64, i64p]
     if path == _LIB_PATH:
@@ -209,6 +214,32 @@ class Oracle:
             out_s = np.empty(cap, dtype=np.int64)
             n = self.lib.oracle_hist_join(Rp, R.shape[0], Sp, nS, R.shape[1], int(metric), float(eps), mode,
                                           out_r.ctypes.data_as(i64), out_s.ctypes.data_as(i64), cap)
+            if n <= cap:
+                return np.stack([out_r[:n], out_s[:n]], axis=1)
+            cap = int(n)
+
+    def dot(self, q, x) -> float:
+        q, qp = _f32(q)
+        x, xp = _f32(x)
+        return float(self.lib.oracle_dot(qp, xp, int(q.shape[-1])))
+
+    def ip_join(self, R, S=None, t: float = 0.0, mode: int | None = None) -> np.ndarray:
+        """Row-index pairs with canonical inner product q.x >= t, in nested-loop order."""
+        R, Rp = _f32(R)
+        if mode is None:
+            mode = MODE_RXS if S is not None else MODE_SELF_UPPER
+        if S is None:
+            S, Sp, nS = R, Rp, R.shape[0]
+        else:
+            S, Sp = _f32(S)
+            nS = S.shape[0]
+        i64 = ctypes.POINTER(ctypes.c_int64)
+        cap = 1 << 16
+        while True:
+            out_r = np.empty(cap, dtype=np.int64)
+            out_s = np.empty(cap, dtype=np.int64)
+            n = self.lib.oracle_ip_join(Rp, R.shape[0], Sp, nS, R.shape[1], float(t), mode,
+                                        out_r.ctypes.data_as(i64), out_s.ctypes.data_as(i64), cap)
             if n <= cap:
                 return np.stack([out_r[:n], out_s[:n]], axis=1)
             cap = int(n)

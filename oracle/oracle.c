@@ -35,6 +35,10 @@
  *     (chi-square, no factor 1/2); every operation rounded to nearest. A pair
  *     matches iff s <= eps (these distances are not squared); their top-k orders
  *     by (distance, store row) as the L2 top-k does.
+ *   - inner-product threshold (the general form of the cosine metric on rows of
+ *     any norm): the canonical dot product s = s + (double)q_k * (double)x_k, k
+ *     ascending, each step rounded to nearest (the FP64 products of two floats are
+ *     exact); a pair matches iff s >= t.
  *   - colour histograms (Sec. 4.1 transformers): a patch is a box of a frame of
  *     8-bit interleaved RGB pixels; channel value v falls in bin floor(v*b/256)
  *     of its channel's b bins, the joint bin is (r*bg + g)*bb + b, and the
@@ -351,4 +355,34 @@ int32_t oracle_hist_topk(const float *Q, int64_t nQ, const float *S, int64_t nS,
     }
     free(c);
     return 0;
+}
+
+/* Canonical dot product (k ascending, FP64, round to nearest; the products are exact). */
+double oracle_dot(const float *q, const float *x, int32_t d)
+{
+    double s = 0.0;
+    for (int32_t k = 0; k < d; ++k) s = s + (double)q[k] * (double)x[k];
+    return s;
+}
+
+/* Inner-product threshold join: pairs with canonical q.x >= t; modes and output as oracle_join. */
+int64_t oracle_ip_join(const float *R, int64_t nR, const float *S, int64_t nS, int32_t d, double t, int32_t mode,
+                       int64_t *out_r, int64_t *out_s, int64_t cap)
+{
+    const float *T = (mode == 0) ? S : R;
+    const int64_t nT = (mode == 0) ? nS : nR;
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < nR; ++i) {
+        int64_t j0 = (mode == 1) ? i + 1 : 0;
+        for (int64_t j = j0; j < nT; ++j) {
+            if (oracle_dot(R + i * (int64_t)d, T + j * (int64_t)d, d) >= t) {
+                if (cnt < cap) {
+                    out_r[cnt] = i;
+                    out_s[cnt] = j;
+                }
+                ++cnt;
+            }
+        }
+    }
+    return cnt;
 }

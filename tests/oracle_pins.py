@@ -490,6 +490,51 @@ def pin_hist_topk_order_ties_and_join(orc):
             assert set(m[:, 1].tolist()) == set(idx[i, :len(m)].tolist())
 
 
+def pin_inner_product_exact(orc):
+    """The canonical dot product within (d+1) 2^-53 sum|q_k x_k| of the exact rational value
+    (products exact in FP64); the inner-product join equal to the exact rational set in all
+    three modes; on unit rows, consistent with the cosine join outside a small margin."""
+    g = _g(37)
+    for d in (1, 3, 16, 40):
+        X = W.mixed_magnitude_rows(g, 6, d) * np.where(g.random((6, d)) < 0.5, -1, 1).astype(np.float32)
+        for i in range(6):
+            for j in range(6):
+                ex = sum(Fraction(a) * Fraction(b) for a, b in zip(X[i].tolist(), X[j].tolist()))
+                mag = sum(abs(Fraction(a) * Fraction(b)) for a, b in zip(X[i].tolist(), X[j].tolist()))
+                assert abs(Fraction(orc.dot(X[i], X[j])) - ex) <= Fraction(d + 1, 2**53) * mag, (d, i, j)
+    R = W.dirichlet_histograms(g, 9, 6) - np.float32(1 / 6)
+    S = W.dirichlet_histograms(g, 11, 6) - np.float32(1 / 6)
+    M = [[sum(Fraction(a) * Fraction(b) for a, b in zip(R[i].tolist(), S[j].tolist())) for j in range(11)]
+         for i in range(9)]
+    vals = sorted(set(v for row in M for v in row))
+    for r in (1, len(vals) // 3, len(vals) - 2):
+        t = float((vals[r - 1] + vals[r]) / 2)
+        want = {(i, j) for i in range(9) for j in range(11) if M[i][j] >= Fraction(t)}
+        assert pair_set(orc.ip_join(R, S, t, MODE_RXS)) == want, r
+    MS = [[sum(Fraction(a) * Fraction(b) for a, b in zip(R[i].tolist(), R[j].tolist())) for j in range(9)]
+          for i in range(9)]
+    t = float(np.median([float(MS[i][j]) for i in range(9) for j in range(9) if i != j]))
+    assert pair_set(orc.ip_join(R, None, t, MODE_SELF_UPPER)) == \
+        {(i, j) for i in range(9) for j in range(i + 1, 9) if MS[i][j] >= Fraction(t)}
+    assert pair_set(orc.ip_join(R, None, t, MODE_SELF_FULL)) == \
+        {(i, j) for i in range(9) for j in range(9) if MS[i][j] >= Fraction(t)}
+    # inclusive threshold on an exact dyadic dot product: [0.5, 0.25] . [0.5, 0.5] = 0.375
+    A = np.array([[0.5, 0.25]], dtype=np.float32)
+    B = np.array([[0.5, 0.5]], dtype=np.float32)
+    assert orc.dot(A[0], B[0]) == 0.375
+    assert pair_set(orc.ip_join(A, B, 0.375, MODE_RXS)) == {(0, 0)}
+    assert pair_set(orc.ip_join(A, B, float(np.nextafter(0.375, 1.0)), MODE_RXS)) == set()
+    U = orc.normalize(W.dirichlet_histograms(g, 20, 8))
+    c = 0.9
+    ip = pair_set(orc.ip_join(U, None, c, MODE_SELF_UPPER))
+    cs = pair_set(orc.cosine_join(U, None, c, MODE_SELF_UPPER))
+    for i in range(20):
+        for j in range(i + 1, 20):
+            v = orc.dot(U[i], U[j])
+            if abs(v - c) > 1e-5:
+                assert ((i, j) in ip) == ((i, j) in cs) == (v >= c), (i, j)
+
+
 # ----------------------------------------------------------------------------------------
 # colour-histogram transformer
 # ----------------------------------------------------------------------------------------
@@ -678,6 +723,7 @@ ALL_PINS = [
     pin_hist_join_matches_exact_rational,
     pin_hist_closed_forms,
     pin_hist_topk_order_ties_and_join,
+    pin_inner_product_exact,
     pin_color_hist_golden_fixture,
     pin_color_hist_binning_definition,
     pin_color_hist_invariants,

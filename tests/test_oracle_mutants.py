@@ -48,6 +48,8 @@ MUTANTS = {
     "hist_joint_index_transposed": ("cnt[(r * bg + g) * bb + b] += 1;", "cnt[(g * br + r) * bb + b] += 1;"),
     "hist_topk_metric_swapped": ("c[j].d2 = (metric == 1) ? oracle_l1dist(q, x, d) : oracle_chi2dist(q, x, d);",
                                  "c[j].d2 = (metric == 2) ? oracle_l1dist(q, x, d) : oracle_chi2dist(q, x, d);"),
+    "dot_sign_flipped": ("s = s + (double)q[k] * (double)x[k];", "s = s - (double)q[k] * (double)x[k];"),
+    "ip_threshold_strict": (">= t) {", "> t) {"),
     "components_max_label": ("const int64_t lo = (la < lb) ? la : lb;", "const int64_t lo = (la > lb) ? la : lb;"),
     "components_one_pass": ("while (changed) {", "if (changed) {"),
     "components_count_inverted": ("c += (label[i] == i);", "c += (label[i] != i);"),
