@@ -189,11 +189,12 @@ class Oracle:
         f = self.lib.oracle_l1dist if metric == METRIC_L1 else self.lib.oracle_chi2dist
         return float(f(qp, xp, int(q.shape[-1])))
 
-    def hist_dist_block(self, R, S, metric: int) -> np.ndarray:
+    def hist_dist_block(self, R, S, metric: int, r0: int = 0, r1: int | None = None) -> np.ndarray:
         R, Rp = _f32(R)
         S, Sp = _f32(S)
-        out = np.empty((R.shape[0], S.shape[0]), dtype=np.float64)
-        self.lib.oracle_hist_dist_block(Rp, 0, R.shape[0], Sp, S.shape[0], R.shape[1], int(metric),
+        r1 = R.shape[0] if r1 is None else r1
+        out = np.empty((r1 - r0, S.shape[0]), dtype=np.float64)
+        self.lib.oracle_hist_dist_block(Rp, r0, r1, Sp, S.shape[0], R.shape[1], int(metric),
                                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
         return out
 

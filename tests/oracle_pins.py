@@ -405,6 +405,43 @@ def pin_hist_dist_within_rounding_of_exact(orc):
                             assert abs(Fraction(got) - D) <= Fraction(slack, 2**53) * D, (metric, d, i, j, got, float(D))
 
 
+def pin_dist_blocks_match_exact(orc):
+    """The block forms equal the exact rational matrices, over any row range [r0, r1).
+
+    oracle_dist_block and oracle_hist_dist_block fill an (r1 - r0) x |S| row-major matrix
+    for rows r0 .. r1-1 of R. On 2^-3-grid rows every squared L2 and every L1 distance is
+    exact in FP64, so each entry must equal the rational value itself; chi-square divides,
+    so on histograms each entry lies within its standard bound (d+6) 2^-53 of the rational
+    value. R and S differ in shape and content, so a transposed layout, a row offset
+    dropped or doubled, the other operand, or the other metric each changes some entry.
+    """
+    g = _g(41)
+    d = 6
+    R = W.grid_points(g, 11, d)
+    S = W.grid_points(g, 7, d)
+    L2 = exact_matrix(R, S)
+    L1 = [[exact_l1(R[i], S[j]) for j in range(7)] for i in range(11)]
+    Hr = W.dirichlet_histograms(g, 9, d)
+    Hs = W.dirichlet_histograms(g, 5, d)
+    C2 = [[exact_chi2(Hr[i], Hs[j]) for j in range(5)] for i in range(9)]
+    for r0, r1 in ((0, 11), (3, 8), (10, 11), (4, 4)):
+        D = orc.dist_block(R, S, r0, r1)
+        assert D.shape == (r1 - r0, 7), (r0, r1, D.shape)
+        A = orc.hist_dist_block(R, S, oracle.METRIC_L1, r0, r1)
+        assert A.shape == (r1 - r0, 7), (r0, r1, A.shape)
+        for i in range(r0, r1):
+            for j in range(7):
+                assert Fraction(float(D[i - r0, j])) == L2[i][j], ("L2", r0, r1, i, j)
+                assert Fraction(float(A[i - r0, j])) == L1[i][j], ("L1", r0, r1, i, j)
+    for r0, r1 in ((0, 9), (2, 7), (8, 9)):
+        X = orc.hist_dist_block(Hr, Hs, oracle.METRIC_CHI2, r0, r1)
+        assert X.shape == (r1 - r0, 5), (r0, r1, X.shape)
+        for i in range(r0, r1):
+            for j in range(5):
+                err = abs(Fraction(float(X[i - r0, j])) - C2[i][j])
+                assert err <= Fraction(d + 6, 2**53) * C2[i][j], ("chi2", r0, r1, i, j)
+
+
 def _thr_between(values, lo_rank: int):
     """A threshold strictly inside a wide gap of the exact values (no distance near it)."""
     vals = sorted(set(values))
@@ -722,6 +759,7 @@ ALL_PINS = [
     pin_hist_dist_within_rounding_of_exact,
     pin_hist_join_matches_exact_rational,
     pin_hist_closed_forms,
+    pin_dist_blocks_match_exact,
     pin_hist_topk_order_ties_and_join,
     pin_inner_product_exact,
     pin_color_hist_golden_fixture,

@@ -53,6 +53,14 @@ MUTANTS = {
     "components_max_label": ("const int64_t lo = (la < lb) ? la : lb;", "const int64_t lo = (la > lb) ? la : lb;"),
     "components_one_pass": ("while (changed) {", "if (changed) {"),
     "components_count_inverted": ("c += (label[i] == i);", "c += (label[i] != i);"),
+    "dist_block_transposed": ("out[(i - r0) * nS + j] = oracle_sqdist(",
+                              "out[(i - r0) + j * (r1 - r0)] = oracle_sqdist("),
+    "dist_block_row_offset_dropped": ("oracle_sqdist(R + i * (int64_t)d, S + j * (int64_t)d, d);",
+                                      "oracle_sqdist(R + (i - r0) * (int64_t)d, S + j * (int64_t)d, d);"),
+    "hist_block_metric_swapped": ("out[(i - r0) * nS + j] = (metric == 1) ?",
+                                  "out[(i - r0) * nS + j] = (metric == 2) ?"),
+    "hist_block_transposed": ("out[(i - r0) * nS + j] = (metric == 1) ?",
+                              "out[(i - r0) + j * (r1 - r0)] = (metric == 1) ?"),
 }
 
 
