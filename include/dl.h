@@ -242,6 +242,10 @@ int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric, int32_t k
  * receives the number of matching pairs. The result is the same set
  * dl_sim_join returns (exact FP32 path: FP32 distances with an error bound,
  * FP64 recheck of the undecided pairs).
+ * Preconditions, each refused with DL_EINVAL: R and S 16-byte aligned when
+ * d % 4 == 0 (else 4-byte), ids and outputs 8-byte aligned (checked before any
+ * launch); every feature finite with |x| <= 2^40, the domain dl_store_create
+ * also enforces (checked on the device; the outputs are then unspecified).
  * Working memory is a 512 KiB static device array in the library, held by every
  * GPU that loads it until exit; it holds at most 65,536 pairs inside the FP32
  * error band of eps^2. A call that needs more returns DL_EOVERFLOW (outputs

@@ -264,7 +264,7 @@ static int run_pass(const PassCfg &c, PassOut *po)
                 ++launches;
             }
         } else {
-            SimtParams sp;
+            SimtParams sp{};
             sp.R = R->x32;
             sp.S = S->x32;
             sp.nR = (int)nR;

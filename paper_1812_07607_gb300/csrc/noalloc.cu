@@ -5,14 +5,18 @@
 // loops that must not hit the allocator, or hosts that forbid cudaMalloc after
 // start-up. dl_sim_join_noalloc serves them: the caller passes its own device
 // buffers for the inputs (features, ids) and the outputs (id pairs), and the
-// only working memory the join needs -- three counters and the list of pairs
+// only working memory the join needs -- four counters and the list of pairs
 // whose FP32 distance lies within its error bound of eps^2 -- lives in the
 // file-scope device array below, which every GPU that loads this library holds
 // until the process exits.
 //
 // It runs the exact FP32 path (K8 in exact mode, then the K6 recheck), so its
-// result is the same set dl_sim_join returns.
+// result is the same set dl_sim_join returns. The rows come straight from the
+// caller, so the domain dl_store_create enforces (every feature finite, |x| <=
+// 2^40, which the FP32 and FP64 error bounds assume) is checked here by a small
+// kernel that raises a flag in the scratch counters.
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 
 #include "kernels.h"
@@ -25,8 +29,32 @@ constexpr unsigned long long kNoAllocBandMax = 65536;
 constexpr size_t kNoAllocCounterBytes = 256;
 constexpr size_t kNoAllocScratchBytes = kNoAllocCounterBytes + kNoAllocBandMax * sizeof(uint2);   // 512 KiB + 256 B
 
-// Counters ([0] pairs out, [1] band pairs, [2] FP64 evaluations) followed by the band list.
+// Counters ([0] pairs out, [1] band pairs, [2] FP64 evaluations, [3] domain flag) followed
+// by the band list.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Raises *flag when any of the n*d features of X is non-finite or above 2^40 in
+// magnitude (the domain of the error bounds; dl_store_create rejects the same).
+__global__ void __launch_bounds__(256) k_noalloc_domain(const float *__restrict__ X, int64_t count,
+                                                        unsigned long long *flag)
+{
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        if (!(fabsf(__ldg(X + i)) <= 1099511627776.0f)) bad = true;   // also catches NaN
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1ull);
+}
+
+static int launch_domain(const float *X, int64_t count, unsigned long long *flag, cudaStream_t st)
+{
+    if (count <= 0) return DL_OK;
+    const int64_t want = (count + 255) / 256;
+    const int grid = (int)(want < (int64_t)device_sm_count() * 8 ? want : (int64_t)device_sm_count() * 8);
+    k_noalloc_domain<<<grid, 256, 0, st>>>(X, count, flag);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_noalloc_domain launch");
+    return DL_OK;
+}
 
 static std::mutex g_noalloc_mu;
 static void *g_noalloc_addr[64];   // device address of g_noalloc_scratch, per device
@@ -96,6 +124,17 @@ extern "C" int dl_sim_join_noalloc(const float *R, const int64_t *r_ids, int64_t
         set_error("dl_sim_join_noalloc: bad output buffers");
         return DL_EINVAL;
     }
+    // The recheck reads rows as 16-byte vectors when d % 4 == 0, and ids and pairs are
+    // 8-byte words: refuse pointers those accesses would fault on, before any launch.
+    const uintptr_t row_align = (d % 4 == 0) ? 15u : 3u;
+    if ((((uintptr_t)R | (uintptr_t)S) & row_align) != 0) {
+        set_error("dl_sim_join_noalloc: R and S must be %d-byte aligned for d=%d", (int)row_align + 1, d);
+        return DL_EINVAL;
+    }
+    if ((((uintptr_t)r_ids | (uintptr_t)s_ids | (uintptr_t)out_r | (uintptr_t)out_s) & 7u) != 0) {
+        set_error("dl_sim_join_noalloc: ids and output pairs must be 8-byte aligned");
+        return DL_EINVAL;
+    }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     void *scratch = nullptr;
     int rc = noalloc_scratch(&scratch);
@@ -105,6 +144,9 @@ extern "C" int dl_sim_join_noalloc(const float *R, const int64_t *r_ids, int64_t
 
     // every call starts from zeroed counters (the array keeps the previous call's contents)
     DL_CUDA_TRY(cudaMemsetAsync(cnt, 0, kNoAllocCounterBytes, st));
+    rc = launch_domain(R, nR * (int64_t)d, cnt + 3, st);
+    if (!rc && !self) rc = launch_domain(S, nS * (int64_t)d, cnt + 3, st);
+    if (rc) return rc;
 
     const double e2 = eps * eps;
     const double g64 = gamma64(d), g32 = gamma32(d);
@@ -113,7 +155,7 @@ extern "C" int dl_sim_join_noalloc(const float *R, const int64_t *r_ids, int64_t
     const float t_rej = f32_ru(e2 * (1.0 + 2.0 * g64) * (1.0 + g32) * (1.0 + 8.881784197001252e-16) + abs32);
     const bool mirror = self && self_mode == DL_SELF_FULL;
 
-    JoinOut jo;
+    JoinOut jo{};
     jo.r_ids = r_ids;
     jo.s_ids = s_ids;
     jo.out_r = out_r;
@@ -127,7 +169,7 @@ extern "C" int dl_sim_join_noalloc(const float *R, const int64_t *r_ids, int64_t
     jo.orig = nullptr;   // caller's row order is the store order here
 
     if (nR > 0 && nS > 0) {
-        SimtParams sp;
+        SimtParams sp{};
         sp.R = R;
         sp.S = self ? R : S;
         sp.nR = (int)nR;
@@ -136,6 +178,7 @@ extern "C" int dl_sim_join_noalloc(const float *R, const int64_t *r_ids, int64_t
         sp.upper = self ? 1 : 0;
         sp.tiles_m = 0;
         sp.exact = 1;
+        sp.metric = 0;   // squared L2
         sp.t_acc = t_acc;
         sp.t_rej = t_rej;
         sp.out = jo;
@@ -149,9 +192,14 @@ extern "C" int dl_sim_join_noalloc(const float *R, const int64_t *r_ids, int64_t
         rc = launch_diag(r_ids, nR, out_r, out_s, cnt + 0, (unsigned long long)out_cap, st);
         if (rc) return rc;
     }
-    unsigned long long h[3] = {0, 0, 0};
+    unsigned long long h[4] = {0, 0, 0, 0};
     DL_CUDA_TRY(cudaMemcpyAsync(h, cnt, sizeof h, cudaMemcpyDeviceToHost, st));
     DL_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h[3]) {
+        set_error("dl_sim_join_noalloc: a feature is non-finite or exceeds 2^40 in magnitude; the output is "
+                  "unspecified");
+        return DL_EINVAL;
+    }
     *n_out = (int64_t)h[0];
     if (h[1] > kNoAllocBandMax) {
         set_error("dl_sim_join_noalloc: %llu pairs fell inside the FP32 error band, more than the %llu the "
