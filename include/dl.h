@@ -273,6 +273,20 @@ int dl_sim_join_noalloc(const float *R, const int64_t *r_ids, int64_t nR, const 
 int dl_debug_scores(const dl_store *R, const dl_store *S, int32_t precision, float *h_out, float *e_out,
                     void *cuda_stream);
 
+/*
+ * Diagnostics for failure detection (no counterpart in the paper). Every
+ * pipeline wait inside the tensor-core kernels is bounded: past its budget the
+ * kernel raises an abort flag, lets its copies in flight land, finishes its
+ * issued MMAs, frees its tensor memory and returns, and the calling entry point
+ * reports DL_ETIMEOUT (a server marks the batch's requests DL_EFAILED). This
+ * sets that budget, in SM clocks, for every tensor-core kernel launched after
+ * the call on any thread; 0 restores the default of 2e9 clocks (about 1 s).
+ * A budget of a few clocks makes a healthy join time out, which is how the
+ * tests drive the abort path without faulting or hanging a GPU. Returns
+ * DL_EINVAL for clocks < 0.
+ */
+int dl_debug_set_wait_budget(int64_t clocks);
+
 /* ---------------------------------------------------------------------------------
  * Batches: many epsilon-join and top-k requests against one resident store.
  * ------------------------------------------------------------------------------- */

@@ -33,6 +33,8 @@
 //               k_finalize turns the candidates into id pairs.
 // A unit is (R tile m, S tiles [nb, ne)); units are handed out round-robin, in the
 // S-range-major order their builders produce.
+#include <atomic>
+
 #include <cuda.h>
 
 #include "kernels.h"
@@ -377,7 +379,7 @@ __global__ void __launch_bounds__(320, 1)
                 const int4 un = p.units[u];
                 const int slot = i % a_slots;
                 const uint32_t use = (uint32_t)(i / a_slots);
-                if (!mbar_wait(a_empty + slot, (use & 1) ^ 1, abort_flag)) {
+                if (!mbar_wait(a_empty + slot, (use & 1) ^ 1, abort_flag, p.wait_budget)) {
                     ok = false;
                     break;
                 }
@@ -388,7 +390,7 @@ __global__ void __launch_bounds__(320, 1)
                 a_pend_par[slot] = use & 1;
                 for (int n = un.y; n < un.z && ok; ++n) {
                     for (int c = 0; c < kc; ++c) {
-                        if (!mbar_wait(empty + stage, phase ^ 1, abort_flag)) {
+                        if (!mbar_wait(empty + stage, phase ^ 1, abort_flag, p.wait_budget)) {
                             ok = false;
                             break;
                         }
@@ -424,7 +426,7 @@ __global__ void __launch_bounds__(320, 1)
                 const int4 un = p.units[u];
                 const int slot = i % a_slots;
                 const uint32_t use = (uint32_t)(i / a_slots);
-                if (!mbar_wait(a_full + slot, use & 1, abort_flag)) {
+                if (!mbar_wait(a_full + slot, use & 1, abort_flag, p.wait_budget)) {
                     ok = false;
                     break;
                 }
@@ -432,14 +434,14 @@ __global__ void __launch_bounds__(320, 1)
                 const uint32_t a_base = smem_u32(sA + slot * a_bytes);
                 for (int n = un.y; n < un.z && ok; ++n) {
                     const uint32_t b = t % kAcc;
-                    if (!mbar_wait(acc_empty + b, ((t / kAcc) & 1) ^ 1, abort_flag)) {
+                    if (!mbar_wait(acc_empty + b, ((t / kAcc) & 1) ^ 1, abort_flag, p.wait_budget)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
                     const uint32_t d_tmem = tmem_base + b * BN;
                     for (int c = 0; c < kc; ++c) {
-                        if (!mbar_wait(full + stage, phase, abort_flag)) {
+                        if (!mbar_wait(full + stage, phase, abort_flag, p.wait_budget)) {
                             ok = false;
                             break;
                         }
@@ -541,7 +543,7 @@ __global__ void __launch_bounds__(320, 1)
             }
             const uint32_t b = t % kAcc;
             const int slot = t & 1;
-            if (!mbar_wait(acc_full + b, (t / kAcc) & 1, abort_flag)) {
+            if (!mbar_wait(acc_full + b, (t / kAcc) & 1, abort_flag, p.wait_budget)) {
                 ok = false;
                 break;
             }
@@ -633,6 +635,7 @@ __global__ void __launch_bounds__(320, 1)
         }
         if constexpr (!TOPK) flush_stage(p, my_stg, scnt);
         if (!ok) {
+            cp_async_wait_all();   // the next tile's column data may still be in flight
             *abort_flag = 1;
             atomicExch(p.err, 1);
         }
@@ -674,13 +677,23 @@ void tc_plan(int BN, int kc, int *stages, int *a_slots, bool fp8)
     }
 }
 
+static std::atomic<long long> g_wait_budget{0};
+
+long long tc_wait_budget()
+{
+    const long long b = g_wait_budget.load(std::memory_order_relaxed);
+    return b > 0 ? b : kWaitBudgetClocks;
+}
+
 template <int BN, bool TOPK, bool FP8>
 static int launch_one(const TcLaunch &L, size_t smem, cudaStream_t st)
 {
     cudaError_t e =
         cudaFuncSetAttribute(tc_join_kernel<BN, TOPK, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_join_kernel)");
-    tc_join_kernel<BN, TOPK, FP8><<<L.grid, 320, smem, st>>>(*L.tmA, *L.tmB, L.p);
+    TcParams p = L.p;
+    p.wait_budget = tc_wait_budget();
+    tc_join_kernel<BN, TOPK, FP8><<<L.grid, 320, smem, st>>>(*L.tmA, *L.tmB, p);
     return DL_OK;
 }
 
@@ -714,3 +727,17 @@ int launch_tc_join(const TcLaunch &L, cudaStream_t st, bool topk, bool fp8)
 }
 
 }  // namespace dl
+
+// Diagnostics: shorten the abortable pipeline waits of every tensor-core kernel
+// launched from now on (0 restores the default), so tests can make a healthy
+// join's wait run out and exercise the abort path.
+extern "C" int dl_debug_set_wait_budget(int64_t clocks)
+{
+    dl::clear_error();
+    if (clocks < 0) {
+        dl::set_error("dl_debug_set_wait_budget: clocks must be >= 0 (got %lld)", (long long)clocks);
+        return DL_EINVAL;
+    }
+    dl::g_wait_budget.store(clocks, std::memory_order_relaxed);
+    return DL_OK;
+}

@@ -29,6 +29,7 @@ struct TcParams {
     unsigned long long *cand_cnt;
     unsigned long long cand_cap;
     int *err;                // set to 1 when a bounded wait expired
+    long long wait_budget;   // SM clocks an abortable pipeline wait may take (set by launch_tc_join)
     // top-k epilogue (units carry the S split in .w; state per (row, split, half) slot)
     int tk_k;                // k
     int tk_cap;              // candidate-list capacity per slot
@@ -52,6 +53,9 @@ struct TcLaunch {
 };
 
 void tc_plan(int BN, int kc, int *stages, int *a_slots, bool fp8 = false);
+// Clock budget of the tensor-core kernels' abortable waits: the default (about 1 s),
+// unless dl_debug_set_wait_budget set another.
+long long tc_wait_budget();
 int launch_tc_join(const TcLaunch &L, cudaStream_t st, bool topk = false, bool fp8 = false);
 
 // ---- K8 SIMT FP32 join (join_simt.cu)

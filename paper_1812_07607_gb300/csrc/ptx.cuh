@@ -59,16 +59,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Wait for the phase with the given parity to complete. Returns false when the
-// clock budget runs out or another role raised the CTA's abort flag.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+// Wait for the phase with the given parity to complete. Returns false when
+// `budget` SM clocks pass or another role raised the CTA's abort flag.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          long long budget = kWaitBudgetClocks)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (clock64() - t0 > kWaitBudgetClocks) return false;
+        if (clock64() - t0 > budget) return false;
     }
 }
 

@@ -38,6 +38,7 @@ EXPORTS = [
     "dl_sim_join_noalloc", "dl_batch_join", "dl_result_request_pairs", "dl_result_request_topk",
     "dl_server_create", "dl_submit", "dl_poll", "dl_cancel", "dl_server_get_stats", "dl_server_destroy",
     "dl_debug_scores", "dl_store_normalize", "dl_color_hist", "dl_components", "dl_dedup", "dl_store_cluster",
+    "dl_debug_set_wait_budget",
 ]
 
 
@@ -136,6 +137,8 @@ def load(path: str | None = None):
     L.dl_dedup.restype = ctypes.c_int
     L.dl_debug_scores.argtypes = [vp, vp, i32, vp, vp, vp]
     L.dl_debug_scores.restype = ctypes.c_int
+    L.dl_debug_set_wait_budget.argtypes = [i64]
+    L.dl_debug_set_wait_budget.restype = ctypes.c_int
     L.dl_last_error.restype = ctypes.c_char_p
     L.dl_version.restype = ctypes.c_char_p
     L.dl_kernel_launches.restype = i64
@@ -518,6 +521,11 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def set_wait_budget(clocks: int = 0):
+    """dl_debug_set_wait_budget: SM-clock budget of the tensor-core kernels' bounded waits (0: default)."""
+    _check(load().dl_debug_set_wait_budget(int(clocks)), "dl_debug_set_wait_budget")
 
 
 def debug_scores(R: Store, S: Store, precision="bf16", stream=None):
