@@ -36,6 +36,7 @@ UNIT = "Gpairs/s"
 SEED_BATCH = 1812076074
 SEED_SERVE = 1812076075
 L2_FLUSH_BYTES = 512 << 20      # > 129 MB L2
+_KEEP = {}                      # workloads the GPU legs generated, reused by the oracle samples
 
 
 def parse():
@@ -54,6 +55,9 @@ def parse():
                     help="skip the colour-histogram, L1 / chi-square and dedup leg")
     ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES), default=None,
                     help="run one small profiling case three times and print its timings (no bench line)")
+    ap.add_argument("--peak-probe", action="store_true",
+                    help="measure the BF16 and FP8 e4m3 cuBLAS GEMM peaks of this GPU and print them (no bench line)")
+    ap.add_argument("--no-latency", action="store_true", help="skip the 2,000 x 2,000 latency leg")
     ap.add_argument("--serving-seconds", type=float, default=4.0)
     ap.add_argument("--serving-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
     return ap.parse_args()
@@ -64,6 +68,15 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def fp8_peak():
+    """The FP8 e4m3 GEMM peak measured on this GPU model by `bench.py --peak-probe` (TFLOP/s), or None."""
+    p = os.path.join(ROOT, "profiles", "fp8_e4m3_peak_gb300.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        return json.load(f).get("fp8_peak_tflops")
 
 
 def peaks():
@@ -179,6 +192,102 @@ def cpu_oracle_rate(wl, budget_s: float):
     return pairs / dt / 1e9, {"rows": rows, "pairs": pairs, "seconds": round(dt, 3)}
 
 
+def host_cpu():
+    """(cores this process may run on, CPU model name)."""
+    import platform
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return cores, model or platform.machine()
+
+
+def _oracle_warm(_):
+    """Spawned worker: import and load the oracle before the timed region."""
+    import oracle
+    oracle.default()
+    time.sleep(0.3)   # so that every worker of the pool takes one warm-up task
+    return os.getpid()
+
+
+def _oracle_shard(task):
+    """Spawned worker: rows [r0, r1) of the memory-mapped store against all of it, FP64 oracle."""
+    import oracle
+    path, r0, r1, eps = task
+    X = np.load(path, mmap_mode="r")
+    t0 = time.perf_counter()
+    oracle.default().join(np.ascontiguousarray(X[r0:r1]), X, eps, oracle.MODE_RXS)
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_all_cores(wl, per_row_s: float, budget_s: float):
+    """The same single-threaded FP64 oracle on every host core at once: one spawned process per
+    core, each on its own shard of query rows against the whole store (the result does not
+    depend on the split). Returns (Gpairs/s over the wall time of all shards, info)."""
+    import multiprocessing as mp
+    cores, model = host_cpu()
+    n = wl.R.shape[0]
+    rows_each = int(max(1, min(n // cores, budget_s / max(per_row_s, 1e-6))))
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "R.npy")
+        np.save(path, wl.R)
+        with mp.get_context("spawn").Pool(cores) as pool:
+            # bounded waits: a pool whose workers cannot start would otherwise wait forever
+            pool.map_async(_oracle_warm, range(cores), chunksize=1).get(timeout=120)
+            tasks = [(path, i * rows_each, (i + 1) * rows_each, wl.eps) for i in range(cores)]
+            t0 = time.perf_counter()
+            worker_s = pool.map_async(_oracle_shard, tasks, chunksize=1).get(timeout=30 * budget_s + 120)
+            dt = time.perf_counter() - t0
+    pairs = cores * rows_each * n
+    return pairs / dt / 1e9, {"cores": cores, "cpu_model": model, "rows": cores * rows_each, "pairs": pairs,
+                              "seconds": round(dt, 3), "slowest_shard_s": round(max(worker_s), 3)}
+
+
+def cpu_oracle_configs(budget_s: float = 3.0):
+    """The FP64 oracle (one thread) on the other configs: the 2,000 x 2,000 join in full, and a
+    bounded slice of query rows x the whole store for the precision, batching and serving
+    workloads (reusing the inputs their GPU legs generated; a config whose leg did not run is
+    skipped)."""
+    import oracle
+    from paper_1812_07607_gb300 import workloads as W
+    orc = oracle.default()
+    out = {}
+    c1 = W.rxs_histograms_2k()
+    t0 = time.perf_counter()
+    n1 = len(orc.join(c1.R, c1.S, c1.eps, oracle.MODE_RXS))
+    dt = time.perf_counter() - t0
+    out["rxs_histograms_2k"] = {"value": c1.pairs / dt / 1e9, "unit": UNIT, "seconds": round(dt, 4),
+                                "pairs_out": n1, "sample": "the whole 2,000 x 2,000 join, d=64"}
+    cases = []
+    if "precision" in _KEEP:
+        wl = _KEEP["precision"]
+        cases.append(("rxs_unit_mixture_1m", wl.R, wl.S, wl.eps))
+    if "batch" in _KEEP:
+        st, Q, table = _KEEP["batch"]
+        cases.append(("batch_store_2m", Q, st.X, W.eps_for_selectivity(table, 2e-3)))
+    if "serve" in _KEEP:
+        sw = _KEEP["serve"]
+        cases.append(("serve_store_4m", sw.queries(64, SEED_SERVE + 99), sw.X, W.eps_for_selectivity(sw.eps_table(), 2e-3)))
+    for name, Q, S, eps in cases:
+        t0 = time.perf_counter()
+        orc.join(Q[:1], S, eps, oracle.MODE_RXS)
+        per_row = time.perf_counter() - t0
+        rows = int(max(1, min(Q.shape[0] - 1, budget_s / max(per_row, 1e-6))))
+        t0 = time.perf_counter()
+        orc.join(Q[1:1 + rows], S, eps, oracle.MODE_RXS)
+        dt = time.perf_counter() - t0
+        out[name] = {"value": rows * S.shape[0] / dt / 1e9, "unit": UNIT, "seconds": round(dt, 3),
+                     "sample": f"{rows} query rows x all {S.shape[0]} store rows, d={S.shape[1]}",
+                     "s_per_query_row": round(dt / rows, 4)}
+    return out
+
+
 def cpu_oracle_rows(W):
     """The FP64 CPU oracle (one thread) on bounded samples of the further rows' workloads, in
     the units of their GPU figures. Inputs come from the generators only."""
@@ -231,6 +340,7 @@ def batch_leg(dl, seed=SEED_BATCH, n_req=4096, reps=2):
         if r["kind"] == "eps":
             r["eps"] = W.eps_for_selectivity(table, r["selectivity"])
     Q = st.queries(off, seed + 1)
+    _KEEP["batch"] = (st, Q, table)
     store = dl.Store(torch.from_numpy(st.ids).cuda(), torch.from_numpy(st.X).cuda())
     Qd = torch.from_numpy(Q).cuda()
     qd = torch.arange(off, dtype=torch.int64).cuda()
@@ -270,6 +380,7 @@ def serving_leg(dl, seconds=4.0, rates=(2000.0, 1000.0, 500.0), seed=SEED_SERVE)
     import torch
     from paper_1812_07607_gb300 import workloads as W
     sw = W.serve_store_4m()
+    _KEEP["serve"] = sw
     store = dl.Store(torch.from_numpy(sw.ids).cuda(), torch.from_numpy(sw.X).cuda())
     out = None
     sweep = []
@@ -346,6 +457,7 @@ def precision_leg(dl, reps=2):
     import torch
     from paper_1812_07607_gb300 import workloads as W
     wl = W.rxs_unit_mixture_1m()
+    _KEEP["precision"] = wl
     n = wl.R.shape[0]
     S = dl.Store(torch.arange(n).cuda(), torch.from_numpy(wl.S).cuda())
     R = dl.Store(torch.arange(n).cuda(), torch.from_numpy(wl.R).cuda())
@@ -366,12 +478,91 @@ def precision_leg(dl, reps=2):
             if i >= warm:
                 ts.append(dt)
         t = statistics.median(ts)
+        tflops = 2.0 * 512 * n * n / (st["ms_main"] / 1e3) / 1e12
+        pk = peaks()["bf16_tflops"] if prec == "bf16" else fp8_peak()
         out[prec] = {"value": n * n / t / 1e9, "unit": UNIT, "ms": 1e3 * t, "ms_main": st["ms_main"],
                      "ms_recheck": st["ms_recheck"], "band_pairs": st["band_pairs"], "fp64_pairs": st["fp64_pairs"],
-                     "pairs_out": st["pairs_out"], "tile_n": st["tile_n"],
-                     "main_tflops": 2.0 * 512 * n * n / (st["ms_main"] / 1e3) / 1e12}
+                     "pairs_out": st["pairs_out"], "tile_n": st["tile_n"], "main_tflops": tflops,
+                     "main_frac_of_measured_peak": (tflops / pk) if pk else None,
+                     "peak_tflops": pk, "peak_source": ("MEASURED_PEAKS.json bf16 burst" if prec == "bf16"
+                                                        else "profiles/fp8_e4m3_peak_gb300.json (bench.py --peak-probe)")}
     R.close()
     S.close()
+    return out
+
+
+def latency_leg(dl, reps=50):
+    """The 2,000 x 2,000 d=64 R x S join (4e6 pairs, ~0.1% selectivity): too small to fill the GPU,
+    so it is reported as per-call latency -- host wall time of dl_sim_join on resident stores,
+    including the synchronisation that returns the pair count."""
+    import torch
+    from paper_1812_07607_gb300 import workloads as W
+    wl = W.rxs_histograms_2k()
+    R = dl.Store(torch.from_numpy(wl.r_ids).cuda(), torch.from_numpy(wl.R).cuda())
+    S = dl.Store(torch.from_numpy(wl.s_ids).cuda(), torch.from_numpy(wl.S).cuda())
+    out = {"config": "rxs_histograms_2k: 2,000 x 2,000, d=64 Dirichlet(0.5) histograms, eps at 0.1% selectivity"}
+    for prec in ("bf16", "fp32"):
+        for _ in range(5):
+            dl.sim_join(R, S, wl.eps, precision=prec).free()
+        ts, n = [], 0
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = dl.sim_join(R, S, wl.eps, precision=prec)
+            n = res.count()
+            ts.append(1e3 * (time.perf_counter() - t0))
+            res.free()
+        ts.sort()
+        p50 = statistics.median(ts)
+        out[prec] = {"p50_ms": p50, "p99_ms": ts[min(len(ts) - 1, int(0.99 * len(ts)))], "pairs_out": n,
+                     "value": wl.pairs / (p50 / 1e3) / 1e9, "unit": UNIT}
+    R.close()
+    S.close()
+    return out
+
+
+def peak_probe(seconds: float = 4.0, n: int = 8192):
+    """Dense tensor-core peaks of this GPU measured through cuBLAS: BF16 (torch.matmul) and FP8
+    e4m3 (torch._scaled_mm, unit scales, BF16 out), n^3 GEMMs counted as 2 n^3 flops. Burst = best
+    of 10 CUDA-event timings; sustained = back-to-back calls for `seconds`. A calibration of the
+    denominators, not a kernel of this library."""
+    import torch
+    torch.manual_seed(0)
+    a16 = torch.randn(n, n, device="cuda", dtype=torch.bfloat16)
+    b16 = torch.randn(n, n, device="cuda", dtype=torch.bfloat16)
+    a8 = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
+    b8 = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn).t()   # column-major operand
+    one = torch.ones((), device="cuda", dtype=torch.float32)
+    fns = {"bf16": lambda: torch.matmul(a16, b16),
+           "fp8_e4m3": lambda: torch._scaled_mm(a8, b8, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)}
+    flops = 2.0 * n ** 3
+    st = torch.cuda.current_stream()
+    sampler = ClockSampler(torch.cuda.current_device())
+    out = {"n": n, "method": f"{n}^3 GEMM, 2n^3 flops; burst: best of 10 (CUDA events); sustained: "
+                             f"back to back for {seconds} s"}
+    sampler.start()
+    for name, f in fns.items():
+        for _ in range(3):
+            f()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            f()
+            e1.record(st)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        calls = max(10, int(seconds / (best / 1e3)))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(calls):
+            f()
+        e1.record(st)
+        e1.synchronize()
+        out[name] = {"burst_tflops": flops / (best / 1e3) / 1e12,
+                     "sustained_tflops": flops * calls / (e0.elapsed_time(e1) / 1e3) / 1e12}
+    out["clocks"] = sampler.stop()
     return out
 
 
@@ -675,6 +866,9 @@ def run_ours(args):
             "peak_kind": f"bf16 dense burst ({pk['source']})",
             "algorithmic": f"2*d flops/pair x {P} pairs = {flops:.4g} flops per launch"}
 
+    latency = None
+    if rank == 0 and not args.no_latency:
+        latency = latency_leg(dl)
     batch = None
     if rank == 0 and not args.no_batch:
         batch = batch_leg(dl)
@@ -693,10 +887,24 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.no_baselines:
-        v, info = cpu_oracle_rate(wl, args.cpu_seconds)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{info['rows']} query rows x all {n} rows ({info['pairs']} pairs, {info['seconds']} s), "
-                         f"FP64 nested loop, 1 thread"}
+        v1, info1 = cpu_oracle_rate(wl, args.cpu_seconds)
+        single = {"value": v1, "unit": UNIT, "cores": 1,
+                  "sample": f"{info1['rows']} query rows x all {n} rows ({info1['pairs']} pairs, "
+                            f"{info1['seconds']} s), FP64 nested loop, 1 thread"}
+        try:
+            va, infoa = cpu_oracle_all_cores(wl, info1["seconds"] / info1["rows"], args.cpu_seconds)
+            cpu = {"value": va, "unit": UNIT, "cores": infoa["cores"], "kind": "oracle",
+                   "cpu_model": infoa["cpu_model"],
+                   "sample": f"{infoa['rows']} query rows x all {n} rows ({infoa['pairs']} pairs) in "
+                             f"{infoa['seconds']} s: the single-threaded FP64 nested loop in {infoa['cores']} "
+                             f"spawned processes, one row shard each",
+                   "single_core": single}
+        except Exception as exc:   # the single-core figure still stands
+            cpu = dict(single, kind="oracle", all_cores_error=repr(exc)[:200])
+        try:
+            cpu["configs"] = cpu_oracle_configs()
+        except Exception as exc:
+            cpu["configs"] = {"error": repr(exc)[:200]}
 
     if rank == 0:
         line = {
@@ -715,6 +923,7 @@ def run_ours(args):
             "roofline": roof,
             "cpu_baseline": cpu,
             "plain_fp32_gpu": plain,
+            "latency_2k": latency,
             "batch": batch,
             "serving": serving,
             "precision": precision,
@@ -819,6 +1028,9 @@ def main():
     args = parse()
     if args.profile_case:
         return run_profile_case(args.profile_case)
+    if args.peak_probe:
+        print(json.dumps(peak_probe()), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

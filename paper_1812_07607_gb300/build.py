@@ -5,7 +5,7 @@ shared library next to this file (git-ignored). The CUDA runtime is linked
 statically so the library loads without a CUDA library path; the driver API
 entry points (tensor-map encoding) are fetched at run time.
 
-    python -m paper_1812_07607_gb300.build [--checked]
+    python -m paper_1812_07607_gb300.build [--ptxas-v]   # --ptxas-v: print registers and spills
 """
 
 from __future__ import annotations

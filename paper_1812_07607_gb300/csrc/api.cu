@@ -215,6 +215,7 @@ static int run_pass(const PassCfg &c, PassOut *po)
 
     int launches = 0;
     if (nR > 0 && nS > 0) {
+        NvtxScope nvtx_pass("join pass: distances, bounds, compaction, recheck");
         if (c.prec == DL_PREC_BF16 || c.prec == DL_PREC_FP8E4M3) {
             const bool fp8 = c.prec == DL_PREC_FP8E4M3;
             if (fp8) {
@@ -281,6 +282,7 @@ static int run_pass(const PassCfg &c, PassOut *po)
             ++launches;
         }
         if (c.timing) cudaEventRecord(ev[1], st);
+        nvtxRangePushA("exact recheck of the band (K6)");
         if (!rc && (c.prec == DL_PREC_BF16 || c.prec == DL_PREC_FP8E4M3)) {
             rc = launch_finalize(band, cnt + 1, (unsigned long long)c.band_cap, R->x32, S->x32, d, c.e2, c.t_acc,
                                  c.t_rej, jo, cnt + 3, cnt + 2, sms * 8, st);
@@ -294,6 +296,7 @@ static int run_pass(const PassCfg &c, PassOut *po)
                                 jo, cnt + 3, sms * 8, st);
             ++launches;
         }
+        nvtxRangePop();
         if (c.timing) cudaEventRecord(ev[2], st);
     } else if (c.timing) {
         cudaEventRecord(ev[1], st);
@@ -615,6 +618,7 @@ extern "C" {
 int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps, const dl_join_opts *opts,
                 dl_result **out)
 {
+    dl::NvtxScope nvtx_scope("dl_sim_join");
     clear_error();
     return sim_join_impl(R, S, metric, eps, opts, out, nullptr);
 }
@@ -625,6 +629,7 @@ int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric, int32_t k
 int dl_debug_scores(const dl_store *R, const dl_store *S, int32_t precision, float *h_out, float *e_out,
                     void *cuda_stream)
 {
+    dl::NvtxScope nvtx_scope("dl_debug_scores");
     clear_error();
     if (!R || !S || !h_out || !e_out || R->d != S->d) {
         set_error("dl_debug_scores: bad arguments");

@@ -143,6 +143,7 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
                              int32_t d, int32_t where, const dl_request *reqs, int32_t n_req, const dl_join_opts *opts,
                              dl_result **out)
 {
+    dl::NvtxScope nvtx_scope("dl_batch_join");
     clear_error();
     if (!out) {
         set_error("dl_batch_join: out is NULL");

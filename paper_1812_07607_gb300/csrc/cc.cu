@@ -217,6 +217,7 @@ extern "C" {
 int dl_components(int64_t n, const int64_t *pair_a, const int64_t *pair_b, int64_t m, int64_t *label,
                   int64_t *n_components, void *cuda_stream)
 {
+    dl::NvtxScope nvtx_scope("dl_components");
     clear_error();
     return components_impl(n, pair_a, pair_b, m, label, nullptr, 0, n_components, (cudaStream_t)cuda_stream);
 }
@@ -224,6 +225,7 @@ int dl_components(int64_t n, const int64_t *pair_a, const int64_t *pair_b, int64
 int dl_dedup(const dl_store *X, int32_t metric, double eps, const int32_t *labels, int32_t target, int32_t plan,
              const dl_join_opts *opts, int64_t *comp, int64_t *n_distinct)
 {
+    dl::NvtxScope nvtx_scope("dl_dedup");
     clear_error();
     if (!X || !comp || !n_distinct) {
         set_error("dl_dedup: NULL argument");

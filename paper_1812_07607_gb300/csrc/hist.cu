@@ -434,6 +434,7 @@ extern "C" int dl_color_hist(const uint8_t *frames, int64_t n_frames, int32_t H,
                              int64_t n_boxes, int32_t br, int32_t bg, int32_t bb, float *out, float *count_ms,
                              void *cuda_stream)
 {
+    dl::NvtxScope nvtx_scope("dl_color_hist");
     clear_error();
     if (count_ms) *count_ms = 0.f;
     return color_hist_impl(frames, n_frames, H, W, boxes, n_boxes, br, bg, bb, out, count_ms,

@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dl.h"
 
 struct dl_store;
@@ -28,6 +30,15 @@ int cuda_fail(cudaError_t e, const char *what);
         cudaError_t _e = (expr);                               \
         if (_e != cudaSuccess) return ::dl::cuda_fail(_e, #expr); \
     } while (0)
+
+// A scoped NVTX range: names an entry point or a stage on the Nsight Systems timeline
+// (header-only NVTX; without a tool attached the push and pop do nothing).
+struct NvtxScope {
+    explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope &) = delete;
+    NvtxScope &operator=(const NvtxScope &) = delete;
+};
 
 extern std::atomic<int64_t> g_launches;
 inline void count_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }

@@ -89,6 +89,7 @@ extern "C" int dl_sim_join_noalloc(const float *R, const int64_t *r_ids, int64_t
                                    int64_t *out_r, int64_t *out_s, int64_t out_cap, int64_t *n_out,
                                    void *cuda_stream)
 {
+    dl::NvtxScope nvtx_scope("dl_sim_join_noalloc");
     clear_error();
     if (!n_out) {
         set_error("dl_sim_join_noalloc: n_out is NULL");

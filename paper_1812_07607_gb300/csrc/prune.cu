@@ -405,6 +405,7 @@ using namespace dl;
 extern "C" int dl_store_cluster(const dl_store *in, int32_t n_clusters, int32_t iters, dl_store **out,
                                 void *cuda_stream)
 {
+    dl::NvtxScope nvtx_scope("dl_store_cluster");
     clear_error();
     if (!in || !out) {
         set_error("dl_store_cluster: NULL argument");

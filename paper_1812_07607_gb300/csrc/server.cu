@@ -153,6 +153,7 @@ static void finish(Server *sv, const std::vector<std::shared_ptr<Req>> &reqs, dl
 
 static void run_batch(Server *sv, int slot, std::vector<std::shared_ptr<Req>> reqs)
 {
+    NvtxScope nvtx_scope("dl_server batch");
     cudaStream_t st = sv->streams[slot];
     int64_t total = 0;
     for (auto &q : reqs) total += q->nq;

@@ -796,11 +796,13 @@ extern "C" {
 int dl_store_create(dl_store **out, const int64_t *ids, const float *feats, int64_t n, int32_t d, int32_t where,
                     void *cuda_stream)
 {
+    dl::NvtxScope nvtx_scope("dl_store_create");
     return store_create_impl(out, ids, feats, n, d, where, cuda_stream, nullptr);
 }
 
 int dl_store_normalize(const dl_store *in, dl_store **out, void *cuda_stream)
 {
+    dl::NvtxScope nvtx_scope("dl_store_normalize");
     clear_error();
     if (!in || !out) {
         set_error("dl_store_normalize: NULL argument");

@@ -670,6 +670,7 @@ using namespace dl;
 extern "C" int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric, int32_t k, const dl_join_opts *opts,
                             dl_result **out)
 {
+    dl::NvtxScope nvtx_scope("dl_topk_join");
     clear_error();
     if (!out) {
         set_error("dl_topk_join: out is NULL");
