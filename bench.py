@@ -364,6 +364,7 @@ def batch_leg(dl, seed=SEED_BATCH, n_req=4096, reps=2):
             "requests_per_s": n_req / t, "query_rows": off, "pairs_evaluated": pairs, "pairs_out": out_pairs,
             "band_pairs": stats["band_pairs"], "fp64_pairs": stats["fp64_pairs"],
             "ms_eps_contraction": stats["ms_main"], "ms_eps_decide_scatter": stats["ms_recheck"],
+            "tile_n": stats["tile_n"], "cta_pair": stats["cta_pair"],
             "ms_device_total": stats["ms_total"],
             "config": "batch_store_2m: 2,097,152 x 128 store; 4,096 requests in one call, sizes lognormal(5,1.5) "
                       "in [1,8192]; 70% eps at selectivity U[0.05%,0.5%], 30% top-k k=10; device inputs"}
@@ -466,7 +467,7 @@ def precision_leg(dl, reps=2):
            "pairs_evaluated": n * n}
     for prec in ("bf16", "fp8"):
         ts, st = [], None
-        warm = 4 if prec == "bf16" else 1   # BF16: the tile autotuner's four trial calls
+        warm = 4 if prec == "bf16" else 3   # the tile autotuner's trial calls (3 candidates BF16, 2 FP8, + 1)
         for i in range(warm + reps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()

@@ -100,6 +100,9 @@ typedef struct dl_join_opts {
     int32_t prune;          /* 1: the exact pruned epsilon-join (tensor-core precisions, L2 and
                                cosine): tile pairs whose bounding balls lie farther apart than
                                eps are skipped; best on stores from dl_store_cluster */
+    int32_t cta_pair;       /* tensor-core epsilon-join: 0 autotuned (with tile_n 0), 1 one SM per
+                               128-row tile, 2 a pair of SMs per 256-row tile (tcgen05 cta_group::2,
+                               tile_n 256 only); the result is the same set either way */
 } dl_join_opts;
 
 /* Fill `o` with defaults: AUTO precision, upper self mode, auto capacity, NULL stream. */
@@ -417,6 +420,8 @@ typedef struct dl_join_stats {
     int32_t kernels_launched;   /* kernels this call launched */
     int64_t tile_pairs;         /* opts.prune: tile pairs of the join (0 without pruning) */
     int64_t tile_pairs_kept;    /* opts.prune: tile pairs that survived the ball test */
+    int32_t cta_pair;           /* 2 when the tensor-core pass ran on SM pairs, else 1 (0 for SIMT paths) */
+    int32_t grid_ctas;          /* CTAs of the (last) tensor-core launch: resident SMs it occupied */
 } dl_join_stats;
 
 int dl_result_stats(const dl_result *r, dl_join_stats *st);

@@ -78,45 +78,49 @@ static void hpool_put(void *p, size_t bytes)
 static std::mutex g_units_mu;
 static std::map<std::tuple<int, int64_t, int64_t, int, int, int>, std::pair<int4 *, int>> g_units;
 
-static int first_upper_tile(int m, int BN, bool upper)
+// R tiles are `tr` rows high: 128 for one SM per tile, 256 for an SM pair (which holds
+// 128 rows each).
+static int first_upper_tile(int m, int BN, bool upper, int tr)
 {
     if (!upper) return 0;
-    const long long num = (long long)m * 128 + 2 - BN;
+    const long long num = (long long)m * tr + 2 - BN;
     return num <= 0 ? 0 : (int)((num + BN - 1) / BN);
 }
 
-static void build_units(int64_t nR, int64_t nS, bool upper, int BN, int L, std::vector<int4> *v)
+static void build_units(int64_t nR, int64_t nS, bool upper, int BN, int L, int tr, std::vector<int4> *v)
 {
-    const int mt = (int)((nR + 127) / 128), nt = (int)((nS + BN - 1) / BN);
+    const int mt = (int)((nR + tr - 1) / tr), nt = (int)((nS + BN - 1) / BN);
     v->clear();
     for (int nb0 = 0; nb0 < nt; nb0 += L)
         for (int m = 0; m < mt; ++m) {
-            const int lo = std::max(nb0, first_upper_tile(m, BN, upper)), hi = std::min(nb0 + L, nt);
+            const int lo = std::max(nb0, first_upper_tile(m, BN, upper, tr)), hi = std::min(nb0 + L, nt);
             if (lo < hi) v->push_back(make_int4(m, lo, hi, 0));
         }
 }
 
-static int get_units(int64_t nR, int64_t nS, bool upper, int BN, int sms, const int4 **d_units, int *n_units)
+static int get_units(int64_t nR, int64_t nS, bool upper, int BN, int sms, const int4 **d_units, int *n_units,
+                     int tr = 128)
 {
     int dev = 0;
     cudaGetDevice(&dev);
-    const int mt = (int)((nR + 127) / 128), nt = (int)((nS + BN - 1) / BN);
-    // the longest ranges (fewest R re-reads) that still give every SM four units
+    const int mt = (int)((nR + tr - 1) / tr), nt = (int)((nS + BN - 1) / BN);
+    const int workers = (tr == 256) ? sms / 2 : sms;   // SMs, or SM pairs
+    // the longest ranges (fewest R re-reads) that still give every worker four units
     int L = 64;
     while (L > 1) {
         long long cnt = 0;
         for (int nb0 = 0; nb0 < nt; nb0 += L)
             for (int m = 0; m < mt; ++m)
-                if (std::max(nb0, first_upper_tile(m, BN, upper)) < std::min(nb0 + L, nt)) ++cnt;
-        if (cnt >= 4LL * sms) break;
+                if (std::max(nb0, first_upper_tile(m, BN, upper, tr)) < std::min(nb0 + L, nt)) ++cnt;
+        if (cnt >= 4LL * workers) break;
         L >>= 1;
     }
-    auto key = std::make_tuple(dev, nR, nS, (int)upper, BN, L);
+    auto key = std::make_tuple(dev, nR, nS, (int)upper * 1000 + tr, BN, L);
     std::lock_guard<std::mutex> lk(g_units_mu);
     auto it = g_units.find(key);
     if (it == g_units.end()) {
         std::vector<int4> v;
-        build_units(nR, nS, upper, BN, L, &v);
+        build_units(nR, nS, upper, BN, L, tr, &v);
         int4 *d = nullptr;
         if (!v.empty()) {
             cudaError_t e = cudaMalloc(&d, v.size() * sizeof(int4));
@@ -137,6 +141,7 @@ struct PassCfg {
     bool self, mirror;
     int prec;
     int BN;
+    bool cg2 = false;       // tensor-core pass on SM pairs (256-row tiles)
     double e2;              // squared-L2 threshold (metric 0), or the L1 / chi-square threshold eps
     int metric;             // 0 squared L2 (and cosine), 1 L1, 2 chi-square
     const int64_t *ids;     // ids written for both sides (self-join only; NULL: the store's ids)
@@ -155,6 +160,7 @@ struct PassOut {
     int err = 0;
     float ms_main = 0, ms_recheck = 0, ms_total = 0;
     int launches = 0;
+    int grid = 0;           // CTAs of the tensor-core launch
 };
 
 static int run_pass(const PassCfg &c, PassOut *po)
@@ -170,9 +176,9 @@ static int run_pass(const PassCfg &c, PassOut *po)
     const size_t cap = (size_t)std::max<int64_t>(c.cap, 1);
     int rc = dev_alloc(&outb, 2 * cap * sizeof(int64_t), st);
     if (rc) return rc;
-    const int64_t mt = (nR + 127) / 128;
+    const int64_t rows_pad = (nR + 255) / 256 * 256;   // per-row parameters cover whole 128- or 256-row tiles
     const size_t b_band = ((size_t)std::max<int64_t>(c.band_cap, 1) * sizeof(uint2) + 255) & ~size_t(255);
-    const size_t b_rowpar = (size_t)mt * 128 * sizeof(float4);
+    const size_t b_rowpar = (size_t)rows_pad * sizeof(float4);
     rc = dev_alloc(&ws, 256 + b_band + b_rowpar, st);
     if (rc) {
         dev_free(outb, st);
@@ -223,20 +229,21 @@ static int run_pass(const PassCfg &c, PassOut *po)
                 if (!rc) rc = ensure_fp8(const_cast<dl_store *>(S), st);
             }
             if (!rc)
-                rc = launch_rowpar(R->nq64, R->rowb, nR, mt * 128, R->dp, c.e2, nullptr, gamma64(d), rowpar, st,
+                rc = launch_rowpar(R->nq64, R->rowb, nR, rows_pad, R->dp, c.e2, nullptr, gamma64(d), rowpar, st,
                                    fp8 ? R->rowb8 : nullptr);
             ++launches;
             const CUtensorMap *tmA = nullptr, *tmB = nullptr;
             if (!rc) rc = fp8 ? get_tmap8(const_cast<dl_store *>(R), 128, &tmA) : get_tmap(const_cast<dl_store *>(R), 128, &tmA);
+            const int b_rows = c.cg2 ? c.BN / 2 : c.BN;   // an SM pair loads half of each S tile per SM
             if (!rc)
-                rc = fp8 ? get_tmap8(const_cast<dl_store *>(S), c.BN, &tmB) : get_tmap(const_cast<dl_store *>(S), c.BN, &tmB);
+                rc = fp8 ? get_tmap8(const_cast<dl_store *>(S), b_rows, &tmB) : get_tmap(const_cast<dl_store *>(S), b_rows, &tmB);
             const int4 *units = nullptr;
             int n_units = 0;
             if (!rc && c.units) {
                 units = c.units;
                 n_units = c.n_units;
             } else if (!rc && !c.pruned) {
-                rc = get_units(nR, nS, c.self, c.BN, sms, &units, &n_units);
+                rc = get_units(nR, nS, c.self, c.BN, sms, &units, &n_units, c.cg2 ? 256 : 128);
             }
             if (!rc && n_units > 0) {
                 TcLaunch L;
@@ -244,13 +251,14 @@ static int run_pass(const PassCfg &c, PassOut *po)
                 L.tmA = tmA;
                 L.tmB = tmB;
                 L.BN = c.BN;
-                L.grid = std::min(n_units, sms);
+                L.cg2 = c.cg2;
+                L.grid = c.cg2 ? 2 * std::min(n_units, sms / 2) : std::min(n_units, sms);
                 L.p.units = units;
                 L.p.n_units = n_units;
                 L.p.nR = (int)nR;
                 L.p.nS = (int)nS;
                 L.p.kc = fp8 ? R->dp8 / 128 : R->dp / 64;
-                tc_plan(c.BN, L.p.kc, &L.p.stages, &L.p.a_slots, fp8);
+                tc_plan(c.BN, L.p.kc, &L.p.stages, &L.p.a_slots, fp8, c.cg2);
                 L.p.upper = c.self ? 1 : 0;
                 L.p.rowpar = rowpar;
                 L.p.beta = S->beta;
@@ -261,7 +269,7 @@ static int run_pass(const PassCfg &c, PassOut *po)
                 L.p.cand_cnt = cnt + 1;
                 L.p.cand_cap = (unsigned long long)c.band_cap;
                 L.p.err = (int *)(cnt + 4);
-                rc = launch_tc_join(L, st, false, fp8);
+                rc = launch_tc_join(L, st, false, fp8, &po->grid);
                 ++launches;
             }
         } else {
@@ -285,7 +293,7 @@ static int run_pass(const PassCfg &c, PassOut *po)
         nvtxRangePushA("exact recheck of the band (K6)");
         if (!rc && (c.prec == DL_PREC_BF16 || c.prec == DL_PREC_FP8E4M3)) {
             rc = launch_finalize(band, cnt + 1, (unsigned long long)c.band_cap, R->x32, S->x32, d, c.e2, c.t_acc,
-                                 c.t_rej, jo, cnt + 3, cnt + 2, sms * 8, st);
+                                 c.t_rej, jo, cnt + 3, cnt + 2, sms * 8, st, (int)nR, (int)nS);
             ++launches;
         } else if (!rc && c.prec == DL_PREC_FP32 && c.metric != 0) {
             rc = launch_hist_recheck(c.metric, band, cnt + 1, (unsigned long long)c.band_cap, R->x32, S->x32, d, c.e2,
@@ -460,10 +468,19 @@ int sim_join_impl(const dl_store *R, const dl_store *S, int32_t metric, double e
         set_error("dl_sim_join: tile_n must be 0, 128 or 256");
         return DL_EINVAL;
     }
+    if (o.cta_pair < 0 || o.cta_pair > 2 || (o.cta_pair == 2 && (o.tile_n == 128 || o.prune))) {
+        set_error("dl_sim_join: cta_pair must be 0, 1 or 2 (2: tile_n 0 or 256, no prune)");
+        return DL_EINVAL;
+    }
+    // tile configuration: given, or autotuned per shape class (tensor-core precisions, dense join)
+    const bool tc = prec == DL_PREC_BF16 || prec == DL_PREC_FP8E4M3;
+    const int tune_kind = (prec == DL_PREC_FP8E4M3) ? (self ? kTuneEpsSelf8 : kTuneEpsRxS8)
+                                                    : (self ? kTuneEpsSelf : kTuneEpsRxS);
     bool tune_trial = false;
-    int BN = o.tile_n;
-    if (BN == 0)
-        BN = (prec == DL_PREC_BF16 && !o.prune) ? tune_pick(R->dp, self ? 1 : 0, R->n, Sx->n, &tune_trial) : 256;
+    int code = (o.tile_n ? o.tile_n : 256) | (o.cta_pair == 2 ? kTunePair : 0);
+    if (tc && !o.prune && o.tile_n == 0 && o.cta_pair == 0) code = tune_pick(R->dp, tune_kind, R->n, Sx->n, &tune_trial);
+    const int BN = tune_bn(code);
+    const bool cg2 = tc && tune_pair(code);
     if (prec == DL_PREC_FP8E4M3 && R->d > 1024) {
         set_error("dl_sim_join: FP8 path supports d <= 1024");
         return DL_EUNSUPPORTED;
@@ -481,6 +498,7 @@ int sim_join_impl(const dl_store *R, const dl_store *S, int32_t metric, double e
     c.mirror = self && o.self_mode == DL_SELF_FULL;
     c.prec = prec;
     c.BN = BN;
+    c.cg2 = cg2;
     c.e2 = e2;
     c.metric = hmetric;
     c.ids = emit_ids;
@@ -579,7 +597,7 @@ int sim_join_impl(const dl_store *R, const dl_store *S, int32_t metric, double e
         g_rate_band = (double)po.band_only / n_pairs;
     }
     if (tune_trial && reruns == 0)
-        tune_record(R->dp, self ? 1 : 0, R->n, Sx->n, BN, po.ms_main,
+        tune_record(R->dp, tune_kind, R->n, Sx->n, code, po.ms_main,
                     self ? 0.5 * (double)R->n * (double)R->n : (double)R->n * (double)Sx->n);
     dl_result *res = new dl_result();
     res->kind = 0;
@@ -597,10 +615,12 @@ int sim_join_impl(const dl_store *R, const dl_store *S, int32_t metric, double e
     s.reruns = reruns;
     s.precision = prec;
     s.tile_n = (prec == DL_PREC_BF16 || prec == DL_PREC_FP8E4M3) ? BN : 0;
+    s.cta_pair = (prec == DL_PREC_BF16 || prec == DL_PREC_FP8E4M3) ? (cg2 ? 2 : 1) : 0;
     s.ms_main = po.ms_main;
     s.ms_recheck = po.ms_recheck;
     s.ms_total = po.ms_total;
     s.kernels_launched = po.launches * (reruns + 1);
+    s.grid_ctas = po.grid;
     s.tile_pairs = tiles_total;
     s.tile_pairs_kept = tiles_kept;
     *out = res;

@@ -17,6 +17,7 @@
 #include <cstring>
 #include <vector>
 
+#include "checked.cuh"
 #include "exact.cuh"
 #include "kernels.h"
 
@@ -62,15 +63,19 @@ __global__ void __launch_bounds__(256)
     k_batch_decide(uint2 *__restrict__ cand, const unsigned long long *__restrict__ cand_cnt, unsigned long long cap,
                    const float *__restrict__ Q, const float *__restrict__ S, int d, const double *__restrict__ row_e2,
                    const int32_t *__restrict__ row_req, unsigned long long *__restrict__ req_cnt,
-                   unsigned long long *__restrict__ n_fp64, unsigned long long *__restrict__ n_band)
+                   unsigned long long *__restrict__ n_fp64, unsigned long long *__restrict__ n_band, int nQ, int nS)
 {
     const unsigned lane = threadIdx.x & 31;
     const unsigned long long n = min(*cand_cnt, cap);
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < n; base += stride) {
         const unsigned long long i = base + threadIdx.x;   // warp-uniform loop bound: base < n
-        const bool valid = i < n;
+        bool valid = i < n;
         const uint2 e = valid ? cand[i] : make_uint2(0u, 0u);
+        if (valid && !DL_CHECK(e.x < (unsigned)nQ && (e.y & ~kBandFlag) < (unsigned)nS, 30, i)) {
+            cand[i] = make_uint2(0u, 0xffffffffu);   // checked build: dropped, so the scatter skips it
+            valid = false;
+        }
         const int r = (int)e.x;
         const int c = (int)(e.y & ~kBandFlag);
         const bool band = valid && (e.y & kBandFlag);
@@ -351,7 +356,9 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
             return DL_EUNSUPPORTED;
         }
         bool tune_trial = false;
-        const int BN = o.tile_n ? o.tile_n : tune_pick(Qe->dp, 0, ne, S->n, &tune_trial);
+        const int BN = o.tile_n ? o.tile_n : tune_bn(tune_pick(Qe->dp, kTuneBatch, ne, S->n, &tune_trial));
+        stats.tile_n = BN;   // the epsilon rows' tile width (the autotuner's choice once decided)
+        stats.cta_pair = 1;
         const int64_t mt = (ne + 127) / 128;
         cudaEvent_t tev[2] = {nullptr, nullptr};
         if (tune_trial)
@@ -426,7 +433,7 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
             }
             if (!rc) {
                 k_batch_decide<<<sms * 8, 256, 0, st>>>(cand, cnt + 0, (unsigned long long)cap, Qe->x32, S->x32, d,
-                                                        row_e2, req_e, req_cnt, cnt + 1, cnt + 2);
+                                                        row_e2, req_e, req_cnt, cnt + 1, cnt + 2, (int)ne, (int)S->n);
                 count_launch(2);
                 e = cudaGetLastError();
                 if (e != cudaSuccess) rc = cuda_fail(e, "k_batch_decide launch");
@@ -483,7 +490,7 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
             if (!rc && tune_trial && attempt == 0) {
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, tev[0], tev[1]);
-                tune_record(Qe->dp, 0, ne, S->n, BN, ms, (double)ne * (double)S->n);
+                tune_record(Qe->dp, kTuneBatch, ne, S->n, BN, ms, (double)ne * (double)S->n);
             }
             dev_free(ws, st);
             break;
@@ -568,3 +575,5 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
     *out = res;
     return DL_OK;
 }
+
+DL_CHECK_READER(batch)

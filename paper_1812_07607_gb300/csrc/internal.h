@@ -152,9 +152,14 @@ void dev_free(void *p, cudaStream_t st);
 
 int device_sm_count();
 
-// Tile-width autotuner (tune.cu). kind: 0 R x S eps-join, 1 self eps-join, 2 top-k.
+// Autotuned tensor-core configuration: a tile width, plus kTunePair for SM-pair tiles.
+constexpr int kTunePair = 1 << 12;
+enum TuneKind { kTuneEpsRxS = 0, kTuneEpsSelf = 1, kTuneTopk = 2, kTuneEpsRxS8 = 3, kTuneEpsSelf8 = 4, kTuneBatch = 5 };
+inline int tune_bn(int code) { return code & 0xfff; }
+inline bool tune_pair(int code) { return (code & kTunePair) != 0; }
 int tune_pick(int dp, int kind, int64_t nR, int64_t nS, bool *trial);
-void tune_record(int dp, int kind, int64_t nR, int64_t nS, int bn, double kernel_ms, double pairs);
+void tune_record(int dp, int kind, int64_t nR, int64_t nS, int code, double kernel_ms, double pairs);
+int tune_trials(int kind);   // calls of a shape class before it is decided
 
 // Host-side directed conversions FP64 -> FP32 (the default conversion rounds to nearest).
 inline float f32_ru(double x)

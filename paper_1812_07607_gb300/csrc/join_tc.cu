@@ -33,11 +33,13 @@
 //               k_finalize turns the candidates into id pairs.
 // A unit is (R tile m, S tiles [nb, ne)); units are handed out round-robin, in the
 // S-range-major order their builders produce.
+#include <algorithm>
 #include <atomic>
 
 #include <cuda.h>
 
 #include "kernels.h"
+#include "checked.cuh"
 #include "ptx.cuh"
 
 namespace dl {
@@ -55,9 +57,11 @@ struct TileIter {
     int u, n;
     int4 un;
     bool valid;
-    __device__ __forceinline__ void start(const TcParams &p)
+    int stride;
+    __device__ __forceinline__ void start(const TcParams &p, int first, int step)
     {
-        u = blockIdx.x;
+        u = first;
+        stride = step;
         valid = u < p.n_units;
         if (valid) {
             un = p.units[u];
@@ -68,7 +72,7 @@ struct TileIter {
     {
         if (!valid) return;
         if (++n == un.z) {
-            u += gridDim.x;
+            u += stride;
             valid = u < p.n_units;
             if (valid) {
                 un = p.units[u];
@@ -79,6 +83,7 @@ struct TileIter {
 };
 
 constexpr int kStageCap = 128;   // candidate entries a warp buffers before flushing
+constexpr int kColSlots = 2;     // epilogue column-data slots: the current tile and the next
 
 // Copy a warp's buffered candidates to the global list (one atomic per flush).
 __device__ __forceinline__ void flush_stage(const TcParams &p, uint2 *stg, uint32_t &scnt)
@@ -167,7 +172,8 @@ __device__ __forceinline__ uint32_t slow_chunk(const TcParams &p, const uint32_t
         while (cm) {
             const int j = __ffs(cm) - 1;
             cm &= cm - 1u;
-            if (k < lim)
+            // staged (lim = ~0) entries must stay inside the warp's kStageCap buffer
+            if (k < lim && DL_CHECK(lim != ~0ULL || k < (unsigned long long)kStageCap, 1, k))
                 dst[k] = make_uint2((uint32_t)r, (uint32_t)(c0 + j) | (((am >> j) & 1u) ? 0u : kBandFlag));
             ++k;
         }
@@ -197,7 +203,8 @@ __device__ __forceinline__ uint32_t slow_chunk(const TcParams &p, const uint32_t
         const unsigned cm = __ballot_sync(0xffffffffu, cand);
         if (cm) {
             if (scnt + __popc(cm) > (uint32_t)kStageCap) flush_stage(p, stg, scnt);
-            if (cand) stg[scnt + __popc(cm & lt)] = make_uint2((uint32_t)rk, (uint32_t)c | (h >= ta ? 0u : kBandFlag));
+            if (cand && DL_CHECK(scnt + __popc(cm & lt) < (uint32_t)kStageCap, 2, scnt + __popc(cm & lt)))
+                stg[scnt + __popc(cm & lt)] = make_uint2((uint32_t)rk, (uint32_t)c | (h >= ta ? 0u : kBandFlag));
             scnt += __popc(cm);
         }
     }
@@ -300,7 +307,15 @@ __device__ __forceinline__ float max_tree32(const uint32_t (&v)[64], int o)
     return fmaxf(fmax3(a, b, c), e);
 }
 
-template <int BN, bool TOPK, bool FP8>
+// CG2: a CTA pair (cluster of two) computes 256-row tiles with tcgen05 cta_group::2. Each
+// CTA loads its own 128 rows of A and its own half (BN/2 rows) of every S tile into its own
+// shared memory, signalling its own barriers; the peer CTA's otherwise idle MMA warp forwards
+// each of its completions to the leader (rank 0), whose single thread issues M = 256 MMAs that
+// read both CTAs' operands and write each CTA's 128 rows into that CTA's TMEM; commits are
+// multicast to both CTAs. Each CTA's epilogue handles its own rows; the peer releases an
+// accumulator with a remote arrive on the leader's barrier. Half the B bytes per stage means
+// twice the stages in the same shared memory beside a resident R tile.
+template <int BN, bool TOPK, bool FP8, bool CG2>
 __global__ void __launch_bounds__(320, 1)
     tc_join_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcParams p)
@@ -308,7 +323,7 @@ __global__ void __launch_bounds__(320, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int kc = p.kc, stages = p.stages, a_slots = p.a_slots;
-    constexpr uint32_t kStageBytes = BN * 128;
+    constexpr uint32_t kStageBytes = (CG2 ? BN / 2 : BN) * 128;   // this CTA's rows of an S tile x 128 B
     constexpr int kChunkCols = FP8 ? 128 : 64;   // columns per 128-byte K chunk
     constexpr int kAcc = 512 / BN;              // TMEM accumulators: 2 of 256 or 4 of 128 columns
     constexpr uint32_t kTmemCols = 512;
@@ -317,11 +332,13 @@ __global__ void __launch_bounds__(320, 1)
     const uint32_t a_bytes = (uint32_t)kc * 16384;
     uint8_t *sA = smem;                                    // a_slots x kc x [128 rows x 128 B]
     uint8_t *sB = smem + a_slots * a_bytes;                // stages x [BN rows x 128 B]
-    float *s_beta = reinterpret_cast<float *>(sB + stages * kStageBytes);    // 8 warps x 2 x HC: beta
-    float4 *s_cst = reinterpret_cast<float4 *>(s_beta + 8 * 2 * HC);       // 8 warps x 2 x kSubW chunk stats
-    uint2 *s_stage = reinterpret_cast<uint2 *>(s_cst + 8 * 2 * kSubW);       // 8 warps x kStageCap candidates
-    float *s_sx = reinterpret_cast<float *>(s_stage + 8 * kStageCap);        // FP8: 8 warps x 2 x kSubW chunk scales
-    uint64_t *bars = reinterpret_cast<uint64_t *>(s_sx + (FP8 ? 8 * 2 * kSubW : 0));
+    // Column data of a tile (beta, chunk stats, FP8 chunk scales) is staged by the epilogue
+    // warps themselves with cp.async, one tile ahead, in kColSlots = 2 slots.
+    float *s_beta = reinterpret_cast<float *>(sB + stages * kStageBytes);    // 8 warps x kColSlots x HC: beta
+    float4 *s_cst = reinterpret_cast<float4 *>(s_beta + 8 * kColSlots * HC); // 8 warps x kColSlots x kSubW chunk stats
+    uint2 *s_stage = reinterpret_cast<uint2 *>(s_cst + 8 * kColSlots * kSubW);   // 8 warps x kStageCap candidates
+    float *s_sx = reinterpret_cast<float *>(s_stage + 8 * kStageCap);        // FP8: 8 warps x kColSlots x kSubW scales
+    uint64_t *bars = reinterpret_cast<uint64_t *>(s_sx + (FP8 ? 8 * kColSlots * kSubW : 0));
     uint64_t *full = bars;                    // [8]
     uint64_t *empty = bars + 8;               // [8]
     uint64_t *a_full = bars + 16;             // [2]
@@ -331,10 +348,23 @@ __global__ void __launch_bounds__(320, 1)
     uint64_t *done = bars + 28;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 29);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 30);
-    float *s_xch = reinterpret_cast<float *>(bars + 32);   // [8 warps x 32] row exchange slots (16-byte aligned)
+    uint64_t *pfull = bars + 32;              // CG2 leader: [8] the peer's half of the stage landed
+    uint64_t *pa_full = bars + 40;            // CG2 leader: [2] the peer's rows of the R tile landed
+    float *s_xch = reinterpret_cast<float *>(bars + 48);   // [8 warps x 32] row exchange slots (16-byte aligned)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    const uint32_t crank = CG2 ? cluster_ctarank() : 0u;   // this CTA's rank in its pair
+    const bool leader = crank == 0u;
+    const int ufirst = CG2 ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;   // units are per CTA pair with CG2
+    const int ustride = CG2 ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+    constexpr int kRowTiles = CG2 ? 2 : 1;    // 128-row tiles per unit row tile
+    // Raise the abort flag of this CTA (and of the peer, so that it stops waiting too).
+    auto raise_abort = [&]() {
+        *abort_flag = 1;
+        if constexpr (CG2) st_shared_remote_u32(mapa_shared(const_cast<int *>(abort_flag), crank ^ 1u), 1u);
+        atomicExch(p.err, 1);
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
@@ -347,15 +377,19 @@ __global__ void __launch_bounds__(320, 1)
         }
         for (int s = 0; s < kAcc; ++s) {
             mbar_init(acc_full + s, 1);
-            mbar_init(acc_empty + s, 8);
+            mbar_init(acc_empty + s, CG2 ? 16 : 8);   // CG2 (leader): both CTAs' epilogue warps
+        }
+        if constexpr (CG2) {
+            for (int s = 0; s < 8; ++s) mbar_init(pfull + s, 1);
+            for (int s = 0; s < 2; ++s) mbar_init(pa_full + s, 1);
         }
         mbar_init(done, 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
     if (warp == 1) {
-        tmem_alloc(tmem_slot, kTmemCols);
-        tmem_relinquish();
+        tmem_alloc<CG2>(tmem_slot, kTmemCols);
+        tmem_relinquish<CG2>();
     }
     if (warp == 0 && lane == 0) {
         tma_prefetch_desc(&tmA);
@@ -363,6 +397,7 @@ __global__ void __launch_bounds__(320, 1)
     }
     tc_fence_before();
     __syncthreads();
+    if constexpr (CG2) cluster_sync_all();   // both CTAs' barriers initialised and TMEM allocated
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
@@ -375,7 +410,7 @@ __global__ void __launch_bounds__(320, 1)
             for (int s = 0; s < 8; ++s) pend[s] = false;
             bool ok = true;
             int i = 0;   // unit count of this CTA
-            for (int u = blockIdx.x; u < p.n_units && ok; u += gridDim.x, ++i) {
+            for (int u = ufirst; u < p.n_units && ok; u += ustride, ++i) {
                 const int4 un = p.units[u];
                 const int slot = i % a_slots;
                 const uint32_t use = (uint32_t)(i / a_slots);
@@ -385,7 +420,8 @@ __global__ void __launch_bounds__(320, 1)
                 }
                 mbar_arrive_expect_tx(a_full + slot, a_bytes);
                 for (int c = 0; c < kc; ++c)   // a K chunk is 128 bytes: 64 BF16 or 128 FP8 columns
-                    tma_load_2d(sA + slot * a_bytes + c * 16384, &tmA, a_full + slot, c * kChunkCols, un.x * 128);
+                    tma_load_2d(sA + slot * a_bytes + c * 16384, &tmA, a_full + slot, c * kChunkCols,
+                                (un.x * kRowTiles + (int)crank) * 128);
                 a_pend[slot] = true;
                 a_pend_par[slot] = use & 1;
                 for (int n = un.y; n < un.z && ok; ++n) {
@@ -395,7 +431,8 @@ __global__ void __launch_bounds__(320, 1)
                             break;
                         }
                         mbar_arrive_expect_tx(full + stage, kStageBytes);
-                        tma_load_2d(sB + stage * kStageBytes, &tmB, full + stage, c * kChunkCols, n * BN);
+                        tma_load_2d(sB + stage * kStageBytes, &tmB, full + stage, c * kChunkCols,
+                                    n * BN + (CG2 ? (int)crank * (BN / 2) : 0));
                         pend[stage] = true;
                         pend_par[stage] = phase;
                         if (++stage == (uint32_t)stages) {
@@ -406,8 +443,7 @@ __global__ void __launch_bounds__(320, 1)
                 }
             }
             if (!ok) {
-                *abort_flag = 1;
-                atomicExch(p.err, 1);
+                raise_abort();
                 // Let every copy this thread started land before the CTA exits.
                 for (int s = 0; s < stages; ++s)
                     if (pend[s]) mbar_wait_plain(full + s, pend_par[s]);
@@ -415,14 +451,16 @@ __global__ void __launch_bounds__(320, 1)
                     if (a_pend[s]) mbar_wait_plain(a_full + s, a_pend_par[s]);
             }
         }
-    } else if (warp == 1) {
-        // ------------------------------------------------------------ MMA issuer
+    } else if (warp == 1 && CG2 && !leader) {
+        // ------------------------------------------------------------ peer: completion forwarder
+        // The leader's MMAs read this CTA's shared memory too: forward each completion of this
+        // CTA's own R-tile and stage barriers, in the producer's order, to the leader.
         if (lane == 0) {
-            constexpr uint32_t idesc = FP8 ? idesc_e4m3_f32(128, BN) : idesc_bf16_f32(128, BN);
-            uint32_t stage = 0, phase = 0, t = 0;
+            const uint32_t r_pfull = mapa_shared(pfull, 0u), r_pa_full = mapa_shared(pa_full, 0u);
+            uint32_t stage = 0, phase = 0;
             bool ok = true;
             int i = 0;
-            for (int u = blockIdx.x; u < p.n_units && ok; u += gridDim.x, ++i) {
+            for (int u = ufirst; u < p.n_units && ok; u += ustride, ++i) {
                 const int4 un = p.units[u];
                 const int slot = i % a_slots;
                 const uint32_t use = (uint32_t)(i / a_slots);
@@ -430,11 +468,53 @@ __global__ void __launch_bounds__(320, 1)
                     ok = false;
                     break;
                 }
+                mbar_arrive_remote(r_pa_full + (uint32_t)slot * 8u);
+                for (int n = un.y; n < un.z && ok; ++n) {
+                    for (int c = 0; c < kc; ++c) {
+                        if (!mbar_wait(full + stage, phase, abort_flag, p.wait_budget)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_arrive_remote(r_pfull + stage * 8u);
+                        if (++stage == (uint32_t)stages) {
+                            stage = 0;
+                            phase ^= 1;
+                        }
+                    }
+                }
+            }
+            if (!ok) raise_abort();
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc =
+                FP8 ? idesc_e4m3_f32(CG2 ? 256 : 128, BN) : idesc_bf16_f32(CG2 ? 256 : 128, BN);
+            uint32_t stage = 0, phase = 0, t = 0;
+            bool ok = true;
+            int i = 0;
+            for (int u = ufirst; u < p.n_units && ok; u += ustride, ++i) {
+                const int4 un = p.units[u];
+                const int slot = i % a_slots;
+                const uint32_t use = (uint32_t)(i / a_slots);
+                if (!mbar_wait(a_full + slot, use & 1, abort_flag, p.wait_budget)) {
+                    ok = false;
+                    break;
+                }
+                if constexpr (CG2) {   // the peer's rows of the R tile
+                    if (!mbar_wait_cluster(pa_full + slot, use & 1, abort_flag, p.wait_budget)) {
+                        ok = false;
+                        break;
+                    }
+                }
                 tc_fence_after();
                 const uint32_t a_base = smem_u32(sA + slot * a_bytes);
                 for (int n = un.y; n < un.z && ok; ++n) {
                     const uint32_t b = t % kAcc;
-                    if (!mbar_wait(acc_empty + b, ((t / kAcc) & 1) ^ 1, abort_flag, p.wait_budget)) {
+                    const bool freed = CG2 ? mbar_wait_cluster(acc_empty + b, ((t / kAcc) & 1) ^ 1, abort_flag,
+                                                               p.wait_budget)
+                                           : mbar_wait(acc_empty + b, ((t / kAcc) & 1) ^ 1, abort_flag, p.wait_budget);
+                    if (!freed) {
                         ok = false;
                         break;
                     }
@@ -445,36 +525,56 @@ __global__ void __launch_bounds__(320, 1)
                             ok = false;
                             break;
                         }
+                        if constexpr (CG2) {   // the peer's half of this stage
+                            if (!mbar_wait_cluster(pfull + stage, phase, abort_flag, p.wait_budget)) {
+                                ok = false;
+                                break;
+                            }
+                        }
                         tc_fence_after();
                         const uint32_t a_addr = a_base + c * 16384;
                         const uint32_t b_addr = smem_u32(sB + stage * kStageBytes);
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {   // 4 x 32 bytes of K per 128-byte chunk
-                            if constexpr (FP8)
-                                mma_f8(d_tmem, smem_desc_sw128(a_addr + k * 32), smem_desc_sw128(b_addr + k * 32),
-                                       idesc, (c | k) != 0);
+                            const uint64_t ad = smem_desc_sw128(a_addr + k * 32), bd = smem_desc_sw128(b_addr + k * 32);
+                            if constexpr (CG2 && FP8)
+                                mma_f8_cg2(d_tmem, ad, bd, idesc, (c | k) != 0);
+                            else if constexpr (CG2)
+                                mma_f16_cg2(d_tmem, ad, bd, idesc, (c | k) != 0);
+                            else if constexpr (FP8)
+                                mma_f8(d_tmem, ad, bd, idesc, (c | k) != 0);
                             else
-                                mma_f16(d_tmem, smem_desc_sw128(a_addr + k * 32), smem_desc_sw128(b_addr + k * 32),
-                                        idesc, (c | k) != 0);
+                                mma_f16(d_tmem, ad, bd, idesc, (c | k) != 0);
                         }
-                        mma_commit(empty + stage);
+                        if constexpr (CG2)
+                            mma_commit_cg2_mc(empty + stage, 3);   // both CTAs may refill their halves
+                        else
+                            mma_commit(empty + stage);
                         if (++stage == (uint32_t)stages) {
                             stage = 0;
                             phase ^= 1;
                         }
                     }
                     if (!ok) break;
-                    mma_commit(acc_full + b);
+                    if constexpr (CG2)
+                        mma_commit_cg2_mc(acc_full + b, 3);   // both CTAs' rows are in their TMEM
+                    else
+                        mma_commit(acc_full + b);
                     ++t;
                 }
-                if (ok) mma_commit(a_empty + slot);
+                if (ok) {
+                    if constexpr (CG2)
+                        mma_commit_cg2_mc(a_empty + slot, 3);
+                    else
+                        mma_commit(a_empty + slot);
+                }
             }
-            if (!ok) {
-                *abort_flag = 1;
-                atomicExch(p.err, 1);
-            }
+            if (!ok) raise_abort();
             // No MMA may still be running when TMEM is released.
-            mma_commit(done);
+            if constexpr (CG2)
+                mma_commit_cg2(done);
+            else
+                mma_commit(done);
             mbar_wait_plain(done, 0);
         }
     } else {
@@ -483,21 +583,23 @@ __global__ void __launch_bounds__(320, 1)
         const int quad = warp & 3;         // TMEM lanes this warp may access: 32*quad .. +31
         const int half = e >> 2;           // which half of the tile's columns
         const uint32_t lane_base = static_cast<uint32_t>(quad * 32) << 16;
-        float *my_bt = s_beta + e * (2 * HC);
-        float *my_sx = s_sx + e * (2 * kSubW);   // FP8 only
-        float4 *my_cs = s_cst + e * (2 * kSubW);
+        float *my_bt = s_beta + e * (kColSlots * HC);
+        float *my_sx = s_sx + e * (kColSlots * kSubW);   // FP8 only
+        float4 *my_cs = s_cst + e * (kColSlots * kSubW);
         uint2 *my_stg = s_stage + e * kStageCap;
         float *my_xch = s_xch + e * 32;
         uint32_t scnt = 0;
         constexpr int kPer = HC / 32;      // beta values a lane stages per tile (4 or 2)
         TileIter cur, nxt;
-        cur.start(p);
+        cur.start(p, ufirst, ustride);
         nxt = cur;
         nxt.next(p);
 
         auto stage_async = [&](const TileIter &it, int s) {
             if (!it.valid) return;
             const int c0 = it.n * BN + half * HC;
+            // the column data (beta [n_pad], chunk stats [n_pad / 32]) covers whole 256-column tiles
+            if (!DL_CHECK(c0 + HC <= (p.nS + 255) / 256 * 256, 4, c0)) return;
             if constexpr (kPer == 4) {
                 cp_async_16(my_bt + s * HC + lane * 4, p.beta + c0 + lane * 4);
                 if (FP8 && lane == kSubW) cp_async_16(my_sx + s * kSubW, p.sc_s + (c0 >> 5));   // 4 chunk scales
@@ -521,9 +623,11 @@ __global__ void __launch_bounds__(320, 1)
         int tcnt = 0;             // top-k: this slot's list fill
         size_t sidx = 0;
         while (cur.valid) {
-            const int r = cur.un.x * 128 + quad * 32 + lane;
+            const int r = (cur.un.x * kRowTiles + (int)crank) * 128 + quad * 32 + lane;
             if (cur.n == cur.un.y) {
-                rp = p.rowpar[r];
+                // per-row parameters cover whole R tiles (256-row tiles for SM pairs)
+                if (DL_CHECK(r < (p.nR + kRowTiles * 128 - 1) / (kRowTiles * 128) * (kRowTiles * 128), 3, r))
+                    rp = p.rowpar[r];
                 if constexpr (FP8) sq = (r < p.nR) ? p.sc_r[r] : 1.0f;
                 if constexpr (TOPK) {   // a unit owns its (row tile, split): start the slots fresh
                     sidx = (size_t)r * p.tk_slots + (size_t)cur.un.w * 2 + half;
@@ -618,7 +722,16 @@ __global__ void __launch_bounds__(320, 1)
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(acc_empty + b);   // TMEM buffer free; the rest is in registers
+            if (lane == 0) {   // TMEM buffer free; the rest is in registers
+                if constexpr (CG2) {
+                    if (leader)
+                        mbar_arrive(acc_empty + b);
+                    else
+                        mbar_arrive_remote(mapa_shared(acc_empty + b, 0u));
+                } else {
+                    mbar_arrive(acc_empty + b);
+                }
+            }
             process64(va, HC == 128 ? 1 : 0);
             if constexpr (TOPK) {
                 if (cur.n + 1 == cur.un.z && r < p.nR) {   // last tile of the unit: publish the slot
@@ -633,41 +746,47 @@ __global__ void __launch_bounds__(320, 1)
             nxt.next(p);
             ++t;
         }
+        cp_async_wait_all();   // no staged column data may still be in flight when the CTA ends
         if constexpr (!TOPK) flush_stage(p, my_stg, scnt);
-        if (!ok) {
-            cp_async_wait_all();   // the next tile's column data may still be in flight
-            *abort_flag = 1;
-            atomicExch(p.err, 1);
-        }
+        if (!ok) raise_abort();
     }
 
     __syncthreads();
+    // CG2: neither CTA of the pair releases its TMEM or exits while the other may still use
+    // it -- the leader's MMAs write the peer's TMEM and read its shared memory, and the peer
+    // arrives on the leader's barriers. Every path of every thread reaches this point.
+    if constexpr (CG2) cluster_sync_all();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem_base, kTmemCols);
+        tmem_dealloc<CG2>(tmem_base, kTmemCols);
     }
 }
 
 static size_t tc_extra_bytes(int BN, bool fp8)
 {
-    // per epilogue warp: 2 x BN/2 floats of beta, 2 x BN/64 chunk stats, the candidate buffer and
-    // (FP8) 2 x BN/64 chunk scales; then 32 barrier / flag words and 8 x 32 exchange floats
-    return (size_t)8 * (2 * (BN / 2) * 4 + 2 * (BN / 64) * 16 + kStageCap * 8 + (fp8 ? 2 * (BN / 64) * 4 : 0)) + 32 * 8 +
-           8 * 32 * 4;
+    // per epilogue warp: kColSlots x BN/2 floats of beta, kColSlots x BN/64 chunk stats, the candidate
+    // buffer and (FP8) kColSlots x BN/64 chunk scales; then 48 barrier / flag words and 8 x 32 exchange floats
+    return (size_t)8 * (kColSlots * (BN / 2) * 4 + kColSlots * (BN / 64) * 16 + kStageCap * 8 +
+                        (fp8 ? kColSlots * (BN / 64) * 4 : 0)) +
+           48 * 8 + 8 * 32 * 4;
 }
 
-static size_t tc_smem_bytes(int BN, int kc, int stages, int a_slots, bool fp8)
+// One S stage per CTA: a 128-byte K chunk of the CTA's rows of an S tile (all BN rows, or
+// BN/2 for a CTA pair).
+static size_t tc_stage_bytes(int BN, bool cg2) { return (size_t)(cg2 ? BN / 2 : BN) * 128; }
+
+static size_t tc_smem_bytes(int BN, int kc, int stages, int a_slots, bool fp8, bool cg2)
 {
-    return 1024 + (size_t)a_slots * kc * 16384 + (size_t)stages * BN * 128 + tc_extra_bytes(BN, fp8);
+    return 1024 + (size_t)a_slots * kc * 16384 + (size_t)stages * tc_stage_bytes(BN, cg2) + tc_extra_bytes(BN, fp8);
 }
 
 // Shared-memory plan: two A slots when that still leaves at least three S stages.
-void tc_plan(int BN, int kc, int *stages, int *a_slots, bool fp8)
+void tc_plan(int BN, int kc, int *stages, int *a_slots, bool fp8, bool cg2)
 {
     const long cap = 232448;
     for (int slots = 2; slots >= 1; --slots) {
         const long avail = cap - 1024 - (long)tc_extra_bytes(BN, fp8) - (long)slots * kc * 16384;
-        long s = avail / ((long)BN * 128);
+        long s = avail / (long)tc_stage_bytes(BN, cg2);
         if (s > 8) s = 8;
         if (s >= 3 || slots == 1) {
             *stages = (int)s;
@@ -685,36 +804,73 @@ long long tc_wait_budget()
     return b > 0 ? b : kWaitBudgetClocks;
 }
 
-template <int BN, bool TOPK, bool FP8>
-static int launch_one(const TcLaunch &L, size_t smem, cudaStream_t st)
+template <int BN, bool TOPK, bool FP8, bool CG2>
+static int launch_one(const TcLaunch &L, size_t smem, cudaStream_t st, int *grid_out)
 {
-    cudaError_t e =
-        cudaFuncSetAttribute(tc_join_kernel<BN, TOPK, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = tc_join_kernel<BN, TOPK, FP8, CG2>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_join_kernel)");
     TcParams p = L.p;
     p.wait_budget = tc_wait_budget();
-    tc_join_kernel<BN, TOPK, FP8><<<L.grid, 320, smem, st>>>(*L.tmA, *L.tmB, p);
+    if constexpr (CG2) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.blockDim = dim3(320);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        // persistent pairs: no more than can be resident at once (GPCs may leave an SM unpaired)
+        cfg.gridDim = dim3(2);
+        int pairs = 0;
+        e = cudaOccupancyMaxActiveClusters(&pairs, kern, &cfg);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveClusters(tc_join_kernel)");
+        if (pairs < 1) {
+            set_error("tensor-core join: no CTA pair fits on this device");
+            return DL_EUNSUPPORTED;
+        }
+        const int want = std::max(1, L.grid / 2);
+        cfg.gridDim = dim3((unsigned)(2 * std::min(want, pairs)));
+        e = cudaLaunchKernelEx(&cfg, kern, *L.tmA, *L.tmB, p);
+        if (e != cudaSuccess) return cuda_fail(e, "tc_join_kernel (CTA pairs) launch");
+        if (grid_out) *grid_out = (int)cfg.gridDim.x;
+    } else {
+        kern<<<L.grid, 320, smem, st>>>(*L.tmA, *L.tmB, p);
+        if (grid_out) *grid_out = L.grid;
+    }
     return DL_OK;
 }
 
-int launch_tc_join(const TcLaunch &L, cudaStream_t st, bool topk, bool fp8)
+int launch_tc_join(const TcLaunch &L, cudaStream_t st, bool topk, bool fp8, int *grid_out)
 {
     if (topk && fp8) {
         set_error("top-k runs on the BF16 path only");
         return DL_EUNSUPPORTED;
     }
-    const size_t smem = tc_smem_bytes(L.BN, L.p.kc, L.p.stages, L.p.a_slots, fp8);
+    if (L.cg2 && (topk || L.BN != 256)) {
+        set_error("tensor-core join: CTA pairs serve the 256-column epsilon-join only");
+        return DL_EUNSUPPORTED;
+    }
+    const size_t smem = tc_smem_bytes(L.BN, L.p.kc, L.p.stages, L.p.a_slots, fp8, L.cg2);
     if (L.p.stages < 2 || smem > 232448) {
         set_error("tensor-core join: no shared-memory plan for d=%d, tile %d", L.p.kc * 64, L.BN);
         return DL_EUNSUPPORTED;
     }
     int rc;
-    if (L.BN == 256)
-        rc = topk ? launch_one<256, true, false>(L, smem, st)
-                  : (fp8 ? launch_one<256, false, true>(L, smem, st) : launch_one<256, false, false>(L, smem, st));
+    if (L.cg2)
+        rc = fp8 ? launch_one<256, false, true, true>(L, smem, st, grid_out) : launch_one<256, false, false, true>(L, smem, st, grid_out);
+    else if (L.BN == 256)
+        rc = topk ? launch_one<256, true, false, false>(L, smem, st, grid_out)
+                  : (fp8 ? launch_one<256, false, true, false>(L, smem, st, grid_out)
+                         : launch_one<256, false, false, false>(L, smem, st, grid_out));
     else if (L.BN == 128)
-        rc = topk ? launch_one<128, true, false>(L, smem, st)
-                  : (fp8 ? launch_one<128, false, true>(L, smem, st) : launch_one<128, false, false>(L, smem, st));
+        rc = topk ? launch_one<128, true, false, false>(L, smem, st, grid_out)
+                  : (fp8 ? launch_one<128, false, true, false>(L, smem, st, grid_out)
+                         : launch_one<128, false, false, false>(L, smem, st, grid_out));
     else {
         set_error("tensor-core tile width %d not supported (128 or 256)", L.BN);
         return DL_EINVAL;
@@ -741,3 +897,5 @@ extern "C" int dl_debug_set_wait_budget(int64_t clocks)
     dl::g_wait_budget.store(clocks, std::memory_order_relaxed);
     return DL_OK;
 }
+
+DL_CHECK_READER(join_tc)

@@ -49,14 +49,17 @@ struct TcLaunch {
     const CUtensorMap *tmA, *tmB;
     TcParams p;
     int BN;
-    int grid;
+    int grid;           // CTAs (with cg2: twice the CTA pairs wanted; clamped to the resident pairs)
+    bool cg2 = false;   // CTA pairs (tcgen05 cta_group::2) on 256-row tiles: units count 256-row tiles,
+                        // tmB's box is BN/2 rows, rowpar covers the rows rounded up to 256
 };
 
-void tc_plan(int BN, int kc, int *stages, int *a_slots, bool fp8 = false);
+void tc_plan(int BN, int kc, int *stages, int *a_slots, bool fp8 = false, bool cg2 = false);
 // Clock budget of the tensor-core kernels' abortable waits: the default (about 1 s),
 // unless dl_debug_set_wait_budget set another.
 long long tc_wait_budget();
-int launch_tc_join(const TcLaunch &L, cudaStream_t st, bool topk = false, bool fp8 = false);
+// *grid_out (optional) receives the CTAs actually launched.
+int launch_tc_join(const TcLaunch &L, cudaStream_t st, bool topk = false, bool fp8 = false, int *grid_out = nullptr);
 
 // ---- K8 SIMT FP32 join (join_simt.cu)
 struct SimtParams {
@@ -87,7 +90,7 @@ int launch_rowpar(const double *nq64, const float4 *rowb, int64_t n, int64_t n_t
 // translated directly, band pairs are rechecked exactly first (recheck.cu).
 int launch_finalize(const uint2 *cand, const unsigned long long *cand_cnt, unsigned long long cand_cap, const float *R,
                     const float *S, int d, double e2, float t_acc, float t_rej, const JoinOut &out,
-                    unsigned long long *n_fp64, unsigned long long *n_band, int grid, cudaStream_t st);
+                    unsigned long long *n_fp64, unsigned long long *n_band, int grid, cudaStream_t st, int nR, int nS);
 int launch_diag(const int64_t *ids, int64_t n, int64_t *out_r, int64_t *out_s, unsigned long long *out_cnt,
                 unsigned long long cap, cudaStream_t st);
 

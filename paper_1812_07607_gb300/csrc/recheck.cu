@@ -11,6 +11,7 @@
 //      nearest with no contraction (__dsub_rn / __dmul_rn / __dadd_rn), compared
 //      with fl64(eps*eps) -- the very expression that defines the result, so the
 //      decision is identical to the FP64 nested loop's.
+#include "checked.cuh"
 #include "exact.cuh"
 #include "kernels.h"
 
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(256)
     k_finalize(const uint2 *__restrict__ cand, const unsigned long long *__restrict__ cand_cnt,
                unsigned long long cand_cap, const float *__restrict__ R, const float *__restrict__ S, int d, double e2,
                float t_acc, float t_rej, JoinOut out, unsigned long long *__restrict__ n_fp64,
-               unsigned long long *__restrict__ n_band)
+               unsigned long long *__restrict__ n_band, int nR, int nS)
 {
     const unsigned lane = threadIdx.x & 31;
     const unsigned long long n = min(*cand_cnt, cand_cap);
@@ -50,7 +51,8 @@ __global__ void __launch_bounds__(256)
     for (unsigned long long base = w0 * 32; base < n; base += nw * 32) {
         const unsigned long long i = base + lane;
         const bool valid = i < n;
-        const uint2 e = valid ? cand[i] : make_uint2(0u, 0u);
+        uint2 e = valid ? cand[i] : make_uint2(0u, 0u);
+        if (valid && !DL_CHECK(e.x < (unsigned)nR && (e.y & ~kBandFlag) < (unsigned)nS, 20, i)) e = make_uint2(0u, 0u);
         const int r = (int)e.x;
         const int c = (int)(e.y & ~kBandFlag);
         const bool band = valid && (e.y & kBandFlag);
@@ -186,9 +188,9 @@ int launch_hist_recheck(int metric, const uint2 *band, const unsigned long long 
 
 int launch_finalize(const uint2 *cand, const unsigned long long *cand_cnt, unsigned long long cand_cap, const float *R,
                     const float *S, int d, double e2, float t_acc, float t_rej, const JoinOut &out,
-                    unsigned long long *n_fp64, unsigned long long *n_band, int grid, cudaStream_t st)
+                    unsigned long long *n_fp64, unsigned long long *n_band, int grid, cudaStream_t st, int nR, int nS)
 {
-    k_finalize<<<grid, 256, 0, st>>>(cand, cand_cnt, cand_cap, R, S, d, e2, t_acc, t_rej, out, n_fp64, n_band);
+    k_finalize<<<grid, 256, 0, st>>>(cand, cand_cnt, cand_cap, R, S, d, e2, t_acc, t_rej, out, n_fp64, n_band, nR, nS);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_finalize launch");
@@ -219,3 +221,5 @@ int launch_diag(const int64_t *ids, int64_t n, int64_t *out_r, int64_t *out_s, u
 }
 
 }  // namespace dl
+
+DL_CHECK_READER(recheck)

@@ -26,6 +26,7 @@
 #include <tuple>
 #include <vector>
 
+#include "checked.cuh"
 #include "kernels.h"
 
 namespace dl {
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(128) k_topk_finalize(const TopkFin f)
                 const bool keep = idx < cs && __uint_as_float(e.y) >= th;
                 const unsigned bm = __ballot_sync(0xffffffffu, keep);
                 const int pos = m + __popc(bm & lt);
-                if (keep && pos < kTkMax) col[pos] = e.x;
+                if (keep && pos < kTkMax) col[pos] = DL_CHECK(e.x < (unsigned)f.nS, 10, e.x) ? e.x : 0u;
                 m += __popc(bm);
             }
         }
@@ -411,7 +412,7 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
     }
     const bool use_tc = (o.precision != DL_PREC_FP32) && Q->dp <= 512;
     bool tune_trial = false;
-    const int BN = o.tile_n ? o.tile_n : (use_tc ? tune_pick(Q->dp, 2, nQ, nS, &tune_trial) : 256);
+    const int BN = o.tile_n ? o.tile_n : (use_tc ? tune_bn(tune_pick(Q->dp, kTuneTopk, nQ, nS, &tune_trial)) : 256);
     const int sms = device_sm_count();
     const int64_t mt = (nQ + 127) / 128, nt = (nS + BN - 1) / BN;
     int splits = 1;
@@ -427,6 +428,7 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
                  b_rth = al256((size_t)std::max<int64_t>(rows, 1) * sizeof(unsigned)),
                  b_ovf = al256((size_t)std::max<int64_t>(nQ, 1) * sizeof(int)),
                  b_rows = al256((size_t)std::max<int64_t>(nQ, 1) * sizeof(int)), b_misc = 256;
+    const bool timing = o.timing || tune_trial;
     void *ws = nullptr;
     int rc = dev_alloc(&ws, b_rowpar + b_heap + b_list + b_cnt + b_theta + b_rth + b_ovf + b_rows + b_misc, st);
     if (rc) return rc;
@@ -449,7 +451,6 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
     pw += b_rows;
     unsigned long long *misc = (unsigned long long *)pw;   // [0] flagged rows [1] fp64 evals [2] err [3] tc err
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    const bool timing = o.timing || tune_trial;
     if (timing)
         for (auto &e : ev) cudaEventCreate(&e);
     auto done = [&](int code) {
@@ -658,7 +659,7 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
     if (tune_trial && flagged == 0) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev[0], ev[1]);
-        tune_record(Q->dp, 2, nQ, nS, BN, ms, (double)nQ * (double)nS);
+        tune_record(Q->dp, kTuneTopk, nQ, nS, BN, ms, (double)nQ * (double)nS);
     }
     return done(DL_OK);
 }
@@ -739,3 +740,5 @@ extern "C" int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric
     *out = res;
     return DL_OK;
 }
+
+DL_CHECK_READER(topk)

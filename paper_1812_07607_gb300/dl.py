@@ -51,7 +51,8 @@ class DLError(RuntimeError):
 class dl_join_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("self_mode", ctypes.c_int32),
                 ("out_capacity", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
-                ("tile_n", ctypes.c_int32), ("timing", ctypes.c_int32), ("prune", ctypes.c_int32)]
+                ("tile_n", ctypes.c_int32), ("timing", ctypes.c_int32), ("prune", ctypes.c_int32),
+                ("cta_pair", ctypes.c_int32)]
 
 
 class dl_join_stats(ctypes.Structure):
@@ -60,7 +61,8 @@ class dl_join_stats(ctypes.Structure):
                 ("reruns", ctypes.c_int64), ("precision", ctypes.c_int32), ("tile_n", ctypes.c_int32),
                 ("ms_main", ctypes.c_float), ("ms_recheck", ctypes.c_float), ("ms_total", ctypes.c_float),
                 ("kernels_launched", ctypes.c_int32), ("tile_pairs", ctypes.c_int64),
-                ("tile_pairs_kept", ctypes.c_int64)]
+                ("tile_pairs_kept", ctypes.c_int64), ("cta_pair", ctypes.c_int32),
+                ("grid_ctas", ctypes.c_int32)]
 
 
 class dl_request(ctypes.Structure):
@@ -85,7 +87,8 @@ def lib_path() -> str:
 
 
 def load(path: str | None = None):
-    """Load the C-ABI library (raises if it has not been built)."""
+    """Load the C-ABI library (raises if it has not been built) and make it the one every call of
+    this binding uses: the in-tree build, or the library at `path` (e.g. the bounds-checked build)."""
     global _lib
     if _lib is not None and path is None:
         return _lib
@@ -146,8 +149,7 @@ def load(path: str | None = None):
                  "dl_result_count", "dl_result_pairs", "dl_result_topk", "dl_result_stats",
                  "dl_result_free"):
         getattr(L, name).restype = ctypes.c_int
-    if path == LIB_PATH:
-        _lib = L
+    _lib = L
     return L
 
 
@@ -320,7 +322,7 @@ class Result:
 
 
 def make_opts(precision="auto", self_mode="upper", out_capacity=0, stream=None, tile_n=0, timing=False,
-              prune=False):
+              prune=False, cta_pair=0):
     o = dl_join_opts()
     load().dl_join_opts_default(ctypes.byref(o))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -330,6 +332,7 @@ def make_opts(precision="auto", self_mode="upper", out_capacity=0, stream=None, 
     o.tile_n = int(tile_n)
     o.timing = 1 if timing else 0
     o.prune = 1 if prune else 0
+    o.cta_pair = int(cta_pair)
     return o
 
 
@@ -386,11 +389,12 @@ def dedup(X: Store, eps: float, labels=None, target: int = 0, plan="all", metric
 
 
 def sim_join(R: Store, S: Store | None, eps: float, precision="auto", self_mode="upper", out_capacity=0,
-             stream=None, tile_n=0, timing=False, allow_overflow=False, metric="l2", prune=False) -> Result:
+             stream=None, tile_n=0, timing=False, allow_overflow=False, metric="l2", prune=False,
+             cta_pair=0) -> Result:
     """dl_sim_join: every pair with canonical squared L2 distance <= eps^2; with
     metric="cosine" (stores from Store.normalized()) every pair with cosine >= eps; with
     metric="l1" / "chi2" every pair whose histogram distance is <= eps."""
-    o = make_opts(precision, self_mode, out_capacity, stream, tile_n, timing, prune)
+    o = make_opts(precision, self_mode, out_capacity, stream, tile_n, timing, prune, cta_pair)
     h = ctypes.c_void_p()
     rc = load().dl_sim_join(R.handle, None if S is None else S.handle, METRICS[metric], float(eps),
                             ctypes.byref(o), ctypes.byref(h))

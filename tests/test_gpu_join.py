@@ -248,8 +248,11 @@ def test_self_clustered_262k_full_size_sampled(dl, orc):
     assert (pos[r] < pos[s]).all()
 
 
-def test_autotuner_tries_both_tiles_and_persists(tmp_path):
-    """Tile width autotuner: first calls of a shape class try 256, 128, 256, 128; then the faster sticks."""
+def test_autotuner_tries_every_configuration_and_persists(tmp_path):
+    """Tile autotuner: the first calls of a shape class try every candidate configuration once
+    -- BF16: 256-column tiles on one SM, 128-column tiles, 256-row tiles on an SM pair; FP8: one
+    SM or an SM pair -- then the first candidate again (its first run was the cold call); from
+    then on the fastest sticks, and a new process starts from the DL_TUNE_CACHE file."""
     import os
     import subprocess
     import sys
@@ -261,21 +264,31 @@ from paper_1812_07607_gb300 import dl, workloads as W
 wl = W.rxs_histograms_2k()
 R = dl.Store(torch.from_numpy(wl.r_ids).cuda(), torch.from_numpy(wl.R).cuda())
 S = dl.Store(torch.from_numpy(wl.s_ids).cuda(), torch.from_numpy(wl.S).cuda())
-tiles = []
-for _ in range(6):
-    r = dl.sim_join(R, S, wl.eps)
-    tiles.append(r.stats()["tile_n"])
-    r.free()
-print(tiles)
+cfg = {}
+for prec, calls in (("bf16", 6), ("fp8", 5)):
+    cfg[prec] = []
+    for _ in range(calls):
+        r = dl.sim_join(R, S, wl.eps, precision=prec)
+        st = r.stats()
+        cfg[prec].append((st["tile_n"], st["cta_pair"]))
+        r.free()
+print(cfg)
 '''
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     env = dict(os.environ, DL_TUNE_CACHE=str(cache))
     out = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stderr
-    tiles = eval(out.stdout.strip().splitlines()[-1])
-    assert tiles[:4] == [256, 128, 256, 128] and tiles[4] == tiles[5] and tiles[4] in (128, 256)
+    cfg = eval(out.stdout.strip().splitlines()[-1])
+    bf, f8 = cfg["bf16"], cfg["fp8"]
+    assert bf[:4] == [(256, 1), (128, 1), (256, 2), (256, 1)], bf
+    assert bf[4] == bf[5] and bf[4] in bf[:3], bf
+    assert f8[:3] == [(256, 1), (256, 2), (256, 1)], f8
+    assert f8[3] == f8[4] and f8[3] in f8[:2], f8
+    code_of = lambda c: c[0] | (4096 if c[1] == 2 else 0)
     lines = cache.read_text().split()
-    assert len(lines) == 2 and int(lines[1]) == tiles[4]
+    assert len(lines) == 4 and sorted(int(v) for v in lines[1::2]) == sorted([code_of(bf[4]), code_of(f8[3])])
     # a new process starts from the cache
     out = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=300)
-    assert eval(out.stdout.strip().splitlines()[-1]) == [tiles[4]] * 6
+    assert out.returncode == 0, out.stderr
+    again = eval(out.stdout.strip().splitlines()[-1])
+    assert again["bf16"] == [bf[4]] * 6 and again["fp8"] == [f8[3]] * 5

@@ -113,3 +113,19 @@ def test_topk_empty_store(dl):
     ids, d2 = res.topk_host()
     assert (ids == -1).all() and (d2 == -1.0).all()
     res.free()
+
+
+@pytest.mark.parametrize("k", [4, 10, 100])
+def test_topk_large_store_with_ties_exact(dl, orc, k):
+    """A 70,000-row store split over ten S splits per query row (many slots per row share the
+    row threshold). Ids and distances must equal the oracle's bit for bit, including exact ties
+    at the k-th distance (600 planted duplicate rows) and query rows that are store rows."""
+    g = W.rng(8800 + k)
+    S, _ = W.clustered_histograms(g, 70_000, 64, 900, 0.01)
+    dup_src = g.choice(70_000, size=600, replace=False)
+    dup_dst = g.choice(np.setdiff1d(np.arange(70_000), dup_src), size=600, replace=False)
+    S[dup_dst] = S[dup_src]
+    Q, _ = W.clustered_histograms(g, 260, 64, 900, 0.012)
+    Q = np.concatenate([Q, S[dup_src[:40]]])
+    st = check_topk(dl, orc, Q, S, k)
+    assert st["band_pairs"] < Q.shape[0]   # rows re-solved by the exact scan stay rare
