@@ -953,6 +953,20 @@ def _case_fp8_unit_d512():
     return lambda: dl.sim_join(Rs, Ts, 0.55, precision="fp8", timing=True)
 
 
+def _case_pair_unit_d512(pair: int = 2, prec: str = "bf16"):
+    """The same 65,536 x 65,536 d=512 join in BF16 with the tensor-core pass on SM pairs
+    (cta_group::2, 256-row tiles), or with pair=1 on one SM per tile."""
+    import torch
+    from paper_1812_07607_gb300 import dl, workloads as W
+    dl.load()
+    g = W.rng(5)
+    R, c = W.unit_mixture(g, 65536, 512, 4096, 0.02)
+    T, _ = W.unit_mixture(g, 65536, 512, 4096, 0.02, centroids=c)
+    Rs = dl.Store(torch.arange(65536).cuda(), torch.from_numpy(R).cuda())
+    Ts = dl.Store(torch.arange(65536).cuda(), torch.from_numpy(T).cuda())
+    return lambda: dl.sim_join(Rs, Ts, 0.55, precision=prec, cta_pair=pair, tile_n=256, timing=True)
+
+
 def _case_dense_d256():
     """16,384 fresh queries x the first 1,048,576 rows of the serving store (d=256), eps at
     0.5% selectivity: a candidate-dense join (BF16, tile 256)."""
@@ -1001,6 +1015,8 @@ def _case_pruned_tracked():
 
 
 PROFILE_CASES = {"fp8_unit_d512_65536": _case_fp8_unit_d512, "dense_d256_16384x1m": _case_dense_d256,
+                 "pair_bf16_d512_65536": _case_pair_unit_d512,
+                 "single_bf16_d512_65536": lambda: _case_pair_unit_d512(pair=1),
                  "pruned_tracked_262k": _case_pruned_tracked,
                  "color_hist_1080p": _case_color_hist_1080p, "l1_hist_16384": _case_l1_16k}
 

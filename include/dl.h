@@ -290,6 +290,22 @@ int dl_debug_scores(const dl_store *R, const dl_store *S, int32_t precision, flo
  */
 int dl_debug_set_wait_budget(int64_t clocks);
 
+/*
+ * Diagnostics of the bounds-checked build (no counterpart in the paper). A
+ * library compiled with -DDL_CHECKED (paper_1812_07607_gb300.build with
+ * checked=True: libdlsimjoin_checked.so) guards computed shared- and global-
+ * memory indices of its hot kernels; a failed check skips the access (nothing
+ * traps) and records the first failure per translation unit as
+ * (site << 40) | (index & (2^40 - 1)). dl_debug_check_word stores the first
+ * recorded failure in *word (0: none) and clears the records; in the normal
+ * build it always stores 0. dl_debug_check_selftest records a failure of site 99
+ * with `index` on purpose (a check of a constant-false condition guarding no
+ * access) so a test can see the mechanism work; it returns DL_EUNSUPPORTED in
+ * the normal build.
+ */
+int dl_debug_check_word(uint64_t *word);
+int dl_debug_check_selftest(int64_t index);
+
 /* ---------------------------------------------------------------------------------
  * Batches: many epsilon-join and top-k requests against one resident store.
  * ------------------------------------------------------------------------------- */

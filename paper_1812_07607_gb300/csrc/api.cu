@@ -15,6 +15,7 @@
 #include <tuple>
 #include <vector>
 
+#include "checked.cuh"
 #include "kernels.h"
 
 namespace dl {
@@ -633,6 +634,20 @@ int sim_join_impl(const dl_store *R, const dl_store *S, int32_t metric, double e
 
 }  // namespace dl
 
+namespace dl {
+int check_read_join_tc(unsigned long long *out);
+int check_read_topk(unsigned long long *out);
+int check_read_recheck(unsigned long long *out);
+int check_read_batch(unsigned long long *out);
+}  // namespace dl
+
+#ifdef DL_CHECKED
+// Records a failed check on a constant-false condition: no memory access is guarded or made.
+__global__ void k_check_selftest(long long index) { DL_CHECK(false, 99, index); }
+#endif
+
+DL_CHECK_READER(api)
+
 extern "C" {
 
 int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps, const dl_join_opts *opts,
@@ -936,6 +951,40 @@ int dl_result_request_topk(dl_result *r, int32_t req, int32_t where, const int64
     if (ids) *ids = hi + o;
     if (dist2) *dist2 = hd + o;
     return DL_OK;
+}
+
+int dl_debug_check_word(uint64_t *word)
+{
+    clear_error();
+    if (!word) {
+        set_error("dl_debug_check_word: word is NULL");
+        return DL_EINVAL;
+    }
+    *word = 0;
+    int (*readers[])(unsigned long long *) = {check_read_api, check_read_join_tc, check_read_topk, check_read_recheck,
+                                              check_read_batch};
+    for (auto rd : readers) {
+        unsigned long long w = 0;
+        const int e = rd(&w);
+        if (e) return cuda_fail((cudaError_t)e, "dl_debug_check_word");
+        if (!*word) *word = w;
+    }
+    return DL_OK;
+}
+
+int dl_debug_check_selftest(int64_t index)
+{
+    clear_error();
+#ifdef DL_CHECKED
+    k_check_selftest<<<1, 1>>>((long long)index);
+    DL_CUDA_TRY(cudaGetLastError());
+    DL_CUDA_TRY(cudaDeviceSynchronize());
+    return DL_OK;
+#else
+    (void)index;
+    set_error("dl_debug_check_selftest: this library was built without DL_CHECKED");
+    return DL_EUNSUPPORTED;
+#endif
 }
 
 }  // extern "C"

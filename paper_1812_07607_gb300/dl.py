@@ -14,6 +14,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdlsimjoin.so")
+CHECKED_LIB_PATH = os.path.join(HERE, "libdlsimjoin_checked.so")   # the bounds-checked build (build(checked=True))
 
 # dl_status
 DL_OK, DL_EINVAL, DL_ENOMEM, DL_EOVERFLOW, DL_EAGAIN, DL_ETIMEOUT, DL_ECUDA, DL_ECANCELED, \
@@ -38,7 +39,7 @@ EXPORTS = [
     "dl_sim_join_noalloc", "dl_batch_join", "dl_result_request_pairs", "dl_result_request_topk",
     "dl_server_create", "dl_submit", "dl_poll", "dl_cancel", "dl_server_get_stats", "dl_server_destroy",
     "dl_debug_scores", "dl_store_normalize", "dl_color_hist", "dl_components", "dl_dedup", "dl_store_cluster",
-    "dl_debug_set_wait_budget",
+    "dl_debug_set_wait_budget", "dl_debug_check_word", "dl_debug_check_selftest",
 ]
 
 
@@ -142,6 +143,10 @@ def load(path: str | None = None):
     L.dl_debug_scores.restype = ctypes.c_int
     L.dl_debug_set_wait_budget.argtypes = [i64]
     L.dl_debug_set_wait_budget.restype = ctypes.c_int
+    L.dl_debug_check_word.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
+    L.dl_debug_check_word.restype = ctypes.c_int
+    L.dl_debug_check_selftest.argtypes = [i64]
+    L.dl_debug_check_selftest.restype = ctypes.c_int
     L.dl_last_error.restype = ctypes.c_char_p
     L.dl_version.restype = ctypes.c_char_p
     L.dl_kernel_launches.restype = i64
@@ -211,6 +216,7 @@ class Store:
             rc = L.dl_store_create(ctypes.byref(h), ids.ctypes.data, feats.ctypes.data, n, d, DL_MEM_HOST, st)
         _check(rc, "dl_store_create")
         self._h = h
+        self._lib = L   # the library that owns the store releases it
         self.n, self.d = int(n), int(d)
 
     @property
@@ -220,25 +226,27 @@ class Store:
     def normalized(self, stream=None) -> "Store":
         """dl_store_normalize: a new store of the unit-normalized rows (for metric="cosine")."""
         h = ctypes.c_void_p()
-        _check(load().dl_store_normalize(self._h, ctypes.byref(h), _stream_handle(stream)), "dl_store_normalize")
+        _check(self._lib.dl_store_normalize(self._h, ctypes.byref(h), _stream_handle(stream)), "dl_store_normalize")
         out = Store.__new__(Store)
         out._h = h
+        out._lib = self._lib
         out.n, out.d = self.n, self.d
         return out
 
     def clustered(self, n_clusters: int, iters: int = 4, stream=None) -> "Store":
         """dl_store_cluster: the same rows in a k-means-grouped order (for sim_join(prune=True))."""
         h = ctypes.c_void_p()
-        _check(load().dl_store_cluster(self._h, int(n_clusters), int(iters), ctypes.byref(h), _stream_handle(stream)),
-               "dl_store_cluster")
+        _check(self._lib.dl_store_cluster(self._h, int(n_clusters), int(iters), ctypes.byref(h),
+                                          _stream_handle(stream)), "dl_store_cluster")
         out = Store.__new__(Store)
         out._h = h
+        out._lib = self._lib
         out.n, out.d = self.n, self.d
         return out
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
-            load().dl_store_destroy(self._h)
+            (getattr(self, "_lib", None) or load()).dl_store_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -530,6 +538,13 @@ class Server:
 def set_wait_budget(clocks: int = 0):
     """dl_debug_set_wait_budget: SM-clock budget of the tensor-core kernels' bounded waits (0: default)."""
     _check(load().dl_debug_set_wait_budget(int(clocks)), "dl_debug_set_wait_budget")
+
+
+def check_word() -> int:
+    """dl_debug_check_word: the first failed bounds check of a checked build, (site << 40) | index; 0 = none."""
+    w = ctypes.c_uint64()
+    _check(load().dl_debug_check_word(ctypes.byref(w)), "dl_debug_check_word")
+    return int(w.value)
 
 
 def debug_scores(R: Store, S: Store, precision="bf16", stream=None):
