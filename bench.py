@@ -345,7 +345,7 @@ def batch_leg(dl, seed=SEED_BATCH, n_req=4096, reps=2):
     Qd = torch.from_numpy(Q).cuda()
     qd = torch.arange(off, dtype=torch.int64).cuda()
     times, stats, out_pairs = [], None, 0
-    warm = 4   # the tile autotuner's four trial calls (the first also sizes the candidate list)
+    warm = 4   # the tile autotuner's trial calls (3 candidates + 1; the first also sizes the candidate list)
     for i in range(warm + reps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -364,7 +364,7 @@ def batch_leg(dl, seed=SEED_BATCH, n_req=4096, reps=2):
             "requests_per_s": n_req / t, "query_rows": off, "pairs_evaluated": pairs, "pairs_out": out_pairs,
             "band_pairs": stats["band_pairs"], "fp64_pairs": stats["fp64_pairs"],
             "ms_eps_contraction": stats["ms_main"], "ms_eps_decide_scatter": stats["ms_recheck"],
-            "tile_n": stats["tile_n"], "cta_pair": stats["cta_pair"],
+            "tile_n": stats["tile_n"], "cta_pair": stats["cta_pair"], "epilogue_warps": stats["epilogue_warps"],
             "ms_device_total": stats["ms_total"],
             "config": "batch_store_2m: 2,097,152 x 128 store; 4,096 requests in one call, sizes lognormal(5,1.5) "
                       "in [1,8192]; 70% eps at selectivity U[0.05%,0.5%], 30% top-k k=10; device inputs"}
@@ -467,7 +467,7 @@ def precision_leg(dl, reps=2):
            "pairs_evaluated": n * n}
     for prec in ("bf16", "fp8"):
         ts, st = [], None
-        warm = 4 if prec == "bf16" else 3   # the tile autotuner's trial calls (3 candidates BF16, 2 FP8, + 1)
+        warm = 5 if prec == "bf16" else 4   # the tile autotuner's trial calls (4 candidates BF16, 3 FP8, + 1)
         for i in range(warm + reps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -503,7 +503,7 @@ def latency_leg(dl, reps=50):
     S = dl.Store(torch.from_numpy(wl.s_ids).cuda(), torch.from_numpy(wl.S).cuda())
     out = {"config": "rxs_histograms_2k: 2,000 x 2,000, d=64 Dirichlet(0.5) histograms, eps at 0.1% selectivity"}
     for prec in ("bf16", "fp32"):
-        for _ in range(5):
+        for _ in range(6):   # warm-up, including the tile autotuner's trial calls (4 candidates + 1)
             dl.sim_join(R, S, wl.eps, precision=prec).free()
         ts, n = [], 0
         for _ in range(reps):
@@ -662,7 +662,7 @@ def rows_leg(dl, sm_mhz=None, reps=5):
         dst.update(r.stats())
         r.free()
 
-    for _ in range(4):   # the tile autotuner's trial calls
+    for _ in range(5):   # the tile autotuner's trial calls (4 candidates + 1)
         dense_call()
     ms_dense = _event_ms(dense_call, 3)
     torch.cuda.synchronize()
@@ -789,7 +789,7 @@ def run_ours(args):
         res.free()
         return st
 
-    for _ in range(4):   # setup: the tile autotuner's trial calls for this shape class
+    for _ in range(5):   # setup: the tile autotuner's trial calls for this shape class (4 candidates + 1)
         one_step()
     for _ in range(args.warmup):
         one_step()

@@ -103,6 +103,10 @@ typedef struct dl_join_opts {
     int32_t cta_pair;       /* tensor-core epsilon-join: 0 autotuned (with tile_n 0), 1 one SM per
                                128-row tile, 2 a pair of SMs per 256-row tile (tcgen05 cta_group::2,
                                tile_n 256 only); the result is the same set either way */
+    int32_t epilogue_warps; /* tensor-core epsilon-join and top-k: 0 autotuned (with tile_n 0 and
+                               cta_pair 0), 8, or 16 (tile_n 256 on one SM: four warps per SM
+                               sub-partition, best when many pairs are candidates); the same result
+                               either way */
 } dl_join_opts;
 
 /* Fill `o` with defaults: AUTO precision, upper self mode, auto capacity, NULL stream. */
@@ -438,6 +442,7 @@ typedef struct dl_join_stats {
     int64_t tile_pairs_kept;    /* opts.prune: tile pairs that survived the ball test */
     int32_t cta_pair;           /* 2 when the tensor-core pass ran on SM pairs, else 1 (0 for SIMT paths) */
     int32_t grid_ctas;          /* CTAs of the (last) tensor-core launch: resident SMs it occupied */
+    int32_t epilogue_warps;     /* epilogue warps of the tensor-core pass (0 for SIMT paths) */
 } dl_join_stats;
 
 int dl_result_stats(const dl_result *r, dl_join_stats *st);

@@ -143,6 +143,7 @@ struct PassCfg {
     int prec;
     int BN;
     bool cg2 = false;       // tensor-core pass on SM pairs (256-row tiles)
+    bool wide = false;      // 16 epilogue warps
     double e2;              // squared-L2 threshold (metric 0), or the L1 / chi-square threshold eps
     int metric;             // 0 squared L2 (and cosine), 1 L1, 2 chi-square
     const int64_t *ids;     // ids written for both sides (self-join only; NULL: the store's ids)
@@ -253,13 +254,14 @@ static int run_pass(const PassCfg &c, PassOut *po)
                 L.tmB = tmB;
                 L.BN = c.BN;
                 L.cg2 = c.cg2;
+                L.wide = c.wide;
                 L.grid = c.cg2 ? 2 * std::min(n_units, sms / 2) : std::min(n_units, sms);
                 L.p.units = units;
                 L.p.n_units = n_units;
                 L.p.nR = (int)nR;
                 L.p.nS = (int)nS;
                 L.p.kc = fp8 ? R->dp8 / 128 : R->dp / 64;
-                tc_plan(c.BN, L.p.kc, &L.p.stages, &L.p.a_slots, fp8, c.cg2);
+                tc_plan(c.BN, L.p.kc, &L.p.stages, &L.p.a_slots, fp8, c.cg2, c.wide);
                 L.p.upper = c.self ? 1 : 0;
                 L.p.rowpar = rowpar;
                 L.p.beta = S->beta;
@@ -473,15 +475,22 @@ int sim_join_impl(const dl_store *R, const dl_store *S, int32_t metric, double e
         set_error("dl_sim_join: cta_pair must be 0, 1 or 2 (2: tile_n 0 or 256, no prune)");
         return DL_EINVAL;
     }
+    if ((o.epilogue_warps != 0 && o.epilogue_warps != 8 && o.epilogue_warps != 16) ||
+        (o.epilogue_warps == 16 && (o.tile_n == 128 || o.cta_pair == 2))) {
+        set_error("dl_sim_join: epilogue_warps must be 0, 8 or 16 (16: tile_n 0 or 256, one SM per tile)");
+        return DL_EINVAL;
+    }
     // tile configuration: given, or autotuned per shape class (tensor-core precisions, dense join)
     const bool tc = prec == DL_PREC_BF16 || prec == DL_PREC_FP8E4M3;
     const int tune_kind = (prec == DL_PREC_FP8E4M3) ? (self ? kTuneEpsSelf8 : kTuneEpsRxS8)
                                                     : (self ? kTuneEpsSelf : kTuneEpsRxS);
     bool tune_trial = false;
-    int code = (o.tile_n ? o.tile_n : 256) | (o.cta_pair == 2 ? kTunePair : 0);
-    if (tc && !o.prune && o.tile_n == 0 && o.cta_pair == 0) code = tune_pick(R->dp, tune_kind, R->n, Sx->n, &tune_trial);
+    int code = (o.tile_n ? o.tile_n : 256) | (o.cta_pair == 2 ? kTunePair : 0) | (o.epilogue_warps == 16 ? kTuneWide : 0);
+    if (tc && !o.prune && o.tile_n == 0 && o.cta_pair == 0 && o.epilogue_warps == 0)
+        code = tune_pick(R->dp, tune_kind, R->n, Sx->n, &tune_trial);
     const int BN = tune_bn(code);
     const bool cg2 = tc && tune_pair(code);
+    const bool wide = tc && tune_wide(code);
     if (prec == DL_PREC_FP8E4M3 && R->d > 1024) {
         set_error("dl_sim_join: FP8 path supports d <= 1024");
         return DL_EUNSUPPORTED;
@@ -500,6 +509,7 @@ int sim_join_impl(const dl_store *R, const dl_store *S, int32_t metric, double e
     c.prec = prec;
     c.BN = BN;
     c.cg2 = cg2;
+    c.wide = wide;
     c.e2 = e2;
     c.metric = hmetric;
     c.ids = emit_ids;
@@ -617,6 +627,7 @@ int sim_join_impl(const dl_store *R, const dl_store *S, int32_t metric, double e
     s.precision = prec;
     s.tile_n = (prec == DL_PREC_BF16 || prec == DL_PREC_FP8E4M3) ? BN : 0;
     s.cta_pair = (prec == DL_PREC_BF16 || prec == DL_PREC_FP8E4M3) ? (cg2 ? 2 : 1) : 0;
+    s.epilogue_warps = (prec == DL_PREC_BF16 || prec == DL_PREC_FP8E4M3) ? (wide ? 16 : 8) : 0;
     s.ms_main = po.ms_main;
     s.ms_recheck = po.ms_recheck;
     s.ms_total = po.ms_total;

@@ -356,9 +356,12 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
             return DL_EUNSUPPORTED;
         }
         bool tune_trial = false;
-        const int BN = o.tile_n ? o.tile_n : tune_bn(tune_pick(Qe->dp, kTuneBatch, ne, S->n, &tune_trial));
-        stats.tile_n = BN;   // the epsilon rows' tile width (the autotuner's choice once decided)
+        const int code = o.tile_n ? o.tile_n : tune_pick(Qe->dp, kTuneBatch, ne, S->n, &tune_trial);
+        const int BN = tune_bn(code);
+        const bool wide = tune_wide(code);
+        stats.tile_n = BN;   // the epsilon rows' configuration (the autotuner's choice once decided)
         stats.cta_pair = 1;
+        stats.epilogue_warps = wide ? 16 : 8;
         const int64_t mt = (ne + 127) / 128;
         cudaEvent_t tev[2] = {nullptr, nullptr};
         if (tune_trial)
@@ -416,7 +419,8 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
                 L.p.nR = (int)ne;
                 L.p.nS = (int)S->n;
                 L.p.kc = Qe->dp / 64;
-                tc_plan(BN, Qe->dp / 64, &L.p.stages, &L.p.a_slots);
+                tc_plan(BN, Qe->dp / 64, &L.p.stages, &L.p.a_slots, false, false, wide);
+                L.wide = wide;
                 L.p.upper = 0;
                 L.p.rowpar = rowpar;
                 L.p.beta = S->beta;
@@ -490,7 +494,7 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
             if (!rc && tune_trial && attempt == 0) {
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, tev[0], tev[1]);
-                tune_record(Qe->dp, kTuneBatch, ne, S->n, BN, ms, (double)ne * (double)S->n);
+                tune_record(Qe->dp, kTuneBatch, ne, S->n, code, ms, (double)ne * (double)S->n);
             }
             dev_free(ws, st);
             break;

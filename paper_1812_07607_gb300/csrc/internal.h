@@ -152,11 +152,14 @@ void dev_free(void *p, cudaStream_t st);
 
 int device_sm_count();
 
-// Autotuned tensor-core configuration: a tile width, plus kTunePair for SM-pair tiles.
+// Autotuned tensor-core configuration: a tile width, plus kTunePair for SM-pair tiles or
+// kTuneWide for the 16-warp epilogue.
 constexpr int kTunePair = 1 << 12;
+constexpr int kTuneWide = 1 << 13;
 enum TuneKind { kTuneEpsRxS = 0, kTuneEpsSelf = 1, kTuneTopk = 2, kTuneEpsRxS8 = 3, kTuneEpsSelf8 = 4, kTuneBatch = 5 };
 inline int tune_bn(int code) { return code & 0xfff; }
 inline bool tune_pair(int code) { return (code & kTunePair) != 0; }
+inline bool tune_wide(int code) { return (code & kTuneWide) != 0; }
 int tune_pick(int dp, int kind, int64_t nR, int64_t nS, bool *trial);
 void tune_record(int dp, int kind, int64_t nR, int64_t nS, int code, double kernel_ms, double pairs);
 int tune_trials(int kind);   // calls of a shape class before it is decided

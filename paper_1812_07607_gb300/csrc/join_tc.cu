@@ -83,6 +83,11 @@ struct TileIter {
 };
 
 constexpr int kStageCap = 128;   // candidate entries a warp buffers before flushing
+// Epilogue warps: 8 (each owning BN/2 columns of a tile, loaded 64 at a time), or -- the wide
+// epilogue of the epsilon-join on 256-column tiles -- 16 (four per SM sub-partition, 64 columns
+// each, loaded 32 at a time), which keeps up better when many chunks hold candidates.
+__host__ __device__ constexpr int tc_epi_warps(bool wide) { return wide ? 16 : 8; }
+__host__ __device__ constexpr int tc_threads(bool wide) { return 64 + 32 * tc_epi_warps(wide); }
 constexpr int kColSlots = 2;     // epilogue column-data slots: the current tile and the next
 
 // Copy a warp's buffered candidates to the global list (one atomic per flush).
@@ -111,8 +116,8 @@ __device__ __forceinline__ void flush_stage(const TcParams &p, uint2 *stg, uint3
 //    candidates' buffer positions come from a ballot prefix.
 //  * Many such rows: every lane classifies its own row's 32 columns into a bit mask, a
 //    warp prefix sum of the mask counts places each lane's candidates.
-template <bool FP8>
-__device__ __forceinline__ uint32_t slow_chunk(const TcParams &p, const uint32_t (&v)[64], int o, const float *bt,
+template <bool FP8, int N>
+__device__ __forceinline__ uint32_t slow_chunk(const TcParams &p, const uint32_t (&v)[N], int o, const float *bt,
                                                float sc, float tau_acc, float tau_rej, bool hit, int r, int c0,
                                                float *xch, uint2 *stg, uint32_t scnt)
 {
@@ -295,7 +300,8 @@ __device__ __forceinline__ float fmax3(float a, float b, float c)
     return d;
 }
 
-__device__ __forceinline__ float max_tree32(const uint32_t (&v)[64], int o)
+template <int N>
+__device__ __forceinline__ float max_tree32(const uint32_t (&v)[N], int o)
 {
     float m[11];
 #pragma unroll
@@ -315,8 +321,8 @@ __device__ __forceinline__ float max_tree32(const uint32_t (&v)[64], int o)
 // multicast to both CTAs. Each CTA's epilogue handles its own rows; the peer releases an
 // accumulator with a remote arrive on the leader's barrier. Half the B bytes per stage means
 // twice the stages in the same shared memory beside a resident R tile.
-template <int BN, bool TOPK, bool FP8, bool CG2>
-__global__ void __launch_bounds__(320, 1)
+template <int BN, bool TOPK, bool FP8, bool CG2, bool WIDE>
+__global__ void __launch_bounds__(tc_threads(WIDE), 1)
     tc_join_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcParams p)
 {
@@ -327,18 +333,20 @@ __global__ void __launch_bounds__(320, 1)
     constexpr int kChunkCols = FP8 ? 128 : 64;   // columns per 128-byte K chunk
     constexpr int kAcc = 512 / BN;              // TMEM accumulators: 2 of 256 or 4 of 128 columns
     constexpr uint32_t kTmemCols = 512;
-    constexpr int HC = BN / 2;               // columns of a tile each epilogue warp owns
+    static_assert(!WIDE || BN == 256, "the wide epilogue serves 256-column tiles");
+    constexpr int kEpi = tc_epi_warps(WIDE);   // epilogue warps
+    constexpr int HC = BN * 4 / kEpi;        // columns of a tile each epilogue warp owns (128 or 64)
     constexpr int kSubW = HC / 32;           // 32-column chunks per warp per tile
     const uint32_t a_bytes = (uint32_t)kc * 16384;
     uint8_t *sA = smem;                                    // a_slots x kc x [128 rows x 128 B]
     uint8_t *sB = smem + a_slots * a_bytes;                // stages x [BN rows x 128 B]
     // Column data of a tile (beta, chunk stats, FP8 chunk scales) is staged by the epilogue
     // warps themselves with cp.async, one tile ahead, in kColSlots = 2 slots.
-    float *s_beta = reinterpret_cast<float *>(sB + stages * kStageBytes);    // 8 warps x kColSlots x HC: beta
-    float4 *s_cst = reinterpret_cast<float4 *>(s_beta + 8 * kColSlots * HC); // 8 warps x kColSlots x kSubW chunk stats
-    uint2 *s_stage = reinterpret_cast<uint2 *>(s_cst + 8 * kColSlots * kSubW);   // 8 warps x kStageCap candidates
-    float *s_sx = reinterpret_cast<float *>(s_stage + 8 * kStageCap);        // FP8: 8 warps x kColSlots x kSubW scales
-    uint64_t *bars = reinterpret_cast<uint64_t *>(s_sx + (FP8 ? 8 * kColSlots * kSubW : 0));
+    float *s_beta = reinterpret_cast<float *>(sB + stages * kStageBytes);    // kEpi warps x kColSlots x HC: beta
+    float4 *s_cst = reinterpret_cast<float4 *>(s_beta + kEpi * kColSlots * HC); // kEpi x kColSlots x kSubW chunk stats
+    uint2 *s_stage = reinterpret_cast<uint2 *>(s_cst + kEpi * kColSlots * kSubW);   // kEpi x kStageCap candidates
+    float *s_sx = reinterpret_cast<float *>(s_stage + kEpi * kStageCap);     // FP8: kEpi x kColSlots x kSubW scales
+    uint64_t *bars = reinterpret_cast<uint64_t *>(s_sx + (FP8 ? kEpi * kColSlots * kSubW : 0));
     uint64_t *full = bars;                    // [8]
     uint64_t *empty = bars + 8;               // [8]
     uint64_t *a_full = bars + 16;             // [2]
@@ -350,7 +358,7 @@ __global__ void __launch_bounds__(320, 1)
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 30);
     uint64_t *pfull = bars + 32;              // CG2 leader: [8] the peer's half of the stage landed
     uint64_t *pa_full = bars + 40;            // CG2 leader: [2] the peer's rows of the R tile landed
-    float *s_xch = reinterpret_cast<float *>(bars + 48);   // [8 warps x 32] row exchange slots (16-byte aligned)
+    float *s_xch = reinterpret_cast<float *>(bars + 48);   // [kEpi warps x 32] row exchange slots (16-byte aligned)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -377,7 +385,7 @@ __global__ void __launch_bounds__(320, 1)
         }
         for (int s = 0; s < kAcc; ++s) {
             mbar_init(acc_full + s, 1);
-            mbar_init(acc_empty + s, CG2 ? 16 : 8);   // CG2 (leader): both CTAs' epilogue warps
+            mbar_init(acc_empty + s, CG2 ? 2 * kEpi : kEpi);   // CG2 (leader): both CTAs' epilogue warps
         }
         if constexpr (CG2) {
             for (int s = 0; s < 8; ++s) mbar_init(pfull + s, 1);
@@ -579,9 +587,9 @@ __global__ void __launch_bounds__(320, 1)
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        const int e = warp - 2;            // 0..7
+        const int e = warp - 2;            // 0 .. kEpi-1
         const int quad = warp & 3;         // TMEM lanes this warp may access: 32*quad .. +31
-        const int half = e >> 2;           // which half of the tile's columns
+        const int half = e >> 2;           // which HC-column part of the tile this warp owns
         const uint32_t lane_base = static_cast<uint32_t>(quad * 32) << 16;
         float *my_bt = s_beta + e * (kColSlots * HC);
         float *my_sx = s_sx + e * (kColSlots * kSubW);   // FP8 only
@@ -590,6 +598,7 @@ __global__ void __launch_bounds__(320, 1)
         float *my_xch = s_xch + e * 32;
         uint32_t scnt = 0;
         constexpr int kPer = HC / 32;      // beta values a lane stages per tile (4 or 2)
+        static_assert(kPer == 4 || kPer == 2, "an epilogue warp owns 128 or 64 columns");
         TileIter cur, nxt;
         cur.start(p, ufirst, ustride);
         nxt = cur;
@@ -630,7 +639,7 @@ __global__ void __launch_bounds__(320, 1)
                     rp = p.rowpar[r];
                 if constexpr (FP8) sq = (r < p.nR) ? p.sc_r[r] : 1.0f;
                 if constexpr (TOPK) {   // a unit owns its (row tile, split): start the slots fresh
-                    sidx = (size_t)r * p.tk_slots + (size_t)cur.un.w * 2 + half;
+                    sidx = (size_t)r * p.tk_slots + (size_t)cur.un.w * (kEpi / 4) + half;   // (split, column part)
                     theta = __int_as_float(0xff800000);
                     tcnt = 0;
                     if (r < p.nR) {
@@ -707,6 +716,82 @@ __global__ void __launch_bounds__(320, 1)
                 }
             };
 
+            // One 32-column chunk ci of this warp's HC columns, values v[o .. o+31] (epsilon-join).
+            auto eps_chunk = [&](auto &v, int o, int ci) {
+                const float sc = FP8 ? sq * sxs[ci] : 1.0f;
+                const float4 cs = cst[ci];
+                const float eh = __fmaf_ru(rp.z, cs.x, __fmaf_ru(rp.w, cs.y, cs.z));
+                if (p.dump_h) {   // diagnostics: every pair's h and bound, at caller row order
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int c = colw + ci * 32 + j;
+                        if (r < p.nR && c < p.nS) {
+                            const float h = __fmaf_rn(__uint_as_float(v[o + j]), sc, -beta[ci * 32 + j]);
+                            const size_t oi = (size_t)p.orig_r[r] * p.nS + p.orig_s[c];
+                            p.dump_h[oi] = h;
+                            p.dump_e[oi] = eh;
+                        }
+                    }
+                }
+                // whole-chunk reject (see process64)
+                const float mx = max_tree32(v, o);
+                const bool hit = __fmaf_ru(mx, sc, -cs.w) >= __fsub_rd(rp.y, eh);
+                if (__any_sync(0xffffffffu, hit))
+                    scnt = slow_chunk<FP8>(p, v, o, beta + ci * 32, sc, __fadd_ru(rp.x, eh), __fsub_rd(rp.y, eh), hit,
+                                           r, colw + ci * 32, my_xch, my_stg, scnt);
+            };
+            auto release_acc = [&]() {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) {   // TMEM buffer free; the rest is in registers
+                    if constexpr (CG2) {
+                        if (leader)
+                            mbar_arrive(acc_empty + b);
+                        else
+                            mbar_arrive_remote(mapa_shared(acc_empty + b, 0u));
+                    } else {
+                        mbar_arrive(acc_empty + b);
+                    }
+                }
+            };
+            // Top-k, one 32-column chunk ci (BF16 only: scale 1): the columns whose upper bound
+            // reaches the best threshold go to the slot's list, their lower bounds to its heap.
+            auto topk_chunk = [&](auto &v, int o, int ci) {
+                const float4 cs = cst[ci];
+                const float ehs = __fadd_ru(__fmaf_ru(rp.z, cs.x, __fmaf_ru(rp.w, cs.y, cs.z)), rp.x);
+                const float mx = max_tree32(v, o);
+                if (__fsub_ru(mx, cs.w) >= __fsub_rd(fmaxf(theta, theta_row), ehs) && r < p.nR) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int c = colw + ci * 32 + j;
+                        const float h = __uint_as_float(v[o + j]) - beta[ci * 32 + j];
+                        const float U = __fadd_ru(h, ehs);
+                        if (c < p.nS && U >= fmaxf(theta, theta_row)) {
+                            const float2 stt = topk_insert(p, sidx, r, c, U, __fsub_rd(h, ehs), theta, tcnt, theta_row);
+                            theta = stt.x;
+                            tcnt = __float_as_int(stt.y);
+                        }
+                    }
+                }
+            };
+            if constexpr (kEpi == 16) {
+                // 64 columns per warp, 32 at a time: the three other epilogue warps of this SM
+                // sub-partition hide each load's latency
+                uint32_t vq[32];
+                tmem_ld_32x32b_x32(tbase, vq);
+                tmem_ld_wait_regs(vq);
+                if constexpr (TOPK)
+                    topk_chunk(vq, 0, 0);
+                else
+                    eps_chunk(vq, 0, 0);
+                tmem_ld_32x32b_x32(tbase + 32, vq);
+                tmem_ld_wait_regs(vq);
+                release_acc();
+                if constexpr (TOPK)
+                    topk_chunk(vq, 0, 1);
+                else
+                    eps_chunk(vq, 0, 1);
+            } else {
             // One 64-column load at a time: the other epilogue warp on this SM
             // sub-partition hides the TMEM load latency.
             uint32_t va[64];
@@ -720,19 +805,9 @@ __global__ void __launch_bounds__(320, 1)
                 tmem_ld_32x32b_x64(tbase, va);
                 tmem_ld_wait_regs(va);
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) {   // TMEM buffer free; the rest is in registers
-                if constexpr (CG2) {
-                    if (leader)
-                        mbar_arrive(acc_empty + b);
-                    else
-                        mbar_arrive_remote(mapa_shared(acc_empty + b, 0u));
-                } else {
-                    mbar_arrive(acc_empty + b);
-                }
-            }
+            release_acc();
             process64(va, HC == 128 ? 1 : 0);
+            }
             if constexpr (TOPK) {
                 if (cur.n + 1 == cur.un.z && r < p.nR) {   // last tile of the unit: publish the slot
                     p.tk_theta[sidx] = theta;
@@ -762,30 +837,32 @@ __global__ void __launch_bounds__(320, 1)
     }
 }
 
-static size_t tc_extra_bytes(int BN, bool fp8)
+static size_t tc_extra_bytes(int BN, bool fp8, bool wide)
 {
-    // per epilogue warp: kColSlots x BN/2 floats of beta, kColSlots x BN/64 chunk stats, the candidate
-    // buffer and (FP8) kColSlots x BN/64 chunk scales; then 48 barrier / flag words and 8 x 32 exchange floats
-    return (size_t)8 * (kColSlots * (BN / 2) * 4 + kColSlots * (BN / 64) * 16 + kStageCap * 8 +
-                        (fp8 ? kColSlots * (BN / 64) * 4 : 0)) +
-           48 * 8 + 8 * 32 * 4;
+    // per epilogue warp (owning HC columns): kColSlots x HC floats of beta, kColSlots x HC/32 chunk
+    // stats, the candidate buffer and (FP8) kColSlots x HC/32 chunk scales; then 48 barrier / flag
+    // words and 32 exchange floats per epilogue warp
+    const size_t epi = (size_t)tc_epi_warps(wide), hc = (size_t)BN * 4 / epi;
+    return epi * (kColSlots * hc * 4 + kColSlots * (hc / 32) * 16 + kStageCap * 8 + (fp8 ? kColSlots * (hc / 32) * 4 : 0)) +
+           48 * 8 + epi * 32 * 4;
 }
 
 // One S stage per CTA: a 128-byte K chunk of the CTA's rows of an S tile (all BN rows, or
 // BN/2 for a CTA pair).
 static size_t tc_stage_bytes(int BN, bool cg2) { return (size_t)(cg2 ? BN / 2 : BN) * 128; }
 
-static size_t tc_smem_bytes(int BN, int kc, int stages, int a_slots, bool fp8, bool cg2)
+static size_t tc_smem_bytes(int BN, int kc, int stages, int a_slots, bool fp8, bool cg2, bool wide)
 {
-    return 1024 + (size_t)a_slots * kc * 16384 + (size_t)stages * tc_stage_bytes(BN, cg2) + tc_extra_bytes(BN, fp8);
+    return 1024 + (size_t)a_slots * kc * 16384 + (size_t)stages * tc_stage_bytes(BN, cg2) +
+           tc_extra_bytes(BN, fp8, wide);
 }
 
 // Shared-memory plan: two A slots when that still leaves at least three S stages.
-void tc_plan(int BN, int kc, int *stages, int *a_slots, bool fp8, bool cg2)
+void tc_plan(int BN, int kc, int *stages, int *a_slots, bool fp8, bool cg2, bool wide)
 {
     const long cap = 232448;
     for (int slots = 2; slots >= 1; --slots) {
-        const long avail = cap - 1024 - (long)tc_extra_bytes(BN, fp8) - (long)slots * kc * 16384;
+        const long avail = cap - 1024 - (long)tc_extra_bytes(BN, fp8, wide) - (long)slots * kc * 16384;
         long s = avail / (long)tc_stage_bytes(BN, cg2);
         if (s > 8) s = 8;
         if (s >= 3 || slots == 1) {
@@ -804,17 +881,17 @@ long long tc_wait_budget()
     return b > 0 ? b : kWaitBudgetClocks;
 }
 
-template <int BN, bool TOPK, bool FP8, bool CG2>
+template <int BN, bool TOPK, bool FP8, bool CG2, bool WIDE = false>
 static int launch_one(const TcLaunch &L, size_t smem, cudaStream_t st, int *grid_out)
 {
-    auto kern = tc_join_kernel<BN, TOPK, FP8, CG2>;
+    auto kern = tc_join_kernel<BN, TOPK, FP8, CG2, WIDE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_join_kernel)");
     TcParams p = L.p;
     p.wait_budget = tc_wait_budget();
     if constexpr (CG2) {
         cudaLaunchConfig_t cfg = {};
-        cfg.blockDim = dim3(320);
+        cfg.blockDim = dim3(tc_threads(WIDE));
         cfg.dynamicSmemBytes = smem;
         cfg.stream = st;
         cudaLaunchAttribute at[1];
@@ -839,7 +916,7 @@ static int launch_one(const TcLaunch &L, size_t smem, cudaStream_t st, int *grid
         if (e != cudaSuccess) return cuda_fail(e, "tc_join_kernel (CTA pairs) launch");
         if (grid_out) *grid_out = (int)cfg.gridDim.x;
     } else {
-        kern<<<L.grid, 320, smem, st>>>(*L.tmA, *L.tmB, p);
+        kern<<<L.grid, tc_threads(WIDE), smem, st>>>(*L.tmA, *L.tmB, p);
         if (grid_out) *grid_out = L.grid;
     }
     return DL_OK;
@@ -851,11 +928,11 @@ int launch_tc_join(const TcLaunch &L, cudaStream_t st, bool topk, bool fp8, int 
         set_error("top-k runs on the BF16 path only");
         return DL_EUNSUPPORTED;
     }
-    if (L.cg2 && (topk || L.BN != 256)) {
-        set_error("tensor-core join: CTA pairs serve the 256-column epsilon-join only");
+    if ((L.cg2 && (topk || L.BN != 256 || L.wide)) || (L.wide && L.BN != 256)) {
+        set_error("tensor-core join: CTA pairs serve the 256-column epsilon-join, the wide epilogue 256-column tiles");
         return DL_EUNSUPPORTED;
     }
-    const size_t smem = tc_smem_bytes(L.BN, L.p.kc, L.p.stages, L.p.a_slots, fp8, L.cg2);
+    const size_t smem = tc_smem_bytes(L.BN, L.p.kc, L.p.stages, L.p.a_slots, fp8, L.cg2, L.wide);
     if (L.p.stages < 2 || smem > 232448) {
         set_error("tensor-core join: no shared-memory plan for d=%d, tile %d", L.p.kc * 64, L.BN);
         return DL_EUNSUPPORTED;
@@ -863,6 +940,10 @@ int launch_tc_join(const TcLaunch &L, cudaStream_t st, bool topk, bool fp8, int 
     int rc;
     if (L.cg2)
         rc = fp8 ? launch_one<256, false, true, true>(L, smem, st, grid_out) : launch_one<256, false, false, true>(L, smem, st, grid_out);
+    else if (L.wide)
+        rc = topk ? launch_one<256, true, false, false, true>(L, smem, st, grid_out)
+                  : (fp8 ? launch_one<256, false, true, false, true>(L, smem, st, grid_out)
+                         : launch_one<256, false, false, false, true>(L, smem, st, grid_out));
     else if (L.BN == 256)
         rc = topk ? launch_one<256, true, false, false>(L, smem, st, grid_out)
                   : (fp8 ? launch_one<256, false, true, false>(L, smem, st, grid_out)

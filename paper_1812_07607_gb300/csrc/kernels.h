@@ -52,9 +52,11 @@ struct TcLaunch {
     int grid;           // CTAs (with cg2: twice the CTA pairs wanted; clamped to the resident pairs)
     bool cg2 = false;   // CTA pairs (tcgen05 cta_group::2) on 256-row tiles: units count 256-row tiles,
                         // tmB's box is BN/2 rows, rowpar covers the rows rounded up to 256
+    bool wide = false;  // 16 epilogue warps (256-column epsilon-join); plan with tc_plan(..., wide)
 };
 
-void tc_plan(int BN, int kc, int *stages, int *a_slots, bool fp8 = false, bool cg2 = false);
+// Shared-memory plan of the tensor-core kernel (wide: the 16-warp epilogue's layout).
+void tc_plan(int BN, int kc, int *stages, int *a_slots, bool fp8 = false, bool cg2 = false, bool wide = false);
 // Clock budget of the tensor-core kernels' abortable waits: the default (about 1 s),
 // unless dl_debug_set_wait_budget set another.
 long long tc_wait_budget();

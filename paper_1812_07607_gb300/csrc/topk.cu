@@ -412,13 +412,21 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
     }
     const bool use_tc = (o.precision != DL_PREC_FP32) && Q->dp <= 512;
     bool tune_trial = false;
-    const int BN = o.tile_n ? o.tile_n : (use_tc ? tune_bn(tune_pick(Q->dp, kTuneTopk, nQ, nS, &tune_trial)) : 256);
+    if ((o.epilogue_warps != 0 && o.epilogue_warps != 8 && o.epilogue_warps != 16) ||
+        (o.epilogue_warps == 16 && o.tile_n == 128)) {
+        set_error("top-k: epilogue_warps must be 0, 8 or 16 (16: tile_n 0 or 256)");
+        return DL_EINVAL;
+    }
+    int code = (o.tile_n ? o.tile_n : 256) | (o.epilogue_warps == 16 ? kTuneWide : 0);
+    if (use_tc && o.tile_n == 0 && o.epilogue_warps == 0) code = tune_pick(Q->dp, kTuneTopk, nQ, nS, &tune_trial);
+    const int BN = tune_bn(code);
+    const bool wide = use_tc && tune_wide(code);   // 16 epilogue warps: slots per (row, split, quarter)
     const int sms = device_sm_count();
     const int64_t mt = (nQ + 127) / 128, nt = (nS + BN - 1) / BN;
     int splits = 1;
     if (mt > 0) splits = (int)std::min<int64_t>(std::max<int64_t>(1, (2 * sms + mt - 1) / mt), std::min<int64_t>(nt, 16));
     if (splits < 1) splits = 1;
-    const int slots = 2 * splits;
+    const int slots = (wide ? 4 : 2) * splits;
     const int cap = std::max(64, (4 * k + 31) / 32 * 32);
     const int64_t rows = mt * 128;
 
@@ -517,7 +525,8 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
                 L.p.nR = (int)nQ;
                 L.p.nS = (int)nS;
                 L.p.kc = Q->dp / 64;
-                tc_plan(BN, Q->dp / 64, &L.p.stages, &L.p.a_slots);
+                tc_plan(BN, Q->dp / 64, &L.p.stages, &L.p.a_slots, false, false, wide);
+                L.wide = wide;
                 L.p.upper = 0;
                 L.p.rowpar = rowpar;
                 L.p.beta = S->beta;
@@ -649,6 +658,7 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
         s.fp64_pairs = (int64_t)h2[1];
         s.precision = use_tc ? DL_PREC_BF16 : DL_PREC_FP32;
         s.tile_n = use_tc ? BN : 0;
+        s.epilogue_warps = use_tc ? (wide ? 16 : 8) : 0;
         s.kernels_launched = launches;
         if (timing) {
             cudaEventElapsedTime(&s.ms_main, ev[0], ev[1]);
@@ -659,7 +669,7 @@ int topk_core(const dl_store *Q, const dl_store *S, int k, const int *row_k, con
     if (tune_trial && flagged == 0) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev[0], ev[1]);
-        tune_record(Q->dp, kTuneTopk, nQ, nS, BN, ms, (double)nQ * (double)nS);
+        tune_record(Q->dp, kTuneTopk, nQ, nS, code, ms, (double)nQ * (double)nS);
     }
     return done(DL_OK);
 }

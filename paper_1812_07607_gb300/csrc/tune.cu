@@ -1,7 +1,8 @@
 // tune.cu -- on-line autotuner for the tensor-core join's tile configuration.
 //
 // A configuration is a code: the tile width (128 or 256 columns) plus kTunePair when the tile
-// runs on a pair of SMs (tcgen05 cta_group::2, 256-row tiles). A tuning key is a shape class:
+// runs on a pair of SMs (tcgen05 cta_group::2, 256-row tiles) or kTuneWide for the 16-warp
+// epilogue (which wins when many chunks hold candidates). A tuning key is a shape class:
 // (device SMs, padded d, join kind, log2 |R|, log2 |S|). Each kind has its own candidate list;
 // the first calls of a class run every candidate once, then the first candidate again (its
 // first run is the class's cold call), with CUDA-event timing of the tensor-core kernel. A
@@ -42,12 +43,14 @@ std::vector<int> candidates(int kind)
     switch (kind) {
     case kTuneEpsRxS:
     case kTuneEpsSelf:
-        return {256, 128, 256 | kTunePair};
+        return {256, 128, 256 | kTuneWide, 256 | kTunePair};
     case kTuneEpsRxS8:
     case kTuneEpsSelf8:
-        return {256, 256 | kTunePair};
-    default:   // top-k and the batched epsilon rows: single-SM tiles
-        return {256, 128};
+        return {256, 256 | kTuneWide, 256 | kTunePair};
+    case kTuneBatch:
+        return {256, 128, 256 | kTuneWide};
+    default:   // top-k: single-SM tiles
+        return {256, 128, 256 | kTuneWide};
     }
 }
 

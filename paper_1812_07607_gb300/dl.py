@@ -53,7 +53,7 @@ class dl_join_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("self_mode", ctypes.c_int32),
                 ("out_capacity", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
                 ("tile_n", ctypes.c_int32), ("timing", ctypes.c_int32), ("prune", ctypes.c_int32),
-                ("cta_pair", ctypes.c_int32)]
+                ("cta_pair", ctypes.c_int32), ("epilogue_warps", ctypes.c_int32)]
 
 
 class dl_join_stats(ctypes.Structure):
@@ -63,7 +63,7 @@ class dl_join_stats(ctypes.Structure):
                 ("ms_main", ctypes.c_float), ("ms_recheck", ctypes.c_float), ("ms_total", ctypes.c_float),
                 ("kernels_launched", ctypes.c_int32), ("tile_pairs", ctypes.c_int64),
                 ("tile_pairs_kept", ctypes.c_int64), ("cta_pair", ctypes.c_int32),
-                ("grid_ctas", ctypes.c_int32)]
+                ("grid_ctas", ctypes.c_int32), ("epilogue_warps", ctypes.c_int32)]
 
 
 class dl_request(ctypes.Structure):
@@ -330,7 +330,7 @@ class Result:
 
 
 def make_opts(precision="auto", self_mode="upper", out_capacity=0, stream=None, tile_n=0, timing=False,
-              prune=False, cta_pair=0):
+              prune=False, cta_pair=0, epilogue_warps=0):
     o = dl_join_opts()
     load().dl_join_opts_default(ctypes.byref(o))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -341,6 +341,7 @@ def make_opts(precision="auto", self_mode="upper", out_capacity=0, stream=None, 
     o.timing = 1 if timing else 0
     o.prune = 1 if prune else 0
     o.cta_pair = int(cta_pair)
+    o.epilogue_warps = int(epilogue_warps)
     return o
 
 
@@ -398,11 +399,11 @@ def dedup(X: Store, eps: float, labels=None, target: int = 0, plan="all", metric
 
 def sim_join(R: Store, S: Store | None, eps: float, precision="auto", self_mode="upper", out_capacity=0,
              stream=None, tile_n=0, timing=False, allow_overflow=False, metric="l2", prune=False,
-             cta_pair=0) -> Result:
+             cta_pair=0, epilogue_warps=0) -> Result:
     """dl_sim_join: every pair with canonical squared L2 distance <= eps^2; with
     metric="cosine" (stores from Store.normalized()) every pair with cosine >= eps; with
     metric="l1" / "chi2" every pair whose histogram distance is <= eps."""
-    o = make_opts(precision, self_mode, out_capacity, stream, tile_n, timing, prune, cta_pair)
+    o = make_opts(precision, self_mode, out_capacity, stream, tile_n, timing, prune, cta_pair, epilogue_warps)
     h = ctypes.c_void_p()
     rc = load().dl_sim_join(R.handle, None if S is None else S.handle, METRICS[metric], float(eps),
                             ctypes.byref(o), ctypes.byref(h))
@@ -414,9 +415,10 @@ def sim_join(R: Store, S: Store | None, eps: float, precision="auto", self_mode=
     return Result(h)
 
 
-def topk_join(Q: Store, S: Store, k: int, precision="auto", stream=None, timing=False, metric="l2") -> Result:
+def topk_join(Q: Store, S: Store, k: int, precision="auto", stream=None, timing=False, metric="l2", tile_n=0,
+              epilogue_warps=0) -> Result:
     """dl_topk_join: the k nearest store rows of every query row, by (canonical D, row)."""
-    o = make_opts(precision, "upper", 0, stream, 0, timing)
+    o = make_opts(precision, "upper", 0, stream, tile_n, timing, epilogue_warps=epilogue_warps)
     h = ctypes.c_void_p()
     rc = load().dl_topk_join(Q.handle, S.handle, METRICS[metric], int(k), ctypes.byref(o), ctypes.byref(h))
     _check(rc, "dl_topk_join")

@@ -250,9 +250,10 @@ def test_self_clustered_262k_full_size_sampled(dl, orc):
 
 def test_autotuner_tries_every_configuration_and_persists(tmp_path):
     """Tile autotuner: the first calls of a shape class try every candidate configuration once
-    -- BF16: 256-column tiles on one SM, 128-column tiles, 256-row tiles on an SM pair; FP8: one
-    SM or an SM pair -- then the first candidate again (its first run was the cold call); from
-    then on the fastest sticks, and a new process starts from the DL_TUNE_CACHE file."""
+    -- BF16: 256-column tiles on one SM, 128-column tiles, 256-column tiles with the 16-warp
+    epilogue, 256-row tiles on an SM pair; FP8: the same without 128-column tiles -- then the
+    first candidate again (its first run was the cold call); from then on the fastest sticks,
+    and a new process starts from the DL_TUNE_CACHE file."""
     import os
     import subprocess
     import sys
@@ -265,12 +266,12 @@ wl = W.rxs_histograms_2k()
 R = dl.Store(torch.from_numpy(wl.r_ids).cuda(), torch.from_numpy(wl.R).cuda())
 S = dl.Store(torch.from_numpy(wl.s_ids).cuda(), torch.from_numpy(wl.S).cuda())
 cfg = {}
-for prec, calls in (("bf16", 6), ("fp8", 5)):
+for prec, calls in (("bf16", 7), ("fp8", 6)):
     cfg[prec] = []
     for _ in range(calls):
         r = dl.sim_join(R, S, wl.eps, precision=prec)
         st = r.stats()
-        cfg[prec].append((st["tile_n"], st["cta_pair"]))
+        cfg[prec].append((st["tile_n"], st["cta_pair"], st["epilogue_warps"]))
         r.free()
 print(cfg)
 '''
@@ -280,15 +281,15 @@ print(cfg)
     assert out.returncode == 0, out.stderr
     cfg = eval(out.stdout.strip().splitlines()[-1])
     bf, f8 = cfg["bf16"], cfg["fp8"]
-    assert bf[:4] == [(256, 1), (128, 1), (256, 2), (256, 1)], bf
-    assert bf[4] == bf[5] and bf[4] in bf[:3], bf
-    assert f8[:3] == [(256, 1), (256, 2), (256, 1)], f8
-    assert f8[3] == f8[4] and f8[3] in f8[:2], f8
-    code_of = lambda c: c[0] | (4096 if c[1] == 2 else 0)
+    assert bf[:5] == [(256, 1, 8), (128, 1, 8), (256, 1, 16), (256, 2, 8), (256, 1, 8)], bf
+    assert bf[5] == bf[6] and bf[5] in bf[:4], bf
+    assert f8[:4] == [(256, 1, 8), (256, 1, 16), (256, 2, 8), (256, 1, 8)], f8
+    assert f8[4] == f8[5] and f8[4] in f8[:3], f8
+    code_of = lambda c: c[0] | (4096 if c[1] == 2 else 0) | (8192 if c[2] == 16 else 0)
     lines = cache.read_text().split()
-    assert len(lines) == 4 and sorted(int(v) for v in lines[1::2]) == sorted([code_of(bf[4]), code_of(f8[3])])
+    assert len(lines) == 4 and sorted(int(v) for v in lines[1::2]) == sorted([code_of(bf[5]), code_of(f8[4])])
     # a new process starts from the cache
     out = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stderr
     again = eval(out.stdout.strip().splitlines()[-1])
-    assert again["bf16"] == [bf[4]] * 6 and again["fp8"] == [f8[3]] * 5
+    assert again["bf16"] == [bf[5]] * 7 and again["fp8"] == [f8[4]] * 6

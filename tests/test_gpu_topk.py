@@ -34,11 +34,11 @@ def _store(dl, ids, X):
                     torch.from_numpy(np.ascontiguousarray(X)).cuda())
 
 
-def check_topk(dl, orc, Q, S, k, precision="auto"):
+def check_topk(dl, orc, Q, S, k, precision="auto", epilogue_warps=0):
     qid = np.arange(Q.shape[0], dtype=np.int64) * 5 + 3
     sid = np.arange(S.shape[0], dtype=np.int64) * 7 + 1_000_000
     Qs, Ss = _store(dl, qid, Q), _store(dl, sid, S)
-    res = dl.topk_join(Qs, Ss, k, precision=precision)
+    res = dl.topk_join(Qs, Ss, k, precision=precision, epilogue_warps=epilogue_warps)
     ids, d2 = res.topk_host()
     st = res.stats()
     res.free()
@@ -129,3 +129,15 @@ def test_topk_large_store_with_ties_exact(dl, orc, k):
     Q = np.concatenate([Q, S[dup_src[:40]]])
     st = check_topk(dl, orc, Q, S, k)
     assert st["band_pairs"] < Q.shape[0]   # rows re-solved by the exact scan stay rare
+
+
+@pytest.mark.parametrize("k", [1, 10, 100])
+def test_topk_wide_epilogue_exact(dl, orc, k):
+    """The 16-warp epilogue (slots per row, split and quarter of a tile): ids and distances equal
+    the oracle's, with exact ties at the k-th distance and ragged store sizes."""
+    g = W.rng(8900 + k)
+    S, _ = W.clustered_histograms(g, 20_011, 64, 400, 0.01)
+    S[g.choice(20_011, 300, replace=False)] = S[g.choice(20_011, 300, replace=False)]
+    Q, _ = W.clustered_histograms(g, 333, 64, 400, 0.012)
+    st = check_topk(dl, orc, Q, S, k, precision="bf16", epilogue_warps=16)
+    assert st["epilogue_warps"] == 16
