@@ -967,6 +967,59 @@ def _case_pair_unit_d512(pair: int = 2, prec: str = "bf16"):
     return lambda: dl.sim_join(Rs, Ts, 0.55, precision=prec, cta_pair=pair, tile_n=256, timing=True)
 
 
+def _case_serve_batch_258():
+    """One serving-sized batch: 258 requests of the serving mix (70% eps at selectivity
+    U[0.05%, 0.5%], 30% top-k with k in {1, 10, 100}, sizes lognormal(4, 1.5) in [1, 4096]) in
+    one dl_batch_join against the 4,194,304 x 256 serving store, queries on the device."""
+    import torch
+    from paper_1812_07607_gb300 import dl, workloads as W
+    dl.load()
+    sw = W.serve_store_4m()
+    g = W.rng(SEED_SERVE + 77)
+    reqs = W.request_mix(g, 258, 4.0, 1.5, 4096, topk_frac=0.3, ks=(1, 10, 100), sel_lo=5e-4, sel_hi=5e-3)
+    table = sw.eps_table()
+    off = 0
+    for r in reqs:
+        r["q_begin"] = off
+        off += r["nq"]
+        if r["kind"] == "eps":
+            r["eps"] = W.eps_for_selectivity(table, r["selectivity"])
+    Q = sw.queries(off, SEED_SERVE + 78)
+    store = dl.Store(torch.from_numpy(sw.ids).cuda(), torch.from_numpy(sw.X).cuda())
+    Qd = torch.from_numpy(Q).cuda()
+    qd = torch.arange(off, dtype=torch.int64).cuda()
+    return lambda: dl.batch_join(store, qd, Qd, reqs, timing=True)
+
+
+def _case_batch_decide_1m_d256():
+    """64 epsilon requests of 256 fresh queries each at 0.3% selectivity in one dl_batch_join
+    against a 1,048,576-row d=256 store drawn like the serving store (32 rows per centre): a
+    band-heavy decision pass (k_batch_decide) at a size a full ncu capture handles."""
+    import torch
+    from paper_1812_07607_gb300 import dl, workloads as W
+    dl.load()
+    X, _ = W.clustered_histograms(W.rng(SEED_SERVE + 90), 1 << 20, 256, 32768, 0.01)
+    Q = W.clustered_queries(64 * 256, SEED_SERVE + 91, SEED_SERVE + 90, 256, 32768, 0.01)
+    eps = W.eps_for_selectivity(W.eps_table()["serve_store_4m:selectivity_eps"], 3e-3)
+    reqs = [{"kind": "eps", "q_begin": 256 * i, "nq": 256, "eps": eps} for i in range(64)]
+    store = dl.Store(torch.arange(X.shape[0]).cuda(), torch.from_numpy(X).cuda())
+    Qd = torch.from_numpy(Q).cuda()
+    qd = torch.arange(Q.shape[0], dtype=torch.int64).cuda()
+    return lambda: dl.batch_join(store, qd, Qd, reqs, timing=True)
+
+
+def _case_topk_1m_d256(k: int = 100, warps: int = 8):
+    """4,096 fresh queries x a 1,048,576-row d=256 clustered store, top-k, the given epilogue."""
+    import torch
+    from paper_1812_07607_gb300 import dl, workloads as W
+    dl.load()
+    X, _ = W.clustered_histograms(W.rng(77), 1 << 20, 256, 32768, 0.01)
+    Q = W.clustered_queries(4096, 78, 77, 256, 32768, 0.01)
+    S = dl.Store(torch.arange(X.shape[0]).cuda(), torch.from_numpy(X).cuda())
+    Qs = dl.Store(torch.arange(Q.shape[0]).cuda(), torch.from_numpy(Q).cuda())
+    return lambda: dl.topk_join(Qs, S, k, precision="bf16", tile_n=256, epilogue_warps=warps, timing=True)
+
+
 def _case_dense_d256():
     """16,384 fresh queries x the first 1,048,576 rows of the serving store (d=256), eps at
     0.5% selectivity: a candidate-dense join (BF16, tile 256)."""
@@ -1016,6 +1069,12 @@ def _case_pruned_tracked():
 
 PROFILE_CASES = {"fp8_unit_d512_65536": _case_fp8_unit_d512, "dense_d256_16384x1m": _case_dense_d256,
                  "pair_bf16_d512_65536": _case_pair_unit_d512,
+                 "serve_batch_258": _case_serve_batch_258,
+                 "batch_decide_1m_d256": _case_batch_decide_1m_d256,
+                 "topk100_1m_d256_w8": lambda: _case_topk_1m_d256(100, 8),
+                 "topk100_1m_d256_w16": lambda: _case_topk_1m_d256(100, 16),
+                 "topk10_1m_d256_w8": lambda: _case_topk_1m_d256(10, 8),
+                 "topk10_1m_d256_w16": lambda: _case_topk_1m_d256(10, 16),
                  "single_bf16_d512_65536": lambda: _case_pair_unit_d512(pair=1),
                  "pruned_tracked_262k": _case_pruned_tracked,
                  "color_hist_1080p": _case_color_hist_1080p, "l1_hist_16384": _case_l1_16k}
