@@ -48,7 +48,7 @@ std::vector<int> candidates(int kind)
     case kTuneEpsSelf8:
         return {256, 256 | kTuneWide, 256 | kTunePair};
     case kTuneBatch:
-        return {256, 128, 256 | kTuneWide};
+        return {256, 256 | kTuneWide};
     default:   // top-k: single-SM tiles
         return {256, 128, 256 | kTuneWide};
     }
@@ -64,10 +64,14 @@ int ilog2(int64_t x)
     return l;
 }
 
+// Batches and top-k calls of a server vary in size from call to call: their query sizes fall
+// in classes a factor of four wide, so that a server's shape classes are few and each is tuned
+// once (the other kinds: a factor of two).
 std::string make_key(int dp, int kind, int64_t nR, int64_t nS)
 {
     char buf[96];
-    std::snprintf(buf, sizeof buf, "sm%d:dp%d:k%d:r%d:s%d", device_sm_count(), dp, kind, ilog2(nR), ilog2(nS));
+    const int lr = (kind == kTuneBatch || kind == kTuneTopk) ? ilog2(nR) / 2 * 2 : ilog2(nR);
+    std::snprintf(buf, sizeof buf, "sm%d:dp%d:k%d:r%d:s%d", device_sm_count(), dp, kind, lr, ilog2(nS));
     return buf;
 }
 
