@@ -54,7 +54,9 @@ def parse():
     ap.add_argument("--no-rows", action="store_true",
                     help="skip the colour-histogram, L1 / chi-square and dedup leg")
     ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES), default=None,
-                    help="run one small profiling case three times and print its timings (no bench line)")
+                    help="run one small profiling case --profile-calls times and print its timings (no bench line)")
+    ap.add_argument("--profile-calls", type=int, default=3,
+                    help="calls of the profiling case (the first calls of a shape class are autotuner trials)")
     ap.add_argument("--peak-probe", action="store_true",
                     help="measure the BF16 and FP8 e4m3 cuBLAS GEMM peaks of this GPU and print them (no bench line)")
     ap.add_argument("--no-latency", action="store_true", help="skip the 2,000 x 2,000 latency leg")
@@ -1083,12 +1085,12 @@ PROFILE_CASES = {"fp8_unit_d512_65536": _case_fp8_unit_d512, "dense_d256_16384x1
                  "color_hist_1080p": _case_color_hist_1080p, "l1_hist_16384": _case_l1_16k}
 
 
-def run_profile_case(name):
+def run_profile_case(name, calls=3):
     from paper_1812_07607_gb300 import build as B
     B.build()
     call = PROFILE_CASES[name]()
     import torch
-    for _ in range(3):
+    for _ in range(calls):
         t0 = time.perf_counter()
         r = call()
         torch.cuda.synchronize()
@@ -1098,15 +1100,16 @@ def run_profile_case(name):
             continue
         st = r.stats()
         r.free()
-        print(json.dumps({"case": name, "ms_main": st["ms_main"], "ms_recheck": st["ms_recheck"],
-                          "band_pairs": st["band_pairs"], "pairs_out": st["pairs_out"]}), flush=True)
+        print(json.dumps({"case": name, "ms_call": dt, "ms_main": st["ms_main"], "ms_recheck": st["ms_recheck"],
+                          "band_pairs": st["band_pairs"], "pairs_out": st["pairs_out"], "tile_n": st.get("tile_n"),
+                          "epilogue_warps": st.get("epilogue_warps")}), flush=True)
     return 0
 
 
 def main():
     args = parse()
     if args.profile_case:
-        return run_profile_case(args.profile_case)
+        return run_profile_case(args.profile_case, args.profile_calls)
     if args.peak_probe:
         print(json.dumps(peak_probe()), flush=True)
         return 0

@@ -33,8 +33,8 @@ struct ReqDev {
 };
 
 __global__ void k_batch_expand(const ReqDev *__restrict__ reqs, int n, int64_t total, int32_t *__restrict__ gather,
-                               double *__restrict__ row_e2, int *__restrict__ row_k, int64_t *__restrict__ row_off,
-                               int32_t *__restrict__ row_req)
+                               double *__restrict__ row_e2, float2 *__restrict__ row_t, int d, int *__restrict__ row_k,
+                               int64_t *__restrict__ row_off, int32_t *__restrict__ row_req)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= total) return;
@@ -50,6 +50,11 @@ __global__ void k_batch_expand(const ReqDev *__restrict__ reqs, int n, int64_t t
     const int64_t local = i - r.seg_off;
     gather[i] = (int32_t)(r.q_begin + local);
     if (row_e2) row_e2[i] = r.e2;
+    if (row_t) {   // the row's FP32 thresholds of the exact decision
+        float ta, tr;
+        fp32_thresholds(r.e2, d, &ta, &tr);
+        row_t[i] = make_float2(ta, tr);
+    }
     if (row_k) row_k[i] = r.k;
     if (row_off) row_off[i] = r.out_off + local * r.k;
     row_req[i] = r.req;
@@ -57,12 +62,13 @@ __global__ void k_batch_expand(const ReqDev *__restrict__ reqs, int n, int64_t t
 
 // Candidates -> decisions in place (rejected entries get column 0xffffffff) and
 // per-request counts. One thread per entry; the warp rechecks its band entries
-// together, one after another (FP32 with its bound, canonical FP64 if needed);
-// counts are aggregated per warp over lanes of the same request.
+// together (FP32 with its bound, then the float-float sum, canonical FP64 if neither
+// decides); counts are aggregated per warp over lanes of the same request.
 __global__ void __launch_bounds__(256)
     k_batch_decide(uint2 *__restrict__ cand, const unsigned long long *__restrict__ cand_cnt, unsigned long long cap,
                    const float *__restrict__ Q, const float *__restrict__ S, int d, const double *__restrict__ row_e2,
-                   const int32_t *__restrict__ row_req, unsigned long long *__restrict__ req_cnt,
+                   const float2 *__restrict__ row_t, const int32_t *__restrict__ row_req,
+                   unsigned long long *__restrict__ req_cnt,
                    unsigned long long *__restrict__ n_fp64, unsigned long long *__restrict__ n_band, int nQ, int nS)
 {
     const unsigned lane = threadIdx.x & 31;
@@ -85,9 +91,11 @@ __global__ void __launch_bounds__(256)
         if (bm) {
             double e2 = 0.0;
             float ta = 0.f, tr = 0.f;
-            if (band) {
+            if (band) {   // the row's thresholds, computed once per row at expansion
                 e2 = row_e2[r];
-                fp32_thresholds(e2, d, &ta, &tr);
+                const float2 t2 = row_t[r];
+                ta = t2.x;
+                tr = t2.y;
             }
             const bool dec = warp_band_decide(bm, Q + (size_t)r * d, S + (size_t)c * d, d, e2, ta, tr, &f64);
             if (band) acc = dec;
@@ -281,7 +289,7 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
     }
     // ---- expansion: per-row parameters of both parts
     const size_t b_tab = al((er.size() + kr.size()) * sizeof(ReqDev));
-    const size_t b_e = al(ne * 4) + al(ne * 8) + al(ne * 4);
+    const size_t b_e = al(ne * 4) + al(ne * 8) + al(ne * 4) + al(ne * 8);
     const size_t b_k = al(nk * 4) + al(nk * 4) + al(nk * 8) + al(nk * 4);
     void *meta = nullptr;
     rc = dev_alloc(&meta, b_tab + b_e + b_k + 256, st);
@@ -299,6 +307,8 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
     pm += al(ne * 8);
     int32_t *req_e = (int32_t *)pm;
     pm += al(ne * 4);
+    float2 *row_t = (float2 *)pm;
+    pm += al(ne * 8);
     int32_t *g_k = (int32_t *)pm;
     pm += al(nk * 4);
     int *row_k = (int *)pm;
@@ -316,13 +326,13 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
         }
     }
     if (ne > 0) {
-        k_batch_expand<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(d_er, (int)er.size(), ne, g_e, row_e2, nullptr,
-                                                                      nullptr, req_e);
+        k_batch_expand<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(d_er, (int)er.size(), ne, g_e, row_e2, row_t, d,
+                                                                      nullptr, nullptr, req_e);
         count_launch();
     }
     if (nk > 0) {
-        k_batch_expand<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(d_kr, (int)kr.size(), nk, g_k, nullptr, row_k,
-                                                                      row_off, req_k);
+        k_batch_expand<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(d_kr, (int)kr.size(), nk, g_k, nullptr, nullptr, d,
+                                                                      row_k, row_off, req_k);
         count_launch();
     }
     // ---- result block: eps pairs are sized after the count pass; top-k slots now
@@ -437,7 +447,8 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
             }
             if (!rc) {
                 k_batch_decide<<<sms * 8, 256, 0, st>>>(cand, cnt + 0, (unsigned long long)cap, Qe->x32, S->x32, d,
-                                                        row_e2, req_e, req_cnt, cnt + 1, cnt + 2, (int)ne, (int)S->n);
+                                                        row_e2, row_t, req_e, req_cnt, cnt + 1, cnt + 2, (int)ne,
+                                                        (int)S->n);
                 count_launch(2);
                 e = cudaGetLastError();
                 if (e != cudaSuccess) rc = cuda_fail(e, "k_batch_decide launch");

@@ -1,4 +1,6 @@
-// exact.cuh -- the exact decision for one pair (FP32 bound first, canonical FP64 if needed).
+// exact.cuh -- the exact decision for one pair: an FP32 sum with its bound first, then a
+// float-float sum with a much tighter bound, and the canonical FP64 sum only for the pairs
+// neither can place (in practice, pairs whose distance ties eps^2 to about 1e-10).
 #pragma once
 
 #include <cstdint>
@@ -17,6 +19,84 @@ __device__ __forceinline__ void fp32_thresholds(double e2, int d, float *t_acc, 
     const double abs32 = (double)(d + 8) * 1.401298464324817e-45 * 2.0;
     *t_acc = __double2float_rd(e2 * (1.0 - g64) * (1.0 - g32) * (1.0 - 8.881784197001252e-16) - abs32);
     *t_rej = __double2float_ru(e2 * (1.0 + 2.0 * g64) * (1.0 + g32) * (1.0 + 8.881784197001252e-16) + abs32);
+}
+
+// ---- float-float stage. The FP32 bound leaves a relative zone of about 2 (d+8) 2^-24 around
+// eps^2 undecided, and the canonical FP64 sum that settles it is a chain of d dependent
+// additions at the FP64 rate. Between the two sits a sum in FP32 error-free transformations:
+//   t_k = q_k - x_k = th + tl exactly (TwoSum);  th^2 = p + pe exactly (FMA);
+//   t_k^2 = p + (pe + 2 th tl) + tl^2, with tl^2 <= 2^-48 th^2 dropped;
+//   the p_k are added with TwoSum, whose errors are collected in FP32 (c), and the small
+//   parts m_k = fl(pe + fl(2 th tl)) in FP32 (m).
+// For non-negative terms every TwoSum error is at most 2^-24 of the whole sum, at most d-1 of
+// them are non-zero, and every FP32 sum here has at most d+32 roundings on any path, so with
+// S = (s + c) + m in FP64:
+//   |S - D| <= [(d+32)(d-1) + 3(d+32) + 6 + 1/16] 2^-48 D (1 + 2^-20) + 4d 2^-150
+//           <= (d+34)^2 2^-48 D + (d+1) 2^-146
+// (the 2^-150 terms are the roundings of products and sums that fall below the normal range).
+// The _rn intrinsics are never contracted into FMAs, so each step rounds exactly once.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    const float av = __fsub_rn(s, bv);
+    e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+}
+
+struct FFSum {
+    float s;   // TwoSum chain of the p_k
+    float c;   // its collected errors
+    float m;   // the small parts
+};
+
+__device__ __forceinline__ void ff_add_term(FFSum &a, float q, float x)
+{
+    float th, tl;
+    two_sum(q, -x, th, tl);
+    const float p = __fmul_rn(th, th);
+    const float pe = __fmaf_rn(th, th, -p);
+    a.m = __fadd_rn(a.m, __fadd_rn(pe, __fmul_rn(__fadd_rn(th, th), tl)));
+    float s, e;
+    two_sum(a.s, p, s, e);
+    a.s = s;
+    a.c = __fadd_rn(a.c, e);
+}
+
+__device__ __forceinline__ void ff_merge(FFSum &a, float bs, float bc, float bm)
+{
+    float s, e;
+    two_sum(a.s, bs, s, e);
+    a.s = s;
+    a.c = __fadd_rn(__fadd_rn(a.c, bc), e);
+    a.m = __fadd_rn(a.m, bm);
+}
+
+// Float-float value S of sum_k (q_k - x_k)^2 by the whole warp (lane l takes k = l, l+32, ...;
+// a butterfly of commutative merges, so every lane returns the same S).
+__device__ __forceinline__ double warp_ff_sq(const float *__restrict__ q, const float *__restrict__ x, int d)
+{
+    const unsigned lane = threadIdx.x & 31;
+    FFSum a{0.f, 0.f, 0.f};
+    for (int k = (int)lane; k < d; k += 32) ff_add_term(a, __ldg(q + k), __ldg(x + k));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        ff_merge(a, __shfl_xor_sync(0xffffffffu, a.s, o), __shfl_xor_sync(0xffffffffu, a.c, o),
+                 __shfl_xor_sync(0xffffffffu, a.m, o));
+    return __dadd_rn(__dadd_rn((double)a.s, (double)a.c), (double)a.m);
+}
+
+// Thresholds of the float-float stage for eps^2 = e2: accept if S <= t_acc (then
+// D <= e2 (1 - g64), so the canonical value C <= D (1 + g64) < e2), reject if S > t_rej (then
+// D > e2 (1 + 2 g64) and C >= D (1 - g64) > e2), with g64 = (d+4) 2^-53 the canonical sum's
+// relative error. Every factor is exact in FP64 and every operation rounds outward.
+__device__ __forceinline__ void ff_thresholds(double e2, int d, double *t_acc, double *t_rej)
+{
+    const double g64 = (double)(d + 4) * 0x1p-53;
+    const double dd = (double)(d + 34);
+    const double del = dd * dd * 0x1p-48;
+    const double abs_ff = (double)(d + 1) * 0x1p-146;
+    *t_acc = __dsub_rd(__dmul_rd(__dmul_rd(e2, 1.0 - g64), 1.0 - del), abs_ff);
+    *t_rej = __dadd_ru(__dmul_ru(__dmul_ru(e2, 1.0 + 2.0 * g64), 1.0 + del), abs_ff);
 }
 
 // FP32 squared distance of (q, x) computed by the whole warp: each lane sums a slice
@@ -53,8 +133,8 @@ __device__ __forceinline__ float warp_sq32(const float *__restrict__ q, const fl
 }
 
 // The canonical FP64 sum of (q, x) by the whole warp: lane l forms the term of dimension
-// k0 + l, then every lane adds the 32 terms in ascending k with __dadd_rn, so the sum is
-// exactly the sequential definition's. Every lane returns it.
+// k0 + l, then lane 0 adds the terms in ascending k with __dadd_rn, so the sum is exactly the
+// sequential definition's. Every lane returns it.
 __device__ __forceinline__ double warp_canonical64(const float *__restrict__ q, const float *__restrict__ x, int d)
 {
     const unsigned lane = threadIdx.x & 31;
@@ -67,13 +147,17 @@ __device__ __forceinline__ double warp_canonical64(const float *__restrict__ q, 
             pk = __dmul_rn(t, t);
         }
         const int lim = min(32, d - k0);
-        for (int l = 0; l < lim; ++l) sum = __dadd_rn(sum, __shfl_sync(0xffffffffu, pk, l));
+        for (int l = 0; l < lim; ++l) {
+            const double v = __shfl_sync(0xffffffffu, pk, l);
+            if (lane == 0) sum = __dadd_rn(sum, v);   // one lane runs the chain: the FP64 rate is low
+        }
     }
-    return sum;
+    return __shfl_sync(0xffffffffu, sum, 0);
 }
 
 // Exact decision for the pair (q, x), taken by the whole warp (same answer in
-// every lane): FP32 first, the canonical FP64 sum only when FP32 cannot decide.
+// every lane): FP32 first, then the float-float sum, the canonical FP64 sum only when
+// neither can decide.
 __device__ __forceinline__ bool warp_exact_decide(const float *__restrict__ q, const float *__restrict__ x, int d,
                                                   double e2, float t_acc, float t_rej,
                                                   unsigned long long *__restrict__ n_fp64)
@@ -81,6 +165,11 @@ __device__ __forceinline__ bool warp_exact_decide(const float *__restrict__ q, c
     const float s = warp_sq32(q, x, d);
     if (s <= t_acc) return true;
     if (s > t_rej) return false;
+    double fa, fr;
+    ff_thresholds(e2, d, &fa, &fr);
+    const double sf = warp_ff_sq(q, x, d);
+    if (sf <= fa) return true;
+    if (sf > fr) return false;
     const double sum = warp_canonical64(q, x, d);
     if ((threadIdx.x & 31) == 0) atomicAdd(n_fp64, 1ULL);
     return sum <= e2;
@@ -91,9 +180,10 @@ __device__ __forceinline__ bool warp_exact_decide(const float *__restrict__ q, c
 // pairs are settled at a time, one per 8-lane group: the group sums the pair's FP32
 // squared distance over 16-byte slices (a shuffle tree within the group; the (d+8) 2^-24
 // bound holds for any order) and compares it with the pair's thresholds. The pairs that
-// FP32 cannot decide are then settled one by one by the whole warp with the canonical
-// FP64 sum. Returns this lane's decision (false for lanes not in bm); *used_fp64 is set in
-// the lanes whose pair needed the FP64 sum.
+// FP32 cannot decide are then settled one by one by the whole warp with the float-float
+// sum, and the few that it cannot place either with the canonical FP64 sum. Returns this
+// lane's decision (false for lanes not in bm); *used_fp64 is set in the lanes whose pair
+// needed the canonical FP64 sum.
 __device__ __forceinline__ bool warp_band_decide(unsigned bm, const float *q, const float *x, int d, double e2,
                                                  float t_acc, float t_rej, bool *used_fp64)
 {
@@ -161,9 +251,9 @@ __device__ __forceinline__ bool warp_band_decide(unsigned bm, const float *q, co
 #pragma unroll
         for (int t = 0; t < 4; ++t) rem &= rem - 1u;   // the four settled entries leave the set
     }
-    *used_fp64 = und;
+    bool f64 = false;
     unsigned um = __ballot_sync(0xffffffffu, und);
-    while (um) {
+    while (um) {   // one by one, the whole warp: the float-float sum, then the canonical one
         const int k = __ffs(um) - 1;
         um &= um - 1u;
         const float *qk = reinterpret_cast<const float *>(
@@ -171,9 +261,17 @@ __device__ __forceinline__ bool warp_band_decide(unsigned bm, const float *q, co
         const float *xk = reinterpret_cast<const float *>(
             __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(x), k));
         const double e2k = __shfl_sync(0xffffffffu, e2, k);
-        const bool dec = warp_canonical64(qk, xk, d) <= e2k;
+        double fa, fr;
+        ff_thresholds(e2k, d, &fa, &fr);
+        const double sf = warp_ff_sq(qk, xk, d);
+        bool dec = sf <= fa;
+        if (!dec && !(sf > fr)) {
+            dec = warp_canonical64(qk, xk, d) <= e2k;
+            if ((int)lane == k) f64 = true;
+        }
         if ((int)lane == k) mine = dec;
     }
+    *used_fp64 = f64;
     return mine;
 }
 

@@ -6,7 +6,9 @@
 //      chains over 16-byte slices + a shuffle tree), bound |D32 - D| <= (d+8) 2^-24 D
 //      + tiny; if that
 //      decides the pair against the canonical-FP64 slack, done;
-//   2. otherwise the canonical FP64 value itself: k ascending,
+//   2. otherwise a float-float sum (FP32 error-free transformations) whose bound,
+//      (d+34)^2 2^-48 D, leaves only near-ties of eps^2 undecided;
+//   3. for those, the canonical FP64 value itself: k ascending,
 //      t = (double)q_k - (double)x_k, s = s + t*t, every operation rounded to
 //      nearest with no contraction (__dsub_rn / __dmul_rn / __dadd_rn), compared
 //      with fl64(eps*eps) -- the very expression that defines the result, so the
