@@ -148,7 +148,10 @@ struct PassCfg {
     int metric;             // 0 squared L2 (and cosine), 1 L1, 2 chi-square
     const int64_t *ids;     // ids written for both sides (self-join only; NULL: the store's ids)
     const int4 *units = nullptr;   // work units of the pruned join
-    int n_units = 0;
+    int n_units = 0;               // (pruned: an upper bound; the count itself is on the device)
+    const int *n_units_dev = nullptr;
+    const uint32_t *tile_mask = nullptr;   // pruned: tiles of a unit with a clear bit are skipped
+    int mask_ntw = 0;
     bool pruned = false;           // the pruned join (units may be empty: every tile pair skipped)
     float t_acc, t_rej;     // FP32 thresholds (exact: recheck/SIMT; plain: SIMT only)
     int64_t cap, band_cap;
@@ -258,6 +261,9 @@ static int run_pass(const PassCfg &c, PassOut *po)
                 L.grid = c.cg2 ? 2 * std::min(n_units, sms / 2) : std::min(n_units, sms);
                 L.p.units = units;
                 L.p.n_units = n_units;
+                L.p.n_units_dev = c.n_units_dev;
+                L.p.tile_mask = c.tile_mask;
+                L.p.mask_ntw = c.mask_ntw;
                 L.p.nR = (int)nR;
                 L.p.nS = (int)nS;
                 L.p.kc = fp8 ? R->dp8 / 128 : R->dp / 64;
@@ -552,24 +558,27 @@ int sim_join_impl(const dl_store *R, const dl_store *S, int32_t metric, double e
         c.band_cap = std::max<int64_t>(1 << 16, want + want / 4);
     }
 
-    int4 *prune_u = nullptr;
+    PruneUnits pu;
     int64_t tiles_total = 0, tiles_kept = 0;
     if (o.prune && (prec == DL_PREC_BF16 || prec == DL_PREC_FP8E4M3) && hmetric == 0) {
-        int pn = 0;
-        rc = prune_units(R, Sx, self, BN, e2, c.st, &prune_u, &pn, &tiles_total, &tiles_kept);
+        rc = prune_units(R, Sx, self, BN, e2, c.st, &pu);
         if (rc) return rc;
-        c.units = prune_u;
-        c.n_units = pn;
+        c.units = pu.units;
+        c.n_units = pu.cap;
+        c.n_units_dev = pu.count;
+        c.tile_mask = pu.mask;
+        c.mask_ntw = pu.ntw;
         c.pruned = true;
+        tiles_total = pu.total;
     }
     struct UnitsGuard {
-        int4 *p;
+        void *p;
         cudaStream_t st;
         ~UnitsGuard()
         {
             if (p) dev_free(p, st);
         }
-    } units_guard{prune_u, c.st};
+    } units_guard{pu.block, c.st};
     PassOut po;
     int reruns = 0;
     for (int attempt = 0;; ++attempt) {
@@ -596,6 +605,16 @@ int sim_join_impl(const dl_store *R, const dl_store *S, int32_t metric, double e
             continue;
         }
         break;
+    }
+    if (pu.kept) {   // the surviving tile pairs (the stream has drained: one small read)
+        unsigned long long kept = 0;
+        cudaError_t e = cudaMemcpyAsync(&kept, pu.kept, sizeof kept, cudaMemcpyDeviceToHost, c.st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
+        if (e != cudaSuccess) {
+            dev_free(po.out_r, c.st);
+            return cuda_fail(e, "dl_sim_join: pruned tile count");
+        }
+        tiles_kept = (int64_t)kept;
     }
     {
         std::lock_guard<std::mutex> lk(const_cast<dl_store *>(R)->mu);

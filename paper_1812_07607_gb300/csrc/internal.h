@@ -127,10 +127,22 @@ int store_nonneg(Store *s, cudaStream_t st, bool *ok);
 int sim_join_impl(const dl_store *R, const dl_store *S, int32_t metric, double eps, const dl_join_opts *opts,
                   dl_result **out, const int64_t *emit_ids);
 
-// Work units of the pruned join: the (R tile, S tile) pairs whose bounding balls may hold a
-// pair within eps (prune.cu). *d_units is device memory from dev_alloc (NULL when none).
-int prune_units(const dl_store *R, const dl_store *S, bool upper, int BN, double e2, cudaStream_t st, int4 **d_units,
-                int *n_units, int64_t *tiles_total, int64_t *tiles_kept);
+// Work units of the pruned join, built on the device with no host round trip (prune.cu): the
+// ball test's tile mask (bit t of R tile m's row: S tile t may hold a pair within eps) and one
+// unit {m, first, last + 1, 0} per (R tile, 64-tile S block) with a surviving tile, in the
+// dense join's S-range-major order; the tensor-core kernel skips the masked-out tiles inside
+// a unit. Everything lives in `block` (dev_alloc), freed by the caller after the join.
+struct PruneUnits {
+    void *block = nullptr;
+    const int4 *units = nullptr;          // [cap]
+    int cap = 0;                          // upper bound of the unit count (sizes the grid)
+    const int *count = nullptr;           // device: units written
+    const uint32_t *mask = nullptr;       // device: [R tiles][ntw]
+    int ntw = 0;
+    unsigned long long *kept = nullptr;   // device: surviving tile pairs
+    int64_t total = 0;                    // tile pairs of the dense join
+};
+int prune_units(const dl_store *R, const dl_store *S, bool upper, int BN, double e2, cudaStream_t st, PruneUnits *pu);
 
 // Build (or fetch from the store's cache) a 2-D BF16 tensor map over the store's
 // BF16 copy with a box of 64 columns x box_rows rows and the 128-byte swizzle.

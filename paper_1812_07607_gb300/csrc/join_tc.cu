@@ -52,17 +52,35 @@ __device__ __forceinline__ bool mbar_wait_plain(uint64_t *bar, uint32_t parity)
     return true;
 }
 
+// The S tile after n in a unit of R tile m ending at `end`: n + 1, or with a tile mask the
+// next tile whose bit is set (end when there is none). Every role steps through a unit with
+// it, so all of them see the same tile sequence.
+__device__ __forceinline__ int tile_after(const TcParams &p, int m, int n, int end)
+{
+    ++n;
+    if (!p.tile_mask) return n;
+    const uint32_t *row = p.tile_mask + (size_t)m * p.mask_ntw;
+    while (n < end) {
+        const uint32_t w = __ldg(row + (n >> 5)) >> (n & 31);
+        if (w) return min(n + __ffs((int)w) - 1, end);
+        n = (n | 31) + 1;
+    }
+    return end;
+}
+
 // Walks this CTA's (unit, S tile) sequence.
 struct TileIter {
     int u, n;
     int4 un;
     bool valid;
     int stride;
-    __device__ __forceinline__ void start(const TcParams &p, int first, int step)
+    int nu;   // unit count
+    __device__ __forceinline__ void start(const TcParams &p, int first, int step, int n_units)
     {
         u = first;
         stride = step;
-        valid = u < p.n_units;
+        nu = n_units;
+        valid = u < nu;
         if (valid) {
             un = p.units[u];
             n = un.y;
@@ -71,9 +89,10 @@ struct TileIter {
     __device__ __forceinline__ void next(const TcParams &p)
     {
         if (!valid) return;
-        if (++n == un.z) {
+        n = tile_after(p, un.x, n, un.z);
+        if (n == un.z) {
             u += stride;
-            valid = u < p.n_units;
+            valid = u < nu;
             if (valid) {
                 un = p.units[u];
                 n = un.y;
@@ -366,6 +385,7 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
     const bool leader = crank == 0u;
     const int ufirst = CG2 ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;   // units are per CTA pair with CG2
     const int ustride = CG2 ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+    const int n_units = p.n_units_dev ? *p.n_units_dev : p.n_units;
     constexpr int kRowTiles = CG2 ? 2 : 1;    // 128-row tiles per unit row tile
     // Raise the abort flag of this CTA (and of the peer, so that it stops waiting too).
     auto raise_abort = [&]() {
@@ -418,7 +438,7 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
             for (int s = 0; s < 8; ++s) pend[s] = false;
             bool ok = true;
             int i = 0;   // unit count of this CTA
-            for (int u = ufirst; u < p.n_units && ok; u += ustride, ++i) {
+            for (int u = ufirst; u < n_units && ok; u += ustride, ++i) {
                 const int4 un = p.units[u];
                 const int slot = i % a_slots;
                 const uint32_t use = (uint32_t)(i / a_slots);
@@ -432,7 +452,7 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
                                 (un.x * kRowTiles + (int)crank) * 128);
                 a_pend[slot] = true;
                 a_pend_par[slot] = use & 1;
-                for (int n = un.y; n < un.z && ok; ++n) {
+                for (int n = un.y; n < un.z && ok; n = tile_after(p, un.x, n, un.z)) {
                     for (int c = 0; c < kc; ++c) {
                         if (!mbar_wait(empty + stage, phase ^ 1, abort_flag, p.wait_budget)) {
                             ok = false;
@@ -468,7 +488,7 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
             uint32_t stage = 0, phase = 0;
             bool ok = true;
             int i = 0;
-            for (int u = ufirst; u < p.n_units && ok; u += ustride, ++i) {
+            for (int u = ufirst; u < n_units && ok; u += ustride, ++i) {
                 const int4 un = p.units[u];
                 const int slot = i % a_slots;
                 const uint32_t use = (uint32_t)(i / a_slots);
@@ -477,7 +497,7 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
                     break;
                 }
                 mbar_arrive_remote(r_pa_full + (uint32_t)slot * 8u);
-                for (int n = un.y; n < un.z && ok; ++n) {
+                for (int n = un.y; n < un.z && ok; n = tile_after(p, un.x, n, un.z)) {
                     for (int c = 0; c < kc; ++c) {
                         if (!mbar_wait(full + stage, phase, abort_flag, p.wait_budget)) {
                             ok = false;
@@ -501,7 +521,7 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
             uint32_t stage = 0, phase = 0, t = 0;
             bool ok = true;
             int i = 0;
-            for (int u = ufirst; u < p.n_units && ok; u += ustride, ++i) {
+            for (int u = ufirst; u < n_units && ok; u += ustride, ++i) {
                 const int4 un = p.units[u];
                 const int slot = i % a_slots;
                 const uint32_t use = (uint32_t)(i / a_slots);
@@ -517,7 +537,7 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
                 }
                 tc_fence_after();
                 const uint32_t a_base = smem_u32(sA + slot * a_bytes);
-                for (int n = un.y; n < un.z && ok; ++n) {
+                for (int n = un.y; n < un.z && ok; n = tile_after(p, un.x, n, un.z)) {
                     const uint32_t b = t % kAcc;
                     const bool freed = CG2 ? mbar_wait_cluster(acc_empty + b, ((t / kAcc) & 1) ^ 1, abort_flag,
                                                                p.wait_budget)
@@ -578,12 +598,15 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
                 }
             }
             if (!ok) raise_abort();
-            // No MMA may still be running when TMEM is released.
-            if constexpr (CG2)
-                mma_commit_cg2(done);
-            else
-                mma_commit(done);
-            mbar_wait_plain(done, 0);
+            // No MMA may still be running when TMEM is released. (A CTA that got no unit --
+            // possible when the units were built on the device -- issued none.)
+            if (CG2 || i > 0 || !ok) {
+                if constexpr (CG2)
+                    mma_commit_cg2(done);
+                else
+                    mma_commit(done);
+                mbar_wait_plain(done, 0);
+            }
         }
     } else {
         // ------------------------------------------------------------ epilogue
@@ -600,7 +623,7 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
         constexpr int kPer = HC / 32;      // beta values a lane stages per tile (4 or 2)
         static_assert(kPer == 4 || kPer == 2, "an epilogue warp owns 128 or 64 columns");
         TileIter cur, nxt;
-        cur.start(p, ufirst, ustride);
+        cur.start(p, ufirst, ustride, n_units);
         nxt = cur;
         nxt.next(p);
 

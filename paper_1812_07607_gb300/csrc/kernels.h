@@ -12,6 +12,9 @@ namespace dl {
 struct TcParams {
     const int4 *units;       // {m, nb, ne, 0}: R tile m against S tiles [nb, ne)
     int n_units;
+    const int *n_units_dev;  // when not NULL the unit count is read here (units built on the device)
+    const uint32_t *tile_mask;   // when not NULL: [R tiles][mask_ntw] bits; a unit's S tiles with a
+    int mask_ntw;                // clear bit are skipped (the pruned join; one-SM tiles only)
     int nR, nS;
     int kc;                  // K chunks of 64 (dp / 64)
     int stages;              // S ring depth

@@ -141,6 +141,76 @@ __global__ void __launch_bounds__(256)
     if ((threadIdx.x & 31) == 0 && t < nt) mask[(int64_t)m * ntw + (t >> 5)] = word;
 }
 
+// First S tile of R tile m a self-join (upper) computes: tiles wholly at or below the diagonal
+// hold no pair c > r.
+__host__ __device__ __forceinline__ int first_upper_tile(int m, int BN, bool upper)
+{
+    if (!upper) return 0;
+    const long long num = (long long)m * 128 + 2 - BN;
+    return num <= 0 ? 0 : (int)((num + BN - 1) / BN);
+}
+
+// Units of the pruned join from the tile mask, in one CTA: block pair i = b * mt + m (S-range-
+// major, as the dense units) covers S tiles [64 b, 64 b + 64) of R tile m from its first upper
+// tile on. A pair with a surviving tile becomes unit {m, first kept, last kept + 1, 0}; a CTA-
+// wide exclusive scan of the keep flags places the units in order. Also counts the surviving
+// tiles. Grid: one CTA of 1024 threads.
+__global__ void __launch_bounds__(1024)
+    k_prune_units(const uint32_t *__restrict__ mask, int mt, int nt, int ntw, int BN, int upper, int4 *__restrict__ units,
+                  int *__restrict__ n_units, unsigned long long *__restrict__ kept)
+{
+    __shared__ int s_warp[32];
+    __shared__ int s_base;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const long long npairs = (long long)((nt + 63) / 64) * mt;
+    if (tid == 0) s_base = 0;
+    unsigned long long my_kept = 0;
+    __syncthreads();
+    for (long long c0 = 0; c0 < npairs; c0 += 1024) {
+        const long long i = c0 + tid;
+        int m = 0, first = -1, last = -1;
+        if (i < npairs) {
+            const int b = (int)(i / mt);
+            m = (int)(i % mt);
+            const int lo = max(b * 64, first_upper_tile(m, BN, upper != 0)), hi = min(b * 64 + 64, nt);
+            for (int wd = lo >> 5; lo < hi && wd <= (hi - 1) >> 5; ++wd) {
+                uint32_t word = mask[(size_t)m * ntw + wd];
+                const int w0 = wd * 32;
+                if (lo > w0) word &= ~0u << (lo - w0);
+                if (hi < w0 + 32) word &= ~0u >> (32 - (hi - w0));
+                if (word) {
+                    if (first < 0) first = w0 + __ffs((int)word) - 1;
+                    last = w0 + 31 - __clz((int)word);
+                    my_kept += (unsigned long long)__popc(word);
+                }
+            }
+        }
+        const bool keep = first >= 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) s_warp[w] = __popc(bal);
+        __syncthreads();
+        if (w == 0) {   // exclusive scan of the 32 warp counts
+            const int v = s_warp[lane];
+            int x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            s_warp[lane] = x - v;
+        }
+        __syncthreads();
+        if (keep) units[s_base + s_warp[w] + __popc(bal & ((1u << lane) - 1u))] = make_int4(m, first, last + 1, 0);
+        __syncthreads();
+        if (tid == 1023) s_base += s_warp[31] + __popc(bal);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) my_kept += __shfl_xor_sync(0xffffffffu, my_kept, o);
+    if (lane == 0 && my_kept) atomicAdd(kept, my_kept);
+    if (tid == 0) *n_units = s_base;
+}
+
 __global__ void __launch_bounds__(256)
     k_label_of_rows(const int64_t *__restrict__ best, const int32_t *__restrict__ orig, int64_t n, int32_t *label)
 {
@@ -303,98 +373,55 @@ int tile_balls(Store *s, int rows, cudaStream_t st, const Store::BallCache **out
     return DL_OK;
 }
 
-int first_upper(int m, int BN, bool upper)
-{
-    if (!upper) return 0;
-    const long long num = (long long)m * 128 + 2 - BN;
-    return num <= 0 ? 0 : (int)((num + BN - 1) / BN);
-}
-
 }  // namespace
 
-// Work units {m, nb, ne, 0} of the tile pairs that survive the ball test (runs of
-// consecutive surviving S tiles, at most 64 per unit, S-range-major as the dense units).
-int prune_units(const dl_store *R, const dl_store *S, bool upper, int BN, double e2, cudaStream_t st, int4 **d_units,
-                int *n_units, int64_t *tiles_total, int64_t *tiles_kept)
+// Work units of the tile pairs that survive the ball test, built on the device (the tile mask,
+// then k_prune_units); nothing is read back, so the join launches right after.
+int prune_units(const dl_store *R, const dl_store *S, bool upper, int BN, double e2, cudaStream_t st, PruneUnits *pu)
 {
-    *d_units = nullptr;
-    *n_units = 0;
+    *pu = PruneUnits();
     const int mt = (int)((R->n + 127) / 128), nt = (int)((S->n + BN - 1) / BN);
-    *tiles_total = 0;
-    *tiles_kept = 0;
     if (mt == 0 || nt == 0) return DL_OK;
+    for (int m = 0; m < mt; ++m) pu->total += std::max(0, nt - first_upper_tile(m, BN, upper));
     const int d = R->d;
     const int ntw = (nt + 31) / 32;
     const size_t n_words = (size_t)mt * ntw;
+    const int64_t cap = (int64_t)((nt + 63) / 64) * mt;
     const Store::BallCache *bR = nullptr, *bS = nullptr;
     int rc = tile_balls(const_cast<dl_store *>(R), 128, st, &bR);
     if (!rc) rc = tile_balls(const_cast<dl_store *>(S), BN, st, &bS);
     if (rc) return rc;
+    const size_t b_units = ((size_t)cap * sizeof(int4) + 255) & ~(size_t)255;
+    const size_t b_mask = (n_words * 4 + 255) & ~(size_t)255;
     void *blk = nullptr;
-    rc = dev_alloc(&blk, n_words * 4 + 256, st);
+    rc = dev_alloc(&blk, b_units + b_mask + 256, st);
     if (rc) return rc;
-    uint32_t *mask = (uint32_t *)blk;
-    std::vector<uint32_t> h(n_words);
-    cudaError_t e = cudaSuccess;
-    if (!rc) {
+    int4 *units = (int4 *)blk;
+    uint32_t *mask = (uint32_t *)((char *)blk + b_units);
+    int *count = (int *)((char *)blk + b_units + b_mask);
+    unsigned long long *kept = (unsigned long long *)(count + 2);
+    cudaError_t e = cudaMemsetAsync(count, 0, 16, st);
+    if (e == cudaSuccess) {
         const float e2_up = std::isinf(e2) ? __builtin_inff() : f32_ru(e2 * (1.0 + 1e-6) + 1e-37);
         const dim3 grid((unsigned)((nt + 255) / 256), (unsigned)mt);
         k_prune_mask<<<grid, 256, (size_t)kMaxSeg * d * sizeof(float), st>>>(bR->centre, bR->radius, bR->nseg, mt,
                                                                               bS->centre, bS->radius, bS->nseg, nt, d,
                                                                               e2_up, mask);
-        count_launch();
+        k_prune_units<<<1, 1024, 0, st>>>(mask, mt, nt, ntw, BN, upper ? 1 : 0, units, count, kept);
+        count_launch(2);
         e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), mask, n_words * 4, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) rc = cuda_fail(e, "prune mask");
     }
-    dev_free(blk, st);
-    if (rc) return rc;
-    std::vector<int4> v;
-    const int L = 64;
-    int64_t total = 0, kept = 0;
-    auto word = [&](int m, int t) { return h[(size_t)m * ntw + (t >> 5)]; };
-    for (int nb0 = 0; nb0 < nt; nb0 += L)
-        for (int m = 0; m < mt; ++m) {
-            const int lo = std::max(nb0, first_upper(m, BN, upper)), hi = std::min(nb0 + L, nt);
-            if (lo >= hi) continue;
-            total += hi - lo;
-            int run = -1;
-            for (int t = lo; t < hi;) {
-                // a whole zero word (no surviving tile) is skipped at once
-                if ((t & 31) == 0 && t + 32 <= hi && word(m, t) == 0u) {
-                    if (run >= 0) {
-                        v.push_back(make_int4(m, run, t, 0));
-                        run = -1;
-                    }
-                    t += 32;
-                    continue;
-                }
-                const bool keep = (word(m, t) >> (t & 31)) & 1u;
-                kept += keep;
-                if (keep && run < 0) run = t;
-                if (!keep && run >= 0) {
-                    v.push_back(make_int4(m, run, t, 0));
-                    run = -1;
-                }
-                ++t;
-            }
-            if (run >= 0) v.push_back(make_int4(m, run, hi, 0));
-        }
-    *tiles_total = total;
-    *tiles_kept = kept;
-    if (v.empty()) return DL_OK;
-    int4 *du = nullptr;
-    rc = dev_alloc((void **)&du, v.size() * sizeof(int4), st);
-    if (rc) return rc;
-    e = cudaMemcpyAsync(du, v.data(), v.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
-        dev_free(du, st);
-        return cuda_fail(e, "prune units upload");
+        dev_free(blk, st);
+        return cuda_fail(e, "prune units");
     }
-    *d_units = du;
-    *n_units = (int)v.size();
+    pu->block = blk;
+    pu->units = units;
+    pu->cap = (int)cap;
+    pu->count = count;
+    pu->mask = mask;
+    pu->ntw = ntw;
+    pu->kept = kept;
     return DL_OK;
 }
 
