@@ -55,20 +55,24 @@ __device__ __forceinline__ bool mbar_wait_plain(uint64_t *bar, uint32_t parity)
 // The S tile after n in a unit of R tile m ending at `end`: n + 1, or with a tile mask the
 // next tile whose bit is set (end when there is none). Every role steps through a unit with
 // it, so all of them see the same tile sequence.
+template <bool MASK>
 __device__ __forceinline__ int tile_after(const TcParams &p, int m, int n, int end)
 {
     ++n;
-    if (!p.tile_mask) return n;
-    const uint32_t *row = p.tile_mask + (size_t)m * p.mask_ntw;
-    while (n < end) {
-        const uint32_t w = __ldg(row + (n >> 5)) >> (n & 31);
-        if (w) return min(n + __ffs((int)w) - 1, end);
-        n = (n | 31) + 1;
+    if constexpr (MASK) {
+        const uint32_t *row = p.tile_mask + (size_t)m * p.mask_ntw;
+        while (n < end) {
+            const uint32_t w = __ldg(row + (n >> 5)) >> (n & 31);
+            if (w) return min(n + __ffs((int)w) - 1, end);
+            n = (n | 31) + 1;
+        }
+        return end;
     }
-    return end;
+    return n;
 }
 
 // Walks this CTA's (unit, S tile) sequence.
+template <bool MASK>
 struct TileIter {
     int u, n;
     int4 un;
@@ -89,7 +93,7 @@ struct TileIter {
     __device__ __forceinline__ void next(const TcParams &p)
     {
         if (!valid) return;
-        n = tile_after(p, un.x, n, un.z);
+        n = tile_after<MASK>(p, un.x, n, un.z);
         if (n == un.z) {
             u += stride;
             valid = u < nu;
@@ -340,7 +344,7 @@ __device__ __forceinline__ float max_tree32(const uint32_t (&v)[N], int o)
 // multicast to both CTAs. Each CTA's epilogue handles its own rows; the peer releases an
 // accumulator with a remote arrive on the leader's barrier. Half the B bytes per stage means
 // twice the stages in the same shared memory beside a resident R tile.
-template <int BN, bool TOPK, bool FP8, bool CG2, bool WIDE>
+template <int BN, bool TOPK, bool FP8, bool CG2, bool WIDE, bool MASK>
 __global__ void __launch_bounds__(tc_threads(WIDE), 1)
     tc_join_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcParams p)
@@ -385,7 +389,7 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
     const bool leader = crank == 0u;
     const int ufirst = CG2 ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;   // units are per CTA pair with CG2
     const int ustride = CG2 ? (int)(gridDim.x >> 1) : (int)gridDim.x;
-    const int n_units = p.n_units_dev ? *p.n_units_dev : p.n_units;
+    const int n_units = MASK ? *p.n_units_dev : p.n_units;   // MASK: units built on the device
     constexpr int kRowTiles = CG2 ? 2 : 1;    // 128-row tiles per unit row tile
     // Raise the abort flag of this CTA (and of the peer, so that it stops waiting too).
     auto raise_abort = [&]() {
@@ -452,7 +456,7 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
                                 (un.x * kRowTiles + (int)crank) * 128);
                 a_pend[slot] = true;
                 a_pend_par[slot] = use & 1;
-                for (int n = un.y; n < un.z && ok; n = tile_after(p, un.x, n, un.z)) {
+                for (int n = un.y; n < un.z && ok; n = tile_after<MASK>(p, un.x, n, un.z)) {
                     for (int c = 0; c < kc; ++c) {
                         if (!mbar_wait(empty + stage, phase ^ 1, abort_flag, p.wait_budget)) {
                             ok = false;
@@ -497,7 +501,7 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
                     break;
                 }
                 mbar_arrive_remote(r_pa_full + (uint32_t)slot * 8u);
-                for (int n = un.y; n < un.z && ok; n = tile_after(p, un.x, n, un.z)) {
+                for (int n = un.y; n < un.z && ok; n = tile_after<MASK>(p, un.x, n, un.z)) {
                     for (int c = 0; c < kc; ++c) {
                         if (!mbar_wait(full + stage, phase, abort_flag, p.wait_budget)) {
                             ok = false;
@@ -537,7 +541,7 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
                 }
                 tc_fence_after();
                 const uint32_t a_base = smem_u32(sA + slot * a_bytes);
-                for (int n = un.y; n < un.z && ok; n = tile_after(p, un.x, n, un.z)) {
+                for (int n = un.y; n < un.z && ok; n = tile_after<MASK>(p, un.x, n, un.z)) {
                     const uint32_t b = t % kAcc;
                     const bool freed = CG2 ? mbar_wait_cluster(acc_empty + b, ((t / kAcc) & 1) ^ 1, abort_flag,
                                                                p.wait_budget)
@@ -599,8 +603,8 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
             }
             if (!ok) raise_abort();
             // No MMA may still be running when TMEM is released. (A CTA that got no unit --
-            // possible when the units were built on the device -- issued none.)
-            if (CG2 || i > 0 || !ok) {
+            // possible only when the units were built on the device -- issued none.)
+            if (!MASK || i > 0 || !ok) {
                 if constexpr (CG2)
                     mma_commit_cg2(done);
                 else
@@ -622,12 +626,12 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
         uint32_t scnt = 0;
         constexpr int kPer = HC / 32;      // beta values a lane stages per tile (4 or 2)
         static_assert(kPer == 4 || kPer == 2, "an epilogue warp owns 128 or 64 columns");
-        TileIter cur, nxt;
+        TileIter<MASK> cur, nxt;
         cur.start(p, ufirst, ustride, n_units);
         nxt = cur;
         nxt.next(p);
 
-        auto stage_async = [&](const TileIter &it, int s) {
+        auto stage_async = [&](const TileIter<MASK> &it, int s) {
             if (!it.valid) return;
             const int c0 = it.n * BN + half * HC;
             // the column data (beta [n_pad], chunk stats [n_pad / 32]) covers whole 256-column tiles
@@ -904,10 +908,10 @@ long long tc_wait_budget()
     return b > 0 ? b : kWaitBudgetClocks;
 }
 
-template <int BN, bool TOPK, bool FP8, bool CG2, bool WIDE = false>
+template <int BN, bool TOPK, bool FP8, bool CG2, bool WIDE = false, bool MASK = false>
 static int launch_one(const TcLaunch &L, size_t smem, cudaStream_t st, int *grid_out)
 {
-    auto kern = tc_join_kernel<BN, TOPK, FP8, CG2, WIDE>;
+    auto kern = tc_join_kernel<BN, TOPK, FP8, CG2, WIDE, MASK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_join_kernel)");
     TcParams p = L.p;
@@ -961,7 +965,25 @@ int launch_tc_join(const TcLaunch &L, cudaStream_t st, bool topk, bool fp8, int 
         return DL_EUNSUPPORTED;
     }
     int rc;
-    if (L.cg2)
+    if (L.p.tile_mask) {   // the pruned join: units and their count built on the device
+        if (topk || L.cg2 || !L.p.n_units_dev) {
+            set_error("tensor-core join: a tile mask serves the one-SM epsilon-join with device-built units");
+            return DL_EUNSUPPORTED;
+        }
+        if (L.wide)
+            rc = fp8 ? launch_one<256, false, true, false, true, true>(L, smem, st, grid_out)
+                     : launch_one<256, false, false, false, true, true>(L, smem, st, grid_out);
+        else if (L.BN == 256)
+            rc = fp8 ? launch_one<256, false, true, false, false, true>(L, smem, st, grid_out)
+                     : launch_one<256, false, false, false, false, true>(L, smem, st, grid_out);
+        else if (L.BN == 128)
+            rc = fp8 ? launch_one<128, false, true, false, false, true>(L, smem, st, grid_out)
+                     : launch_one<128, false, false, false, false, true>(L, smem, st, grid_out);
+        else {
+            set_error("tensor-core tile width %d not supported (128 or 256)", L.BN);
+            return DL_EINVAL;
+        }
+    } else if (L.cg2)
         rc = fp8 ? launch_one<256, false, true, true>(L, smem, st, grid_out) : launch_one<256, false, false, true>(L, smem, st, grid_out);
     else if (L.wide)
         rc = topk ? launch_one<256, true, false, false, true>(L, smem, st, grid_out)
