@@ -31,7 +31,14 @@
 
 namespace dl {
 
-constexpr int kTkMax = 512;          // candidates a finalize warp holds in shared memory
+constexpr int kTkMax = 480;          // candidates a finalize warp holds in shared memory (5 CTAs per SM)
+// Canonical FP64 sums are costed per warp instruction (the FP64 rate is low and a warp-wide
+// instruction occupies the pipe whatever its active lanes), so the finalize batches them: a row
+// with at most kTkPendRow columns left queues them, and one lane-parallel pass computes the
+// queued columns of many rows (up to kTkPend columns of kTkPendRows rows) at once.
+constexpr int kTkPend = 64;
+constexpr int kTkPendRow = 32;
+constexpr int kTkPendRows = 32;
 constexpr int kTkFallbackCap = 8192; // candidates a fallback block can rank
 
 struct TopkFin {
@@ -119,11 +126,49 @@ __global__ void __launch_bounds__(128) k_topk_finalize(const TopkFin f)
     __shared__ float s_l[4][kTkMax];
     __shared__ double s_d[4][kTkMax];
     __shared__ float s_kth[4];
+    __shared__ int s_prow[4][kTkPend];       // queued columns: query row,
+    __shared__ uint32_t s_pcol[4][kTkPend];  // store row
+    __shared__ int2 s_pseg[4][kTkPendRows];  // queued rows: {query row, first entry | count << 16}
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     uint32_t *col = s_col[w];
     float *su = s_u[w], *sl = s_l[w];
     double *sd = s_d[w];
+    int np = 0, ns = 0;   // queued columns and rows of this warp (warp-uniform)
+    // The queued columns' canonical distances (one per lane), then each queued row's exact rank
+    // by (D64, caller's store row) and its outputs. Uses sd as scratch.
+    auto flush = [&]() {
+        for (int e = lane; e < np; e += 32)
+            sd[e] = canon_d64(f.Q + (size_t)s_prow[w][e] * f.d, f.S + (size_t)s_pcol[w][e] * f.d, f.d);
+        __syncwarp();
+        for (int g = 0; g < ns; ++g) {
+            const int2 sg = s_pseg[w][g];
+            const int i = sg.x, e0 = sg.y & 0xffff, n = sg.y >> 16;
+            const int kk = f.row_k ? f.row_k[i] : f.k;
+            const int64_t base = f.row_off ? f.row_off[i] : (int64_t)f.q_orig[i] * f.k;
+            for (int a = lane; a < n; a += 32) {
+                const double da = sd[e0 + a];
+                const uint32_t ca = s_pcol[w][e0 + a];
+                const int32_t oa = f.s_orig[ca];
+                int rank = 0;
+                for (int b = 0; b < n; ++b) {
+                    const double db = sd[e0 + b];
+                    rank += (db < da) || (db == da && f.s_orig[s_pcol[w][e0 + b]] < oa);
+                }
+                if (rank < kk) {
+                    f.out_ids[base + rank] = f.s_ids[ca];
+                    f.out_d2[base + rank] = da;
+                }
+            }
+            for (int t = n + lane; t < kk; t += 32) {
+                f.out_ids[base + t] = -1;
+                f.out_d2[base + t] = -1.0;
+            }
+        }
+        __syncwarp();
+        np = 0;
+        ns = 0;
+    };
     for (int i = blockIdx.x * 4 + w; i < f.nQ; i += gridDim.x * 4) {
         if (f.overflow[i]) continue;
         // the row's k-th largest lower bound over all slots' heaps (the heaps hold each
@@ -177,14 +222,34 @@ __global__ void __launch_bounds__(128) k_topk_finalize(const TopkFin f)
         }
         __syncwarp();
         const float kth = __fmul_ru(s_kth[w], 1.0f + f.slack);
+        // the columns that can still be in the top k: each needs its canonical distance
         int kept = 0;
+        for (int a0 = 0; a0 < m; a0 += 32) kept += __popc(__ballot_sync(0xffffffffu, a0 + lane < m && sl[a0 + lane] <= kth));
+        if (lane == 0 && kept) atomicAdd(f.n_fp64, (unsigned long long)kept);
+        if (kept <= kTkPendRow) {   // queue them with other rows' columns
+            if (np + kept > kTkPend || ns == kTkPendRows) flush();
+            int pos = np;
+            for (int a0 = 0; a0 < m; a0 += 32) {
+                const int a = a0 + lane;
+                const bool keep = a < m && sl[a] <= kth;
+                const unsigned bm = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    s_prow[w][pos + __popc(bm & lt)] = i;
+                    s_pcol[w][pos + __popc(bm & lt)] = col[a];
+                }
+                pos += __popc(bm);
+            }
+            if (lane == 0) s_pseg[w][ns] = make_int2(i, np | (kept << 16));
+            np += kept;
+            ++ns;
+            __syncwarp();
+            continue;
+        }
+        flush();   // sd is this row's now
         for (int a0 = 0; a0 < m; a0 += 32) {
             const int a = a0 + lane;
             const bool keep = a < m && sl[a] <= kth;
             if (a < m) sd[a] = keep ? canon_d64(q, f.S + (size_t)col[a] * f.d, f.d) : __longlong_as_double(0x7ff0000000000000LL);
-            const unsigned bm = __ballot_sync(0xffffffffu, keep);
-            kept += __popc(bm);
-            if (lane == 0 && bm) atomicAdd(f.n_fp64, (unsigned long long)__popc(bm));
         }
         __syncwarp();
         const int64_t base = f.row_off ? f.row_off[i] : (int64_t)f.q_orig[i] * f.k;
@@ -210,6 +275,7 @@ __global__ void __launch_bounds__(128) k_topk_finalize(const TopkFin f)
         }
         __syncwarp();
     }
+    flush();
 }
 
 struct TopkFb {
