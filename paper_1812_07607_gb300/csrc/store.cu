@@ -104,34 +104,52 @@ __global__ void __launch_bounds__(256) k1_norm_quant(const float *__restrict__ x
                                                      int *__restrict__ err)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t row = (int64_t)blockIdx.x * 8 + warp;
-    if (row >= n) return;
-    const float *xr = x32 + row * d;
-    __nv_bfloat16 *br = xb + row * dp;
-    double s1 = 0.0;
-    float s2 = 0.f, s3 = 0.f;   // rounded up at every step: upper bounds of the exact sums
-    bool bad = false;
-    for (int k = lane; k < dp; k += 32) {
-        const float v = (k < d) ? __ldg(xr + k) : 0.0f;
-        if (!(fabsf(v) <= 1099511627776.0f)) bad = true;  // also catches NaN
-        const __nv_bfloat16 b = __float2bfloat16_rn(v);
-        br[k] = b;
-        const float fb = __bfloat162float(b);
-        const float e = v - fb;   // exact: x~ shares x's leading bits
-        const double dv = (double)v;
-        s1 = __dadd_rn(s1, __dmul_rn(dv, dv));
-        s2 = __fmaf_ru(e, e, s2);
-        s3 = __fmaf_ru(fb, fb, s3);
-    }
+    const int64_t row0 = ((int64_t)blockIdx.x * 8 + warp) * 32;   // this warp's 32 rows
+    if (row0 >= n) return;
+    const int rows = (int)(n - row0 < 32 ? n - row0 : 32);
+    // the sums of row r end in lane r, so the per-row tail (FP64, a square root) runs once per
+    // 32 rows with every lane busy: a warp-wide FP64 instruction costs the same at one lane
+    double m1 = 0.0;
+    float m2 = 0.f, m3 = 0.f;
+    bool mbad = false;
+    for (int r = 0; r < rows; ++r) {
+        const int64_t row = row0 + r;
+        const float *xr = x32 + row * d;
+        __nv_bfloat16 *br = xb + row * dp;
+        double s1 = 0.0;
+        float s2 = 0.f, s3 = 0.f;   // rounded up at every step: upper bounds of the exact sums
+        bool bad = false;
+        for (int k = lane; k < dp; k += 32) {
+            const float v = (k < d) ? __ldg(xr + k) : 0.0f;
+            if (!(fabsf(v) <= 1099511627776.0f)) bad = true;  // also catches NaN
+            const __nv_bfloat16 b = __float2bfloat16_rn(v);
+            br[k] = b;
+            const float fb = __bfloat162float(b);
+            const float e = v - fb;   // exact: x~ shares x's leading bits
+            const double dv = (double)v;
+            s1 = __dadd_rn(s1, __dmul_rn(dv, dv));
+            s2 = __fmaf_ru(e, e, s2);
+            s3 = __fmaf_ru(fb, fb, s3);
+        }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s1 = __dadd_rn(s1, __shfl_xor_sync(0xffffffffu, s1, o));
-        s2 = __fadd_ru(s2, __shfl_xor_sync(0xffffffffu, s2, o));
-        s3 = __fadd_ru(s3, __shfl_xor_sync(0xffffffffu, s3, o));
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 = __dadd_rn(s1, __shfl_xor_sync(0xffffffffu, s1, o));
+            s2 = __fadd_ru(s2, __shfl_xor_sync(0xffffffffu, s2, o));
+            s3 = __fadd_ru(s3, __shfl_xor_sync(0xffffffffu, s3, o));
+        }
+        bad = __any_sync(0xffffffffu, bad);
+        if (lane == r) {
+            m1 = s1;
+            m2 = s2;
+            m3 = s3;
+            mbad = bad;
+        }
     }
-    bad = __any_sync(0xffffffffu, bad);
-    if (lane == 0) {
-        if (bad) atomicOr(err, 1);
+    if (lane < rows) {
+        const int64_t row = row0 + lane;
+        const double s1 = m1;
+        const float s2 = m2, s3 = m3;
+        if (mbad) atomicOr(err, 1);
         // Any-order FP64 sum of dp non-negative exact terms: relative error <= (dp-1) 2^-53.
         const double fac = 1.0 + (double)(dp + 4) * 2.220446049250313e-16;
         const double grow = 1.0 + 8.881784197001252e-16;   // 1 + 2^-50 covers the sqrt / product roundings
@@ -673,7 +691,8 @@ int store_create_impl(dl_store **out, const int64_t *ids, const float *feats, in
             count_launch(3);
         }
         k_gather_rows<<<gw, 256, 0, st>>>(src_x, src_ids, gather ? gather : perm, n, d, s->x32, s->ids, s->orig);
-        k1_norm_quant<<<gw, 256, 0, st>>>(s->x32, n, d, s->dp, s->xb, s->nq64, s->beta, s->rowb, d_err);
+        k1_norm_quant<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->x32, n, d, s->dp, s->xb, s->nq64, s->beta,
+                                                                  s->rowb, d_err);   // 32 rows per warp
         count_launch(3);
     }
     const float g2 = f32_ru(gamma_tc(s->dp) + 1.01 * kU32);
