@@ -68,6 +68,21 @@ def test_topk_ragged(dl, orc, nQ, nS, d, k):
     check_topk(dl, orc, Q, S, k)
 
 
+@pytest.mark.parametrize("nQ,nS0,d,k", [(330000, 150, 8, 1), (60000, 1000, 16, 3), (60000, 1000, 16, 12),
+                                         (60000, 1000, 16, 40)])
+def test_topk_many_rows_per_warp_exact(dl, orc, nQ, nS0, d, k):
+    """Enough query rows that each finalize warp takes several: rows with few columns left
+    queue them and share lane-parallel passes of canonical FP64 distances (k = 1 with 34 rows
+    per warp fills the queue's 32 row slots; k = 12 fills its 64 columns), and rows with more
+    take the direct path after the queue is flushed (k = 40). A quarter of the store rows are
+    duplicated, so distances tie and the rank falls back to the store row."""
+    g = W.rng(4300 + k)
+    S0 = W.dirichlet_histograms(g, nS0, d)
+    S = np.concatenate([S0, S0[: nS0 // 4]])
+    Q = W.dirichlet_histograms(g, nQ, d)
+    check_topk(dl, orc, Q, S, k)
+
+
 def test_topk_clustered_self(dl, orc):
     """Queries are the store itself: each row's nearest is itself at distance 0."""
     g = W.rng(41)
