@@ -74,10 +74,14 @@ __global__ void __launch_bounds__(256)
     const unsigned lane = threadIdx.x & 31;
     const unsigned long long n = min(*cand_cnt, cap);
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < n; base += stride) {
+    unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x;
+    uint2 nxt = base + threadIdx.x < n ? cand[base + threadIdx.x] : make_uint2(0u, 0u);
+    for (; base < n; base += stride) {
         const unsigned long long i = base + threadIdx.x;   // warp-uniform loop bound: base < n
         bool valid = i < n;
-        const uint2 e = valid ? cand[i] : make_uint2(0u, 0u);
+        const uint2 e = nxt;
+        // the next window's entry loads while this one is decided (no entry is read after its write)
+        nxt = i + stride < n ? cand[i + stride] : make_uint2(0u, 0u);
         if (valid && !DL_CHECK(e.x < (unsigned)nQ && (e.y & ~kBandFlag) < (unsigned)nS, 30, i)) {
             cand[i] = make_uint2(0u, 0xffffffffu);   // checked build: dropped, so the scatter skips it
             valid = false;

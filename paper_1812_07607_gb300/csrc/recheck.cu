@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256)
 // proven matches are emitted as they are, the band entries are rechecked by the
 // whole warp one after another (vector loads of both rows, FP32 with its bound,
 // canonical FP64 if needed), then the warp emits the survivors.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 5)
     k_finalize(const uint2 *__restrict__ cand, const unsigned long long *__restrict__ cand_cnt,
                unsigned long long cand_cap, const float *__restrict__ R, const float *__restrict__ S, int d, double e2,
                float t_acc, float t_rej, JoinOut out, unsigned long long *__restrict__ n_fp64,
@@ -50,10 +50,12 @@ __global__ void __launch_bounds__(256)
     const unsigned long long n = min(*cand_cnt, cand_cap);
     const unsigned long long w0 = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    uint2 nxt = w0 * 32 + lane < n ? cand[w0 * 32 + lane] : make_uint2(0u, 0u);
     for (unsigned long long base = w0 * 32; base < n; base += nw * 32) {
         const unsigned long long i = base + lane;
         const bool valid = i < n;
-        uint2 e = valid ? cand[i] : make_uint2(0u, 0u);
+        uint2 e = nxt;
+        nxt = i + nw * 32 < n ? cand[i + nw * 32] : make_uint2(0u, 0u);   // the next window, loaded early
         if (valid && !DL_CHECK(e.x < (unsigned)nR && (e.y & ~kBandFlag) < (unsigned)nS, 20, i)) e = make_uint2(0u, 0u);
         const int r = (int)e.x;
         const int c = (int)(e.y & ~kBandFlag);
