@@ -288,9 +288,10 @@ int dl_debug_scores(const dl_store *R, const dl_store *S, int32_t precision, flo
  * reports DL_ETIMEOUT (a server marks the batch's requests DL_EFAILED). This
  * sets that budget, in SM clocks, for every tensor-core kernel launched after
  * the call on any thread; 0 restores the default of 2e9 clocks (about 1 s).
- * A budget of a few clocks makes a healthy join time out, which is how the
- * tests drive the abort path without faulting or hanging a GPU. Returns
- * DL_EINVAL for clocks < 0.
+ * A budget below 64 clocks makes every abortable wait expire at once, so a
+ * healthy join times out deterministically; this is how the tests drive the
+ * abort path without faulting or hanging a GPU. Returns DL_EINVAL for
+ * clocks < 0.
  */
 int dl_debug_set_wait_budget(int64_t clocks);
 

@@ -122,10 +122,13 @@ __global__ void __launch_bounds__(256)
 {
     const unsigned long long n = min(*cand_cnt, cap);
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < n; base += stride) {
+    unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x;
+    uint2 nxt = base + threadIdx.x < n ? cand[base + threadIdx.x] : make_uint2(0u, 0xffffffffu);
+    for (; base < n; base += stride) {
         const unsigned long long i = base + threadIdx.x;
         const bool valid = i < n;
-        const uint2 e = valid ? cand[i] : make_uint2(0u, 0xffffffffu);
+        const uint2 e = nxt;
+        nxt = i + stride < n ? cand[i + stride] : make_uint2(0u, 0xffffffffu);   // the next window, early
         const bool acc = valid && e.y != 0xffffffffu;
         const int32_t q = acc ? row_req[e.x] : 0;
         const unsigned long long pos = grouped_add(cursor, q, acc, 1u);

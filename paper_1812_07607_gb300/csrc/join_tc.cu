@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
             constexpr uint32_t idesc =
                 FP8 ? idesc_e4m3_f32(CG2 ? 256 : 128, BN) : idesc_bf16_f32(CG2 ? 256 : 128, BN);
             uint32_t stage = 0, phase = 0, t = 0;
-            bool ok = true;
+            bool ok = true, any_mma = false;
             int i = 0;
             for (int u = ufirst; u < n_units && ok; u += ustride, ++i) {
                 const int4 un = p.units[u];
@@ -578,6 +578,7 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
                             else
                                 mma_f16(d_tmem, ad, bd, idesc, (c | k) != 0);
                         }
+                        any_mma = true;
                         if constexpr (CG2)
                             mma_commit_cg2_mc(empty + stage, 3);   // both CTAs may refill their halves
                         else
@@ -602,9 +603,9 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
                 }
             }
             if (!ok) raise_abort();
-            // No MMA may still be running when TMEM is released. (A CTA that got no unit --
-            // possible only when the units were built on the device -- issued none.)
-            if (!MASK || i > 0 || !ok) {
+            // No MMA may still be running when TMEM is released. (A CTA that issued none -- one
+            // that got no unit, or whose first wait ran out -- has nothing to wait for.)
+            if (CG2 || any_mma) {
                 if constexpr (CG2)
                     mma_commit_cg2(done);
                 else

@@ -59,11 +59,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
+// A budget below this many clocks is a test setting: every abortable wait expires at once.
+// (mbarrier.try_wait may itself block until the phase completes, so a short budget alone
+// does not make a wait on a small, fast join run out.)
+constexpr long long kExpireAtOnce = 64;
+
 // Wait for the phase with the given parity to complete. Returns false when
 // `budget` SM clocks pass or another role raised the CTA's abort flag.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
                                           long long budget = kWaitBudgetClocks)
 {
+    if (budget < kExpireAtOnce) return false;
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (true) {
@@ -91,6 +97,7 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t pa
 __device__ __forceinline__ bool mbar_wait_cluster(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
                                                   long long budget = kWaitBudgetClocks)
 {
+    if (budget < kExpireAtOnce) return false;
     if (mbar_try_wait_cluster(bar, parity)) return true;
     const long long t0 = clock64();
     while (true) {
