@@ -240,7 +240,9 @@ __device__ __forceinline__ uint32_t slow_chunk(const TcParams &p, const uint32_t
 }
 
 // ---------------------------------------------------------------- top-k epilogue
-// A slot's state is (theta, list fill) in registers plus, in global memory, a
+constexpr int kHeapArity = 8;   // children per node of a top-k slot's heap (8 measured faster than 4 and 2)
+
+// A slot's state is (theta, list fill) in registers plus, in global memory, a kHeapArity-ary
 // min-heap of the k largest lower bounds L = fl_rd(h - E) seen so far above the row's
 // published threshold (theta is its minimum: at least k columns have h >= theta) and
 // the list of every column
@@ -273,12 +275,23 @@ __device__ __noinline__ float2 topk_insert(const TcParams &p, size_t sidx, int r
         float *heap = p.tk_heap + sidx * (size_t)p.tk_k;
         const int k = p.tk_k;
         int i = 0;
-        while (true) {   // replace the minimum by L and sift down
-            const int l = 2 * i + 1;
-            if (l >= k) break;
-            const int rr = l + 1;
-            const int m = (rr < k && heap[rr] < heap[l]) ? rr : l;
-            const float hm = heap[m];
+        // replace the minimum by L and sift down a kHeapArity-ary heap (children of i at
+        // kHeapArity * i + 1 ...): a third of a binary heap's levels at k = 100, the loads of
+        // a level issued together
+        while (true) {
+            const int c0 = kHeapArity * i + 1;
+            if (c0 >= k) break;
+            float hc[kHeapArity];
+#pragma unroll
+            for (int j = 0; j < kHeapArity; ++j) hc[j] = c0 + j < k ? heap[c0 + j] : __int_as_float(0x7f800000);
+            int m = c0;
+            float hm = hc[0];
+#pragma unroll
+            for (int j = 1; j < kHeapArity; ++j)
+                if (hc[j] < hm) {
+                    hm = hc[j];
+                    m = c0 + j;
+                }
             if (hm >= L) break;
             heap[i] = hm;
             i = m;
