@@ -267,7 +267,7 @@ static int run_pass(const PassCfg &c, PassOut *po)
                 L.p.nR = (int)nR;
                 L.p.nS = (int)nS;
                 L.p.kc = fp8 ? R->dp8 / 128 : R->dp / 64;
-                tc_plan(c.BN, L.p.kc, &L.p.stages, &L.p.a_slots, fp8, c.cg2, c.wide);
+                tc_plan(c.BN, L.p.kc, &L.p.stages, &L.p.a_slots, fp8, c.cg2, c.wide, !c.pruned);
                 L.p.upper = c.self ? 1 : 0;
                 L.p.rowpar = rowpar;
                 L.p.beta = S->beta;

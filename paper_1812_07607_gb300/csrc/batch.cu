@@ -436,7 +436,7 @@ extern "C" int dl_batch_join(const dl_store *S, const int64_t *q_ids, const floa
                 L.p.nR = (int)ne;
                 L.p.nS = (int)S->n;
                 L.p.kc = Qe->dp / 64;
-                tc_plan(BN, Qe->dp / 64, &L.p.stages, &L.p.a_slots, false, false, wide);
+                tc_plan(BN, Qe->dp / 64, &L.p.stages, &L.p.a_slots, false, false, wide, true);
                 L.wide = wide;
                 L.p.upper = 0;
                 L.p.rowpar = rowpar;

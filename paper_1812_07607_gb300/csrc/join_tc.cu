@@ -357,7 +357,7 @@ __device__ __forceinline__ float max_tree32(const uint32_t (&v)[N], int o)
 // multicast to both CTAs. Each CTA's epilogue handles its own rows; the peer releases an
 // accumulator with a remote arrive on the leader's barrier. Half the B bytes per stage means
 // twice the stages in the same shared memory beside a resident R tile.
-template <int BN, bool TOPK, bool FP8, bool CG2, bool WIDE, bool MASK>
+template <int BN, bool TOPK, bool FP8, bool CG2, bool WIDE, bool MASK, bool STREAM>
 __global__ void __launch_bounds__(tc_threads(WIDE), 1)
     tc_join_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcParams p)
@@ -366,6 +366,10 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int kc = p.kc, stages = p.stages, a_slots = p.a_slots;
     constexpr uint32_t kStageBytes = (CG2 ? BN / 2 : BN) * 128;   // this CTA's rows of an S tile x 128 B
+    // STREAM: no resident R tile; each stage also carries the R tile's matching 128-byte K chunk
+    // (128 rows, 16 KB), so a large d keeps four stages instead of two beside a resident tile
+    static_assert(!STREAM || (!CG2 && !TOPK && !MASK), "streamed R chunks serve the one-SM epsilon-join");
+    constexpr uint32_t kStageStride = STREAM ? kStageBytes + 16384 : kStageBytes;
     constexpr int kChunkCols = FP8 ? 128 : 64;   // columns per 128-byte K chunk
     constexpr int kAcc = 512 / BN;              // TMEM accumulators: 2 of 256 or 4 of 128 columns
     constexpr uint32_t kTmemCols = 512;
@@ -375,10 +379,10 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
     constexpr int kSubW = HC / 32;           // 32-column chunks per warp per tile
     const uint32_t a_bytes = (uint32_t)kc * 16384;
     uint8_t *sA = smem;                                    // a_slots x kc x [128 rows x 128 B]
-    uint8_t *sB = smem + a_slots * a_bytes;                // stages x [BN rows x 128 B]
+    uint8_t *sB = smem + (STREAM ? 0 : a_slots * a_bytes);   // stages x [BN rows x 128 B (+ R chunk)]
     // Column data of a tile (beta, chunk stats, FP8 chunk scales) is staged by the epilogue
     // warps themselves with cp.async, one tile ahead, in kColSlots = 2 slots.
-    float *s_beta = reinterpret_cast<float *>(sB + stages * kStageBytes);    // kEpi warps x kColSlots x HC: beta
+    float *s_beta = reinterpret_cast<float *>(sB + stages * kStageStride);    // kEpi warps x kColSlots x HC: beta
     float4 *s_cst = reinterpret_cast<float4 *>(s_beta + kEpi * kColSlots * HC); // kEpi x kColSlots x kSubW chunk stats
     uint2 *s_stage = reinterpret_cast<uint2 *>(s_cst + kEpi * kColSlots * kSubW);   // kEpi x kStageCap candidates
     float *s_sx = reinterpret_cast<float *>(s_stage + kEpi * kStageCap);     // FP8: kEpi x kColSlots x kSubW scales
@@ -457,27 +461,32 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
             int i = 0;   // unit count of this CTA
             for (int u = ufirst; u < n_units && ok; u += ustride, ++i) {
                 const int4 un = p.units[u];
-                const int slot = i % a_slots;
-                const uint32_t use = (uint32_t)(i / a_slots);
-                if (!mbar_wait(a_empty + slot, (use & 1) ^ 1, abort_flag, p.wait_budget)) {
-                    ok = false;
-                    break;
+                if constexpr (!STREAM) {
+                    const int slot = i % a_slots;
+                    const uint32_t use = (uint32_t)(i / a_slots);
+                    if (!mbar_wait(a_empty + slot, (use & 1) ^ 1, abort_flag, p.wait_budget)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(a_full + slot, a_bytes);
+                    for (int c = 0; c < kc; ++c)   // a K chunk is 128 bytes: 64 BF16 or 128 FP8 columns
+                        tma_load_2d(sA + slot * a_bytes + c * 16384, &tmA, a_full + slot, c * kChunkCols,
+                                    (un.x * kRowTiles + (int)crank) * 128);
+                    a_pend[slot] = true;
+                    a_pend_par[slot] = use & 1;
                 }
-                mbar_arrive_expect_tx(a_full + slot, a_bytes);
-                for (int c = 0; c < kc; ++c)   // a K chunk is 128 bytes: 64 BF16 or 128 FP8 columns
-                    tma_load_2d(sA + slot * a_bytes + c * 16384, &tmA, a_full + slot, c * kChunkCols,
-                                (un.x * kRowTiles + (int)crank) * 128);
-                a_pend[slot] = true;
-                a_pend_par[slot] = use & 1;
                 for (int n = un.y; n < un.z && ok; n = tile_after<MASK>(p, un.x, n, un.z)) {
                     for (int c = 0; c < kc; ++c) {
                         if (!mbar_wait(empty + stage, phase ^ 1, abort_flag, p.wait_budget)) {
                             ok = false;
                             break;
                         }
-                        mbar_arrive_expect_tx(full + stage, kStageBytes);
-                        tma_load_2d(sB + stage * kStageBytes, &tmB, full + stage, c * kChunkCols,
+                        mbar_arrive_expect_tx(full + stage, kStageStride);
+                        tma_load_2d(sB + stage * kStageStride, &tmB, full + stage, c * kChunkCols,
                                     n * BN + (CG2 ? (int)crank * (BN / 2) : 0));
+                        if constexpr (STREAM)   // the R tile's chunk c beside it
+                            tma_load_2d(sB + stage * kStageStride + kStageBytes, &tmA, full + stage, c * kChunkCols,
+                                        un.x * 128);
                         pend[stage] = true;
                         pend_par[stage] = phase;
                         if (++stage == (uint32_t)stages) {
@@ -540,20 +549,23 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
             int i = 0;
             for (int u = ufirst; u < n_units && ok; u += ustride, ++i) {
                 const int4 un = p.units[u];
-                const int slot = i % a_slots;
-                const uint32_t use = (uint32_t)(i / a_slots);
-                if (!mbar_wait(a_full + slot, use & 1, abort_flag, p.wait_budget)) {
-                    ok = false;
-                    break;
-                }
-                if constexpr (CG2) {   // the peer's rows of the R tile
-                    if (!mbar_wait_cluster(pa_full + slot, use & 1, abort_flag, p.wait_budget)) {
+                const int slot = STREAM ? 0 : i % a_slots;
+                uint32_t a_base = 0;
+                if constexpr (!STREAM) {   // the unit's resident R tile
+                    const uint32_t use = (uint32_t)(i / a_slots);
+                    if (!mbar_wait(a_full + slot, use & 1, abort_flag, p.wait_budget)) {
                         ok = false;
                         break;
                     }
+                    if constexpr (CG2) {   // the peer's rows of the R tile
+                        if (!mbar_wait_cluster(pa_full + slot, use & 1, abort_flag, p.wait_budget)) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                    tc_fence_after();
+                    a_base = smem_u32(sA + slot * a_bytes);
                 }
-                tc_fence_after();
-                const uint32_t a_base = smem_u32(sA + slot * a_bytes);
                 for (int n = un.y; n < un.z && ok; n = tile_after<MASK>(p, un.x, n, un.z)) {
                     const uint32_t b = t % kAcc;
                     const bool freed = CG2 ? mbar_wait_cluster(acc_empty + b, ((t / kAcc) & 1) ^ 1, abort_flag,
@@ -577,8 +589,9 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
                             }
                         }
                         tc_fence_after();
-                        const uint32_t a_addr = a_base + c * 16384;
-                        const uint32_t b_addr = smem_u32(sB + stage * kStageBytes);
+                        const uint32_t a_addr =
+                            STREAM ? smem_u32(sB + stage * kStageStride + kStageBytes) : a_base + c * 16384;
+                        const uint32_t b_addr = smem_u32(sB + stage * kStageStride);
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {   // 4 x 32 bytes of K per 128-byte chunk
                             const uint64_t ad = smem_desc_sw128(a_addr + k * 32), bd = smem_desc_sw128(b_addr + k * 32);
@@ -608,7 +621,7 @@ __global__ void __launch_bounds__(tc_threads(WIDE), 1)
                         mma_commit(acc_full + b);
                     ++t;
                 }
-                if (ok) {
+                if (ok && !STREAM) {
                     if constexpr (CG2)
                         mma_commit_cg2_mc(a_empty + slot, 3);
                     else
@@ -892,14 +905,18 @@ static size_t tc_extra_bytes(int BN, bool fp8, bool wide)
 // BN/2 for a CTA pair).
 static size_t tc_stage_bytes(int BN, bool cg2) { return (size_t)(cg2 ? BN / 2 : BN) * 128; }
 
+// a_slots == 0: streamed R chunks, 16 KB more per stage and no resident tile
 static size_t tc_smem_bytes(int BN, int kc, int stages, int a_slots, bool fp8, bool cg2, bool wide)
 {
-    return 1024 + (size_t)a_slots * kc * 16384 + (size_t)stages * tc_stage_bytes(BN, cg2) +
+    return 1024 + (size_t)a_slots * kc * 16384 + (size_t)stages * (tc_stage_bytes(BN, cg2) + (a_slots ? 0 : 16384)) +
            tc_extra_bytes(BN, fp8, wide);
 }
 
-// Shared-memory plan: two A slots when that still leaves at least three S stages.
-void tc_plan(int BN, int kc, int *stages, int *a_slots, bool fp8, bool cg2, bool wide)
+// Shared-memory plan: two A slots when that still leaves at least three S stages, else one;
+// with `stream` (the one-SM epsilon-join), a plan that would be left with fewer than three
+// stages beside one resident R tile streams the R tile's chunks with the S chunks instead
+// (a_slots = 0).
+void tc_plan(int BN, int kc, int *stages, int *a_slots, bool fp8, bool cg2, bool wide, bool stream)
 {
     const long cap = 232448;
     for (int slots = 2; slots >= 1; --slots) {
@@ -909,9 +926,14 @@ void tc_plan(int BN, int kc, int *stages, int *a_slots, bool fp8, bool cg2, bool
         if (s >= 3 || slots == 1) {
             *stages = (int)s;
             *a_slots = slots;
-            return;
+            if (s >= 3 || !stream || cg2) return;
+            break;
         }
     }
+    long s = (cap - 1024 - (long)tc_extra_bytes(BN, fp8, wide)) / (long)(tc_stage_bytes(BN, cg2) + 16384);
+    if (s > 8) s = 8;
+    *stages = (int)s;
+    *a_slots = 0;
 }
 
 static std::atomic<long long> g_wait_budget{0};
@@ -922,10 +944,10 @@ long long tc_wait_budget()
     return b > 0 ? b : kWaitBudgetClocks;
 }
 
-template <int BN, bool TOPK, bool FP8, bool CG2, bool WIDE = false, bool MASK = false>
+template <int BN, bool TOPK, bool FP8, bool CG2, bool WIDE = false, bool MASK = false, bool STREAM = false>
 static int launch_one(const TcLaunch &L, size_t smem, cudaStream_t st, int *grid_out)
 {
-    auto kern = tc_join_kernel<BN, TOPK, FP8, CG2, WIDE, MASK>;
+    auto kern = tc_join_kernel<BN, TOPK, FP8, CG2, WIDE, MASK, STREAM>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_join_kernel)");
     TcParams p = L.p;
@@ -979,7 +1001,25 @@ int launch_tc_join(const TcLaunch &L, cudaStream_t st, bool topk, bool fp8, int 
         return DL_EUNSUPPORTED;
     }
     int rc;
-    if (L.p.tile_mask) {   // the pruned join: units and their count built on the device
+    if (L.p.a_slots == 0) {   // streamed R chunks (tc_plan with stream): the one-SM epsilon-join
+        if (topk || L.cg2 || L.p.tile_mask) {
+            set_error("tensor-core join: streamed R chunks serve the dense one-SM epsilon-join");
+            return DL_EUNSUPPORTED;
+        }
+        if (L.wide)
+            rc = fp8 ? launch_one<256, false, true, false, true, false, true>(L, smem, st, grid_out)
+                     : launch_one<256, false, false, false, true, false, true>(L, smem, st, grid_out);
+        else if (L.BN == 256)
+            rc = fp8 ? launch_one<256, false, true, false, false, false, true>(L, smem, st, grid_out)
+                     : launch_one<256, false, false, false, false, false, true>(L, smem, st, grid_out);
+        else if (L.BN == 128)
+            rc = fp8 ? launch_one<128, false, true, false, false, false, true>(L, smem, st, grid_out)
+                     : launch_one<128, false, false, false, false, false, true>(L, smem, st, grid_out);
+        else {
+            set_error("tensor-core tile width %d not supported (128 or 256)", L.BN);
+            return DL_EINVAL;
+        }
+    } else if (L.p.tile_mask) {   // the pruned join: units and their count built on the device
         if (topk || L.cg2 || !L.p.n_units_dev) {
             set_error("tensor-core join: a tile mask serves the one-SM epsilon-join with device-built units");
             return DL_EUNSUPPORTED;

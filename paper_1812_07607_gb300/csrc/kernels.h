@@ -59,7 +59,10 @@ struct TcLaunch {
 };
 
 // Shared-memory plan of the tensor-core kernel (wide: the 16-warp epilogue's layout).
-void tc_plan(int BN, int kc, int *stages, int *a_slots, bool fp8 = false, bool cg2 = false, bool wide = false);
+// stream: a plan left with fewer than three stages beside one resident R tile streams the R
+// tile's chunks with the S chunks instead (a_slots = 0; the one-SM epsilon-join only).
+void tc_plan(int BN, int kc, int *stages, int *a_slots, bool fp8 = false, bool cg2 = false, bool wide = false,
+             bool stream = false);
 // Clock budget of the tensor-core kernels' abortable waits: the default (about 1 s),
 // unless dl_debug_set_wait_budget set another.
 long long tc_wait_budget();
