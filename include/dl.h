@@ -58,9 +58,13 @@ typedef enum dl_metric {
                              the normalized rows is <= fl64(2 - 2c) (cos >= c for unit rows) */
     DL_METRIC_L1 = 2,     /* histogram L1 distance: canonical FP64 sum_k |q_k - x_k| <= eps
                              (k ascending, every step rounded to nearest); epsilon-join only */
-    DL_METRIC_CHI2 = 3    /* chi-square histogram distance on non-negative features: canonical FP64
+    DL_METRIC_CHI2 = 3,   /* chi-square histogram distance on non-negative features: canonical FP64
                              sum over bins with q_k + x_k > 0 of (q_k - x_k)^2 / (q_k + x_k) <= eps
                              (no factor 1/2); epsilon-join only */
+    DL_METRIC_IP = 4      /* inner-product threshold on rows of any norm (Sec. 3.2 "threshold the
+                             similarity"): a pair matches iff the canonical FP64 dot product
+                             sum_k q_k x_k (k ascending, every addition rounded to nearest; the
+                             products are exact) is >= eps; epsilon-join only */
 } dl_metric;
 
 typedef enum dl_precision {
@@ -220,7 +224,11 @@ int dl_dedup(const dl_store *X, int32_t metric, double eps, const int32_t *label
  * threshold c in [-1, 1] and both stores must come from dl_store_normalize. With
  * DL_METRIC_L1 / DL_METRIC_CHI2 the predicate is the histogram distance <= eps; these
  * run with DL_PREC_FP32 (AUTO picks it) or DL_PREC_FP32_PLAIN (BF16 / FP8 give
- * DL_EUNSUPPORTED), and CHI2 gives DL_EINVAL when a feature is negative. opts may be
+ * DL_EUNSUPPORTED), and CHI2 gives DL_EINVAL when a feature is negative. With
+ * DL_METRIC_IP, eps is the inner-product threshold t (any value but NaN; -inf returns
+ * every pair, +inf none); it runs on the BF16 tensor-core path (AUTO picks it), for
+ * R x S and the upper self mode, without pruning (FP32 / FP8 precisions, the full self
+ * mode and opts->prune give DL_EUNSUPPORTED). opts may be
  * NULL (defaults). On success *out holds the result (free with
  * dl_result_free); on DL_EOVERFLOW *out is also set so that the required
  * count can be read. The pair order is unspecified (the result is a set).

@@ -153,6 +153,7 @@ struct PassCfg {
     const uint32_t *tile_mask = nullptr;   // pruned: tiles of a unit with a clear bit are skipped
     int mask_ntw = 0;
     bool pruned = false;           // the pruned join (units may be empty: every tile pair skipped)
+    bool ip = false;               // inner-product join: e2 holds the threshold t of q.x >= t
     float t_acc, t_rej;     // FP32 thresholds (exact: recheck/SIMT; plain: SIMT only)
     int64_t cap, band_cap;
     bool timing;
@@ -233,7 +234,10 @@ static int run_pass(const PassCfg &c, PassOut *po)
                 rc = ensure_fp8(const_cast<dl_store *>(R), st);
                 if (!rc) rc = ensure_fp8(const_cast<dl_store *>(S), st);
             }
-            if (!rc)
+            if (!rc && c.ip) rc = ensure_ip(const_cast<dl_store *>(S), st);
+            if (!rc && c.ip)
+                rc = launch_rowpar_ip(R->rowb, nR, rows_pad, R->dp, c.e2, rowpar, st);
+            else if (!rc)
                 rc = launch_rowpar(R->nq64, R->rowb, nR, rows_pad, R->dp, c.e2, nullptr, gamma64(d), rowpar, st,
                                    fp8 ? R->rowb8 : nullptr);
             ++launches;
@@ -270,8 +274,8 @@ static int run_pass(const PassCfg &c, PassOut *po)
                 tc_plan(c.BN, L.p.kc, &L.p.stages, &L.p.a_slots, fp8, c.cg2, c.wide, !c.pruned);
                 L.p.upper = c.self ? 1 : 0;
                 L.p.rowpar = rowpar;
-                L.p.beta = S->beta;
-                L.p.cstat = fp8 ? S->cstat8 : S->cstat;
+                L.p.beta = c.ip ? S->beta_ip : S->beta;
+                L.p.cstat = fp8 ? S->cstat8 : (c.ip ? S->cstat_ip : S->cstat);
                 L.p.sc_r = fp8 ? R->sc8 : nullptr;
                 L.p.sc_s = fp8 ? S->scc8 : nullptr;
                 L.p.cand = band;                 // candidates share the band buffer and counter
@@ -300,7 +304,11 @@ static int run_pass(const PassCfg &c, PassOut *po)
         }
         if (c.timing) cudaEventRecord(ev[1], st);
         nvtxRangePushA("exact recheck of the band (K6)");
-        if (!rc && (c.prec == DL_PREC_BF16 || c.prec == DL_PREC_FP8E4M3)) {
+        if (!rc && c.ip) {
+            rc = launch_finalize_ip(band, cnt + 1, (unsigned long long)c.band_cap, R->x32, S->x32, d, c.e2, jo, cnt + 3,
+                                    cnt + 2, sms * 8, st, (int)nR, (int)nS);
+            ++launches;
+        } else if (!rc && (c.prec == DL_PREC_BF16 || c.prec == DL_PREC_FP8E4M3)) {
             rc = launch_finalize(band, cnt + 1, (unsigned long long)c.band_cap, R->x32, S->x32, d, c.e2, c.t_acc,
                                  c.t_rej, jo, cnt + 3, cnt + 2, sms * 8, st, (int)nR, (int)nS);
             ++launches;
@@ -423,6 +431,12 @@ int sim_join_impl(const dl_store *R, const dl_store *S, int32_t metric, double e
             return DL_EINVAL;
         }
         e2 = eps;   // histogram distances are compared unsquared
+    } else if (metric == DL_METRIC_IP) {
+        if (std::isnan(eps)) {
+            set_error("dl_sim_join: the inner-product threshold is NaN");
+            return DL_EINVAL;
+        }
+        e2 = eps;   // the threshold t of q.x >= t
     } else {
         set_error("dl_sim_join: unsupported metric %d", metric);
         return DL_EINVAL;
@@ -450,7 +464,13 @@ int sim_join_impl(const dl_store *R, const dl_store *S, int32_t metric, double e
     // AUTO: BF16 while its R tile fits in shared memory (d <= 512), else the FP8 tensor-core
     // path (d <= 1024, always within the domain); both give the exact set. The histogram
     // distances are not contractions: they run on the CUDA cores (FP32 + bound + FP64).
-    if (prec == DL_PREC_AUTO) prec = hmetric ? DL_PREC_FP32 : (R->dp <= 512) ? DL_PREC_BF16 : DL_PREC_FP8E4M3;
+    const bool ip = metric == DL_METRIC_IP;
+    if (prec == DL_PREC_AUTO)
+        prec = hmetric ? DL_PREC_FP32 : (ip || R->dp <= 512) ? DL_PREC_BF16 : DL_PREC_FP8E4M3;
+    if (ip && (prec != DL_PREC_BF16 || (self && o.self_mode == DL_SELF_FULL) || o.prune)) {
+        set_error("dl_sim_join: the inner-product join runs in BF16, R x S or the upper self mode, without pruning");
+        return DL_EUNSUPPORTED;
+    }
     if (hmetric && (prec == DL_PREC_BF16 || prec == DL_PREC_FP8E4M3)) {
         set_error("dl_sim_join: L1 and chi-square run on DL_PREC_FP32 (or FP32_PLAIN), not on tensor cores");
         return DL_EUNSUPPORTED;
@@ -518,6 +538,7 @@ int sim_join_impl(const dl_store *R, const dl_store *S, int32_t metric, double e
     c.wide = wide;
     c.e2 = e2;
     c.metric = hmetric;
+    c.ip = ip;
     c.ids = emit_ids;
     if (prec == DL_PREC_FP32_PLAIN && hmetric) {
         c.t_acc = (float)eps;

@@ -275,6 +275,108 @@ __device__ __forceinline__ bool warp_band_decide(unsigned bm, const float *q, co
     return mine;
 }
 
+// The canonical FP64 dot product of (q, x) by the whole warp: lane l forms the (exact) product
+// of dimension k0 + l, lane 0 adds the products in ascending k with __dadd_rn -- the
+// sequential definition. Every lane returns it.
+__device__ __forceinline__ double warp_canonical_dot(const float *__restrict__ q, const float *__restrict__ x, int d)
+{
+    const unsigned lane = threadIdx.x & 31;
+    double sum = 0.0;
+    for (int k0 = 0; k0 < d; k0 += 32) {
+        double pk = 0.0;
+        const int k = k0 + (int)lane;
+        if (k < d) pk = __dmul_rn((double)__ldg(q + k), (double)__ldg(x + k));   // exact: 24 x 24 bits
+        const int lim = min(32, d - k0);
+        for (int l = 0; l < lim; ++l) {
+            const double v = __shfl_sync(0xffffffffu, pk, l);
+            if (lane == 0) sum = __dadd_rn(sum, v);
+        }
+    }
+    return __shfl_sync(0xffffffffu, sum, 0);
+}
+
+// Exact decisions of the inner-product join's band entries (q.x >= t by the canonical FP64
+// dot), one 8-lane group per pair as in warp_band_decide: the FP32 dot S32 and A32 =
+// sum |q_k x_k| over 16-byte slices; with B = cf A32 + ca (which covers the FP32 error, the
+// canonical dot's own error and A32's rounding), accept if RD(S32 - B) >= t_ru (then the
+// canonical dot is >= t), reject if RU(S32 + B) < t_rd, else the canonical FP64 dot decides.
+// t_ru / t_rd: t rounded up / down to FP32. *used_fp64 marks the lanes that needed it.
+__device__ __forceinline__ bool warp_band_decide_ip(unsigned bm, const float *q, const float *x, int d, double t,
+                                                    float t_ru, float t_rd, float cf, float ca, bool *used_fp64)
+{
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const int grp = (int)(lane >> 3), gl = (int)(lane & 7);
+    bool mine = false, und = false;
+    unsigned rem = bm;
+    while (rem) {
+        const unsigned pos = __fns(rem, 0, grp + 1);
+        const bool have = pos < 32u;
+        const int k = have ? (int)pos : 0;
+        const float *qk = reinterpret_cast<const float *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(q), k));
+        const float *xk = reinterpret_cast<const float *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(x), k));
+        float sd = 0.f, sa = 0.f;
+        if (have) {
+            if ((d & 3) == 0) {
+                const float4 *q4 = reinterpret_cast<const float4 *>(qk);
+                const float4 *x4 = reinterpret_cast<const float4 *>(xk);
+                const int n4 = d >> 2;
+                for (int i = gl; i < n4; i += 8) {
+                    const float4 a = __ldg(q4 + i), b = __ldg(x4 + i);
+                    sd = fmaf(a.x, b.x, sd);
+                    sa = fmaf(fabsf(a.x), fabsf(b.x), sa);
+                    sd = fmaf(a.y, b.y, sd);
+                    sa = fmaf(fabsf(a.y), fabsf(b.y), sa);
+                    sd = fmaf(a.z, b.z, sd);
+                    sa = fmaf(fabsf(a.z), fabsf(b.z), sa);
+                    sd = fmaf(a.w, b.w, sd);
+                    sa = fmaf(fabsf(a.w), fabsf(b.w), sa);
+                }
+            } else {
+                for (int i = gl; i < d; i += 8) {
+                    const float a = __ldg(qk + i), b = __ldg(xk + i);
+                    sd = fmaf(a, b, sd);
+                    sa = fmaf(fabsf(a), fabsf(b), sa);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+            sd += __shfl_xor_sync(0xffffffffu, sd, o);
+            sa += __shfl_xor_sync(0xffffffffu, sa, o);
+        }
+        const float bnd = __fmaf_ru(cf, sa, ca);
+        const bool accept = __fsub_rd(sd, bnd) >= t_ru;
+        const bool reject = __fadd_ru(sd, bnd) < t_rd;
+        const unsigned accm = __ballot_sync(0xffffffffu, have && gl == 0 && accept);
+        const unsigned undm = __ballot_sync(0xffffffffu, have && gl == 0 && !accept && !reject);
+        if ((rem >> lane) & 1u) {
+            const int r = __popc(rem & below);
+            if (r < 4) {
+                mine = ((accm >> (8 * r)) & 1u) != 0u;
+                und = ((undm >> (8 * r)) & 1u) != 0u;
+            }
+        }
+#pragma unroll
+        for (int tt = 0; tt < 4; ++tt) rem &= rem - 1u;
+    }
+    *used_fp64 = und;
+    unsigned um = __ballot_sync(0xffffffffu, und);
+    while (um) {
+        const int k = __ffs(um) - 1;
+        um &= um - 1u;
+        const float *qk = reinterpret_cast<const float *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(q), k));
+        const float *xk = reinterpret_cast<const float *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(x), k));
+        const bool dec = warp_canonical_dot(qk, xk, d) >= t;
+        if ((int)lane == k) mine = dec;
+    }
+    return mine;
+}
+
 // Warp-aggregated atomicAdd of `v` to counter[key]: lanes with equal keys are
 // grouped (__match_any_sync), the group's lowest lane adds the group's total and
 // every lane gets its own offset. Every lane of the warp must call it; lanes

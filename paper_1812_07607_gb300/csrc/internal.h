@@ -97,6 +97,9 @@ struct Store {
     float *scc8 = nullptr;   // [n_pad/32] the chunk scales (power of two)
     float2 *rowb8 = nullptr; // [n] {||x - s x8|| up, ||s x8|| up}
     float4 *cstat8 = nullptr;// [n_pad/32] {P1, P2 (FP8), P3, beta_min}
+    void *ip_block = nullptr;   // inner-product joins (built on first use): the column term
+    float *beta_ip = nullptr;   // [n_pad] 0 (the dot product has no column term); +inf in padding
+    float4 *cstat_ip = nullptr; // [n_pad / 32] chunk stats {P1, P2, P3, min beta_ip} for that term
     TmapCache tmaps8[3];     // FP8 boxes
     struct BallCache {       // bounding balls of the pruned join's tiles, per tile height
         int rows = 0;
@@ -150,6 +153,8 @@ int get_tmap(Store *s, int box_rows, const CUtensorMap **out);
 
 // FP8 copy of a store (built once, on first use) and its tensor maps (128-byte rows).
 int ensure_fp8(Store *s, cudaStream_t st);
+// Column arrays of the inner-product join (built once, on first use): beta_ip and cstat_ip.
+int ensure_ip(Store *s, cudaStream_t st);
 int get_tmap8(Store *s, int box_rows, const CUtensorMap **out);
 
 // Assumed bound of the tensor-core accumulation of dp8 e4m3 x e4m3 products: dp8 * 2^-20,

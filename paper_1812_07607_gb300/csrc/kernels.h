@@ -99,6 +99,12 @@ int launch_rowpar(const double *nq64, const float4 *rowb, int64_t n, int64_t n_t
 int launch_finalize(const uint2 *cand, const unsigned long long *cand_cnt, unsigned long long cand_cap, const float *R,
                     const float *S, int d, double e2, float t_acc, float t_rej, const JoinOut &out,
                     unsigned long long *n_fp64, unsigned long long *n_band, int grid, cudaStream_t st, int nR, int nS);
+// The inner-product join (recheck.cu): per-row thresholds for the tensor-core epilogue, and the
+// exact decision of its candidates (FP32 dot with its bound, canonical FP64 dot if needed).
+int launch_rowpar_ip(const float4 *rowb, int64_t n, int64_t n_tot, int dp, double t, float4 *rowpar, cudaStream_t st);
+int launch_finalize_ip(const uint2 *cand, const unsigned long long *cand_cnt, unsigned long long cand_cap,
+                       const float *R, const float *S, int d, double t, const JoinOut &out,
+                       unsigned long long *n_fp64, unsigned long long *n_band, int grid, cudaStream_t st, int nR, int nS);
 int launch_diag(const int64_t *ids, int64_t n, int64_t *out_r, int64_t *out_s, unsigned long long *out_cnt,
                 unsigned long long cap, cudaStream_t st);
 

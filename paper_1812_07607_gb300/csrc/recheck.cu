@@ -13,6 +13,8 @@
 //      nearest with no contraction (__dsub_rn / __dmul_rn / __dadd_rn), compared
 //      with fl64(eps*eps) -- the very expression that defines the result, so the
 //      decision is identical to the FP64 nested loop's.
+#include <cmath>
+
 #include "checked.cuh"
 #include "exact.cuh"
 #include "kernels.h"
@@ -146,6 +148,66 @@ __global__ void __launch_bounds__(256)
     rowpar[i] = make_float4(__double2float_ru(a_acc), __double2float_rd(a_rej), r8.x, r8.y);
 }
 
+// Per-row thresholds of the inner-product join (h = q.x, no column term): accept iff
+// h >= RU32(t) + E, reject iff h < RD32(t) - E. The row's residual term grows by
+// g64 ||q||_up, so that E also covers the canonical dot product's own error,
+// |C - q.x| <= g64 sum_k |q_k x_k| <= g64 ||q|| ||x|| (g64 = (dp+4) 2^-53 >= gamma_{d-1}).
+__global__ void __launch_bounds__(256)
+    k_rowpar_ip(const float4 *__restrict__ rowb, int64_t n, int64_t n_tot, int dp, double t, float4 *__restrict__ rowpar)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_tot) return;
+    const float inf = __int_as_float(0x7f800000);
+    if (i >= n) {
+        rowpar[i] = make_float4(inf, inf, 0.f, 0.f);
+        return;
+    }
+    const float4 rb = rowb[i];   // {||q - q~|| up, ||q~|| up, ||q|| up, beta error}
+    const double g64 = (double)(dp + 4) * 1.1102230246251565e-16;
+    const float rq = __double2float_ru(__dadd_ru((double)rb.x, __dmul_ru(__dmul_ru((double)rb.z, g64), 1.0 + 0x1p-20)));
+    rowpar[i] = make_float4(__double2float_ru(t), __double2float_rd(t), rq, rb.y);
+}
+
+// Candidates of the inner-product join -> id pairs: proven matches as they are, band pairs
+// decided exactly by warp_band_decide_ip (an FP32 dot with its bound, else the canonical
+// FP64 dot); the next window's entries load while this one is decided.
+__global__ void __launch_bounds__(256)
+    k_finalize_ip(const uint2 *__restrict__ cand, const unsigned long long *__restrict__ cand_cnt,
+                  unsigned long long cand_cap, const float *__restrict__ R, const float *__restrict__ S, int d,
+                  double t, float t_ru, float t_rd, float cf, float ca, JoinOut out,
+                  unsigned long long *__restrict__ n_fp64, unsigned long long *__restrict__ n_band, int nR, int nS)
+{
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned long long n = min(*cand_cnt, cand_cap);
+    const unsigned long long w0 = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    uint2 nxt = w0 * 32 + lane < n ? cand[w0 * 32 + lane] : make_uint2(0u, 0u);
+    for (unsigned long long base = w0 * 32; base < n; base += nw * 32) {
+        const unsigned long long i = base + lane;
+        const bool valid = i < n;
+        uint2 e = nxt;
+        nxt = i + nw * 32 < n ? cand[i + nw * 32] : make_uint2(0u, 0u);
+        if (valid && !DL_CHECK(e.x < (unsigned)nR && (e.y & ~kBandFlag) < (unsigned)nS, 21, i)) e = make_uint2(0u, 0u);
+        const int r = (int)e.x;
+        const int c = (int)(e.y & ~kBandFlag);
+        const bool band = valid && (e.y & kBandFlag);
+        bool acc = valid && !band;
+        bool f64 = false;
+        const unsigned bm = __ballot_sync(0xffffffffu, band);
+        if (bm) {
+            const bool dec =
+                warp_band_decide_ip(bm, R + (size_t)r * d, S + (size_t)c * d, d, t, t_ru, t_rd, cf, ca, &f64);
+            if (band) acc = dec;
+        }
+        const unsigned fm = __ballot_sync(0xffffffffu, f64);
+        if (lane == 0) {
+            if (bm) atomicAdd(n_band, (unsigned long long)__popc(bm));
+            if (fm) atomicAdd(n_fp64, (unsigned long long)__popc(fm));
+        }
+        warp_emit(out, acc, false, r, c);
+    }
+}
+
 // Self-join full mode: every (i, i) is a pair (canonical D = 0 <= eps^2).
 __global__ void __launch_bounds__(256) k_diag(const int64_t *__restrict__ ids, int64_t n, int64_t *out_r,
                                              int64_t *out_s, unsigned long long *out_cnt, unsigned long long cap)
@@ -187,6 +249,38 @@ int launch_hist_recheck(int metric, const uint2 *band, const unsigned long long 
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_hist_recheck launch");
+    return DL_OK;
+}
+
+int launch_rowpar_ip(const float4 *rowb, int64_t n, int64_t n_tot, int dp, double t, float4 *rowpar, cudaStream_t st)
+{
+    if (n_tot <= 0) return DL_OK;
+    k_rowpar_ip<<<(unsigned)((n_tot + 255) / 256), 256, 0, st>>>(rowb, n, n_tot, dp, t, rowpar);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_rowpar_ip launch");
+    return DL_OK;
+}
+
+int launch_finalize_ip(const uint2 *cand, const unsigned long long *cand_cnt, unsigned long long cand_cap,
+                       const float *R, const float *S, int d, double t, const JoinOut &out,
+                       unsigned long long *n_fp64, unsigned long long *n_band, int grid, cudaStream_t st, int nR, int nS)
+{
+    // FP32 dot bound: |S32 - q.x| <= (d+2) 2^-24 A, A = sum |q_k x_k| <= A32 (1 + (d+2) 2^-24),
+    // plus the canonical dot's (d+4) 2^-53 A; cf = (2d+16) 2^-24 covers both with room, and ca
+    // the products that fall below the normal range (at most 2^-149 each).
+    const float cf = (float)((2.0 * d + 16.0) * 5.9604644775390625e-08);
+    const float ca = (float)((double)d * 1.1210387714598537e-44 + 1.401298464324817e-45);   // d 2^-146 + 2^-149
+    float t_ru, t_rd;
+    t_ru = (float)t;
+    t_rd = (float)t;
+    if ((double)t_ru < t) t_ru = std::nextafter(t_ru, __builtin_inff());
+    if ((double)t_rd > t) t_rd = std::nextafter(t_rd, -__builtin_inff());
+    k_finalize_ip<<<grid, 256, 0, st>>>(cand, cand_cnt, cand_cap, R, S, d, t, t_ru, t_rd, cf, ca, out, n_fp64, n_band, nR,
+                                        nS);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_finalize_ip launch");
     return DL_OK;
 }
 

@@ -473,6 +473,40 @@ int ensure_fp8(Store *s, cudaStream_t st)
     return DL_OK;
 }
 
+// The inner-product join's column term is 0: h = q.x. Its chunk stats come from the same
+// kernel as the squared-L2 ones, run on a zero column term, so P1 and P2 (the encoding and
+// accumulation terms of the BF16 bound) are the store's own and P3 keeps the L2 beta error
+// (a conservative extra); padding rows get +inf, so they never match.
+int ensure_ip(Store *s, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->ip_block) return DL_OK;
+    const size_t b_b = align256(sizeof(float) * s->n_pad), b_cs = align256(sizeof(float4) * (s->n_pad / 32));
+    void *blk = nullptr;
+    int rc = dev_alloc(&blk, b_b + b_cs, st);
+    if (rc) return rc;
+    float *beta_ip = (float *)blk;
+    float4 *cstat_ip = (float4 *)((char *)blk + b_b);
+    cudaError_t e = cudaMemsetAsync(beta_ip, 0, sizeof(float) * s->n_pad, st);
+    if (e == cudaSuccess) {
+        const float g2 = f32_ru(gamma_tc(s->dp) + 1.01 * kU32);
+        const float p3a = f32_ru(abs_slack_tc(s->dp));
+        k1_chunk_stats<<<(unsigned)((s->n_pad / 32 + 7) / 8), 256, 0, st>>>(beta_ip, s->rowb, s->n, s->n_pad, g2, p3a,
+                                                                            beta_ip, cstat_ip);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        dev_free(blk, st);
+        return cuda_fail(e, "inner-product column arrays");
+    }
+    s->beta_ip = beta_ip;
+    s->cstat_ip = cstat_ip;
+    s->ip_block = blk;
+    return DL_OK;
+}
+
 // ------------------------------------------------------------------ tensor maps
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
@@ -881,6 +915,7 @@ int dl_store_destroy(dl_store *s)
     if (prev != s->device) cudaSetDevice(s->device);
     dev_free(s->ids, 0);   // ids is the base of the store's single allocation
     if (s->fp8_block) dev_free(s->fp8_block, 0);
+    if (s->ip_block) dev_free(s->ip_block, 0);
     if (s->clabel) dev_free(s->clabel, 0);
     for (auto &b : s->balls)
         if (b.blk) dev_free(b.blk, 0);

@@ -22,8 +22,8 @@ DL_OK, DL_EINVAL, DL_ENOMEM, DL_EOVERFLOW, DL_EAGAIN, DL_ETIMEOUT, DL_ECUDA, DL_
 STATUS_NAMES = {0: "DL_OK", 1: "DL_EINVAL", 2: "DL_ENOMEM", 3: "DL_EOVERFLOW", 4: "DL_EAGAIN",
                 5: "DL_ETIMEOUT", 6: "DL_ECUDA", 7: "DL_ECANCELED", 8: "DL_ENOMEM_ADMIT",
                 9: "DL_EFAILED", 10: "DL_EUNSUPPORTED"}
-DL_METRIC_L2, DL_METRIC_COSINE, DL_METRIC_L1, DL_METRIC_CHI2 = 0, 1, 2, 3
-METRICS = {"l2": DL_METRIC_L2, "cosine": DL_METRIC_COSINE, "l1": DL_METRIC_L1, "chi2": DL_METRIC_CHI2}
+DL_METRIC_L2, DL_METRIC_COSINE, DL_METRIC_L1, DL_METRIC_CHI2, DL_METRIC_IP = 0, 1, 2, 3, 4
+METRICS = {"l2": DL_METRIC_L2, "cosine": DL_METRIC_COSINE, "l1": DL_METRIC_L1, "chi2": DL_METRIC_CHI2, "ip": DL_METRIC_IP}
 DL_DEDUP_ALL, DL_DEDUP_FILTER_MATCH, DL_DEDUP_MATCH_FILTER = 0, 1, 2
 DEDUP_PLANS = {"all": DL_DEDUP_ALL, "filter_match": DL_DEDUP_FILTER_MATCH, "match_filter": DL_DEDUP_MATCH_FILTER}
 DL_PREC_AUTO, DL_PREC_BF16, DL_PREC_FP8E4M3, DL_PREC_FP32, DL_PREC_FP32_PLAIN = range(5)
@@ -402,7 +402,8 @@ def sim_join(R: Store, S: Store | None, eps: float, precision="auto", self_mode=
              cta_pair=0, epilogue_warps=0) -> Result:
     """dl_sim_join: every pair with canonical squared L2 distance <= eps^2; with
     metric="cosine" (stores from Store.normalized()) every pair with cosine >= eps; with
-    metric="l1" / "chi2" every pair whose histogram distance is <= eps."""
+    metric="l1" / "chi2" every pair whose histogram distance is <= eps; with metric="ip"
+    every pair whose canonical inner product is >= eps."""
     o = make_opts(precision, self_mode, out_capacity, stream, tile_n, timing, prune, cta_pair, epilogue_warps)
     h = ctypes.c_void_p()
     rc = load().dl_sim_join(R.handle, None if S is None else S.handle, METRICS[metric], float(eps),
