@@ -593,8 +593,9 @@ def _event_ms(fn, reps, flush=None):
 
 
 def rows_leg(dl, sm_mhz=None, reps=5):
-    """The further rows: the colour-histogram transformer, the L1 / chi-square self-joins and q4
-    deduplication, each on its own seeded workload at full size (parity in the GPU tests)."""
+    """The further rows: the colour-histogram transformer, the L1 / chi-square self-joins, the
+    inner-product join, the pruned join and q4 deduplication, each on its own seeded workload at
+    full size (parity in the GPU tests)."""
     import torch
     from paper_1812_07607_gb300 import workloads as W
     pk = peaks()
@@ -654,6 +655,40 @@ def rows_leg(dl, sm_mhz=None, reps=5):
                                     "peak": peak / 1e12, "unit": "Tops/s", "frac": ops / (kern_ms / 1e3) / peak,
                                     "algorithmic": f"{unit_ops} x d x {P} pairs ({what}), at {mhz:.0f} MHz"}}
     Xs.close()
+
+    # the inner-product threshold join on rows of any norm (BF16 tensor cores, exact)
+    g = W.rng(W.SEED_BASE + 120)
+    nip, dip = 65536, 128
+    Rip = (g.standard_normal((nip, dip)) * 2.0 ** g.uniform(-1.0, 1.0, (nip, 1))).astype(np.float32)
+    Sip = (g.standard_normal((nip, dip)) * 2.0 ** g.uniform(-1.0, 1.0, (nip, 1))).astype(np.float32)
+    t_ip = float(np.quantile(Rip[:256].astype(np.float64) @ Sip.astype(np.float64).T, 1.0 - 5e-4))
+    Rs_ip = dl.Store(torch.arange(nip, device="cuda"), torch.from_numpy(Rip).cuda())
+    Ss_ip = dl.Store(torch.arange(nip, device="cuda") + nip, torch.from_numpy(Sip).cuda())
+    st = {}
+
+    def call_ip():
+        r = dl.sim_join(Rs_ip, Ss_ip, t_ip, metric="ip", timing=True)
+        st.update(r.stats())
+        r.free()
+
+    call_ip()   # the autotuner's trials of this shape class
+    for _ in range(4):
+        call_ip()
+    ms = _event_ms(call_ip, reps)
+    P = nip * nip
+    kern_ms = st["ms_main"]
+    out["inner_product"] = {"config": f"{nip} x {nip}, d={dip} signed rows of norms spanning a factor 4, "
+                                      f"t at the 0.9995 quantile of q.x ({t_ip:.6g})",
+                            "value": P / (ms / 1e3) / 1e9, "unit": "Gpairs/s", "ms": ms, "ms_main": kern_ms,
+                            "pairs_out": st["pairs_out"], "band_pairs": st["band_pairs"],
+                            "fp64_pairs": st["fp64_pairs"],
+                            "roofline": {"bound": "tensor", "achieved": 2.0 * dip * P / (kern_ms / 1e3) / 1e12,
+                                         "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                                         "frac": 2.0 * dip * P / (kern_ms / 1e3) / 1e12 / pk["bf16_tflops"],
+                                         "kernel": "tc_join_kernel<256> (BF16, zero column term)"}}
+    Rs_ip.close()
+    Ss_ip.close()
+    del Rip, Sip
 
     # the exact pruned join on tracked objects: dense join, store clustering (one-time), pruned join
     wt = W.tracked_objects_262k()
