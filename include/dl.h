@@ -57,10 +57,10 @@ typedef enum dl_metric {
                              threshold c in [-1, 1] and a pair matches iff the canonical D of
                              the normalized rows is <= fl64(2 - 2c) (cos >= c for unit rows) */
     DL_METRIC_L1 = 2,     /* histogram L1 distance: canonical FP64 sum_k |q_k - x_k| <= eps
-                             (k ascending, every step rounded to nearest); epsilon-join only */
+                             (k ascending, every step rounded to nearest); epsilon- and top-k joins */
     DL_METRIC_CHI2 = 3,   /* chi-square histogram distance on non-negative features: canonical FP64
                              sum over bins with q_k + x_k > 0 of (q_k - x_k)^2 / (q_k + x_k) <= eps
-                             (no factor 1/2); epsilon-join only */
+                             (no factor 1/2); epsilon- and top-k joins */
     DL_METRIC_IP = 4      /* inner-product threshold on rows of any norm (Sec. 3.2 "threshold the
                              similarity"): a pair matches iff the canonical FP64 dot product
                              sum_k q_k x_k (k ascending, every addition rounded to nearest; the
@@ -241,7 +241,11 @@ int dl_sim_join(const dl_store *R, const dl_store *S, int32_t metric, double eps
  * rows of S with the smallest canonical D, ordered by (D, S row index); ties
  * beyond the k-th are not returned. 1 <= k <= 1024. With DL_METRIC_COSINE (both
  * stores from dl_store_normalize) these are the k most similar rows, and the
- * distances returned are the canonical D of the normalized rows (2 - 2 cos).
+ * distances returned are the canonical D of the normalized rows (2 - 2 cos). With
+ * DL_METRIC_L1 / DL_METRIC_CHI2 (DL_PREC_AUTO or FP32; BF16 gives DL_EUNSUPPORTED,
+ * negative features under chi-square DL_EINVAL) the rows with the smallest canonical
+ * histogram distance, which is what the distances hold; DL_EOVERFLOW if more than
+ * 8,192 columns of one row tie within the FP32 bound of its k-th distance.
  */
 int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric, int32_t k,
                  const dl_join_opts *opts, dl_result **out);

@@ -29,7 +29,7 @@ LIB = os.path.join(HERE, "libdlsimjoin.so")
 BUILD_CHECKED = os.path.join(HERE, "_build_checked")
 LIB_CHECKED = os.path.join(HERE, "libdlsimjoin_checked.so")
 
-SOURCES = ["store.cu", "api.cu", "join_tc.cu", "join_simt.cu", "recheck.cu", "topk.cu", "noalloc.cu", "batch.cu", "server.cu", "tune.cu", "hist.cu", "cc.cu", "prune.cu"]
+SOURCES = ["store.cu", "api.cu", "join_tc.cu", "join_simt.cu", "recheck.cu", "topk.cu", "noalloc.cu", "batch.cu", "server.cu", "tune.cu", "hist.cu", "cc.cu", "prune.cu", "hist_topk.cu"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off,-O2",

@@ -105,6 +105,10 @@ int launch_rowpar_ip(const float4 *rowb, int64_t n, int64_t n_tot, int dp, doubl
 int launch_finalize_ip(const uint2 *cand, const unsigned long long *cand_cnt, unsigned long long cand_cap,
                        const float *R, const float *S, int d, double t, const JoinOut &out,
                        unsigned long long *n_fp64, unsigned long long *n_band, int grid, cudaStream_t st, int nR, int nS);
+// Top-k under the L1 (metric 1) or chi-square (metric 2) distance (hist_topk.cu): outputs at
+// the caller's query row order, [nQ][k] ids and canonical distances, -1 past the store.
+int hist_topk(const dl_store *Q, const dl_store *S, int metric, int k, int64_t *out_ids, double *out_d,
+              cudaStream_t st, dl_join_stats *stats);
 int launch_diag(const int64_t *ids, int64_t n, int64_t *out_r, int64_t *out_s, unsigned long long *out_cnt,
                 unsigned long long cap, cudaStream_t st);
 

@@ -758,12 +758,13 @@ extern "C" int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric
         set_error("dl_topk_join: NULL store");
         return DL_EINVAL;
     }
+    const bool hist = metric == DL_METRIC_L1 || metric == DL_METRIC_CHI2;
     if (metric == DL_METRIC_COSINE) {   // the most similar rows are the nearest normalized rows
         if (!Q->unit || !S->unit) {
             set_error("dl_topk_join: the cosine metric needs stores made by dl_store_normalize");
             return DL_EINVAL;
         }
-    } else if (metric != DL_METRIC_L2) {
+    } else if (metric != DL_METRIC_L2 && !hist) {
         set_error("dl_topk_join: unsupported metric %d", metric);
         return DL_EINVAL;
     }
@@ -791,14 +792,32 @@ extern "C" int dl_topk_join(const dl_store *Q, const dl_store *S, int32_t metric
         return DL_EUNSUPPORTED;
     }
     cudaStream_t st = (cudaStream_t)o.cuda_stream;
+    if (hist && o.precision == DL_PREC_BF16) {
+        set_error("dl_topk_join: the L1 and chi-square distances run in DL_PREC_FP32 (not on tensor cores)");
+        return DL_EUNSUPPORTED;
+    }
+    int rc = DL_OK;
+    if (metric == DL_METRIC_CHI2) {
+        bool ok = false;
+        rc = store_nonneg(const_cast<dl_store *>(Q), st, &ok);
+        if (!rc && ok) rc = store_nonneg(const_cast<dl_store *>(S), st, &ok);
+        if (rc) return rc;
+        if (!ok) {
+            set_error("dl_topk_join: the chi-square distance needs non-negative features");
+            return DL_EINVAL;
+        }
+    }
     const int64_t nQ = Q->n;
     void *resb = nullptr;
-    int rc = dev_alloc(&resb, std::max<size_t>(16, (size_t)nQ * k * 16), st);
+    rc = dev_alloc(&resb, std::max<size_t>(16, (size_t)nQ * k * 16), st);
     if (rc) return rc;
     int64_t *out_ids = (int64_t *)resb;
     double *out_d2 = (double *)(out_ids + (size_t)nQ * k);
     dl_join_stats stats{};
-    rc = topk_core(Q, S, k, nullptr, nullptr, out_ids, out_d2, o, st, &stats);
+    if (hist)
+        rc = hist_topk(Q, S, metric == DL_METRIC_L1 ? 1 : 2, k, out_ids, out_d2, st, &stats);
+    else
+        rc = topk_core(Q, S, k, nullptr, nullptr, out_ids, out_d2, o, st, &stats);
     if (rc) {
         dev_free(resb, st);
         return rc;

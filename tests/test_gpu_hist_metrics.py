@@ -127,6 +127,7 @@ def test_rejections(dl):
         dl.sim_join(Ys, None, 0.5, metric="chi2")
     assert ei.value.status == dl.DL_EINVAL
     dl.sim_join(Ys, None, 0.5, metric="l1").free()      # L1 takes signed features
+    dl.topk_join(Xs, Xs, 3, metric="l1").free()   # served by the histogram top-k (test_gpu_hist_topk.py)
     with pytest.raises(dl.DLError) as ei:
-        dl.topk_join(Xs, Xs, 3, metric="l1")
-    assert ei.value.status in (dl.DL_EINVAL, dl.DL_EUNSUPPORTED)
+        dl.topk_join(Ys, Xs, 3, metric="chi2")
+    assert ei.value.status == dl.DL_EINVAL
