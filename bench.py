@@ -654,6 +654,17 @@ def rows_leg(dl, sm_mhz=None, reps=5):
                        "roofline": {"bound": "alu", "achieved": ops / (kern_ms / 1e3) / 1e12,
                                     "peak": peak / 1e12, "unit": "Tops/s", "frac": ops / (kern_ms / 1e3) / peak,
                                     "algorithmic": f"{unit_ops} x d x {P} pairs ({what}), at {mhz:.0f} MHz"}}
+    # top-10 under each histogram distance: 4,096 query rows against the same store
+    for metric in ("l1", "chi2"):
+        Qs = dl.Store(torch.arange(4096, device="cuda"), torch.from_numpy(X[:4096]).cuda())
+
+        def call_tk():
+            dl.topk_join(Qs, Xs, 10, metric=metric).free()
+
+        ms = _event_ms(call_tk, 3)
+        out[metric + "_topk10"] = {"config": f"4,096 query rows x hist_clustered_64k ({n} x d=128), k=10",
+                                   "value": 4096 * n / (ms / 1e3) / 1e9, "unit": "Gpairs/s", "ms": ms}
+        Qs.close()
     Xs.close()
 
     # the inner-product threshold join on rows of any norm (BF16 tensor cores, exact)
